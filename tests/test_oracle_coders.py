@@ -1,0 +1,127 @@
+"""Pins of the oracle's range coder, exact arithmetic coder and count model."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import countmodel
+from oracle.quantize import TOTAL, cumulative, quantize
+from oracle.rangecoder import Decoder, Encoder, decode_all, encode_all, exact_decode, exact_encode
+from oracle.mixer import softmax
+from oracle.tokenizer import base_codes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_tables(rng, n, A, temp):
+    P = softmax(rng.normal(0, temp, (n, A)))
+    f = quantize(P)
+    return f, cumulative(f)
+
+
+def _ideal_bits(sym, freq, total):
+    return sum(-math.log2(freq[i][s] / total) for i, s in enumerate(sym))
+
+
+@pytest.mark.parametrize("A,temp", [(4, 1.0), (64, 3.0), (256, 8.0), (4096, 0.5)])
+def test_round_trip_and_length_bound(A, temp):
+    rng = np.random.default_rng(A)
+    n = 600
+    freq, cum = _random_tables(rng, n, A, temp)
+    # draw symbols from the coded distributions, plus some very unlikely ones
+    sym = [int(rng.choice(A, p=freq[i] / TOTAL)) for i in range(n)]
+    for i in range(0, n, 50):
+        sym[i] = int(freq[i].argmin())
+    data = encode_all(sym, cum, TOTAL)
+    assert decode_all(data, cum, TOTAL) == sym
+    ideal = _ideal_bits(sym, freq, TOTAL)
+    assert 8 * len(data) <= ideal + n * 2.0 ** -24 / math.log(2) * 1.0001 + 8
+    assert 8 * len(data) >= ideal - 56  # cannot beat the information content by more than the window
+
+
+def test_carry_propagation_exercised():
+    class Counting(Encoder):
+        carries = 0
+
+        def _shift_low(self):
+            if self.low >= 1 << 56:
+                Counting.carries += 1
+            super()._shift_low()
+
+    rng = np.random.default_rng(11)
+    A = 16
+    freq, cum = _random_tables(rng, 20000, A, 6.0)
+    sym = [int(rng.choice(A, p=freq[i] / TOTAL)) for i in range(20000)]
+    enc = Counting()
+    for i, s in enumerate(sym):
+        enc.encode(int(cum[i][s]), int(freq[i][s]), TOTAL)
+    data = enc.finish()
+    assert Counting.carries > 0
+    assert decode_all(data, cum, TOTAL) == sym
+
+
+@pytest.mark.parametrize("k", [1, 3, 6, 8])
+def test_uniform_tokens_cost_2k_bits(k):
+    A = 4 ** k
+    u = TOTAL // A
+    cum = [np.arange(A + 1, dtype=np.int64) * u] * 300
+    rng = np.random.default_rng(k)
+    sym = [int(x) for x in rng.integers(0, A, 300)]
+    data = encode_all(sym, cum, TOTAL)
+    assert decode_all(data, cum, TOTAL) == sym
+    assert 300 * 2 * k - 8 <= 8 * len(data) <= 300 * 2 * k + 8
+
+
+def test_exact_coder_bound_and_round_trip():
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        n, A = int(rng.integers(1, 12)), int(rng.integers(2, 9))
+        freq, cum = _random_tables(rng, n, A, 2.0)
+        sym = [int(rng.integers(0, A)) for _ in range(n)]
+        bits = exact_encode(sym, cum, TOTAL)
+        W = Fraction(1)
+        for i, s in enumerate(sym):
+            W *= Fraction(int(freq[i][s]), TOTAL)
+        assert len(bits) <= math.ceil(-math.log2(W)) + 1 <= _ideal_bits(sym, freq, TOTAL) + 2
+        assert exact_decode(bits, cum, TOTAL) == sym
+        data = encode_all(sym, cum, TOTAL)
+        assert 8 * len(data) <= len(bits) + 8 + 1  # range coder within a byte of the ideal coder
+
+
+def test_empty_and_single_symbol_streams():
+    assert Encoder().finish() == b""
+    cum = [np.array([0, 1, TOTAL])]
+    for s in (0, 1):
+        data = encode_all([s], cum, TOTAL)
+        assert decode_all(data, cum, TOTAL) == [s]
+    dec = Decoder(b"")
+    assert dec.decode(np.array([0, TOTAL // 2, TOTAL]), TOTAL) == 0
+
+
+def test_count_model_hand_worked():
+    for line in open(os.path.join(GOLDEN, "countmodel_acac.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        s, m, *qs = line.split()
+        probs = countmodel.probabilities(base_codes(s.encode()), int(m))
+        want = [Fraction(q) for q in qs]
+        assert [Fraction(f, t) for f, t in probs] == want
+
+
+@pytest.mark.parametrize("m", [0, 1, 3, 6])
+def test_count_model_round_trip_and_length(m):
+    import synth
+    codes = base_codes(synth.markov(4000, 2, 0.45, 17 + m).tobytes())
+    data = countmodel.encode(codes, m)
+    assert np.array_equal(countmodel.decode(data, codes.size, m), codes)
+    ideal = sum(-math.log2(f / t) for f, t in countmodel.probabilities(codes, m))
+    assert 8 * len(data) <= ideal + 8 + 1e-3
+
+
+def test_count_model_halving():
+    codes = np.zeros(5000, dtype=np.uint8)  # one context, counts hit the limit repeatedly
+    probs = countmodel.probabilities(codes, 2)
+    assert max(t for _, t in probs) <= 2 * 4 * countmodel.LIMIT + 4
+    assert np.array_equal(countmodel.decode(countmodel.encode(codes, 2), 5000, 2), codes)
