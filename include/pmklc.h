@@ -1,0 +1,230 @@
+/*
+ * pmklc.h — C ABI of libpmklc.so, a GB300 (sm_103a) implementation of the
+ * per-block learned-compression loop of PMKLC (Sun et al., arXiv 2507.12805).
+ *
+ * Conventions for every entry point
+ *   - Return 0 (PMKLC_OK) on success or a negative PMKLC_E* code; nothing
+ *     aborts, traps or exits.  pmklc_strerror() names a code.
+ *   - "d_" arguments are device pointers (CUDA global memory of the current
+ *     device), everything else is host memory.  Inputs are read-only and stay
+ *     owned by the caller.  Buffers returned through `uint8_t **` etc. are
+ *     allocated by the library and released with pmklc_free().
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     is ordered on it; calls that return host results synchronise it.
+ *   - Sizes are element counts unless the name says bytes.
+ *   - Token arrays are uint16 (k <= 8, so 4^k <= 65536 symbols).
+ *   - A model's parameters are one FP32 array in the layout
+ *         Emb[A][E] | W1[t*E][H] | b1[H] | W2[H][A] | b2[A]     (A = 4^k)
+ *     (row-major), see pmklc_model_count().
+ */
+#ifndef PMKLC_H
+#define PMKLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMKLC_ABI_VERSION 1
+
+/* error codes */
+#define PMKLC_OK 0
+#define PMKLC_EINVAL (-1)   /* bad argument, non-ACGT byte, s > k, k > 8, ... */
+#define PMKLC_ENOMEM (-2)   /* host or device allocation failed */
+#define PMKLC_ECUDA (-3)    /* a CUDA runtime call failed */
+#define PMKLC_ECORRUPT (-4) /* malformed container, checksum or token mismatch */
+#define PMKLC_EMODEL (-5)   /* static weights differ from the ones in the container */
+#define PMKLC_ETIMEOUT (-6) /* a bounded device wait expired */
+#define PMKLC_ENOSPC (-7)   /* caller's output buffer too small */
+
+/* precision forms */
+#define PMKLC_FP32_PLAIN 0
+#define PMKLC_BF16_BATCHED 1
+/* optimisers */
+#define PMKLC_ADAM 0
+#define PMKLC_SGD 1
+/* step-wise model passing schedules */
+#define PMKLC_SMP_NONE 0
+#define PMKLC_SMP_CHAIN 1
+#define PMKLC_SMP_TREE 2
+
+/*
+ * Model and run configuration (paper §4.2 AMKLCF, §4.3 DC + SMP, §5.1.4
+ * parameters).  struct_size must be sizeof(pmklc_model_cfg).
+ */
+typedef struct {
+  uint32_t struct_size;
+  uint32_t s, k;               /* (s,k)-mer step and window, 1 <= s <= k <= 8 (§4.1) */
+  uint32_t use_static;         /* S0 of Eq. (1): mix in the frozen static predictor */
+  uint32_t emb_s, ctx_s, hid_s;/* static predictor: embedding E, context t, hidden H */
+  uint32_t emb_d, ctx_d, hid_d;/* dynamic predictor (trained online, §4.2.4) */
+  uint32_t lanes_per_block;    /* M: parallel sub-streams per block (bs, §5.8); 0 = default */
+  uint32_t precision;          /* PMKLC_FP32_PLAIN or PMKLC_BF16_BATCHED */
+  uint32_t optimizer;          /* PMKLC_ADAM or PMKLC_SGD */
+  float lr;                    /* learning rate of the Backward Controller (§4.2.6) */
+  float alpha_init;            /* initial mixing weight alpha of Eq. (1) */
+  uint32_t smp_mode;           /* PMKLC_SMP_* (§4.3, Fig. 5) */
+  float smp_fraction;          /* f: share of a parent's steps before it hands over (paper: 0.05) */
+  uint32_t count_order;        /* order m of the count-model judge, 0..7 */
+  uint32_t fallback;           /* 1: code a block with the count model when that is smaller */
+  uint64_t seed;               /* seed of the dynamic model's initialisation */
+  const float *static_weights; /* host FP32 static parameters (layout above); NULL if unused */
+} pmklc_model_cfg;
+
+int pmklc_abi_version(void);
+const char *pmklc_strerror(int rc);
+void pmklc_free(void *p);
+
+/* Number of FP32 parameters of an MLP predictor with alphabet 4^k. */
+size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid);
+
+/*
+ * Seeded initial parameters of an MLP predictor (the paper's "randomly
+ * initialized parameters", §4.3; reading R8: counter-based splitmix64 draws
+ * scaled by 1 for the embedding and 1/sqrt(fan_in) for W1, W2; biases 0).
+ * out: host array of pmklc_model_count(k, emb, ctx, hid) floats.
+ */
+int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint64_t seed, float *out);
+
+/* Default configuration for (s,k) with dynamic model (E,t,H) = (emb, ctx, hid). */
+void pmklc_default_cfg(pmklc_model_cfg *cfg, uint32_t s, uint32_t k, uint32_t emb, uint32_t ctx,
+                       uint32_t hid);
+
+/*
+ * Compress n ASCII bases (A, C, G, T only) split into n_blocks blocks
+ * (block_lens sums to n; the paper's Data Chunker, §4.3) into a container
+ * (format in the design doc §3).  The static weights are not stored, only their
+ * hash (§4.2.2: the public static model is part of the compressor).
+ * Output: *out (library-allocated, pmklc_free) of *out_len bytes.
+ * Errors: EINVAL (bad cfg, non-ACGT byte, block lengths), ENOMEM, ECUDA.
+ */
+int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                   const pmklc_model_cfg *cfg, void *stream, uint8_t **out, size_t *out_len);
+
+/*
+ * Inverse of pmklc_compress (paper §2, decompression: the decoder replays
+ * the same model updates).  static_weights/static_count must be the ones
+ * used to compress when the container says a static model was used.
+ * Outputs: *seq (*n bases) and *block_lens (*n_blocks entries), both
+ * library-allocated.  Errors: ECORRUPT, EMODEL, ENOMEM, ECUDA, ETIMEOUT.
+ */
+int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weights, size_t static_count,
+                     void *stream, uint8_t **seq, size_t *n, uint64_t **block_lens, size_t *n_blocks);
+
+/* Upper bound of the container size of pmklc_compress_dev for this input. */
+size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg);
+
+/*
+ * Device-resident forms: input and output in device memory (the container
+ * header is assembled on the host and copied in).  d_out must hold
+ * pmklc_compress_bound() bytes; *out_len receives the container size.
+ */
+int pmklc_compress_dev(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                       const pmklc_model_cfg *cfg, void *stream, uint8_t *d_out, size_t out_cap,
+                       size_t *out_len);
+/* d_seq must hold seq_cap bytes; *n receives the number of bases. */
+int pmklc_decompress_dev(const uint8_t *d_in, size_t in_len, const float *static_weights,
+                         size_t static_count, void *stream, uint8_t *d_seq, size_t seq_cap, size_t *n);
+
+/* ---------------------------------------------------------------------------
+ * Single-step entry points (device buffers), each running exactly the device
+ * code the compressor uses for that step.  They exist so each step can be
+ * checked on its own against the oracle.
+ */
+
+/*
+ * (s,k)-mer encoding, GskE (paper §4.1, Fig. 3): d_tokens[j] =
+ * sum_m 4^(k-1-m) code(d_seq[j*s+m]) for j < l = floor((n-k)/s)+1 (0 if n < k);
+ * the n - covered trailing bases go to d_tail as codes 0..3 (at most 7).
+ * d_tokens holds l entries.  *n_tokens receives l.  EINVAL on a non-ACGT byte.
+ */
+int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint16_t *d_tokens,
+                   uint8_t *d_tail, size_t *n_tokens, void *stream);
+
+/*
+ * Quantisation of probabilities into an integer frequency table (paper §2
+ * step 3; reading R10): for each of `rows` rows of A probabilities,
+ * freq_j = 1 + floor(P_j*(2^24 - A)) (FP32 product), the remainder added to
+ * the first maximal entry.  d_P: rows x A FP32; d_freq: rows x A uint32.
+ */
+int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_t *d_freq, void *stream);
+
+/*
+ * Probability Mixer, Eq. (1), + softmax + quantisation, per row:
+ * P = softmax(alpha*Lu + (1-alpha)*Lm) (Lu ignored when use_static = 0).
+ * d_Lu, d_Lm: rows x A FP32 logits; d_P: rows x A FP32; d_freq: rows x A.
+ */
+int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32_t A, float alpha,
+                       uint32_t use_static, float *d_P, uint32_t *d_freq, void *stream);
+
+/*
+ * Range coding of independent streams (paper §2 step 3, reading R11).
+ * Stream i codes L symbols d_sym[i*L + j] with frequency tables
+ * d_freq[(i*L + j)*A .. +A) (each summing to 2^24).  Output bytes of stream i
+ * go to d_out[i*cap ...], their count to d_len[i]; cap >= 3*L + 8 always
+ * suffices.  ENOSPC if a stream overflows cap.
+ */
+int pmklc_range_encode(const uint32_t *d_freq, const uint16_t *d_sym, uint32_t n_streams, uint32_t L,
+                       uint32_t A, uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream);
+/* Decoding of the streams written by pmklc_range_encode (same layout). */
+int pmklc_range_decode(const uint32_t *d_freq, const uint8_t *d_in, const uint32_t *d_len, uint32_t n_streams,
+                       uint32_t L, uint32_t A, uint32_t cap, uint16_t *d_sym, void *stream);
+
+/*
+ * Predictor forward (paper §2 step 3; MLP of the measured configurations):
+ * logits[r] = relu(X_r W1 + b1) W2 + b2 with X_r the embeddings of the t
+ * context tokens d_ctx[r*t .. r*t+t) (oldest first).  d_params in the model
+ * layout for (A=4^k, E, t, H); d_logits rows x A.  precision as in the cfg.
+ */
+int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H,
+                  const uint16_t *d_ctx, size_t rows, uint32_t precision, float *d_logits, void *stream);
+
+/*
+ * One update of G dynamic models from their own batches of M rows each
+ * (paper §2 step 4, Eq. 1 and Eq. 2 with the Backward Controller):
+ * forward of the dynamic (and, if use_static, static) predictor, Eq. (1)
+ * mixing, softmax, mean cross entropy over the M rows, backward, and the
+ * optimiser step at update count tau (1-based).
+ *   d_params/d_m/d_v: G x P (P = pmklc_model_count of the dynamic shape),
+ *     updated in place; d_alpha/d_alpha_m/d_alpha_v: G entries, in place.
+ *   d_ctx: G*M rows of t_eff = max(ctx_d, use_static ? ctx_s : 0) tokens,
+ *     oldest first; each model reads the last t of its own context length.
+ *   d_target: G*M tokens.  d_static: the static parameters (if use_static).
+ *   d_P (optional, G*M x A) receives the mixed probabilities before the
+ *   update; d_grad (optional, G x P) the gradient; d_dalpha (optional, G).
+ */
+int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *d_params, float *d_m,
+                     float *d_v, float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static,
+                     const uint16_t *d_ctx, const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad,
+                     float *d_dalpha, void *stream);
+
+/*
+ * Order-m count model (judge/fallback; reading R15): codes each of n_blocks
+ * blocks of ASCII bases (d_seq, block b at d_off[b], d_off has n_blocks+1
+ * entries) as one stream into d_out + b*cap; lengths to d_len.
+ * cap >= 2*block_len + 8 suffices.  EINVAL for m > 7 or a non-ACGT byte.
+ */
+int pmklc_count_encode(const uint8_t *d_seq, const uint64_t *d_off, uint32_t n_blocks, uint32_t m,
+                       uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream);
+/* Decodes the streams of pmklc_count_encode back into ASCII bases at d_seq + d_off[b]. */
+int pmklc_count_decode(const uint8_t *d_in, const uint32_t *d_len, uint32_t cap, const uint64_t *d_off,
+                       uint32_t n_blocks, uint32_t m, uint8_t *d_seq, void *stream);
+
+/* CRC-32 (IEEE 802.3, reflected, as zlib) of n device bytes. */
+int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
+
+/* Last run's statistics (per thread): compressed payload split and timings. */
+typedef struct {
+  uint64_t net_blocks, count_blocks;
+  uint64_t global_steps;
+  uint64_t kernel_launches;
+  double ms_total;
+} pmklc_stats;
+int pmklc_last_stats(pmklc_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMKLC_H */

@@ -354,7 +354,8 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> byte
                 payload += x
     flags = (1 if cfg.use_static else 0) | (2 if cfg.fallback else 0)
     head = HEADER.pack(MAGIC, VERSION, cfg.s, cfg.k, flags, cfg.precision, cfg.optimizer, cfg.smp_mode,
-                       cfg.count_order, cfg.emb_d, cfg.ctx_d, cfg.hid_d, cfg.emb_s, cfg.ctx_s, cfg.hid_s,
+                       cfg.count_order, cfg.emb_d, cfg.ctx_d, cfg.hid_d,
+                       *((cfg.emb_s, cfg.ctx_s, cfg.hid_s) if cfg.use_static else (0, 0, 0)),
                        cfg.lanes_per_block, cfg.lr, cfg.alpha_init, cfg.smp_fraction, cfg.seed,
                        static_hash(static_w if cfg.use_static else None), codes.size, len(block_lens),
                        zlib.crc32(bytes(np.asarray(seq, dtype=np.uint8) if isinstance(seq, np.ndarray) else seq)),

@@ -1,0 +1,1128 @@
+// Host orchestration and the C ABI of libpmklc (include/pmklc.h).
+//
+// Compression follows the paper's loop (§2 steps (1)-(4)) organised as in §4:
+// blocks from the Data Chunker (§4.3) are tokenised by GskE (§4.1); each block
+// gets its own dynamic model and its tokens are split into lanes that advance
+// in lockstep (the batch size bs of §5.1.4); every global step runs, for all
+// blocks at once, the predictor forward, the Eq. (1) mixer + CDF + range
+// coder, and the Backward Controller's update (Eq. 2); Step-wise Model
+// Passing (§4.3, Fig. 5) copies a parent's state into a child at the child's
+// start step.  The count model judges every block.  The host builds the lane
+// tables and the schedule, launches the per-step kernels, and assembles the
+// container.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "internal.h"
+
+namespace pmklc {
+
+namespace {
+
+thread_local pmklc_stats g_stats;
+
+// ---------------------------------------------------------------- utilities
+
+struct Arena {  // stream-ordered device allocations, released together
+  cudaStream_t st;
+  std::vector<void *> ptrs;
+  bool failed = false;
+  explicit Arena(cudaStream_t s) : st(s) {}
+  template <class T>
+  T *alloc(size_t n) {
+    void *p = nullptr;
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    T *d = alloc<T>(v.size());
+    if (d && !v.empty()) cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    return d;
+  }
+  ~Arena() {
+    for (void *p : ptrs) cudaFreeAsync(p, st);
+  }
+};
+
+uint64_t sm64_draw(uint64_t seed, uint64_t i) {  // splitmix64 output i of the stream seeded with `seed`
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Seeded initial parameters (reading R8): w = (2u - 2^24) 2^-24, value = w * bound (float32 RN).
+void init_params(const Dims &d, uint64_t seed, std::vector<float> &out) {
+  out.assign(d.count(), 0.f);
+  auto fill = [&](size_t lo, size_t hi, float bound) {
+    for (size_t i = lo; i < hi; ++i) {
+      int64_t u = (int64_t)(sm64_draw(seed, i) >> 40);
+      float w = (float)(2 * u - (1 << 24)) * (1.0f / 16777216.0f);
+      volatile float v = w * bound;  // one IEEE product, no contraction
+      out[i] = v;
+    }
+  };
+  fill(d.off_emb(), d.off_w1(), 1.0f);
+  fill(d.off_w1(), d.off_b1(), 1.0f / sqrtf((float)(d.t * d.E)));
+  fill(d.off_w2(), d.off_b2(), 1.0f / sqrtf((float)d.H));
+}
+
+uint64_t fnv1a(const void *p, size_t n) {
+  const uint8_t *b = (const uint8_t *)p;
+  uint64_t h = 0xCBF29CE484222325ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001B3ull;
+  return h;
+}
+
+long long n_tokens_of(long long n, int s, int k) { return n < k ? 0 : (n - k) / s + 1; }
+long long tail_len_of(long long n, int s, int k) {
+  long long l = n_tokens_of(n, s, k);
+  return l == 0 ? n : n - ((l - 1) * s + k);
+}
+
+void put_varint(std::vector<uint8_t> &o, uint64_t x) {
+  while (true) {
+    uint8_t b = x & 0x7F;
+    x >>= 7;
+    if (x) {
+      o.push_back(b | 0x80);
+    } else {
+      o.push_back(b);
+      return;
+    }
+  }
+}
+size_t varint_len(uint64_t x) {
+  size_t n = 1;
+  while (x >>= 7) ++n;
+  return n;
+}
+bool get_varint(const uint8_t *buf, size_t len, size_t &pos, uint64_t &x) {
+  x = 0;
+  for (int shift = 0; shift < 64; shift += 7) {
+    if (pos >= len) return false;
+    uint8_t b = buf[pos++];
+    x |= (uint64_t)(b & 0x7F) << shift;
+    if (!(b & 0x80)) return true;
+  }
+  return false;
+}
+
+template <class T>
+void put_le(std::vector<uint8_t> &o, T v) {
+  uint8_t b[sizeof(T)];
+  memcpy(b, &v, sizeof(T));  // both supported hosts (x86-64, aarch64) are little-endian
+  o.insert(o.end(), b, b + sizeof(T));
+}
+template <class T>
+T get_le(const uint8_t *p) {
+  T v;
+  memcpy(&v, p, sizeof(T));
+  return v;
+}
+
+constexpr size_t kHeader = 80;
+constexpr uint8_t kVersion = 1;
+
+// ---------------------------------------------------------------- configuration
+
+struct Cfg {
+  int s, k, use_static, precision, optimizer, smp_mode, count_order, fallback;
+  Dims dm, st;
+  int lanes;
+  float lr, alpha0, smp_f;
+  uint64_t seed;
+  int A() const { return 1 << (2 * k); }
+  int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
+};
+
+int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
+  if (!c || c->struct_size != sizeof(pmklc_model_cfg)) return PMKLC_EINVAL;
+  if (c->s < 1 || c->s > c->k || c->k > 8) return PMKLC_EINVAL;
+  if (c->emb_d < 1 || c->ctx_d < 1 || c->hid_d < 1 || c->emb_d > 4096 || c->ctx_d > 4096 || c->hid_d > 65535)
+    return PMKLC_EINVAL;
+  if (c->use_static && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
+                        c->hid_s > 65535 || !c->static_weights))
+    return PMKLC_EINVAL;
+  if (c->precision != PMKLC_FP32_PLAIN) return PMKLC_EINVAL;
+  if (c->optimizer > PMKLC_SGD || c->smp_mode > PMKLC_SMP_TREE || c->count_order > 7) return PMKLC_EINVAL;
+  if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
+  if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
+  if (c->lanes_per_block > (1u << 20)) return PMKLC_EINVAL;
+  o.s = (int)c->s;
+  o.k = (int)c->k;
+  o.use_static = c->use_static ? 1 : 0;
+  o.precision = (int)c->precision;
+  o.optimizer = (int)c->optimizer;
+  o.smp_mode = (int)c->smp_mode;
+  o.count_order = (int)c->count_order;
+  o.fallback = c->fallback ? 1 : 0;
+  int A = 1 << (2 * c->k);
+  o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
+  o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
+  o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
+  o.lr = c->lr;
+  o.alpha0 = c->alpha_init;
+  o.smp_f = c->smp_fraction;
+  o.seed = c->seed;
+  return PMKLC_OK;
+}
+
+// ---------------------------------------------------------------- lanes + schedule
+
+struct Layout {
+  int G = 0, NL = 0, Mmax = 0;
+  std::vector<long long> base_off, tok_off;  // G+1
+  std::vector<int> lane_off, base_len, extra, steps;
+  std::vector<long long> lane_tok;
+  std::vector<int> lane_len, lane_grp;
+  long long n_tok = 0;
+};
+
+void make_layout(const std::vector<unsigned long long> &lens, int s, int k, int M, Layout &L) {
+  L.G = (int)lens.size();
+  L.base_off.assign(L.G + 1, 0);
+  L.tok_off.assign(L.G + 1, 0);
+  L.lane_off.assign(L.G + 1, 0);
+  L.base_len.assign(L.G, 0);
+  L.extra.assign(L.G, 0);
+  L.steps.assign(L.G, 0);
+  for (int g = 0; g < L.G; ++g) {
+    long long n = (long long)lens[g];
+    long long l = n_tokens_of(n, s, k);
+    L.base_off[g + 1] = L.base_off[g] + n;
+    L.tok_off[g + 1] = L.tok_off[g] + l;
+    int Mb = (int)std::min<long long>(M, l);
+    L.lane_off[g + 1] = L.lane_off[g] + Mb;
+    if (Mb > 0) {
+      long long base = l / Mb, extra = l % Mb;
+      L.base_len[g] = (int)base;
+      L.extra[g] = (int)extra;
+      L.steps[g] = (int)(base + (extra > 0));
+      for (int r = 0; r < Mb; ++r) {
+        L.lane_tok.push_back(L.tok_off[g] + r * base + std::min<long long>(r, extra));
+        L.lane_len.push_back((int)(base + (r < extra)));
+        L.lane_grp.push_back(g);
+      }
+    }
+    L.Mmax = std::max(L.Mmax, Mb);
+  }
+  L.NL = L.lane_off[L.G];
+  L.n_tok = L.tok_off[L.G];
+}
+
+struct Schedule {
+  std::vector<int> start, parent, tau0;
+  int T_total = 0, max_tau = 0;
+  std::vector<std::vector<int>> pairs_at;  // T -> flattened (child, parent) pairs
+};
+
+void make_schedule(const Layout &L, int mode, float f32, int t_eff, Schedule &S) {
+  int G = L.G;
+  double f = (double)f32;
+  S.start.assign(G, 0);
+  S.parent.assign(G, -1);
+  S.tau0.assign(G, 0);
+  if (G > 0 && mode == PMKLC_SMP_CHAIN) {
+    for (int g = 1; g < G; ++g) {
+      S.parent[g] = g - 1;
+      S.start[g] = S.start[g - 1] + (int)ceil(f * L.steps[g - 1]);
+    }
+  } else if (G > 0 && mode == PMKLC_SMP_TREE) {
+    int mx = *std::max_element(L.steps.begin(), L.steps.end());
+    int D = (int)ceil(f * mx);
+    for (int g = 1; g < G; ++g) {
+      int lvl = 32 - __builtin_clz((unsigned)g);
+      S.parent[g] = g - (1 << (lvl - 1));
+      S.start[g] = lvl * D;
+    }
+  }
+  S.T_total = 0;
+  S.max_tau = 0;
+  for (int g = 0; g < G; ++g) {
+    int p = S.parent[g];
+    if (p >= 0) {
+      int ran = std::min(S.start[g] - S.start[p], L.steps[p]);
+      S.tau0[g] = S.tau0[p] + std::max(0, ran - t_eff);
+    }
+    S.T_total = std::max(S.T_total, S.start[g] + L.steps[g]);
+    S.max_tau = std::max(S.max_tau, S.tau0[g] + std::max(0, L.steps[g] - t_eff));
+  }
+  // Hand-overs happen at the child's start step (children starting at 0 already hold the
+  // init, which is what their parent holds then).  Copies of one step run in parallel, so a
+  // parent that itself receives a copy at the same step is replaced by its own source.
+  S.pairs_at.assign(S.T_total + 1, {});
+  for (int g = 0; g < G; ++g)
+    if (S.parent[g] >= 0 && S.start[g] > 0 && S.start[g] <= S.T_total) {
+      int src = S.parent[g];
+      while (S.parent[src] >= 0 && S.start[src] == S.start[g]) src = S.parent[src];
+      S.pairs_at[S.start[g]].push_back(g);
+      S.pairs_at[S.start[g]].push_back(src);
+    }
+}
+
+// ---------------------------------------------------------------- device run
+
+struct Run {
+  Plan p{};
+  Layout L;
+  Schedule S;
+  Cfg c;
+  int *d_pairs = nullptr;
+  std::vector<int> pair_off;  // T -> offset (pairs) into d_pairs
+  uint64_t launches = 0;
+};
+
+// Allocates the model state, activations and tables of a run.  lane_buf / caps / enc / dec are set by the caller.
+int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *d_static) {
+  const Cfg &c = R.c;
+  const Layout &L = R.L;
+  Plan &p = R.p;
+  p.G = L.G;
+  p.NL = L.NL;
+  p.Mmax = L.Mmax;
+  p.t_eff = c.t_eff();
+  p.use_static = c.use_static;
+  p.optimizer = c.optimizer;
+  p.lr = c.lr;
+  p.dm = c.dm;
+  p.st = c.st;
+  p.P = c.dm.count();
+  size_t G = (size_t)std::max(L.G, 1), NL = (size_t)std::max(L.NL, 1);
+  p.grp_start = ar.upload(R.S.start);
+  p.grp_steps = ar.upload(L.steps);
+  p.grp_lane_off = ar.upload(L.lane_off);
+  p.grp_base = ar.upload(L.base_len);
+  p.grp_extra = ar.upload(L.extra);
+  p.grp_mode = ar.upload(grp_mode);
+  p.grp_tau0 = ar.upload(R.S.tau0);
+  p.lane_tok = ar.upload(L.lane_tok);
+  p.lane_len = ar.upload(L.lane_len);
+  p.lane_grp = ar.upload(L.lane_grp);
+  p.params = ar.alloc<float>(G * p.P);
+  p.m = ar.alloc<float>(G * p.P);
+  p.v = ar.alloc<float>(G * p.P);
+  p.grad = ar.alloc<float>(G * p.P);
+  p.alpha = ar.alloc<float>(G);
+  p.alpha_m = ar.alloc<float>(G);
+  p.alpha_v = ar.alloc<float>(G);
+  p.dalpha_grp = ar.alloc<float>(G);
+  p.static_params = d_static;
+  int A = c.A();
+  p.hd = ar.alloc<float>(NL * c.dm.H);
+  p.hs = c.use_static ? ar.alloc<float>(NL * c.st.H) : nullptr;
+  p.zm = ar.alloc<float>(NL * A);
+  p.zu = c.use_static ? ar.alloc<float>(NL * A) : nullptr;
+  p.dz = ar.alloc<float>(NL * A);
+  p.dh = ar.alloc<float>(NL * c.dm.H);
+  p.dalpha_row = ar.alloc<float>(NL);
+  p.out_P = nullptr;
+  p.demb_acc = ar.alloc<long long>(G * A * c.dm.E);
+  p.err = ar.alloc<int>(1);
+  std::vector<float> bc1(R.S.max_tau + 2), bc2(R.S.max_tau + 2);
+  for (size_t t = 0; t < bc1.size(); ++t) {
+    bc1[t] = (float)(1.0 - pow(0.9, (double)t));
+    bc2[t] = (float)(1.0 - pow(0.999, (double)t));
+  }
+  p.bc1 = ar.upload(bc1);
+  p.bc2 = ar.upload(bc2);
+  // SMP hand-over pairs by start step
+  std::vector<int> flat;
+  R.pair_off.assign(R.S.T_total + 2, 0);
+  for (int T = 0; T <= R.S.T_total; ++T) {
+    R.pair_off[T] = (int)flat.size() / 2;
+    flat.insert(flat.end(), R.S.pairs_at[T].begin(), R.S.pairs_at[T].end());
+  }
+  R.pair_off[R.S.T_total + 1] = (int)flat.size() / 2;
+  R.d_pairs = ar.upload(flat);
+  if (ar.failed) return PMKLC_ENOMEM;
+  cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
+  cudaMemsetAsync(p.err, 0, sizeof(int), ar.st);
+  std::vector<float> init;
+  init_params(c.dm, c.seed, init);
+  float *d_init = ar.upload(init);
+  if (ar.failed) return PMKLC_ENOMEM;
+  launch_init_groups(p, d_init, c.alpha0, ar.st);
+  return PMKLC_OK;
+}
+
+// The lockstep loop over global steps.
+void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
+  const Layout &L = R.L;
+  const Schedule &S = R.S;
+  const int t_eff = R.p.t_eff;
+  for (int T = 0; T < S.T_total; ++T) {
+    int np = R.pair_off[T + 1] - R.pair_off[T];
+    if (np > 0) {
+      launch_smp_copy(R.p, R.d_pairs + 2 * R.pair_off[T], np, st);
+      R.launches++;
+    }
+    bool any_pred = false, any_code = false;
+    for (int g = 0; g < L.G; ++g) {
+      int j = T - S.start[g];
+      if (j < 0 || j >= L.steps[g]) continue;
+      if (j >= t_eff) any_pred = true;
+      if (grp_mode[g] != kReplay) any_code = true;
+    }
+    if (any_pred) {
+      launch_forward(R.p, T, st);
+      R.launches += R.c.use_static ? 4 : 2;
+    }
+    if (any_pred || any_code) {
+      launch_mixcode(R.p, T, st);
+      R.launches++;
+    }
+    if (any_pred) {
+      launch_backward_update(R.p, T, st);
+      R.launches += 6;
+    }
+  }
+}
+
+__global__ void gather_kernel(const unsigned long long *seg, int n_seg, const uint8_t *src0, const uint8_t *src1,
+                              uint8_t *dst) {
+  int q = blockIdx.x;
+  if (q >= n_seg) return;
+  unsigned long long so = seg[4 * q], dof = seg[4 * q + 1], len = seg[4 * q + 2], which = seg[4 * q + 3];
+  const uint8_t *s = (which ? src1 : src0) + so;
+  for (unsigned long long i = threadIdx.x; i < len; i += blockDim.x) dst[dof + i] = s[i];
+}
+
+__global__ void check_tokens_kernel(const uint16_t *tok, long long n, int A, int *err) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool bad = i < n && tok[i] >= A;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrCorrupt);
+}
+
+int err_to_rc(int e) {
+  if (e & kErrBadBase) return PMKLC_EINVAL;
+  if (e & kErrCorrupt) return PMKLC_ECORRUPT;
+  if (e & kErrTimeout) return PMKLC_ETIMEOUT;
+  if (e & kErrOverflow) return PMKLC_ENOSPC;
+  return PMKLC_OK;
+}
+
+size_t bound_of(const std::vector<unsigned long long> &lens, const Cfg &c) {
+  size_t b = kHeader;
+  for (unsigned long long n : lens) {
+    long long l = n_tokens_of((long long)n, c.s, c.k);
+    long long Mb = std::min<long long>(c.lanes, l);
+    b += 10 + 1 + 2 + (size_t)Mb * 10 + (size_t)l * 3 + (size_t)Mb * 8;
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------- compress
+
+int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                      const pmklc_model_cfg *cfg, cudaStream_t st, uint8_t *d_out, size_t out_cap, size_t *out_len) {
+  auto t0 = std::chrono::steady_clock::now();
+  Run R;
+  int rc = check_cfg(cfg, R.c);
+  if (rc) return rc;
+  const Cfg &c = R.c;
+  if ((n && !d_seq) || (n_blocks && !block_lens) || !out_len || !d_out) return PMKLC_EINVAL;
+  if (n_blocks > (1u << 24)) return PMKLC_EINVAL;
+  std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
+  unsigned long long sum = 0;
+  for (auto x : lens) sum += x;
+  if (sum != n) return PMKLC_EINVAL;
+  if (out_cap < bound_of(lens, c)) return PMKLC_ENOSPC;
+  make_layout(lens, c.s, c.k, c.lanes, R.L);
+  make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
+  const Layout &L = R.L;
+  Arena ar(st);
+  // static weights
+  const float *d_static = nullptr;
+  uint64_t shash = 0;
+  if (c.use_static) {
+    size_t cnt = c.st.count();
+    shash = fnv1a(cfg->static_weights, cnt * sizeof(float));
+    float *d = ar.alloc<float>(cnt);
+    if (!d) return PMKLC_ENOMEM;
+    cudaMemcpyAsync(d, cfg->static_weights, cnt * sizeof(float), cudaMemcpyHostToDevice, st);
+    d_static = d;
+  }
+  std::vector<int> grp_mode(L.G, kEncode);
+  long long *d_base_off = ar.upload(L.base_off);
+  long long *d_tok_off = ar.upload(L.tok_off);
+  uint16_t *d_tokens = ar.alloc<uint16_t>(L.n_tok);
+  uint8_t *d_tail = ar.alloc<uint8_t>((size_t)L.G * 8);
+  // lane output buffers: cap = 3 len + 8 (at most 3 byte shifts per symbol + flush)
+  std::vector<unsigned long long> lane_off(L.NL + 1, 0);
+  std::vector<uint32_t> lane_cap(L.NL);
+  for (int r = 0; r < L.NL; ++r) {
+    lane_cap[r] = (uint32_t)(3ull * L.lane_len[r] + 8);
+    lane_off[r + 1] = lane_off[r] + ((lane_cap[r] + 15) & ~15u);
+  }
+  uint8_t *d_lane_buf = ar.alloc<uint8_t>(lane_off[L.NL]);
+  R.p.lane_buf = d_lane_buf;
+  R.p.lane_buf_off = ar.upload(lane_off);
+  R.p.lane_buf_cap = ar.upload(lane_cap);
+  R.p.enc = ar.alloc<EncState>(L.NL);
+  R.p.dec = nullptr;
+  R.p.tokens = d_tokens;
+  uint32_t *d_lane_len = ar.alloc<uint32_t>(L.NL);
+  if (ar.failed) return PMKLC_ENOMEM;
+  rc = setup_run(ar, R, grp_mode, d_static);
+  if (rc) return rc;
+  launch_validate(d_seq, n, R.p.err, st);
+  launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
+  launch_tails(d_seq, d_base_off, d_tok_off, L.G, c.s, c.k, d_tail, st);
+  // count model (judge)
+  std::vector<uint32_t> cnt_len(L.G, 0);
+  uint8_t *d_cnt_buf = nullptr;
+  std::vector<unsigned long long> cnt_off(L.G + 1, 0);
+  uint32_t *d_cnt_len = nullptr;
+  if (c.fallback && L.G > 0) {
+    std::vector<uint32_t> cap(L.G);
+    for (int g = 0; g < L.G; ++g) {
+      cap[g] = (uint32_t)std::min<unsigned long long>(2ull * lens[g] + 8, 0xFFFFFFF0ull);
+      cnt_off[g + 1] = cnt_off[g] + ((cap[g] + 15) & ~15u);
+    }
+    d_cnt_buf = ar.alloc<uint8_t>(cnt_off[L.G]);
+    unsigned long long *d_cnt_off = ar.upload(cnt_off);
+    uint32_t *d_cap = ar.upload(cap);
+    d_cnt_len = ar.alloc<uint32_t>(L.G);
+    std::vector<unsigned long long> boff(L.base_off.begin(), L.base_off.end());
+    unsigned long long *d_boff = ar.upload(boff);
+    if (ar.failed) return PMKLC_ENOMEM;
+    rc = launch_count_encode(d_seq, d_boff, L.G, c.count_order, d_cnt_buf, d_cnt_off, d_cap, d_cnt_len, R.p.err, st);
+    if (rc) return rc;
+    R.launches++;
+  }
+  launch_coder_init(R.p, 1, st);
+  run_steps(R, grp_mode, st);
+  launch_coder_finish(R.p, d_lane_len, st);
+  // results to the host
+  std::vector<uint32_t> lane_len(L.NL);
+  std::vector<uint8_t> tails((size_t)L.G * 8);
+  int h_err = 0;
+  if (L.NL) cudaMemcpyAsync(lane_len.data(), d_lane_len, sizeof(uint32_t) * L.NL, cudaMemcpyDeviceToHost, st);
+  if (L.G) cudaMemcpyAsync(tails.data(), d_tail, tails.size(), cudaMemcpyDeviceToHost, st);
+  if (d_cnt_len) cudaMemcpyAsync(cnt_len.data(), d_cnt_len, sizeof(uint32_t) * L.G, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  if (h_err) return err_to_rc(h_err);
+  uint32_t crc = 0;
+  rc = crc32_device(d_seq, n, &crc, st);
+  if (rc) return rc;
+  // container
+  std::vector<uint8_t> H;
+  H.reserve(kHeader + (size_t)L.G * 16 + (size_t)L.NL * 3);
+  H.insert(H.end(), {'P', 'M', 'K', 'L'});
+  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback ? 2 : 0));
+  uint8_t b8[8] = {kVersion, (uint8_t)c.s, (uint8_t)c.k, flags, (uint8_t)c.precision, (uint8_t)c.optimizer,
+                   (uint8_t)c.smp_mode, (uint8_t)c.count_order};
+  H.insert(H.end(), b8, b8 + 8);
+  put_le<uint16_t>(H, (uint16_t)c.dm.E);
+  put_le<uint16_t>(H, (uint16_t)c.dm.t);
+  put_le<uint16_t>(H, (uint16_t)c.dm.H);
+  put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.E : 0));
+  put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.t : 0));
+  put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.H : 0));
+  put_le<uint32_t>(H, (uint32_t)c.lanes);
+  put_le<float>(H, c.lr);
+  put_le<float>(H, c.alpha0);
+  put_le<float>(H, c.smp_f);
+  put_le<uint64_t>(H, c.seed);
+  put_le<uint64_t>(H, shash);
+  put_le<uint64_t>(H, (uint64_t)n);
+  put_le<uint32_t>(H, (uint32_t)n_blocks);
+  put_le<uint32_t>(H, crc);
+  put_le<uint32_t>(H, 0u);  // kernel variant
+  put_le<uint32_t>(H, 0u);
+  std::vector<unsigned long long> seg;  // (src, dst-relative, len, which)
+  unsigned long long pay = 0;
+  uint64_t n_net = 0, n_cnt = 0;
+  for (int g = 0; g < L.G; ++g) {
+    long long tl = tail_len_of((long long)lens[g], c.s, c.k);
+    size_t tbytes = (size_t)(tl * 2 + 7) / 8;
+    size_t net_cost = tbytes;
+    for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) net_cost += lane_len[r] + varint_len(lane_len[r]);
+    bool use_cnt = c.fallback && (cnt_len[g] + varint_len(cnt_len[g]) < net_cost);
+    put_varint(H, lens[g]);
+    if (use_cnt) {
+      H.push_back(1);
+      put_varint(H, cnt_len[g]);
+      seg.insert(seg.end(), {cnt_off[g], pay, cnt_len[g], 1ull});
+      pay += cnt_len[g];
+      n_cnt++;
+    } else {
+      H.push_back(0);
+      uint8_t tb[2] = {0, 0};
+      for (long long i = 0; i < tl; ++i) tb[i >> 2] |= (uint8_t)(tails[(size_t)g * 8 + i] << (2 * (i & 3)));
+      H.insert(H.end(), tb, tb + tbytes);
+      for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) {
+        put_varint(H, lane_len[r]);
+        if (lane_len[r]) seg.insert(seg.end(), {lane_off[r], pay, lane_len[r], 0ull});
+        pay += lane_len[r];
+      }
+      n_net++;
+    }
+  }
+  size_t total = H.size() + pay;
+  if (total > out_cap) return PMKLC_ENOSPC;
+  for (size_t q = 0; q < seg.size(); q += 4) seg[q + 1] += H.size();
+  cudaMemcpyAsync(d_out, H.data(), H.size(), cudaMemcpyHostToDevice, st);
+  int n_seg = (int)(seg.size() / 4);
+  if (n_seg) {
+    unsigned long long *d_seg = ar.upload(seg);
+    if (!d_seg) return PMKLC_ENOMEM;
+    gather_kernel<<<n_seg, 128, 0, st>>>(d_seg, n_seg, d_lane_buf, d_cnt_buf, d_out);
+  }
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  *out_len = total;
+  g_stats.net_blocks = n_net;
+  g_stats.count_blocks = n_cnt;
+  g_stats.global_steps = (uint64_t)R.S.T_total;
+  g_stats.kernel_launches = R.launches;
+  g_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return PMKLC_OK;
+}
+
+// ---------------------------------------------------------------- decompress
+
+struct Parsed {
+  Cfg c;
+  uint64_t shash = 0, n = 0;
+  uint32_t n_blocks = 0, crc = 0;
+  std::vector<unsigned long long> lens;
+  std::vector<int> mode;                 // per block
+  std::vector<uint8_t> tails;            // per block x 8 codes
+  std::vector<std::vector<uint64_t>> sizes;  // per block: lane sizes or {count size}
+  size_t header_len = 0;
+  unsigned long long payload = 0;
+};
+
+int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
+  if (len < kHeader || memcmp(h, "PMKL", 4) != 0 || h[4] != kVersion) return PMKLC_ECORRUPT;
+  Cfg &c = P.c;
+  c.s = h[5];
+  c.k = h[6];
+  c.use_static = h[7] & 1;
+  c.fallback = (h[7] >> 1) & 1;
+  c.precision = h[8];
+  c.optimizer = h[9];
+  c.smp_mode = h[10];
+  c.count_order = h[11];
+  if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 || c.precision != 0)
+    return PMKLC_ECORRUPT;
+  int A = 1 << (2 * c.k);
+  c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
+  c.st = Dims{A, get_le<uint16_t>(h + 18), get_le<uint16_t>(h + 20), get_le<uint16_t>(h + 22)};
+  if (c.dm.E < 1 || c.dm.t < 1 || c.dm.H < 1) return PMKLC_ECORRUPT;
+  if (c.use_static && (c.st.E < 1 || c.st.t < 1 || c.st.H < 1)) return PMKLC_ECORRUPT;
+  c.lanes = (int)get_le<uint32_t>(h + 24);
+  if (c.lanes < 1) return PMKLC_ECORRUPT;
+  c.lr = get_le<float>(h + 28);
+  c.alpha0 = get_le<float>(h + 32);
+  c.smp_f = get_le<float>(h + 36);
+  c.seed = get_le<uint64_t>(h + 40);
+  P.shash = get_le<uint64_t>(h + 48);
+  P.n = get_le<uint64_t>(h + 56);
+  P.n_blocks = get_le<uint32_t>(h + 64);
+  P.crc = get_le<uint32_t>(h + 68);
+  if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !isfinite(c.lr)) return PMKLC_ECORRUPT;
+  return PMKLC_OK;
+}
+
+int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
+  const Cfg &c = P.c;
+  size_t pos = kHeader;
+  P.lens.resize(P.n_blocks);
+  P.mode.resize(P.n_blocks);
+  P.tails.assign((size_t)P.n_blocks * 8, 0);
+  P.sizes.assign(P.n_blocks, {});
+  unsigned long long sum = 0, pay = 0;
+  for (uint32_t b = 0; b < P.n_blocks; ++b) {
+    uint64_t nb;
+    if (!get_varint(h, len, pos, nb)) return PMKLC_ECORRUPT;
+    P.lens[b] = nb;
+    sum += nb;
+    if (pos >= len) return PMKLC_ECORRUPT;
+    int mode = h[pos++];
+    P.mode[b] = mode;
+    if (mode == 0) {
+      long long tl = tail_len_of((long long)nb, c.s, c.k);
+      size_t tbytes = (size_t)(tl * 2 + 7) / 8;
+      if (pos + tbytes > len) return PMKLC_ECORRUPT;
+      for (long long i = 0; i < tl; ++i) P.tails[(size_t)b * 8 + i] = (h[pos + (i >> 2)] >> (2 * (i & 3))) & 3;
+      pos += tbytes;
+      long long l = n_tokens_of((long long)nb, c.s, c.k);
+      long long Mb = std::min<long long>(c.lanes, l);
+      for (long long r = 0; r < Mb; ++r) {
+        uint64_t x;
+        if (!get_varint(h, len, pos, x)) return PMKLC_ECORRUPT;
+        P.sizes[b].push_back(x);
+        pay += x;
+      }
+    } else if (mode == 1) {
+      uint64_t x;
+      if (!get_varint(h, len, pos, x)) return PMKLC_ECORRUPT;
+      P.sizes[b].push_back(x);
+      pay += x;
+    } else {
+      return PMKLC_ECORRUPT;
+    }
+  }
+  if (sum != P.n) return PMKLC_ECORRUPT;
+  P.header_len = pos;
+  P.payload = pay;
+  if (pos + pay != in_len) return PMKLC_ECORRUPT;
+  return PMKLC_OK;
+}
+
+int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_weights, size_t static_count,
+                        cudaStream_t st, uint8_t *d_seq, size_t seq_cap, size_t *n_out,
+                        std::vector<unsigned long long> *lens_out) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!d_in || !n_out || in_len < kHeader) return in_len < kHeader ? PMKLC_ECORRUPT : PMKLC_EINVAL;
+  Parsed P;
+  std::vector<uint8_t> h(kHeader);
+  PMKLC_CUDA_TRY(cudaMemcpyAsync(h.data(), d_in, kHeader, cudaMemcpyDeviceToHost, st));
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  int rc = parse_fixed(h.data(), kHeader, P);
+  if (rc) return rc;
+  size_t rec_bound = kHeader + (size_t)P.n_blocks * 23 + (size_t)P.n_blocks * (size_t)P.c.lanes * 10;
+  size_t hl = std::min(rec_bound, in_len);
+  h.resize(hl);
+  PMKLC_CUDA_TRY(cudaMemcpyAsync(h.data(), d_in, hl, cudaMemcpyDeviceToHost, st));
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = parse_records(h.data(), hl, in_len, P);
+  if (rc) return rc;
+  if (lens_out) *lens_out = P.lens;
+  *n_out = (size_t)P.n;
+  if (P.n > seq_cap || (P.n && !d_seq)) return PMKLC_ENOSPC;
+  Run R;
+  R.c = P.c;
+  const Cfg &c = R.c;
+  if (c.use_static) {
+    if (!static_weights || static_count != c.st.count()) return PMKLC_EMODEL;
+    if (fnv1a(static_weights, static_count * sizeof(float)) != P.shash) return PMKLC_EMODEL;
+  }
+  make_layout(P.lens, c.s, c.k, c.lanes, R.L);
+  make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
+  const Layout &L = R.L;
+  Arena ar(st);
+  const float *d_static = nullptr;
+  if (c.use_static) {
+    float *d = ar.alloc<float>(static_count);
+    if (!d) return PMKLC_ENOMEM;
+    cudaMemcpyAsync(d, static_weights, static_count * sizeof(float), cudaMemcpyHostToDevice, st);
+    d_static = d;
+  }
+  std::vector<int> grp_mode(L.G), net_sel(L.G), cnt_sel(L.G);
+  for (int g = 0; g < L.G; ++g) {
+    grp_mode[g] = P.mode[g] == 0 ? kDecode : kReplay;
+    net_sel[g] = P.mode[g] == 0;
+    cnt_sel[g] = P.mode[g] == 1;
+  }
+  // payload offsets (relative to the payload start)
+  const uint8_t *d_pay = d_in + P.header_len;
+  std::vector<unsigned long long> lane_off(std::max(L.NL, 1), 0), cnt_in_off(L.G, 0);
+  std::vector<uint32_t> lane_cap(std::max(L.NL, 1), 0), cnt_in_len(L.G, 0);
+  unsigned long long pos = 0;
+  bool any_cnt = false;
+  for (int g = 0; g < L.G; ++g) {
+    if (P.mode[g] == 1) {
+      cnt_in_off[g] = pos;
+      cnt_in_len[g] = (uint32_t)P.sizes[g][0];
+      pos += P.sizes[g][0];
+      any_cnt = true;
+    } else {
+      for (int r = L.lane_off[g], q = 0; r < L.lane_off[g + 1]; ++r, ++q) {
+        lane_off[r] = pos;
+        lane_cap[r] = (uint32_t)P.sizes[g][q];
+        pos += P.sizes[g][q];
+      }
+    }
+  }
+  long long *d_base_off = ar.upload(L.base_off);
+  long long *d_tok_off = ar.upload(L.tok_off);
+  uint16_t *d_tokens = ar.alloc<uint16_t>(L.n_tok);
+  uint8_t *d_tail = ar.upload(P.tails);
+  int *d_net_sel = ar.upload(net_sel);
+  R.p.lane_buf = const_cast<uint8_t *>(d_pay);
+  R.p.lane_buf_off = ar.upload(lane_off);
+  R.p.lane_buf_cap = ar.upload(lane_cap);
+  R.p.enc = nullptr;
+  R.p.dec = ar.alloc<DecState>(L.NL);
+  R.p.tokens = d_tokens;
+  if (ar.failed) return PMKLC_ENOMEM;
+  rc = setup_run(ar, R, grp_mode, d_static);
+  if (rc) return rc;
+  if (any_cnt) {
+    std::vector<unsigned long long> boff(L.base_off.begin(), L.base_off.end());
+    unsigned long long *d_boff = ar.upload(boff);
+    unsigned long long *d_cio = ar.upload(cnt_in_off);
+    uint32_t *d_cil = ar.upload(cnt_in_len);
+    int *d_cnt_sel = ar.upload(cnt_sel);
+    if (ar.failed) return PMKLC_ENOMEM;
+    rc = launch_count_decode(d_pay, d_cio, d_cil, d_boff, d_cnt_sel, L.G, c.count_order, d_seq, st);
+    if (rc) return rc;
+    // tokens of the count-coded blocks (the net blocks' tokens are overwritten while decoding)
+    launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
+  }
+  launch_coder_init(R.p, 0, st);
+  run_steps(R, grp_mode, st);
+  launch_detokenize(d_tokens, d_tail, d_base_off, d_tok_off, d_net_sel, L.G, (long long)P.n, c.s, c.k, d_seq,
+                    R.p.err, st);
+  int h_err = 0;
+  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  if (h_err) return (h_err & kErrBadBase) ? PMKLC_ECORRUPT : err_to_rc(h_err);
+  uint32_t crc = 0;
+  rc = crc32_device(d_seq, (size_t)P.n, &crc, st);
+  if (rc) return rc;
+  if (crc != P.crc) return PMKLC_ECORRUPT;
+  g_stats.global_steps = (uint64_t)R.S.T_total;
+  g_stats.kernel_launches = R.launches;
+  g_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return PMKLC_OK;
+}
+
+}  // namespace
+}  // namespace pmklc
+
+using namespace pmklc;
+
+extern "C" {
+
+int pmklc_abi_version(void) { return PMKLC_ABI_VERSION; }
+
+const char *pmklc_strerror(int rc) {
+  switch (rc) {
+    case PMKLC_OK: return "ok";
+    case PMKLC_EINVAL: return "invalid argument";
+    case PMKLC_ENOMEM: return "out of memory";
+    case PMKLC_ECUDA: return "CUDA error";
+    case PMKLC_ECORRUPT: return "corrupt compressed stream";
+    case PMKLC_EMODEL: return "static model mismatch";
+    case PMKLC_ETIMEOUT: return "device wait timed out";
+    case PMKLC_ENOSPC: return "output buffer too small";
+  }
+  return "unknown error";
+}
+
+void pmklc_free(void *p) { free(p); }
+
+size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid) {
+  if (k < 1 || k > 8) return 0;
+  Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
+  return d.count();
+}
+
+void pmklc_default_cfg(pmklc_model_cfg *c, uint32_t s, uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->struct_size = sizeof(*c);
+  c->s = s;
+  c->k = k;
+  c->emb_d = emb;
+  c->ctx_d = ctx;
+  c->hid_d = hid;
+  c->lanes_per_block = 64;
+  c->precision = PMKLC_FP32_PLAIN;
+  c->optimizer = PMKLC_ADAM;
+  c->lr = 1e-3f;
+  c->alpha_init = 0.5f;
+  c->smp_mode = PMKLC_SMP_TREE;
+  c->smp_fraction = 0.05f;
+  c->count_order = 6;
+  c->fallback = 1;
+  c->seed = 42;
+}
+
+size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg) {
+  Cfg c;
+  if (check_cfg(cfg, c) || (n_blocks && !block_lens)) return 0;
+  std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
+  (void)n;
+  return bound_of(lens, c);
+}
+
+int pmklc_compress_dev(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                       const pmklc_model_cfg *cfg, void *stream, uint8_t *d_out, size_t out_cap, size_t *out_len) {
+  return compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, (cudaStream_t)stream, d_out, out_cap, out_len);
+}
+
+int pmklc_decompress_dev(const uint8_t *d_in, size_t in_len, const float *static_weights, size_t static_count,
+                         void *stream, uint8_t *d_seq, size_t seq_cap, size_t *n) {
+  return decompress_dev_impl(d_in, in_len, static_weights, static_count, (cudaStream_t)stream, d_seq, seq_cap, n,
+                             nullptr);
+}
+
+int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                   const pmklc_model_cfg *cfg, void *stream, uint8_t **out, size_t *out_len) {
+  if (!out || !out_len || (n && !seq)) return PMKLC_EINVAL;
+  *out = nullptr;
+  *out_len = 0;
+  size_t cap = pmklc_compress_bound(n, block_lens, n_blocks, cfg);
+  if (cap == 0) return PMKLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint8_t *d_seq = nullptr, *d_out = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_seq, n ? n : 1, st));
+  if (cudaMallocAsync((void **)&d_out, cap, st) != cudaSuccess) {
+    cudaFreeAsync(d_seq, st);
+    return PMKLC_ENOMEM;
+  }
+  if (n) cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
+  size_t len = 0;
+  int rc = compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, st, d_out, cap, &len);
+  uint8_t *h = nullptr;
+  if (rc == PMKLC_OK) {
+    h = (uint8_t *)malloc(len ? len : 1);
+    if (!h) rc = PMKLC_ENOMEM;
+    else if (cudaMemcpyAsync(h, d_out, len, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess)
+      rc = PMKLC_ECUDA;
+  }
+  cudaFreeAsync(d_seq, st);
+  cudaFreeAsync(d_out, st);
+  if (rc) {
+    free(h);
+    return rc;
+  }
+  *out = h;
+  *out_len = len;
+  return PMKLC_OK;
+}
+
+int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weights, size_t static_count,
+                     void *stream, uint8_t **seq, size_t *n, uint64_t **block_lens, size_t *n_blocks) {
+  if (!in || !seq || !n) return PMKLC_EINVAL;
+  *seq = nullptr;
+  *n = 0;
+  if (in_len < kHeader) return PMKLC_ECORRUPT;
+  cudaStream_t st = (cudaStream_t)stream;
+  Parsed P;
+  int rc = parse_fixed(in, in_len, P);
+  if (rc) return rc;
+  uint8_t *d_in = nullptr, *d_seq = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_in, in_len, st));
+  if (cudaMallocAsync((void **)&d_seq, P.n ? P.n : 1, st) != cudaSuccess) {
+    cudaFreeAsync(d_in, st);
+    return PMKLC_ENOMEM;
+  }
+  cudaMemcpyAsync(d_in, in, in_len, cudaMemcpyHostToDevice, st);
+  size_t nn = 0;
+  std::vector<unsigned long long> lens;
+  rc = decompress_dev_impl(d_in, in_len, static_weights, static_count, st, d_seq, P.n, &nn, &lens);
+  uint8_t *h = nullptr;
+  if (rc == PMKLC_OK) {
+    h = (uint8_t *)malloc(nn ? nn : 1);
+    if (!h) rc = PMKLC_ENOMEM;
+    else if (cudaMemcpyAsync(h, d_seq, nn, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess)
+      rc = PMKLC_ECUDA;
+  }
+  cudaFreeAsync(d_in, st);
+  cudaFreeAsync(d_seq, st);
+  if (rc) {
+    free(h);
+    return rc;
+  }
+  if (block_lens && n_blocks) {
+    uint64_t *bl = (uint64_t *)malloc(sizeof(uint64_t) * (lens.size() ? lens.size() : 1));
+    if (!bl) {
+      free(h);
+      return PMKLC_ENOMEM;
+    }
+    for (size_t i = 0; i < lens.size(); ++i) bl[i] = lens[i];
+    *block_lens = bl;
+    *n_blocks = lens.size();
+  }
+  *seq = h;
+  *n = nn;
+  return PMKLC_OK;
+}
+
+int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint64_t seed, float *out) {
+  if (k < 1 || k > 8 || !emb || !ctx || !hid || !out) return PMKLC_EINVAL;
+  Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
+  std::vector<float> v;
+  init_params(d, seed, v);
+  memcpy(out, v.data(), v.size() * sizeof(float));
+  return PMKLC_OK;
+}
+
+int pmklc_last_stats(pmklc_stats *st) {
+  if (!st) return PMKLC_EINVAL;
+  *st = g_stats;
+  return PMKLC_OK;
+}
+
+int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream) {
+  if (!crc || (n && !d_data)) return PMKLC_EINVAL;
+  return crc32_device(d_data, n, crc, (cudaStream_t)stream);
+}
+
+int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint16_t *d_tokens, uint8_t *d_tail,
+                   size_t *n_tokens, void *stream) {
+  if (s < 1 || s > k || k > 8 || !n_tokens || (n && !d_seq)) return PMKLC_EINVAL;
+  long long l = n_tokens_of((long long)n, (int)s, (int)k);
+  if ((l && !d_tokens) || (!d_tail && tail_len_of((long long)n, (int)s, (int)k))) return PMKLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar(st);
+  std::vector<long long> boff = {0, (long long)n}, toff = {0, l};
+  long long *d_boff = ar.upload(boff), *d_toff = ar.upload(toff);
+  int *d_err = ar.alloc<int>(1);
+  uint8_t *d_t8 = ar.alloc<uint8_t>(8);
+  if (ar.failed) return PMKLC_ENOMEM;
+  cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  launch_validate(d_seq, n, d_err, st);
+  launch_tokenize(d_seq, d_boff, d_toff, 1, l, (int)s, (int)k, d_tokens, st);
+  launch_tails(d_seq, d_boff, d_toff, 1, (int)s, (int)k, d_t8, st);
+  long long tl = tail_len_of((long long)n, (int)s, (int)k);
+  if (tl) cudaMemcpyAsync(d_tail, d_t8, (size_t)tl, cudaMemcpyDeviceToDevice, st);
+  int h_err = 0;
+  cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  *n_tokens = (size_t)l;
+  return h_err ? PMKLC_EINVAL : PMKLC_OK;
+}
+
+// Single-step form of the hot loop: G groups of M lanes whose token sequences are
+// [context (t_eff tokens), target]; one global step at T = t_eff runs the same kernels.
+static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float *d_m, float *d_v, float *d_alpha,
+                    float *d_alpha_m, float *d_alpha_v, const float *d_static, const uint16_t *d_ctx,
+                    const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad, float *d_dalpha,
+                    float *d_logits_only, cudaStream_t st) {
+  const int te = c.t_eff();
+  Run R;
+  R.c = c;
+  Layout &L = R.L;
+  L.G = (int)G;
+  L.NL = (int)(G * M);
+  L.Mmax = (int)M;
+  L.base_off.assign(G + 1, 0);
+  L.tok_off.assign(G + 1, 0);
+  L.lane_off.assign(G + 1, 0);
+  L.base_len.assign(G, te + 1);
+  L.extra.assign(G, 0);
+  L.steps.assign(G, te + 1);
+  for (uint32_t g = 0; g < G; ++g) {
+    L.lane_off[g + 1] = (int)((g + 1) * M);
+    for (uint32_t r = 0; r < M; ++r) {
+      L.lane_tok.push_back((long long)(g * M + r) * (te + 1));
+      L.lane_len.push_back(te + 1);
+      L.lane_grp.push_back((int)g);
+    }
+  }
+  L.n_tok = (long long)G * M * (te + 1);
+  R.S.start.assign(G, 0);
+  R.S.parent.assign(G, -1);
+  R.S.tau0.assign(G, (int)tau - 1);
+  R.S.T_total = te + 1;
+  R.S.max_tau = (int)tau;
+  R.S.pairs_at.assign(R.S.T_total + 1, {});
+  Arena ar(st);
+  uint16_t *d_tok = ar.alloc<uint16_t>(L.n_tok);
+  if (ar.failed) return PMKLC_ENOMEM;
+  size_t rows = (size_t)G * M;
+  cudaMemcpy2DAsync(d_tok, (te + 1) * sizeof(uint16_t), d_ctx, te * sizeof(uint16_t), te * sizeof(uint16_t), rows,
+                    cudaMemcpyDeviceToDevice, st);
+  if (d_target)
+    cudaMemcpy2DAsync(d_tok + te, (te + 1) * sizeof(uint16_t), d_target, sizeof(uint16_t), sizeof(uint16_t), rows,
+                      cudaMemcpyDeviceToDevice, st);
+  // caller-provided tokens index the embedding tables: reject any >= 4^k before use
+  int *d_chk = ar.alloc<int>(1);
+  if (!d_chk) return PMKLC_ENOMEM;
+  cudaMemsetAsync(d_chk, 0, sizeof(int), st);
+  if (!d_target) cudaMemsetAsync(d_tok, 0, sizeof(uint16_t) * L.n_tok, st), cudaMemcpy2DAsync(
+      d_tok, (te + 1) * sizeof(uint16_t), d_ctx, te * sizeof(uint16_t), te * sizeof(uint16_t), rows,
+      cudaMemcpyDeviceToDevice, st);
+  check_tokens_kernel<<<(unsigned)((L.n_tok + 255) / 256), 256, 0, st>>>(d_tok, L.n_tok, c.A(), d_chk);
+  int h_chk = 0;
+  cudaMemcpyAsync(&h_chk, d_chk, sizeof(int), cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_chk) return PMKLC_EINVAL;
+  std::vector<int> mode(G, kReplay);
+  R.p.tokens = d_tok;
+  R.p.lane_buf = nullptr;
+  R.p.lane_buf_off = nullptr;
+  R.p.lane_buf_cap = nullptr;
+  int rc = setup_run(ar, R, mode, d_static);
+  if (rc) return rc;
+  // use the caller's state in place of the seeded init
+  R.p.params = d_params;
+  R.p.m = d_m;
+  R.p.v = d_v;
+  R.p.alpha = d_alpha;
+  R.p.alpha_m = d_alpha_m;
+  R.p.alpha_v = d_alpha_v;
+  const int T = te;
+  if (d_logits_only) {
+    launch_forward(R.p, T, st);
+    cudaMemcpyAsync(d_logits_only, R.p.zm, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
+  } else {
+    std::vector<unsigned long long> off(rows, 0);
+    std::vector<uint32_t> cap(rows, 0);
+    R.p.lane_buf_off = ar.upload(off);
+    R.p.lane_buf_cap = ar.upload(cap);
+    R.p.lane_buf = ar.alloc<uint8_t>(16);
+    R.p.out_P = d_P;
+    if (ar.failed) return PMKLC_ENOMEM;
+    launch_forward(R.p, T, st);
+    launch_mixcode(R.p, T, st);
+    launch_backward(R.p, T, st);
+    if (d_grad) launch_export_grad(R.p, d_grad, st);
+    if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
+    launch_update(R.p, T, st);
+  }
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  return PMKLC_OK;
+}
+
+int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,
+                  size_t rows, uint32_t precision, float *d_logits, void *stream) {
+  if (k < 1 || k > 8 || !E || !t || !H || precision != PMKLC_FP32_PLAIN || (rows && (!d_params || !d_ctx || !d_logits)))
+    return PMKLC_EINVAL;
+  if (rows == 0) return PMKLC_OK;
+  pmklc_model_cfg mc;
+  pmklc_default_cfg(&mc, 1, k, E, t, H);
+  Cfg c;
+  int rc = check_cfg(&mc, c);
+  if (rc) return rc;
+  // a throw-away copy of the parameters: the forward never writes them, but the plan wants a mutable pointer
+  return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
+}
+
+int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *d_params, float *d_m, float *d_v,
+                     float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static, const uint16_t *d_ctx,
+                     const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad, float *d_dalpha,
+                     void *stream) {
+  Cfg c;
+  pmklc_model_cfg tmp;
+  if (!cfg) return PMKLC_EINVAL;
+  tmp = *cfg;
+  if (tmp.use_static && !tmp.static_weights) tmp.static_weights = (const float *)d_static;  // only checked non-null
+  int rc = check_cfg(&tmp, c);
+  if (rc) return rc;
+  if (!G || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||
+      !d_target || (c.use_static && !d_static))
+    return PMKLC_EINVAL;
+  return one_step(c, G, M, d_params, d_m, d_v, d_alpha, d_alpha_m, d_alpha_v, d_static, d_ctx, d_target, tau, d_P,
+                  d_grad, d_dalpha, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Shared device-side definitions of libpmklc (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pmklc.h"
+
+namespace pmklc {
+
+constexpr int kTotalBits = 24;             // frequency tables sum to 2^24 (reading R10)
+constexpr uint32_t kTotal = 1u << kTotalBits;
+
+enum GroupMode : int { kEncode = 0, kDecode = 1, kReplay = 2 };
+
+// Error word bits written by kernels (host turns them into PMKLC_E* codes).
+enum ErrBits : int { kErrBadBase = 1, kErrOverflow = 2, kErrCorrupt = 4, kErrTimeout = 8 };
+
+// Dimensions of one MLP predictor: alphabet A = 4^k, embedding E, context t, hidden H.
+struct Dims {
+  int A, E, t, H;
+  __host__ __device__ int K1() const { return t * E; }
+  __host__ __device__ size_t off_emb() const { return 0; }
+  __host__ __device__ size_t off_w1() const { return (size_t)A * E; }
+  __host__ __device__ size_t off_b1() const { return off_w1() + (size_t)t * E * H; }
+  __host__ __device__ size_t off_w2() const { return off_b1() + H; }
+  __host__ __device__ size_t off_b2() const { return off_w2() + (size_t)H * A; }
+  __host__ __device__ size_t count() const { return off_b2() + A; }
+};
+
+// Per-lane range-coder states (reading R11).
+struct EncState {
+  unsigned long long low, range;
+  uint32_t cache, pending, pos, has_cache;
+};
+struct DecState {
+  unsigned long long code, range;
+  uint32_t pos, pad;
+};
+
+// Everything the per-step kernels of one run need (device pointers + sizes).
+struct Plan {
+  int G;             // groups (= blocks)
+  int NL;            // lanes (= rows of every per-step GEMM)
+  int Mmax;          // largest number of lanes in a group
+  int t_eff;         // uniform-coded prefix length per lane
+  int use_static;
+  int optimizer;     // PMKLC_ADAM / PMKLC_SGD
+  float lr;
+  Dims dm, st;
+  size_t P;          // dm.count()
+  // schedule (per group)
+  const int *grp_start, *grp_steps, *grp_lane_off, *grp_base, *grp_extra, *grp_mode, *grp_tau0;
+  // lanes
+  const long long *lane_tok;   // absolute token index of the lane's first token
+  const int *lane_len, *lane_grp;
+  uint16_t *tokens;
+  // model state
+  float *params, *m, *v, *grad, *alpha, *alpha_m, *alpha_v;
+  const float *static_params;
+  const float *bc1, *bc2;      // Adam bias corrections 1 - beta^tau, indexed by tau
+  // activations (NL rows)
+  float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
+  float *out_P;                // optional: mixed probabilities of predicted rows (tests)
+  long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
+  // coders
+  EncState *enc;
+  DecState *dec;
+  uint8_t *lane_buf;           // encode: output bytes; decode: input bytes
+  const unsigned long long *lane_buf_off;
+  const uint32_t *lane_buf_cap;  // encode: capacity; decode: payload length
+  int *err;
+};
+
+__device__ __forceinline__ int row_local_step(const Plan &p, int T, int g) { return T - p.grp_start[g]; }
+
+// Number of lanes of group g still live at local step j (lanes differ by at most one token).
+__device__ __forceinline__ int live_lanes(const Plan &p, int g, int j) {
+  int M = p.grp_lane_off[g + 1] - p.grp_lane_off[g];
+  int base = p.grp_base[g];
+  return j < base ? M : (j == base ? p.grp_extra[g] : 0);
+}
+
+// A lane is predicted (and trained on) at step T iff its local step j has t_eff <= j < len.
+__device__ __forceinline__ bool row_pred(const Plan &p, int T, int r, int g) {
+  int j = T - p.grp_start[g];
+  return j >= p.t_eff && j < p.lane_len[r];
+}
+
+// Group g trains at step T iff some lane predicts: t_eff <= j < steps.
+__device__ __forceinline__ bool group_trains(const Plan &p, int T, int g) {
+  int j = T - p.grp_start[g];
+  return j >= p.t_eff && j < p.grp_steps[g];
+}
+
+// Fixed point scale of the embedding gradient accumulators (integer adds are order-free,
+// so the sum is deterministic; resolution 2^-40, range +-2^23).
+constexpr double kEmbFix = 1099511627776.0;  // 2^40
+
+}  // namespace pmklc
+
+#define PMKLC_CUDA_TRY(expr)                   \
+  do {                                         \
+    cudaError_t e_ = (expr);                   \
+    if (e_ != cudaSuccess) return PMKLC_ECUDA; \
+  } while (0)

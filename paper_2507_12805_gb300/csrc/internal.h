@@ -1,0 +1,50 @@
+// Host-side interfaces between the translation units of libpmklc.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pmklc {
+
+// tokenize.cu ---------------------------------------------------------------
+// Checks every byte is one of A, C, G, T (sets kErrBadBase in *d_err otherwise).
+void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st);
+// Tokens of every block: block b has bases [base_off[b], base_off[b+1]) and tokens
+// [tok_off[b], tok_off[b+1]) in d_tokens.
+void launch_tokenize(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
+                     long long n_tok, int s, int k, uint16_t *d_tokens, cudaStream_t st);
+// Tail codes of every block (at most 7 per block) into d_tail[b*8 + i].
+void launch_tails(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
+                  int s, int k, uint8_t *d_tail, cudaStream_t st);
+// Inverse of tokenize for the blocks with d_sel[b] != 0: writes ASCII bases; sets kErrCorrupt
+// when overlapping windows disagree.
+void launch_detokenize(const uint16_t *d_tokens, const uint8_t *d_tail, const long long *d_base_off,
+                       const long long *d_tok_off, const int *d_sel, int n_blocks, long long n_bases, int s, int k,
+                       uint8_t *d_seq, int *d_err, cudaStream_t st);
+int crc32_device(const uint8_t *d_data, size_t n, uint32_t *crc, cudaStream_t st);
+
+// countmodel.cu --------------------------------------------------------------
+int launch_count_encode(const uint8_t *d_seq, const unsigned long long *d_off, int n_blocks, int m, uint8_t *d_out,
+                        const unsigned long long *d_out_off, const uint32_t *d_cap, uint32_t *d_len, int *d_err,
+                        cudaStream_t st);
+int launch_count_decode(const uint8_t *d_in, const unsigned long long *d_in_off, const uint32_t *d_len,
+                        const unsigned long long *d_off, const int *d_sel, int n_blocks, int m, uint8_t *d_seq,
+                        cudaStream_t st);
+
+// mixcode.cu -----------------------------------------------------------------
+void launch_mixcode(const Plan &p, int T, cudaStream_t st);
+void launch_coder_init(const Plan &p, int encode, cudaStream_t st);
+void launch_coder_finish(const Plan &p, uint32_t *d_lane_len, cudaStream_t st);
+
+// predictor.cu ---------------------------------------------------------------
+void launch_forward(const Plan &p, int T, cudaStream_t st);
+void launch_backward(const Plan &p, int T, cudaStream_t st);
+void launch_update(const Plan &p, int T, cudaStream_t st);
+void launch_backward_update(const Plan &p, int T, cudaStream_t st);
+// gradient of every group (embedding part from the fixed-point accumulators) into d_out (G x P)
+void launch_export_grad(const Plan &p, float *d_out, cudaStream_t st);
+void launch_smp_copy(const Plan &p, const int *d_pairs, int n_pairs, cudaStream_t st);
+void launch_init_groups(const Plan &p, const float *d_init, float alpha0, cudaStream_t st);
+
+}  // namespace pmklc

@@ -1,0 +1,442 @@
+// Probability Mixer (Eq. 1) + softmax + integer CDF + range coding, one warp
+// per lane row, and the cross-entropy gradient the Backward Controller needs
+// (Eq. 2).
+//
+// Per predicted row:  z_a = alpha*L^u_a + (1-alpha)*L^m_a     (Eq. 1, S = (1,0,1))
+//                     P_a = exp(z_a - max) * (1/sum)            (softmax)
+//                     freq_a = 1 + floor(P_a * (2^24 - A)), remainder to the first maximum
+// then the lane's token is range coded with (cum, freq) (or decoded from it)
+// and dL^m = (1-alpha)(P - onehot)/n, dalpha_row = sum (P - onehot)/n (L^u - L^m).
+//
+// Determinism (encoder and decoder must build identical tables): every value
+// is recomputed from the same inputs with the same instructions in every pass;
+// all floating-point operations of the table are explicit round-to-nearest
+// intrinsics (no contraction); each lane owns a contiguous chunk of the
+// alphabet, reduces it sequentially, and warp results are combined in a fixed
+// butterfly order and then broadcast from lane 0, so every lane holds the same
+// value.  No float atomics.
+#include "internal.h"
+#include "rangecoder.cuh"
+
+namespace pmklc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct RowView {
+  const float *zu, *zm;  // zu unused when !use_static
+  float alpha, oma;
+  int use_static;
+  __device__ __forceinline__ float z(int a) const {
+    return use_static ? __fadd_rn(__fmul_rn(alpha, zu[a]), __fmul_rn(oma, zm[a])) : __fmul_rn(oma, zm[a]);
+  }
+};
+
+__device__ __forceinline__ uint32_t qfreq(float P, float scale) { return 1u + (uint32_t)floorf(__fmul_rn(P, scale)); }
+
+// Alphabet chunk of a lane: [a0, a0 + n)
+__device__ __forceinline__ void lane_chunk(int A, int lane, int &a0, int &n) {
+  if (A >= 32) {
+    n = A >> 5;
+    a0 = lane * n;
+  } else {
+    n = lane < A ? 1 : 0;
+    a0 = lane;
+  }
+}
+
+struct RowTable {
+  float mx, inv;
+  uint32_t argmax;  // first index of maximal freq
+  int rem;          // 2^24 - sum(freq before the remainder)
+  uint32_t cbase;   // exclusive prefix of this lane's chunk (incl. remainder)
+  uint32_t csum;    // this lane's chunk sum (incl. remainder)
+  __device__ __forceinline__ float prob(const RowView &v, int a) const {
+    return __fmul_rn(__expf(__fsub_rn(v.z(a), mx)), inv);
+  }
+  __device__ __forceinline__ uint32_t freq(const RowView &v, int a, float scale) const {
+    uint32_t f = qfreq(prob(v, a), scale);
+    return a == (int)argmax ? (uint32_t)((int)f + rem) : f;
+  }
+};
+
+// Warp-cooperative distribution and frequency table of one row (all lanes call it).
+__device__ __forceinline__ void row_table(const RowView &v, int A, RowTable &t) {
+  const int lane = threadIdx.x & 31;
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  const float scale = (float)(kTotal - (uint32_t)A);
+  // max
+  float mx = -INFINITY;
+  for (int i = 0; i < n; ++i) mx = fmaxf(mx, v.z(a0 + i));
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+  t.mx = mx;
+  // sum of exponentials: chunk in order, butterfly, lane 0's value broadcast
+  float s = 0.f;
+  for (int i = 0; i < n; ++i) s = __fadd_rn(s, __expf(__fsub_rn(v.z(a0 + i), mx)));
+  for (int o = 16; o; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(kFull, s, o));
+  s = __shfl_sync(kFull, s, 0);
+  t.inv = __frcp_rn(s);
+  // frequencies before the remainder: sum and first maximum
+  uint32_t fs = 0, fmx = 0, amx = 0xffffffffu;
+  t.argmax = 0xffffffffu;
+  t.rem = 0;
+  for (int i = 0; i < n; ++i) {
+    uint32_t f = qfreq(t.prob(v, a0 + i), scale);
+    fs += f;
+    if (f > fmx) {
+      fmx = f;
+      amx = a0 + i;
+    }
+  }
+  uint32_t tot = fs;
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(kFull, tot, o);
+    uint32_t of = __shfl_xor_sync(kFull, fmx, o), oa = __shfl_xor_sync(kFull, amx, o);
+    if (of > fmx || (of == fmx && oa < amx)) {
+      fmx = of;
+      amx = oa;
+    }
+  }
+  t.argmax = amx;
+  t.rem = (int)(kTotal - tot);
+  // chunk sums with the remainder, exclusive scan over lanes
+  uint32_t cs = fs + ((amx >= (uint32_t)a0 && amx < (uint32_t)(a0 + n)) ? (uint32_t)t.rem : 0u);
+  uint32_t inc = cs;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  t.csum = cs;
+  t.cbase = inc - cs;
+}
+
+// (cum, freq) of symbol e, gathered at lane 0 (all lanes call it).
+__device__ __forceinline__ void symbol_interval(const RowView &v, int A, const RowTable &t, int e, uint32_t &cum,
+                                                uint32_t &freq) {
+  const int lane = threadIdx.x & 31;
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  const float scale = (float)(kTotal - (uint32_t)A);
+  uint32_t c = 0, f = 0;
+  int owner = A >= 32 ? e / (A >> 5) : e;
+  if (lane == owner) {
+    c = t.cbase;
+    for (int a = a0; a < e; ++a) c += t.freq(v, a, scale);
+    f = t.freq(v, e, scale);
+  }
+  cum = __shfl_sync(kFull, c, owner);
+  freq = __shfl_sync(kFull, f, owner);
+}
+
+// Symbol whose interval contains target value x (all lanes call it; result on all lanes).
+__device__ __forceinline__ int symbol_of(const RowView &v, int A, const RowTable &t, uint32_t x, uint32_t &cum,
+                                         uint32_t &freq) {
+  const int lane = threadIdx.x & 31;
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  const float scale = (float)(kTotal - (uint32_t)A);
+  bool mine = n > 0 && x >= t.cbase && x - t.cbase < t.csum;
+  unsigned bal = __ballot_sync(kFull, mine);
+  int owner = bal ? __ffs(bal) - 1 : 0;
+  int sym = 0;
+  uint32_t c = 0, f = 0;
+  if (lane == owner) {
+    c = t.cbase;
+    sym = a0 + n - 1;
+    for (int a = a0; a < a0 + n; ++a) {
+      uint32_t fa = t.freq(v, a, scale);
+      if (x < c + fa) {
+        sym = a;
+        f = fa;
+        break;
+      }
+      c += fa;
+    }
+    if (f == 0) f = t.freq(v, sym, scale);  // corrupt input: clamp into the last symbol
+  }
+  sym = __shfl_sync(kFull, sym, owner);
+  cum = __shfl_sync(kFull, c, owner);
+  freq = __shfl_sync(kFull, f, owner);
+  return sym;
+}
+
+__global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= p.NL) return;
+  const int g = p.lane_grp[r];
+  const int j = T - p.grp_start[g];
+  if (j < 0 || j >= p.lane_len[r]) return;
+  const int mode = p.grp_mode[g];
+  const int A = p.dm.A;
+  const long long tpos = p.lane_tok[r] + j;
+  uint8_t *buf = p.lane_buf + p.lane_buf_off[r];
+  const uint32_t cap = p.lane_buf_cap[r];
+  if (j < p.t_eff) {  // uniform distribution for the first t symbols (§2)
+    if (lane == 0 && mode != kReplay) {
+      const uint32_t u = kTotal / (uint32_t)A;
+      if (mode == kEncode) {
+        EncState s = p.enc[r];
+        uint32_t e = p.tokens[tpos];
+        enc_code24(s, e * u, u, buf, cap, p.err);
+        p.enc[r] = s;
+      } else {
+        DecState s = p.dec[r];
+        unsigned long long rr;
+        uint32_t x = dec_target24(s, rr);
+        uint32_t e = x / u;
+        dec_consume(s, rr, e * u, u, buf, cap);
+        p.dec[r] = s;
+        p.tokens[tpos] = (uint16_t)e;
+      }
+    }
+    return;
+  }
+  const float alpha = p.alpha[g];
+  RowView v{p.zu + (size_t)r * A, p.zm + (size_t)r * A, alpha, __fsub_rn(1.f, alpha), p.use_static};
+  RowTable t;
+  row_table(v, A, t);
+  int e;
+  if (mode == kDecode) {
+    DecState s;
+    unsigned long long rr = 0;
+    uint32_t x = 0;
+    if (lane == 0) {
+      s = p.dec[r];
+      x = dec_target24(s, rr);
+    }
+    x = __shfl_sync(kFull, x, 0);
+    uint32_t cum, freq;
+    e = symbol_of(v, A, t, x, cum, freq);
+    if (lane == 0) {
+      dec_consume(s, rr, cum, freq, buf, cap);
+      p.dec[r] = s;
+      p.tokens[tpos] = (uint16_t)e;
+    }
+  } else {
+    e = p.tokens[tpos];
+    if (mode == kEncode) {
+      uint32_t cum, freq;
+      symbol_interval(v, A, t, e, cum, freq);
+      if (lane == 0) {
+        EncState s = p.enc[r];
+        enc_code24(s, cum, freq, buf, cap, p.err);
+        p.enc[r] = s;
+      }
+    }
+  }
+  // Backward Controller inputs: mean cross entropy over the group's predicted lanes
+  const int n_pred = live_lanes(p, g, j);
+  const float inv_n = 1.f / (float)n_pred;
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  float da = 0.f;
+  float *dz = p.dz + (size_t)r * A;
+  float *outP = p.out_P ? p.out_P + (size_t)r * A : nullptr;
+  for (int a = a0; a < a0 + n; ++a) {
+    float P = t.prob(v, a);
+    if (outP) outP[a] = P;
+    float d = (P - (a == e ? 1.f : 0.f)) * inv_n;
+    dz[a] = v.oma * d;
+    float diff = p.use_static ? v.zu[a] - v.zm[a] : -v.zm[a];
+    da = fmaf(d, diff, da);
+  }
+  for (int o = 16; o; o >>= 1) da += __shfl_xor_sync(kFull, da, o);
+  if (lane == 0) p.dalpha_row[r] = da;
+}
+
+__global__ void coder_init_kernel(Plan p, int encode) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p.NL) return;
+  if (encode) {
+    EncState s;
+    enc_init(s);
+    p.enc[r] = s;
+  } else {
+    DecState s;
+    dec_init(s, p.lane_buf + p.lane_buf_off[r], p.lane_buf_cap[r]);
+    p.dec[r] = s;
+  }
+}
+
+__global__ void coder_finish_kernel(Plan p, uint32_t *lane_len) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p.NL) return;
+  EncState s = p.enc[r];
+  lane_len[r] = enc_finish(s, p.lane_buf + p.lane_buf_off[r], p.lane_buf_cap[r], p.err);
+  p.enc[r] = s;
+}
+
+// ---- standalone kernels for the single-step entry points ----
+
+__global__ void quantize_kernel(const float *P, int rows, int A, uint32_t *freq) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  // a RowTable whose probabilities are given directly
+  const float *pr = P + (size_t)r * A;
+  const float scale = (float)(kTotal - (uint32_t)A);
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  uint32_t fs = 0, fmx = 0, amx = 0xffffffffu;
+  for (int i = 0; i < n; ++i) {
+    uint32_t f = qfreq(pr[a0 + i], scale);
+    fs += f;
+    if (f > fmx) {
+      fmx = f;
+      amx = a0 + i;
+    }
+  }
+  uint32_t tot = fs;
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(kFull, tot, o);
+    uint32_t of = __shfl_xor_sync(kFull, fmx, o), oa = __shfl_xor_sync(kFull, amx, o);
+    if (of > fmx || (of == fmx && oa < amx)) {
+      fmx = of;
+      amx = oa;
+    }
+  }
+  int rem = (int)(kTotal - tot);
+  for (int i = 0; i < n; ++i) {
+    int a = a0 + i;
+    uint32_t f = qfreq(pr[a], scale);
+    freq[(size_t)r * A + a] = a == (int)amx ? (uint32_t)((int)f + rem) : f;
+  }
+}
+
+__global__ void mix_quantize_kernel(const float *Lu, const float *Lm, int rows, int A, float alpha, int use_static,
+                                    float *P, uint32_t *freq) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  RowView v{Lu ? Lu + (size_t)r * A : nullptr, Lm + (size_t)r * A, alpha, __fsub_rn(1.f, alpha), use_static};
+  RowTable t;
+  row_table(v, A, t);
+  const float scale = (float)(kTotal - (uint32_t)A);
+  int a0, n;
+  lane_chunk(A, lane, a0, n);
+  for (int a = a0; a < a0 + n; ++a) {
+    P[(size_t)r * A + a] = t.prob(v, a);
+    freq[(size_t)r * A + a] = t.freq(v, a, scale);
+  }
+}
+
+__global__ void range_encode_kernel(const uint32_t *freq, const uint16_t *sym, int n_streams, int L, int A,
+                                    uint8_t *out, uint32_t cap, uint32_t *len, int *err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_streams) return;
+  EncState s;
+  enc_init(s);
+  uint8_t *o = out + (size_t)i * cap;
+  for (int j = 0; j < L; ++j) {
+    const uint32_t *f = freq + ((size_t)i * L + j) * A;
+    int e = sym[(size_t)i * L + j];
+    uint32_t cum = 0;
+    for (int a = 0; a < e; ++a) cum += f[a];
+    enc_code24(s, cum, f[e], o, cap, err);
+  }
+  len[i] = enc_finish(s, o, cap, err);
+}
+
+__global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, const uint32_t *len, int n_streams,
+                                    int L, int A, uint32_t cap, uint16_t *sym) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_streams) return;
+  DecState s;
+  const uint8_t *b = in + (size_t)i * cap;
+  dec_init(s, b, len[i]);
+  for (int j = 0; j < L; ++j) {
+    const uint32_t *f = freq + ((size_t)i * L + j) * A;
+    unsigned long long rr;
+    uint32_t x = dec_target24(s, rr);
+    uint32_t cum = 0;
+    int e = A - 1;
+    for (int a = 0; a < A; ++a) {
+      if (x < cum + f[a]) {
+        e = a;
+        break;
+      }
+      cum += f[a];
+    }
+    dec_consume(s, rr, cum, f[e], b, len[i]);
+    sym[(size_t)i * L + j] = (uint16_t)e;
+  }
+}
+
+}  // namespace
+
+void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
+  if (p.NL <= 0) return;
+  mixcode_kernel<<<(p.NL * 32 + 255) / 256, 256, 0, st>>>(p, T);
+}
+
+void launch_coder_init(const Plan &p, int encode, cudaStream_t st) {
+  if (p.NL <= 0) return;
+  coder_init_kernel<<<(p.NL + 127) / 128, 128, 0, st>>>(p, encode);
+}
+
+void launch_coder_finish(const Plan &p, uint32_t *d_lane_len, cudaStream_t st) {
+  if (p.NL <= 0) return;
+  coder_finish_kernel<<<(p.NL + 127) / 128, 128, 0, st>>>(p, d_lane_len);
+}
+
+}  // namespace pmklc
+
+using namespace pmklc;
+
+static bool pow4(uint32_t A) { return A >= 4 && A <= 65536 && (A & (A - 1)) == 0 && (__builtin_ctz(A) % 2 == 0); }
+
+extern "C" int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_t *d_freq, void *stream) {
+  if (!pow4(A) || (rows && (!d_P || !d_freq))) return PMKLC_EINVAL;
+  if (rows == 0) return PMKLC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  quantize_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(d_P, (int)rows, (int)A, d_freq);
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PMKLC_OK;
+}
+
+extern "C" int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32_t A, float alpha,
+                                  uint32_t use_static, float *d_P, uint32_t *d_freq, void *stream) {
+  if (!pow4(A) || (rows && (!d_Lm || !d_P || !d_freq || (use_static && !d_Lu)))) return PMKLC_EINVAL;
+  if (rows == 0) return PMKLC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  mix_quantize_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(d_Lu, d_Lm, (int)rows, (int)A, alpha,
+                                                                             (int)(use_static != 0), d_P, d_freq);
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PMKLC_OK;
+}
+
+extern "C" int pmklc_range_encode(const uint32_t *d_freq, const uint16_t *d_sym, uint32_t n_streams, uint32_t L,
+                                  uint32_t A, uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream) {
+  if (!pow4(A) || !d_len || (n_streams && (!d_out || (L && (!d_freq || !d_sym))))) return PMKLC_EINVAL;
+  if (n_streams == 0) return PMKLC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d_err = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_err, sizeof(int), st));
+  cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  range_encode_kernel<<<(n_streams + 63) / 64, 64, 0, st>>>(d_freq, d_sym, (int)n_streams, (int)L, (int)A, d_out, cap,
+                                                            d_len, d_err);
+  int h = 0;
+  cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_err, st);
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  return h ? PMKLC_ENOSPC : PMKLC_OK;
+}
+
+extern "C" int pmklc_range_decode(const uint32_t *d_freq, const uint8_t *d_in, const uint32_t *d_len,
+                                  uint32_t n_streams, uint32_t L, uint32_t A, uint32_t cap, uint16_t *d_sym,
+                                  void *stream) {
+  if (!pow4(A) || (n_streams && (!d_in || !d_len || (L && (!d_freq || !d_sym))))) return PMKLC_EINVAL;
+  if (n_streams == 0) return PMKLC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  range_decode_kernel<<<(n_streams + 63) / 64, 64, 0, st>>>(d_freq, d_in, d_len, (int)n_streams, (int)L, (int)A, cap,
+                                                            d_sym);
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PMKLC_OK;
+}

@@ -1,0 +1,277 @@
+// (s,k)-mer encoding and decoding (GskE, paper §4.1 and Fig. 3), input
+// validation and a parallel CRC-32, on sm_103a.
+//
+// The paper's encoder maps A/C/G/T to 0..3 and reads each window of k bases,
+// taken every s bases, as a base-4 number with the first base most
+// significant ("CGG" -> 26).  Here one thread produces one token; the
+// bases are read as bytes (they are HBM-bound streams of <= 8 bytes per token).
+#include <stdio.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace pmklc {
+
+__device__ __forceinline__ bool is_acgt(uint32_t c) { return c == 'A' || c == 'C' || c == 'G' || c == 'T'; }
+// A=0x41 -> 0, C=0x43 -> 1, G=0x47 -> 2, T=0x54 -> 3
+__device__ __forceinline__ uint32_t base_code(uint32_t c) { return ((c >> 1) & 3u) ^ ((c >> 2) & 1u); }
+
+__global__ void validate_kernel(const uint8_t *__restrict__ seq, size_t n, int *err) {
+  size_t head = (16 - (reinterpret_cast<uintptr_t>(seq) & 15)) & 15;
+  if (head > n) head = n;
+  size_t nvec = (n - head) / 16;
+  const uint4 *v = reinterpret_cast<const uint4 *>(seq + head);
+  size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (size_t i = tid; i < nvec; i += stride) {
+    uint4 w = v[i];
+    uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bad |= !is_acgt((words[q] >> (8 * b)) & 0xFF);
+  }
+  if (tid < head) bad |= !is_acgt(seq[tid]);
+  size_t t0 = head + nvec * 16;
+  if (t0 + tid < n) bad |= !is_acgt(seq[t0 + tid]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrBadBase);
+}
+
+void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st) {
+  if (n == 0) return;
+  size_t nvec = n / 16 + 1;
+  size_t grid = (nvec + 255) / 256;
+  if (grid > 152u * 16u) grid = 152u * 16u;
+  validate_kernel<<<(unsigned)grid, 256, 0, st>>>(d_seq, n, d_err);
+}
+
+__device__ __forceinline__ int find_block(const long long *off, int n_blocks, long long x) {
+  // largest b with off[b] <= x (off has n_blocks + 1 ascending entries)
+  int lo = 0, hi = n_blocks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void tokenize_kernel(const uint8_t *__restrict__ seq, const long long *__restrict__ base_off,
+                                const long long *__restrict__ tok_off, int n_blocks, long long n_tok, int s, int k,
+                                uint16_t *__restrict__ tokens) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_tok) return;
+  int b = find_block(tok_off, n_blocks, i);
+  long long j = i - tok_off[b];
+  const uint8_t *p = seq + base_off[b] + j * s;
+  uint32_t v = 0;
+  for (int m = 0; m < k; ++m) v = (v << 2) | base_code(p[m]);
+  tokens[i] = (uint16_t)v;
+}
+
+void launch_tokenize(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
+                     long long n_tok, int s, int k, uint16_t *d_tokens, cudaStream_t st) {
+  if (n_tok <= 0) return;
+  tokenize_kernel<<<(unsigned)((n_tok + 255) / 256), 256, 0, st>>>(d_seq, d_base_off, d_tok_off, n_blocks, n_tok, s,
+                                                                    k, d_tokens);
+}
+
+__global__ void tails_kernel(const uint8_t *__restrict__ seq, const long long *__restrict__ base_off,
+                             const long long *__restrict__ tok_off, int n_blocks, int s, int k, uint8_t *tail) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  long long n = base_off[b + 1] - base_off[b];
+  long long l = tok_off[b + 1] - tok_off[b];
+  long long covered = l > 0 ? (l - 1) * s + k : 0;
+  for (int i = 0; i < 8; ++i)
+    tail[b * 8 + i] = (covered + i < n) ? (uint8_t)base_code(seq[base_off[b] + covered + i]) : 0;
+}
+
+void launch_tails(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
+                  int s, int k, uint8_t *d_tail, cudaStream_t st) {
+  if (n_blocks <= 0) return;
+  tails_kernel<<<(n_blocks + 127) / 128, 128, 0, st>>>(d_seq, d_base_off, d_tok_off, n_blocks, s, k, d_tail);
+}
+
+// One thread per output base of the selected blocks.  Base i of a block is digit i of
+// token 0 when i < k, else digit k-s+m of token j = (i-k)/s + 1 (m = (i-k) mod s), else
+// tail[i - covered].  The thread owning the first new base of token j >= 1 also checks
+// that the k-s overlapping digits agree with token j-1.
+__global__ void detokenize_kernel(const uint16_t *__restrict__ tokens, const uint8_t *__restrict__ tail,
+                                  const long long *__restrict__ base_off, const long long *__restrict__ tok_off,
+                                  const int *__restrict__ sel, int n_blocks, long long n_bases, int s, int k,
+                                  uint8_t *__restrict__ seq, int *err) {
+  long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (x >= n_bases) return;
+  int b = find_block(base_off, n_blocks, x);
+  if (!sel[b]) return;
+  long long i = x - base_off[b];
+  long long l = tok_off[b + 1] - tok_off[b];
+  long long covered = l > 0 ? (l - 1) * s + k : 0;
+  uint32_t code;
+  if (i >= covered) {
+    code = tail[b * 8 + (i - covered)];
+  } else if (i < k) {
+    uint32_t t0 = tokens[tok_off[b]];
+    code = (t0 >> (2 * (k - 1 - i))) & 3u;
+  } else {
+    long long j = (i - k) / s + 1;
+    int m = (int)((i - k) % s);
+    uint32_t tj = tokens[tok_off[b] + j];
+    int d = k - s + m;
+    code = (tj >> (2 * (k - 1 - d))) & 3u;
+    if (m == 0 && s < k) {
+      uint32_t prev = tokens[tok_off[b] + j - 1];
+      uint32_t lo = prev & ((1u << (2 * (k - s))) - 1u);
+      if (lo != (tj >> (2 * s))) atomicOr(err, kErrCorrupt);
+    }
+  }
+  seq[x] = "ACGT"[code];
+}
+
+void launch_detokenize(const uint16_t *d_tokens, const uint8_t *d_tail, const long long *d_base_off,
+                       const long long *d_tok_off, const int *d_sel, int n_blocks, long long n_bases, int s, int k,
+                       uint8_t *d_seq, int *d_err, cudaStream_t st) {
+  if (n_bases <= 0) return;
+  detokenize_kernel<<<(unsigned)((n_bases + 255) / 256), 256, 0, st>>>(d_tokens, d_tail, d_base_off, d_tok_off, d_sel,
+                                                                        n_blocks, n_bases, s, k, d_seq, d_err);
+}
+
+// ---------------------------------------------------------------------------
+// CRC-32 (reflected polynomial 0xEDB88320, zlib's).  The register update
+// c <- T[(c ^ byte) & 0xFF] ^ (c >> 8) is linear over GF(2), so the register
+// after a chunk D started from c equals R(D, 0) xor Z_|D| c, where Z_n is the
+// 32x32 matrix of n zero bytes.  Chunks are processed in parallel from 0 and
+// folded left with Z; the ragged end is finished byte by byte.
+
+constexpr int kCrcChunk = 4096;
+constexpr int kCrcFold = 256;  // threads of the folding kernel
+
+__device__ __forceinline__ uint32_t crc_table_entry(uint32_t i) {
+  uint32_t c = i;
+  for (int b = 0; b < 8; ++b) c = (c & 1u) ? (0xEDB88320u ^ (c >> 1)) : (c >> 1);
+  return c;
+}
+
+__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *mat, uint32_t v) {
+  uint32_t out = 0;
+  for (int i = 0; v; ++i, v >>= 1)
+    if (v & 1u) out ^= mat[i];
+  return out;
+}
+
+__global__ void crc_chunks_kernel(const uint8_t *__restrict__ data, long long n_chunks, uint32_t *__restrict__ regs) {
+  __shared__ uint32_t tab[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = crc_table_entry(i);
+  __syncthreads();
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= n_chunks) return;
+  const uint4 *p = reinterpret_cast<const uint4 *>(data + c * kCrcChunk);
+  uint32_t r = 0;
+  for (int q = 0; q < kCrcChunk / 16; ++q) {
+    uint4 w = p[q];
+    uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) r = tab[(r ^ (words[t] >> (8 * b))) & 0xFFu] ^ (r >> 8);
+  }
+  regs[c] = r;
+}
+
+// mats: [0] = Z_chunk, [1] = Z_(chunk*per), [2] = Z_(chunk*last_count); 32 words each
+__global__ void crc_fold_kernel(const uint8_t *__restrict__ head, int head_len, const uint32_t *__restrict__ regs,
+                                long long n_chunks, long long per, const uint32_t *__restrict__ mats,
+                                const uint8_t *__restrict__ rest, int rest_len, uint32_t *out) {
+  __shared__ uint32_t part[kCrcFold];
+  __shared__ uint32_t tab[256];
+  __shared__ uint32_t m[3][32];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = crc_table_entry(i);
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) m[i / 32][i % 32] = mats[i];
+  __syncthreads();
+  long long lo = threadIdx.x * per, hi = lo + per < n_chunks ? lo + per : n_chunks;
+  uint32_t x = 0;
+  for (long long c = lo; c < hi; ++c) x = regs[c] ^ gf2_apply(m[0], x);
+  part[threadIdx.x] = x;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  uint32_t acc = 0xFFFFFFFFu;
+  for (int i = 0; i < head_len; ++i) acc = tab[(acc ^ head[i]) & 0xFFu] ^ (acc >> 8);
+  for (int t = 0; t < kCrcFold; ++t) {
+    long long a = t * per, e = a + per < n_chunks ? a + per : n_chunks;
+    if (a >= e) break;
+    acc = part[t] ^ gf2_apply(e - a == per ? m[1] : m[2], acc);
+  }
+  for (int i = 0; i < rest_len; ++i) acc = tab[(acc ^ rest[i]) & 0xFFu] ^ (acc >> 8);
+  *out = ~acc;
+}
+
+namespace {
+// column i = image of basis vector e_i
+void gf2_mul(const uint32_t *a, const uint32_t *b, uint32_t *out) {  // out = a*b
+  for (int i = 0; i < 32; ++i) {
+    uint32_t v = b[i], r = 0;
+    for (int j = 0; v; ++j, v >>= 1)
+      if (v & 1u) r ^= a[j];
+    out[i] = r;
+  }
+}
+void zero_bytes_matrix(unsigned long long nbytes, uint32_t *out) {
+  uint32_t one[32], acc[32], tmp[32];
+  for (int i = 0; i < 32; ++i) {  // one zero byte: c -> T[c & 0xFF] ^ (c >> 8)
+    uint32_t c = 1u << i, t = c & 0xFFu, e = t;
+    for (int b = 0; b < 8; ++b) e = (e & 1u) ? (0xEDB88320u ^ (e >> 1)) : (e >> 1);
+    one[i] = e ^ (c >> 8);
+    acc[i] = 1u << i;
+    (void)t;
+  }
+  while (nbytes) {
+    if (nbytes & 1) {
+      gf2_mul(one, acc, tmp);
+      for (int i = 0; i < 32; ++i) acc[i] = tmp[i];
+    }
+    gf2_mul(one, one, tmp);
+    for (int i = 0; i < 32; ++i) one[i] = tmp[i];
+    nbytes >>= 1;
+  }
+  for (int i = 0; i < 32; ++i) out[i] = acc[i];
+}
+}  // namespace
+
+int crc32_device(const uint8_t *d_all, size_t n_all, uint32_t *crc, cudaStream_t st) {
+  size_t head = (16 - (reinterpret_cast<uintptr_t>(d_all) & 15)) & 15;
+  if (head > n_all) head = n_all;
+  const uint8_t *d_data = d_all + head;
+  size_t n = n_all - head;
+  long long n_chunks = (long long)(n / kCrcChunk);
+  long long per = (n_chunks + kCrcFold - 1) / kCrcFold;
+  if (per == 0) per = 1;
+  long long last = n_chunks - (n_chunks > 0 ? ((n_chunks - 1) / per) * per : 0);
+  uint32_t mats[96];
+  zero_bytes_matrix(kCrcChunk, mats);
+  zero_bytes_matrix((unsigned long long)kCrcChunk * per, mats + 32);
+  zero_bytes_matrix((unsigned long long)kCrcChunk * (last > 0 ? last : 1), mats + 64);
+  uint32_t *d_regs = nullptr, *d_mats = nullptr, *d_out = nullptr;
+  size_t bytes = sizeof(uint32_t) * (size_t)(n_chunks + 96 + 1);
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_regs, bytes, st));
+  d_mats = d_regs + n_chunks;
+  d_out = d_mats + 96;
+  cudaMemcpyAsync(d_mats, mats, sizeof(mats), cudaMemcpyHostToDevice, st);
+  if (n_chunks > 0)
+    crc_chunks_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, st>>>(d_data, n_chunks, d_regs);
+  int rest_len = (int)(n - (size_t)n_chunks * kCrcChunk);
+  crc_fold_kernel<<<1, kCrcFold, 0, st>>>(d_all, (int)head, d_regs, n_chunks, per, d_mats, d_data + (size_t)n_chunks * kCrcChunk,
+                                          rest_len, d_out);
+  uint32_t h = 0;
+  cudaMemcpyAsync(&h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_regs, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  *crc = h;
+  return PMKLC_OK;
+}
+
+}  // namespace pmklc

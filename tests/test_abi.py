@@ -1,0 +1,66 @@
+"""The C-ABI library loads on the CPU and exports every entry point of include/pmklc.h.
+
+No call here touches a GPU: only host-side entry points and argument checks that
+return before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_12805_gb300 as P
+    return P
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pmklc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pmklc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(P):
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(P.lib, name), name
+    assert set(names) == set(P.EXPORTED)
+
+
+def test_host_entry_points(P):
+    assert P.pmklc_abi_version() == 1
+    assert P.lib.pmklc_strerror(P.PMKLC_ECORRUPT) == b"corrupt compressed stream"
+    # parameter count: A*E + t*E*H + H + H*A + A
+    assert P.model_count(4, 32, 32, 128) == 256 * 32 + 1024 * 128 + 128 + 128 * 256 + 256 == 172416
+    assert P.model_count(6, 32, 64, 256) == 1708288
+    c = P.CModelCfg()
+    P.lib.pmklc_default_cfg(ctypes.byref(c), 2, 4, 32, 32, 128)
+    assert c.struct_size == ctypes.sizeof(P.CModelCfg) and (c.s, c.k, c.hid_d) == (2, 4, 128)
+
+
+def test_init_model_matches_oracle_bit_for_bit(P):
+    from oracle.model import Shape, init_params
+    for (k, E, t, H, seed) in [(3, 16, 16, 32, 42), (4, 32, 32, 128, 7), (1, 3, 5, 7, 0)]:
+        a = P.pmklc_init_model(k, E, t, H, seed)
+        b = init_params(Shape(4 ** k, E, t, H), seed)
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_bad_config_rejected_before_any_device_work(P):
+    cfg = P.ModelConfig(s=4, k=3)
+    with pytest.raises(P.PmklcError) as e:
+        P.pmklc_compress(b"ACGTACGT", [8], cfg)
+    assert e.value.rc == P.PMKLC_EINVAL
+    cfg = P.ModelConfig(s=1, k=9)
+    assert P.pmklc_compress_bound(8, [8], cfg) == 0
+    with pytest.raises(P.PmklcError) as e:
+        P.pmklc_decompress(b"XMKL" + bytes(100))
+    assert e.value.rc == P.PMKLC_ECORRUPT
