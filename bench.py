@@ -165,6 +165,31 @@ def run_reference(args, w, kw, sw):
 
 
 METRIC = "compress+decompress throughput (Eq. 4 THP) on 1 GB300"
+PROFILE_EVERY = 8  # every 8th global step's launches are bracketed with CUDA events
+SM_COUNT, FP32_LANES_PER_SM = 152, 128
+
+
+def roofline(prof: dict, pk: dict, pk_kind: str):
+    """Achieved vs peak of the kernel with the largest sampled time."""
+    if not prof:
+        return None, {}
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[name]
+    per = {k: {"launches": v["launches"], "ms_avg": v["ms"] / max(v["launches"], 1),
+               "share": v["ms"] / sum(x["ms"] for x in prof.values())} for k, v in prof.items()}
+    if d["flops"] > 0:
+        # FP32 FMA on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = d["flops"] / (d["ms"] / 1e3) / 1e12
+        r = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock", "traffic": None,
+             "work_per_launch": d["flops"] / d["launches"]}
+    else:
+        peak = pk["hbm_gbs"]
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+             "peak_source": f"{pk_kind} hbm_gbs", "traffic": None, "work_per_launch": d["bytes"] / d["launches"]}
+    return r, per
 
 
 def main():
@@ -218,6 +243,8 @@ def main():
     assert torch.equal(d_back, d_seq), "round trip failed"
 
     times, launches, clen, st1 = [], 0, 0, None
+    P.pmklc_profile_read()  # drop anything recorded during warm-up
+    P.pmklc_profile_enable(PROFILE_EVERY)
     with ClockSampler(dev) as clk:
         if world > 1:
             torch.distributed.barrier()
@@ -234,6 +261,8 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+    P.pmklc_profile_enable(0)
+    prof = P.pmklc_profile_read()
     ms = statistics.mean(times)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -269,6 +298,7 @@ def main():
                    "static_model": f"seeded random (init seed {STATIC_SEED})"},
         "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "peaks": pk_kind,
     }
+    line["roofline"], line["kernels"] = roofline(prof, pk, pk_kind)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, kw, sw)
     print(json.dumps(line))

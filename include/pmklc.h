@@ -224,6 +224,22 @@ typedef struct {
 } pmklc_stats;
 int pmklc_last_stats(pmklc_stats *st);
 
+/*
+ * Measurement support (not part of the paper's method): sampled per-kernel
+ * timing.  pmklc_profile_enable(every) brackets every kernel launch of every
+ * `every`-th global step (0 = off) with CUDA events on the launching stream,
+ * together with the launch's algorithmic work (FLOPs of its contraction or
+ * bytes it must move).  pmklc_profile_read() waits for the events, returns up
+ * to `max` per-kernel totals (*n = number of kernels seen) and clears them.
+ */
+typedef struct {
+  char name[32];
+  uint64_t launches;
+  double ms, flops, bytes;
+} pmklc_kernel_prof;
+int pmklc_profile_enable(int every);
+int pmklc_profile_read(pmklc_kernel_prof *out, int max, int *n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,11 @@ class CModelCfg(ctypes.Structure):
                 ("static_weights", ctypes.POINTER(ctypes.c_float))]
 
 
+class CKernelProf(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class CStats(ctypes.Structure):
     _fields_ = [("net_blocks", ctypes.c_uint64), ("count_blocks", ctypes.c_uint64),
                 ("global_steps", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
@@ -78,6 +83,8 @@ _sigs = {
     "pmklc_crc32": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
     "pmklc_init_model": ([_u32, _u32, _u32, _u32, _u64, _vp], _i),
+    "pmklc_profile_enable": ([_i], _i),
+    "pmklc_profile_read": ([ctypes.POINTER(CKernelProf), _i, ctypes.POINTER(_i)], _i),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(lib, _name)
@@ -280,6 +287,19 @@ def pmklc_last_stats() -> dict:
     st = CStats()
     _check(lib.pmklc_last_stats(ctypes.byref(st)), "pmklc_last_stats")
     return {name: getattr(st, name) for name, _ in CStats._fields_}
+
+
+def pmklc_profile_enable(every: int) -> None:
+    _check(lib.pmklc_profile_enable(every), "pmklc_profile_enable")
+
+
+def pmklc_profile_read() -> dict:
+    """Per-kernel totals over the sampled launches: {name: dict(launches, ms, flops, bytes)}."""
+    buf = (CKernelProf * 64)()
+    n = ctypes.c_int()
+    _check(lib.pmklc_profile_read(buf, 64, ctypes.byref(n)), "pmklc_profile_read")
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "flops": buf[i].flops,
+                                   "bytes": buf[i].bytes} for i in range(min(n.value, 64))}
 
 
 def pmklc_abi_version() -> int:

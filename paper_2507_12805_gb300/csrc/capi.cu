@@ -370,12 +370,19 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     bool any_pred = false, any_code = false;
+    StepWork w{0.0, 0.0};
     for (int g = 0; g < L.G; ++g) {
       int j = T - S.start[g];
       if (j < 0 || j >= L.steps[g]) continue;
-      if (j >= t_eff) any_pred = true;
+      if (j >= t_eff) {
+        any_pred = true;
+        int M = L.lane_off[g + 1] - L.lane_off[g];
+        w.pred_rows += j < L.base_len[g] ? M : (j == L.base_len[g] ? L.extra[g] : 0);
+        w.train_groups += 1;
+      }
       if (grp_mode[g] != kReplay) any_code = true;
     }
+    prof_step(T, w);
     if (any_pred) {
       launch_forward(R.p, T, st);
       R.launches += R.c.use_static ? 4 : 2;
@@ -389,6 +396,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches += 6;
     }
   }
+  prof_stop_sampling();
 }
 
 __global__ void gather_kernel(const unsigned long long *seg, int n_seg, const uint8_t *src0, const uint8_t *src1,

@@ -7,6 +7,29 @@
 
 namespace pmklc {
 
+// profile.cu ----------------------------------------------------------------
+// Work of the current global step, set by the step loop before its launches.
+struct StepWork {
+  double pred_rows;     // predicted (and trained) lane rows over all groups
+  double train_groups;  // groups that update their model
+};
+void prof_step(int T, const StepWork &w);
+void prof_stop_sampling();
+const StepWork &prof_work();
+// Brackets one kernel launch with events when the current step is sampled.
+class ProfScope {
+ public:
+  ProfScope(const char *name, double flops, double bytes, cudaStream_t st);
+  ~ProfScope();
+
+ private:
+  const char *name_;
+  double flops_, bytes_;
+  cudaStream_t st_;
+  bool active_;
+  void *a_ = nullptr;
+};
+
 // tokenize.cu ---------------------------------------------------------------
 // Checks every byte is one of A, C, G, T (sets kErrBadBase in *d_err otherwise).
 void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st);

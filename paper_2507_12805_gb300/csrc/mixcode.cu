@@ -369,6 +369,7 @@ __global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, con
 
 void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
   if (p.NL <= 0) return;
+  ProfScope ps("mix_cdf_code", 0, 0, st);
   mixcode_kernel<<<(p.NL * 32 + 255) / 256, 256, 0, st>>>(p, T);
 }
 

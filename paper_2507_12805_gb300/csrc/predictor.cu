@@ -321,30 +321,54 @@ __global__ void init_groups_kernel(Plan p, const float *init, float alpha0) {
 }  // namespace
 
 void launch_forward(const Plan &p, int T, cudaStream_t st) {
-  HiddenOp hd{{p, T}, 0};
-  run_ggemm(hd, p.Mmax, p.dm.H, p.G, st);
-  LogitsOp ld{{p, T}, 0};
-  run_ggemm(ld, p.Mmax, p.dm.A, p.G, st);
+  const double R = prof_work().pred_rows;
+  {
+    ProfScope ps("fwd_hidden_dm", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
+    run_ggemm(HiddenOp{{p, T}, 0}, p.Mmax, p.dm.H, p.G, st);
+  }
+  {
+    ProfScope ps("fwd_logits_dm", 2.0 * R * p.dm.H * p.dm.A, 0, st);
+    run_ggemm(LogitsOp{{p, T}, 0}, p.Mmax, p.dm.A, p.G, st);
+  }
   if (p.use_static) {
-    HiddenOp hs{{p, T}, 1};
-    run_ggemm(hs, p.Mmax, p.st.H, p.G, st);
-    LogitsOp ls{{p, T}, 1};
-    run_ggemm(ls, p.Mmax, p.st.A, p.G, st);
+    {
+      ProfScope ps("fwd_hidden_static", 2.0 * R * p.st.K1() * p.st.H, 0, st);
+      run_ggemm(HiddenOp{{p, T}, 1}, p.Mmax, p.st.H, p.G, st);
+    }
+    ProfScope ps("fwd_logits_static", 2.0 * R * p.st.H * p.st.A, 0, st);
+    run_ggemm(LogitsOp{{p, T}, 1}, p.Mmax, p.st.A, p.G, st);
   }
 }
 
 void launch_backward(const Plan &p, int T, cudaStream_t st) {
-  run_ggemm(DhOp{{p, T}}, p.Mmax, p.dm.H, p.G, st);
-  run_ggemm(DW2Op{{p, T}}, p.dm.H, p.dm.A, p.G, st);
-  run_ggemm(DW1Op{{p, T}}, p.dm.K1(), p.dm.H, p.G, st);
-  run_ggemm(DXOp{{p, T}}, p.Mmax, p.dm.K1(), p.G, st);
+  const double R = prof_work().pred_rows;
+  {
+    ProfScope ps("bwd_dh", 2.0 * R * p.dm.A * p.dm.H, 0, st);
+    run_ggemm(DhOp{{p, T}}, p.Mmax, p.dm.H, p.G, st);
+  }
+  {
+    ProfScope ps("bwd_dw2", 2.0 * R * p.dm.A * p.dm.H, 0, st);
+    run_ggemm(DW2Op{{p, T}}, p.dm.H, p.dm.A, p.G, st);
+  }
+  {
+    ProfScope ps("bwd_dw1", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
+    run_ggemm(DW1Op{{p, T}}, p.dm.K1(), p.dm.H, p.G, st);
+  }
+  {
+    ProfScope ps("bwd_dx_demb", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
+    run_ggemm(DXOp{{p, T}}, p.Mmax, p.dm.K1(), p.G, st);
+  }
   int cols = p.dm.A + p.dm.H + 1;
+  ProfScope ps("bias_grad", 0, 0, st);
   bias_grad_kernel<<<dim3((cols + 127) / 128, p.G), 128, 0, st>>>(p, T);
 }
 
 void launch_update(const Plan &p, int T, cudaStream_t st) {
   unsigned gx = (unsigned)((p.P + 1023) / 1024);
   if (gx > 64) gx = 64;
+  // Adam: read w, m, v, grad (16 B) and write w, m, v (12 B) per parameter of every training group
+  const double nemb = (double)p.dm.A * p.dm.E;
+  ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * 28.0 + nemb * 12.0), st);
   update_kernel<<<dim3(gx, p.G), 256, 0, st>>>(p, T);
 }
 
