@@ -120,7 +120,7 @@ def cpu_baseline(w, kw, sw, budget_s: float = 20.0):
     from oracle import codec as ocodec
     cfg = ocodec.Config(**{k: v for k, v in kw.items()})
     n = int(w.block_lens[0])
-    frac = 16
+    frac = 2
     sample = w.seq[: n // frac].tobytes()
     t0 = time.perf_counter()
     out = ocodec.compress(sample, [len(sample)], cfg, sw)
@@ -144,7 +144,7 @@ def run_reference(args, w, kw, sw):
     """--impl reference: the CPU oracle, timed on the host cores, same metric."""
     from oracle import codec as ocodec
     cfg = ocodec.Config(**kw)
-    n = int(w.block_lens[0]) // 16
+    n = int(w.block_lens[0]) // 2
     sample = w.seq[:n].tobytes()
     for _ in range(min(args.warmup, 1)):
         ocodec.decompress(ocodec.compress(sample, [n], cfg, sw), sw)

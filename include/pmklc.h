@@ -67,8 +67,9 @@ typedef struct {
   float alpha_init;            /* initial mixing weight alpha of Eq. (1) */
   uint32_t smp_mode;           /* PMKLC_SMP_* (§4.3, Fig. 5) */
   float smp_fraction;          /* f: share of a parent's steps before it hands over (paper: 0.05) */
-  uint32_t count_order;        /* order m of the count-model judge, 0..7 */
-  uint32_t fallback;           /* 1: code a block with the count model when that is smaller */
+  uint32_t count_order;        /* order m of the count model, 0..7 */
+  uint32_t fallback;           /* 0: network only; 1: per block, the count model when it is smaller
+                                  (needs lanes_per_block <= 1024); 2: count model only */
   uint64_t seed;               /* seed of the dynamic model's initialisation */
   const float *static_weights; /* host FP32 static parameters (layout above); NULL if unused */
 } pmklc_model_cfg;
@@ -87,6 +88,19 @@ size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid);
  * out: host array of pmklc_model_count(k, emb, ctx, hid) floats.
  */
 int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint64_t seed, float *out);
+
+/*
+ * Pre-training of a static predictor (paper §4, MSGD pre-training of the static
+ * public model, Fig. 2(a)) with the library's own forward/backward/optimiser
+ * kernels: the n training bases are tokenised with (cfg->s, cfg->k) and cut into
+ * cfg->lanes_per_block lanes; the dynamic-model loop of pmklc_compress runs over
+ * them `epochs` times without coding (each epoch continues from the previous
+ * state).  The trained FP32 parameters of shape (emb_d, ctx_d, hid_d), starting
+ * from pmklc_init_model(..., cfg->seed), go to out (host,
+ * pmklc_model_count(k, emb_d, ctx_d, hid_d) floats).  cfg->use_static must be 0.
+ */
+int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, uint32_t epochs, void *stream,
+                      float *out);
 
 /* Default configuration for (s,k) with dynamic model (E,t,H) = (emb, ctx, hid). */
 void pmklc_default_cfg(pmklc_model_cfg *cfg, uint32_t s, uint32_t k, uint32_t emb, uint32_t ctx,
@@ -199,18 +213,6 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
                      float *d_v, float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static,
                      const uint16_t *d_ctx, const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad,
                      float *d_dalpha, void *stream);
-
-/*
- * Order-m count model (judge/fallback; reading R15): codes each of n_blocks
- * blocks of ASCII bases (d_seq, block b at d_off[b], d_off has n_blocks+1
- * entries) as one stream into d_out + b*cap; lengths to d_len.
- * cap >= 2*block_len + 8 suffices.  EINVAL for m > 7 or a non-ACGT byte.
- */
-int pmklc_count_encode(const uint8_t *d_seq, const uint64_t *d_off, uint32_t n_blocks, uint32_t m,
-                       uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream);
-/* Decodes the streams of pmklc_count_encode back into ASCII bases at d_seq + d_off[b]. */
-int pmklc_count_decode(const uint8_t *d_in, const uint32_t *d_len, uint32_t cap, const uint64_t *d_off,
-                       uint32_t n_blocks, uint32_t m, uint8_t *d_seq, void *stream);
 
 /* CRC-32 (IEEE 802.3, reflected, as zlib) of n device bytes. */
 int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);

@@ -21,8 +21,10 @@ Readings where the paper is silent (each listed in the design doc):
            from the seeded init; CHAIN: parent g-1, start[g] = start[g-1] +
            ceil(f*L_{g-1}) (the paper's GPU-0 -> GPU-1 passing); TREE: parent
            g - 2^floor(log2 g), start[g] = (floor(log2 g)+1)*ceil(f*max L).
-  judge    with the count model enabled, a block is coded by it when that costs
-           fewer bytes than the network's lanes (flag in the container).
+  judge    fallback 1: the count model (countmodel.py) codes every block in the
+           same lanes alongside the network, and a block is stored with it when
+           that costs fewer bytes (flag in the container); fallback 2: the count
+           model alone (the method without the learned network); 0: network only.
 Parity: each step is pinned in its own module; the full run is pinned by the
 exact decode round trip.  The exact probability trajectory over a whole run is
 "parity unpinned" (online FP64 training amplifies any rounding difference); the
@@ -79,7 +81,7 @@ class Config:
     smp_mode: int = SMP_TREE
     smp_fraction: float = 0.05
     count_order: int = 6
-    fallback: bool = True
+    fallback: int = 1
     seed: int = 42
     variant: int = 0
 
@@ -219,10 +221,46 @@ class _Block:
     replay: bool = False         # tokens known; no coding (count-coded block)
     enc: list = field(default_factory=list)
     dec: list = field(default_factory=list)
+    count_encode: bool = False   # also code the block with the count model
+    count_decode: bool = False   # tokens come from the count model's lane decoders
+    cenc: list = field(default_factory=list)
+    cdec: list = field(default_factory=list)
+    table: object = None
 
 
 def _ctx(tokens, start, j, t):
     return tokens[start + j - t: start + j]
+
+
+def _count_step(cfg: Config, b: _Block, j: int):
+    """The count model's sub-steps of local step j for every live lane of block b (countmodel.py)."""
+    live = [r for r in range(len(b.lens)) if j < b.lens[r]]
+    if not live:
+        return
+    nb = cfg.k if j == 0 else cfg.s
+    got = {r: [] for r in live}
+    for q in range(nb):
+        xs = []
+        for r in live:
+            f, tot = b.table.freqs(r)
+            if b.count_encode:
+                x = countmodel.new_digits(b.tokens[b.starts[r] + j], j, cfg.s, cfg.k)[q]
+                b.cenc[r].encode(int(f[:x].sum()), int(f[x]), tot)
+            else:
+                x = b.cdec[r].decode(np.concatenate([[0], np.cumsum(f)]), tot)
+            xs.append(int(x))
+            got[r].append(int(x))
+        b.table.finish_substep(live, xs)
+    if b.count_decode:
+        for r in live:
+            v = 0
+            for x in got[r]:
+                v = v * 4 + x
+            pos = b.starts[r] + j
+            if j == 0:
+                b.tokens[pos] = v
+            else:  # keep the k - s digits shared with the previous token
+                b.tokens[pos] = (int(b.tokens[pos - 1]) % (4 ** (cfg.k - cfg.s))) * (4 ** cfg.s) + v
 
 
 def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
@@ -251,6 +289,10 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
             j = T - start[g]
             if j < 0 or j >= steps[g]:
                 continue
+            if b.count_encode or b.count_decode:
+                _count_step(cfg, b, j)
+            if cfg.fallback == 2:
+                continue  # count model only: no network
             st = groups[g]
             live = [r for r in range(len(b.lens)) if j < b.lens[r]]
             pred = [r for r in live if j >= t_eff]
@@ -332,27 +374,24 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> byte
     cblocks = [codes[offs[i]:offs[i + 1]] for i in range(len(block_lens))]
     blocks, tails = _prepare(cfg, cblocks)
     for b in blocks:
-        b.enc = [Encoder() for _ in b.lens]
+        b.enc = [Encoder() for _ in b.lens] if cfg.fallback != 2 else []
+        if cfg.fallback:
+            b.count_encode = True
+            b.cenc = [Encoder() for _ in b.lens]
+            b.table = countmodel.Table(cfg.count_order, len(b.lens))
     sw = None if static_w is None else np.asarray(static_w, dtype=np.float32).astype(np.float64)
     _run(cfg, blocks, sw, on_probs)
     out_hdr, payload = bytearray(), bytearray()
-    for b, tail, cb in zip(blocks, tails, cblocks):
-        lanes_bytes = [e.finish() for e in b.enc]
-        net_cost = sum(len(x) + len(varint(len(x))) for x in lanes_bytes) + len(pack_tail(tail))
-        use_count = False
-        if cfg.fallback:
-            cbytes = countmodel.encode(cb, cfg.count_order)
-            use_count = len(cbytes) + len(varint(len(cbytes))) < net_cost
-        out_hdr += varint(b.n)
-        if use_count:
-            out_hdr += bytes([1]) + varint(len(cbytes))
-            payload += cbytes
-        else:
-            out_hdr += bytes([0]) + pack_tail(tail)
-            for x in lanes_bytes:
-                out_hdr += varint(len(x))
-                payload += x
-    flags = (1 if cfg.use_static else 0) | (2 if cfg.fallback else 0)
+    cost = lambda streams: sum(len(x) + len(varint(len(x))) for x in streams)
+    for b, tail in zip(blocks, tails):
+        net = [e.finish() for e in b.enc]
+        cnt = [e.finish() for e in b.cenc]
+        use_count = cfg.fallback == 2 or (cfg.fallback == 1 and cost(cnt) < cost(net))
+        out_hdr += varint(b.n) + bytes([1 if use_count else 0]) + pack_tail(tail)
+        for x in (cnt if use_count else net):
+            out_hdr += varint(len(x))
+            payload += x
+    flags = (1 if cfg.use_static else 0) | (int(cfg.fallback) << 1)
     head = HEADER.pack(MAGIC, VERSION, cfg.s, cfg.k, flags, cfg.precision, cfg.optimizer, cfg.smp_mode,
                        cfg.count_order, cfg.emb_d, cfg.ctx_d, cfg.hid_d,
                        *((cfg.emb_s, cfg.ctx_s, cfg.hid_s) if cfg.use_static else (0, 0, 0)),
@@ -369,7 +408,7 @@ def parse_header(data: bytes):
     f = HEADER.unpack_from(data, 0)
     if f[0] != MAGIC or f[1] != VERSION:
         raise CorruptStream("bad magic or version")
-    cfg = Config(s=f[2], k=f[3], use_static=bool(f[4] & 1), fallback=bool(f[4] & 2), precision=f[5],
+    cfg = Config(s=f[2], k=f[3], use_static=bool(f[4] & 1), fallback=(f[4] >> 1) & 3, precision=f[5],
                  optimizer=f[6], smp_mode=f[7], count_order=f[8], emb_d=f[9], ctx_d=f[10], hid_d=f[11],
                  emb_s=f[12], ctx_s=f[13], hid_s=f[14], lanes_per_block=f[15], lr=f[16], alpha_init=f[17],
                  smp_fraction=f[18], seed=f[19], variant=f[24])
@@ -380,51 +419,49 @@ def decompress(data: bytes, static_w=None) -> bytes:
     cfg, meta = parse_header(data)
     if cfg.use_static and static_hash(static_w) != meta["static_hash"]:
         raise ModelMismatch("static weights differ from the ones used to compress")
+    if cfg.fallback > 2:
+        raise CorruptStream("bad fallback mode")
     pos = HEADER.size
     recs = []
     for _ in range(meta["n_blocks"]):
         n, pos = read_varint(data, pos)
+        if pos >= len(data):
+            raise CorruptStream("truncated block record")
         mode = data[pos]
         pos += 1
-        if mode == 0:
-            tl = tail_len(n, cfg.s, cfg.k)
-            nb = (tl * 2 + 7) // 8
-            tail = unpack_tail(data[pos:pos + nb], tl)
-            pos += nb
-            nl = len(lanes(n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0])
-            sizes = []
-            for _ in range(nl):
-                x, pos = read_varint(data, pos)
-                sizes.append(x)
-            recs.append((n, 0, tail, sizes))
-        elif mode == 1:
-            x, pos = read_varint(data, pos)
-            recs.append((n, 1, None, [x]))
-        else:
+        if mode > 1 or (mode == 0 and cfg.fallback == 2):
             raise CorruptStream("bad block mode")
-    blocks, cblocks = [], []
+        tl = tail_len(n, cfg.s, cfg.k)
+        nb = (tl * 2 + 7) // 8
+        if pos + nb > len(data):
+            raise CorruptStream("truncated tail")
+        tail = unpack_tail(data[pos:pos + nb], tl)
+        pos += nb
+        sizes = []
+        for _ in range(len(lanes(n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0])):
+            x, pos = read_varint(data, pos)
+            sizes.append(x)
+        recs.append((n, mode, tail, sizes))
+    blocks = []
     for n, mode, tail, sizes in recs:
         l = n_tokens(n, cfg.s, cfg.k)
         starts, lens = lanes(l, cfg.lanes_per_block)
+        b = _Block(n, np.zeros(l, dtype=np.int64), starts, lens)
+        streams = []
+        for x in sizes:
+            streams.append(Decoder(data[pos:pos + x]))
+            pos += x
         if mode == 1:
-            cb = countmodel.decode(data[pos:pos + sizes[0]], n, cfg.count_order)
-            pos += sizes[0]
-            b = _Block(n, tokenize(cb, cfg.s, cfg.k)[0], starts, lens, replay=True)
-            cblocks.append(cb)
+            b.count_decode, b.replay, b.cdec = True, True, streams
+            b.table = countmodel.Table(cfg.count_order, len(lens))
         else:
-            b = _Block(n, np.zeros(l, dtype=np.int64), starts, lens, decode=True)
-            for x in sizes:
-                b.dec.append(Decoder(data[pos:pos + x]))
-                pos += x
-            cblocks.append(tail)
+            b.decode, b.dec = True, streams
         blocks.append(b)
     if pos != len(data):
         raise CorruptStream("trailing or missing payload bytes")
     sw = None if static_w is None else np.asarray(static_w, dtype=np.float32).astype(np.float64)
     _run(cfg, blocks, sw)
-    out = []
-    for b, (n, mode, tail, _), cb in zip(blocks, recs, cblocks):
-        out.append(cb if mode == 1 else detokenize(b.tokens, tail, cfg.s, cfg.k))
+    out = [detokenize(b.tokens, tail, cfg.s, cfg.k) for b, (n, mode, tail, _) in zip(blocks, recs)]
     codes = np.concatenate(out) if out else np.zeros(0, dtype=np.uint8)
     seq = np.frombuffer(b"ACGT", dtype=np.uint8)[codes.astype(np.int64)].tobytes()
     if zlib.crc32(seq) != meta["crc"] or len(seq) != meta["n"]:

@@ -78,11 +78,10 @@ _sigs = {
     "pmklc_predict": ([_vp, _u32, _u32, _u32, _u32, _vp, _sz, _u32, _vp, _vp], _i),
     "pmklc_train_step": ([_cfgp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
                           _vp], _i),
-    "pmklc_count_encode": ([_vp, _vp, _u32, _u32, _vp, _u32, _vp, _vp], _i),
-    "pmklc_count_decode": ([_vp, _vp, _u32, _vp, _u32, _u32, _vp, _vp], _i),
     "pmklc_crc32": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
     "pmklc_init_model": ([_u32, _u32, _u32, _u32, _u64, _vp], _i),
+    "pmklc_train_model": ([_vp, _sz, _cfgp, _u32, _vp, _vp], _i),
     "pmklc_profile_enable": ([_i], _i),
     "pmklc_profile_read": ([ctypes.POINTER(CKernelProf), _i, ctypes.POINTER(_i)], _i),
 }
@@ -118,7 +117,7 @@ class ModelConfig:
     smp_mode: int = PMKLC_SMP_TREE
     smp_fraction: float = 0.05
     count_order: int = 6
-    fallback: bool = True
+    fallback: int = 1
     seed: int = 42
     static_weights: np.ndarray | None = field(default=None, repr=False)
 
@@ -266,16 +265,6 @@ def pmklc_train_step(cfg: ModelConfig, G: int, M: int, d_params, d_m, d_v, d_alp
                                 _ptr(d_P), _ptr(d_grad), _ptr(d_dalpha), _stream(stream)), "pmklc_train_step")
 
 
-def pmklc_count_encode(d_seq, d_off, n_blocks: int, m: int, d_out, cap: int, d_len, stream=None):
-    _check(lib.pmklc_count_encode(_ptr(d_seq), _ptr(d_off), n_blocks, m, _ptr(d_out), cap, _ptr(d_len),
-                                  _stream(stream)), "pmklc_count_encode")
-
-
-def pmklc_count_decode(d_in, d_len, cap: int, d_off, n_blocks: int, m: int, d_seq, stream=None):
-    _check(lib.pmklc_count_decode(_ptr(d_in), _ptr(d_len), cap, _ptr(d_off), n_blocks, m, _ptr(d_seq),
-                                  _stream(stream)), "pmklc_count_decode")
-
-
 def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:
     crc = ctypes.c_uint32()
     _check(lib.pmklc_crc32(_ptr(d_data), d_data.numel() if n is None else n, ctypes.byref(crc), _stream(stream)),
@@ -304,6 +293,16 @@ def pmklc_profile_read() -> dict:
 
 def pmklc_abi_version() -> int:
     return int(lib.pmklc_abi_version())
+
+
+def pmklc_train_model(seq, cfg: ModelConfig, epochs: int = 1, stream=None) -> np.ndarray:
+    """Pre-train a static predictor of shape (emb_d, ctx_d, hid_d) on host bases with the library's kernels."""
+    a = _host(seq)
+    out = np.zeros(model_count(cfg.k, cfg.emb_d, cfg.ctx_d, cfg.hid_d), dtype=np.float32)
+    c = cfg.to_c()
+    _check(lib.pmklc_train_model(a.ctypes.data_as(_vp), a.size, ctypes.byref(c), epochs, _stream(stream),
+                                 out.ctypes.data_as(_vp)), "pmklc_train_model")
+    return out
 
 
 def pmklc_init_model(k: int, E: int, t: int, H: int, seed: int) -> np.ndarray:

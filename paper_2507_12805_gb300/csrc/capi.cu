@@ -160,7 +160,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (c->optimizer > PMKLC_SGD || c->smp_mode > PMKLC_SMP_TREE || c->count_order > 7) return PMKLC_EINVAL;
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
-  if (c->lanes_per_block > (1u << 20)) return PMKLC_EINVAL;
+  if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
   o.s = (int)c->s;
   o.k = (int)c->k;
   o.use_static = c->use_static ? 1 : 0;
@@ -168,7 +168,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   o.optimizer = (int)c->optimizer;
   o.smp_mode = (int)c->smp_mode;
   o.count_order = (int)c->count_order;
-  o.fallback = c->fallback ? 1 : 0;
+  o.fallback = (int)c->fallback;
   int A = 1 << (2 * c->k);
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
   o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
@@ -283,7 +283,29 @@ struct Run {
   int *d_pairs = nullptr;
   std::vector<int> pair_off;  // T -> offset (pairs) into d_pairs
   uint64_t launches = 0;
+  bool net = true;            // run the network (false: count model only)
+  CountPlan cp{};
+  std::vector<int> cmode;     // per group: count model 0 off, 1 encode, 2 decode
 };
+
+// Count-model state of a run: one table per group, per-lane contexts and coder states.
+// buf/buf_off/buf_cap are set by the caller.
+int setup_count(Arena &ar, Run &R) {
+  const Layout &L = R.L;
+  CountPlan &c = R.cp;
+  c.m = R.c.count_order;
+  c.s = R.c.s;
+  c.k = R.c.k;
+  c.grp_cmode = ar.upload(R.cmode);
+  size_t tab = ((size_t)std::max(L.G, 1) << (2 * c.m)) * 4;
+  c.table = ar.alloc<uint32_t>(tab);
+  c.ctx = ar.alloc<uint32_t>(std::max(L.NL, 1));
+  c.enc = ar.alloc<EncState>(std::max(L.NL, 1));
+  c.dec = ar.alloc<DecState>(std::max(L.NL, 1));
+  if (ar.failed) return PMKLC_ENOMEM;
+  cudaMemsetAsync(c.table, 0, tab * sizeof(uint32_t), ar.st);
+  return PMKLC_OK;
+}
 
 // Allocates the model state, activations and tables of a run.  lane_buf / caps / enc / dec are set by the caller.
 int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *d_static) {
@@ -369,7 +391,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       launch_smp_copy(R.p, R.d_pairs + 2 * R.pair_off[T], np, st);
       R.launches++;
     }
-    bool any_pred = false, any_code = false;
+    bool any_pred = false, any_code = false, any_count = false;
     StepWork w{0.0, 0.0};
     for (int g = 0; g < L.G; ++g) {
       int j = T - S.start[g];
@@ -381,8 +403,14 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
         w.train_groups += 1;
       }
       if (grp_mode[g] != kReplay) any_code = true;
+      if (!R.cmode.empty() && R.cmode[g]) any_count = true;
     }
     prof_step(T, w);
+    if (any_count) {  // before the network: a count-decoded token is the network's target and context
+      launch_count_step(R.p, R.cp, T, st);
+      R.launches++;
+    }
+    if (!R.net) continue;
     if (any_pred) {
       launch_forward(R.p, T, st);
       R.launches += R.c.use_static ? 4 : 2;
@@ -393,7 +421,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
     }
     if (any_pred) {
       launch_backward_update(R.p, T, st);
-      R.launches += 6;
+      R.launches += 5;
     }
   }
   prof_stop_sampling();
@@ -486,41 +514,48 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   if (ar.failed) return PMKLC_ENOMEM;
   rc = setup_run(ar, R, grp_mode, d_static);
   if (rc) return rc;
-  launch_validate(d_seq, n, R.p.err, st);
-  launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
-  launch_tails(d_seq, d_base_off, d_tok_off, L.G, c.s, c.k, d_tail, st);
-  // count model (judge)
-  std::vector<uint32_t> cnt_len(L.G, 0);
-  uint8_t *d_cnt_buf = nullptr;
-  std::vector<unsigned long long> cnt_off(L.G + 1, 0);
-  uint32_t *d_cnt_len = nullptr;
-  if (c.fallback && L.G > 0) {
-    std::vector<uint32_t> cap(L.G);
-    for (int g = 0; g < L.G; ++g) {
-      cap[g] = (uint32_t)std::min<unsigned long long>(2ull * lens[g] + 8, 0xFFFFFFF0ull);
-      cnt_off[g + 1] = cnt_off[g] + ((cap[g] + 15) & ~15u);
-    }
-    d_cnt_buf = ar.alloc<uint8_t>(cnt_off[L.G]);
-    unsigned long long *d_cnt_off = ar.upload(cnt_off);
-    uint32_t *d_cap = ar.upload(cap);
-    d_cnt_len = ar.alloc<uint32_t>(L.G);
-    std::vector<unsigned long long> boff(L.base_off.begin(), L.base_off.end());
-    unsigned long long *d_boff = ar.upload(boff);
-    if (ar.failed) return PMKLC_ENOMEM;
-    rc = launch_count_encode(d_seq, d_boff, L.G, c.count_order, d_cnt_buf, d_cnt_off, d_cap, d_cnt_len, R.p.err, st);
-    if (rc) return rc;
-    R.launches++;
+  prof_step(0, StepWork{0.0, 0.0});
+  {
+    ProfScope ps("validate_tokenize", 0, 2.0 * n + 2.0 * L.n_tok, st);
+    launch_validate(d_seq, n, R.p.err, st);
+    launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
   }
-  launch_coder_init(R.p, 1, st);
+  launch_tails(d_seq, d_base_off, d_tok_off, L.G, c.s, c.k, d_tail, st);
+  // count model (judge / fallback): same lanes, coded inside the same steps
+  R.net = c.fallback != 2;
+  std::vector<unsigned long long> cnt_off(L.NL + 1, 0);
+  std::vector<uint32_t> cnt_len(L.NL, 0);
+  uint8_t *d_cnt_buf = nullptr;
+  uint32_t *d_cnt_len = nullptr;
+  if (c.fallback) {
+    if (L.Mmax > 1024) return PMKLC_EINVAL;
+    R.cmode.assign(L.G, 1);
+    std::vector<uint32_t> cap(L.NL);
+    for (int r = 0; r < L.NL; ++r) {  // at most 15 bits per base
+      cap[r] = (uint32_t)(2ull * (c.k + (unsigned long long)c.s * (L.lane_len[r] - 1)) + 8);
+      cnt_off[r + 1] = cnt_off[r] + ((cap[r] + 15) & ~15u);
+    }
+    if (setup_count(ar, R)) return PMKLC_ENOMEM;
+    d_cnt_buf = ar.alloc<uint8_t>(cnt_off[L.NL]);
+    R.cp.buf = d_cnt_buf;
+    R.cp.buf_off = ar.upload(cnt_off);
+    R.cp.buf_cap = ar.upload(cap);
+    d_cnt_len = ar.alloc<uint32_t>(L.NL);
+    if (ar.failed) return PMKLC_ENOMEM;
+    launch_count_init(R.p, R.cp, 1, st);
+  }
+  if (R.net) launch_coder_init(R.p, 1, st);
   run_steps(R, grp_mode, st);
-  launch_coder_finish(R.p, d_lane_len, st);
+  if (R.net) launch_coder_finish(R.p, d_lane_len, st);
+  if (c.fallback) launch_count_finish(R.p, R.cp, d_cnt_len, st);
   // results to the host
-  std::vector<uint32_t> lane_len(L.NL);
+  std::vector<uint32_t> lane_len(L.NL, 0);
   std::vector<uint8_t> tails((size_t)L.G * 8);
   int h_err = 0;
-  if (L.NL) cudaMemcpyAsync(lane_len.data(), d_lane_len, sizeof(uint32_t) * L.NL, cudaMemcpyDeviceToHost, st);
+  if (L.NL && R.net) cudaMemcpyAsync(lane_len.data(), d_lane_len, sizeof(uint32_t) * L.NL, cudaMemcpyDeviceToHost, st);
+  if (L.NL && d_cnt_len)
+    cudaMemcpyAsync(cnt_len.data(), d_cnt_len, sizeof(uint32_t) * L.NL, cudaMemcpyDeviceToHost, st);
   if (L.G) cudaMemcpyAsync(tails.data(), d_tail, tails.size(), cudaMemcpyDeviceToHost, st);
-  if (d_cnt_len) cudaMemcpyAsync(cnt_len.data(), d_cnt_len, sizeof(uint32_t) * L.G, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
   PMKLC_CUDA_TRY(cudaGetLastError());
@@ -532,7 +567,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   std::vector<uint8_t> H;
   H.reserve(kHeader + (size_t)L.G * 16 + (size_t)L.NL * 3);
   H.insert(H.end(), {'P', 'M', 'K', 'L'});
-  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback ? 2 : 0));
+  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback << 1));
   uint8_t b8[8] = {kVersion, (uint8_t)c.s, (uint8_t)c.k, flags, (uint8_t)c.precision, (uint8_t)c.optimizer,
                    (uint8_t)c.smp_mode, (uint8_t)c.count_order};
   H.insert(H.end(), b8, b8 + 8);
@@ -559,28 +594,24 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   for (int g = 0; g < L.G; ++g) {
     long long tl = tail_len_of((long long)lens[g], c.s, c.k);
     size_t tbytes = (size_t)(tl * 2 + 7) / 8;
-    size_t net_cost = tbytes;
-    for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) net_cost += lane_len[r] + varint_len(lane_len[r]);
-    bool use_cnt = c.fallback && (cnt_len[g] + varint_len(cnt_len[g]) < net_cost);
-    put_varint(H, lens[g]);
-    if (use_cnt) {
-      H.push_back(1);
-      put_varint(H, cnt_len[g]);
-      seg.insert(seg.end(), {cnt_off[g], pay, cnt_len[g], 1ull});
-      pay += cnt_len[g];
-      n_cnt++;
-    } else {
-      H.push_back(0);
-      uint8_t tb[2] = {0, 0};
-      for (long long i = 0; i < tl; ++i) tb[i >> 2] |= (uint8_t)(tails[(size_t)g * 8 + i] << (2 * (i & 3)));
-      H.insert(H.end(), tb, tb + tbytes);
-      for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) {
-        put_varint(H, lane_len[r]);
-        if (lane_len[r]) seg.insert(seg.end(), {lane_off[r], pay, lane_len[r], 0ull});
-        pay += lane_len[r];
-      }
-      n_net++;
+    size_t net_cost = 0, cnt_cost = 0;
+    for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) {
+      net_cost += lane_len[r] + varint_len(lane_len[r]);
+      cnt_cost += cnt_len[r] + varint_len(cnt_len[r]);
     }
+    bool use_cnt = c.fallback == 2 || (c.fallback == 1 && cnt_cost < net_cost);
+    put_varint(H, lens[g]);
+    H.push_back(use_cnt ? 1 : 0);
+    uint8_t tb[2] = {0, 0};
+    for (long long i = 0; i < tl; ++i) tb[i >> 2] |= (uint8_t)(tails[(size_t)g * 8 + i] << (2 * (i & 3)));
+    H.insert(H.end(), tb, tb + tbytes);
+    for (int r = L.lane_off[g]; r < L.lane_off[g + 1]; ++r) {
+      uint32_t ln = use_cnt ? cnt_len[r] : lane_len[r];
+      put_varint(H, ln);
+      if (ln) seg.insert(seg.end(), {use_cnt ? cnt_off[r] : lane_off[r], pay, ln, use_cnt ? 1ull : 0ull});
+      pay += ln;
+    }
+    (use_cnt ? n_cnt : n_net)++;
   }
   size_t total = H.size() + pay;
   if (total > out_cap) return PMKLC_ENOSPC;
@@ -623,12 +654,13 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.s = h[5];
   c.k = h[6];
   c.use_static = h[7] & 1;
-  c.fallback = (h[7] >> 1) & 1;
   c.precision = h[8];
   c.optimizer = h[9];
   c.smp_mode = h[10];
   c.count_order = h[11];
-  if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 || c.precision != 0)
+  c.fallback = (h[7] >> 1) & 3;
+  if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 || c.precision != 0 ||
+      c.fallback > 2)
     return PMKLC_ECORRUPT;
   int A = 1 << (2 * c.k);
   c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
@@ -665,27 +697,19 @@ int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
     if (pos >= len) return PMKLC_ECORRUPT;
     int mode = h[pos++];
     P.mode[b] = mode;
-    if (mode == 0) {
-      long long tl = tail_len_of((long long)nb, c.s, c.k);
-      size_t tbytes = (size_t)(tl * 2 + 7) / 8;
-      if (pos + tbytes > len) return PMKLC_ECORRUPT;
-      for (long long i = 0; i < tl; ++i) P.tails[(size_t)b * 8 + i] = (h[pos + (i >> 2)] >> (2 * (i & 3))) & 3;
-      pos += tbytes;
-      long long l = n_tokens_of((long long)nb, c.s, c.k);
-      long long Mb = std::min<long long>(c.lanes, l);
-      for (long long r = 0; r < Mb; ++r) {
-        uint64_t x;
-        if (!get_varint(h, len, pos, x)) return PMKLC_ECORRUPT;
-        P.sizes[b].push_back(x);
-        pay += x;
-      }
-    } else if (mode == 1) {
+    if (mode > 1 || (mode == 0 && c.fallback == 2)) return PMKLC_ECORRUPT;
+    long long tl = tail_len_of((long long)nb, c.s, c.k);
+    size_t tbytes = (size_t)(tl * 2 + 7) / 8;
+    if (pos + tbytes > len) return PMKLC_ECORRUPT;
+    for (long long i = 0; i < tl; ++i) P.tails[(size_t)b * 8 + i] = (h[pos + (i >> 2)] >> (2 * (i & 3))) & 3;
+    pos += tbytes;
+    long long l = n_tokens_of((long long)nb, c.s, c.k);
+    long long Mb = std::min<long long>(c.lanes, l);
+    for (long long r = 0; r < Mb; ++r) {
       uint64_t x;
-      if (!get_varint(h, len, pos, x)) return PMKLC_ECORRUPT;
+      if (!get_varint(h, len, pos, x) || x > 0xFFFFFFFFull) return PMKLC_ECORRUPT;
       P.sizes[b].push_back(x);
       pay += x;
-    } else {
-      return PMKLC_ECORRUPT;
     }
   }
   if (sum != P.n) return PMKLC_ECORRUPT;
@@ -734,37 +758,32 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
     cudaMemcpyAsync(d, static_weights, static_count * sizeof(float), cudaMemcpyHostToDevice, st);
     d_static = d;
   }
-  std::vector<int> grp_mode(L.G), net_sel(L.G), cnt_sel(L.G);
-  for (int g = 0; g < L.G; ++g) {
-    grp_mode[g] = P.mode[g] == 0 ? kDecode : kReplay;
-    net_sel[g] = P.mode[g] == 0;
-    cnt_sel[g] = P.mode[g] == 1;
-  }
-  // payload offsets (relative to the payload start)
-  const uint8_t *d_pay = d_in + P.header_len;
-  std::vector<unsigned long long> lane_off(std::max(L.NL, 1), 0), cnt_in_off(L.G, 0);
-  std::vector<uint32_t> lane_cap(std::max(L.NL, 1), 0), cnt_in_len(L.G, 0);
-  unsigned long long pos = 0;
+  std::vector<int> grp_mode(L.G), all_sel(L.G, 1);
+  R.net = c.fallback != 2;
+  R.cmode.assign(L.G, 0);
   bool any_cnt = false;
   for (int g = 0; g < L.G; ++g) {
-    if (P.mode[g] == 1) {
-      cnt_in_off[g] = pos;
-      cnt_in_len[g] = (uint32_t)P.sizes[g][0];
-      pos += P.sizes[g][0];
-      any_cnt = true;
-    } else {
-      for (int r = L.lane_off[g], q = 0; r < L.lane_off[g + 1]; ++r, ++q) {
-        lane_off[r] = pos;
-        lane_cap[r] = (uint32_t)P.sizes[g][q];
-        pos += P.sizes[g][q];
-      }
-    }
+    grp_mode[g] = P.mode[g] == 0 ? kDecode : kReplay;
+    R.cmode[g] = P.mode[g] == 1 ? 2 : 0;
+    any_cnt |= P.mode[g] == 1;
   }
+  if (any_cnt && L.Mmax > 1024) return PMKLC_ECORRUPT;
+  // every lane's payload (network or count model) at its offset from the payload start
+  const uint8_t *d_pay = d_in + P.header_len;
+  std::vector<unsigned long long> lane_off(std::max(L.NL, 1), 0);
+  std::vector<uint32_t> lane_cap(std::max(L.NL, 1), 0);
+  unsigned long long pos = 0;
+  for (int g = 0; g < L.G; ++g)
+    for (int r = L.lane_off[g], q = 0; r < L.lane_off[g + 1]; ++r, ++q) {
+      lane_off[r] = pos;
+      lane_cap[r] = (uint32_t)P.sizes[g][q];
+      pos += P.sizes[g][q];
+    }
   long long *d_base_off = ar.upload(L.base_off);
   long long *d_tok_off = ar.upload(L.tok_off);
   uint16_t *d_tokens = ar.alloc<uint16_t>(L.n_tok);
   uint8_t *d_tail = ar.upload(P.tails);
-  int *d_net_sel = ar.upload(net_sel);
+  int *d_all_sel = ar.upload(all_sel);
   R.p.lane_buf = const_cast<uint8_t *>(d_pay);
   R.p.lane_buf_off = ar.upload(lane_off);
   R.p.lane_buf_cap = ar.upload(lane_cap);
@@ -775,20 +794,15 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
   rc = setup_run(ar, R, grp_mode, d_static);
   if (rc) return rc;
   if (any_cnt) {
-    std::vector<unsigned long long> boff(L.base_off.begin(), L.base_off.end());
-    unsigned long long *d_boff = ar.upload(boff);
-    unsigned long long *d_cio = ar.upload(cnt_in_off);
-    uint32_t *d_cil = ar.upload(cnt_in_len);
-    int *d_cnt_sel = ar.upload(cnt_sel);
-    if (ar.failed) return PMKLC_ENOMEM;
-    rc = launch_count_decode(d_pay, d_cio, d_cil, d_boff, d_cnt_sel, L.G, c.count_order, d_seq, st);
-    if (rc) return rc;
-    // tokens of the count-coded blocks (the net blocks' tokens are overwritten while decoding)
-    launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
+    if (setup_count(ar, R)) return PMKLC_ENOMEM;
+    R.cp.buf = const_cast<uint8_t *>(d_pay);
+    R.cp.buf_off = R.p.lane_buf_off;
+    R.cp.buf_cap = R.p.lane_buf_cap;
+    launch_count_init(R.p, R.cp, 0, st);
   }
-  launch_coder_init(R.p, 0, st);
+  if (R.net) launch_coder_init(R.p, 0, st);
   run_steps(R, grp_mode, st);
-  launch_detokenize(d_tokens, d_tail, d_base_off, d_tok_off, d_net_sel, L.G, (long long)P.n, c.s, c.k, d_seq,
+  launch_detokenize(d_tokens, d_tail, d_base_off, d_tok_off, d_all_sel, L.G, (long long)P.n, c.s, c.k, d_seq,
                     R.p.err, st);
   int h_err = 0;
   cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -961,6 +975,57 @@ int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weigh
   return PMKLC_OK;
 }
 
+int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, uint32_t epochs, void *stream,
+                      float *out) {
+  Cfg c;
+  int rc = check_cfg(cfg, c);
+  if (rc) return rc;
+  if (c.use_static || !out || (n && !seq) || epochs < 1) return PMKLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Run R;
+  R.c = c;
+  // one group holding all training tokens; epochs are consecutive groups chained with f = 1
+  std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
+  make_layout(lens, c.s, c.k, c.lanes, R.L);
+  make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
+  Arena ar(st);
+  uint8_t *d_seq = ar.alloc<uint8_t>(n);
+  long long *d_base_off = ar.upload(R.L.base_off);
+  long long *d_tok_off = ar.upload(R.L.tok_off);
+  uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
+  if (ar.failed) return PMKLC_ENOMEM;
+  // every epoch reads the same bases: the blocks all start at offset 0
+  std::vector<long long> zero_off(R.L.G + 1, 0);
+  for (int g = 0; g <= R.L.G; ++g) zero_off[g] = (long long)n * std::min(g, 1);
+  long long *d_epoch_off = ar.upload(zero_off);
+  std::vector<long long> tok_one = {0, R.L.tok_off[1]};
+  long long *d_tok_one = ar.upload(tok_one);
+  std::vector<int> grp_mode(R.L.G, kReplay);
+  R.p.tokens = d_tokens;
+  R.p.lane_buf = nullptr;
+  std::vector<unsigned long long> zoff(std::max(R.L.NL, 1), 0);
+  std::vector<uint32_t> zcap(std::max(R.L.NL, 1), 0);
+  R.p.lane_buf_off = ar.upload(zoff);
+  R.p.lane_buf_cap = ar.upload(zcap);
+  if (ar.failed) return PMKLC_ENOMEM;
+  rc = setup_run(ar, R, grp_mode, nullptr);
+  if (rc) return rc;
+  cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
+  launch_validate(d_seq, n, R.p.err, st);
+  for (int g = 0; g < R.L.G; ++g)  // identical tokens for every epoch
+    launch_tokenize(d_seq, d_epoch_off, d_tok_one, 1, R.L.tok_off[1], c.s, c.k, d_tokens + R.L.tok_off[g], st);
+  (void)d_base_off;
+  (void)d_tok_off;
+  run_steps(R, grp_mode, st);
+  int h_err = 0;
+  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int last = R.L.G - 1;
+  cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  return h_err ? err_to_rc(h_err) : PMKLC_OK;
+}
+
 int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint64_t seed, float *out) {
   if (k < 1 || k > 8 || !emb || !ctx || !hid || !out) return PMKLC_EINVAL;
   Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
@@ -1092,8 +1157,8 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     launch_mixcode(R.p, T, st);
     launch_backward(R.p, T, st);
     if (d_grad) launch_export_grad(R.p, d_grad, st);
+    launch_update(R.p, T, st);  // also forms dalpha of every group
     if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
-    launch_update(R.p, T, st);
   }
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
   PMKLC_CUDA_TRY(cudaGetLastError());

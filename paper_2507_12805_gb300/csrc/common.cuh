@@ -71,6 +71,19 @@ struct Plan {
   int *err;
 };
 
+// The count model's per-run state (its lanes are the network's lanes).
+struct CountPlan {
+  int m, s, k;               // order, (s,k)
+  const int *grp_cmode;      // per group: 0 off, 1 encode, 2 decode
+  uint32_t *table;           // G x 4^m x 4 counts
+  uint32_t *ctx;             // per lane: context (previous m bases)
+  EncState *enc;
+  DecState *dec;
+  uint8_t *buf;              // per-lane payload bytes (output when encoding, input when decoding)
+  const unsigned long long *buf_off;
+  const uint32_t *buf_cap;   // capacity when encoding, payload length when decoding
+};
+
 __device__ __forceinline__ int row_local_step(const Plan &p, int T, int g) { return T - p.grp_start[g]; }
 
 // Number of lanes of group g still live at local step j (lanes differ by at most one token).

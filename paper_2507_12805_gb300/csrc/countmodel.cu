@@ -1,14 +1,21 @@
 // Adaptive order-m count model: the integer, exact judge and fallback coder of
 // a block (not a component of the paper's method; it guards the learned path,
-// which codes a block only when it spends fewer bytes).
+// which keeps a block only when it spends fewer bytes on it).
 //
-// One thread block per data block; the block's bases are coded one by one as a
-// single range-coded stream.  Context = the previous m base codes (oldest most
-// significant; positions before the block read as A).  Counts c[ctx][b] live in
-// shared memory as four uint16; freq_b = 2c_b + 1, total = 2 sum c + 4
-// (Krichevsky-Trofimov); after coding base x, c[ctx][x] += 1 and when it
-// reaches 1024 all four counts of the context are halved.  Thread 0 codes;
-// the other threads only clear the table.
+// It codes a block in the same lanes as the network, inside the same global
+// steps: lane r's base stream is the k digits of its first token followed by
+// the last s digits of each later token, so at local step j every live lane
+// codes the bases its j-th token adds (k at j = 0, else s), one sub-step per
+// base.  One table per block (counts c[ctx][b], ctx = previous m bases of the
+// lane's stream, positions before its start read as A) is shared by all its
+// lanes with a deterministic three-phase update per sub-step:
+//   A  every live lane reads its context's counts and codes freq_b = 2c_b+1 out of
+//      2 sum(c) + 4 (Krichevsky-Trofimov);
+//   B  every live lane adds 1 to c[ctx][base] (integer atomics: order-free);
+//   C  every used context whose largest count reached 1024 is halved once (by the
+//      first live lane that used it).
+// One thread block per data block and one thread per lane (<= 1024 lanes); table
+// reads bypass L1 (ld.global.cg) so a phase sees the previous phase's atomics.
 #include "internal.h"
 #include "rangecoder.cuh"
 
@@ -18,192 +25,138 @@ namespace {
 
 constexpr uint32_t kCountLimit = 1024;
 
-__device__ __forceinline__ uint32_t code_of(uint32_t c) { return ((c >> 1) & 3u) ^ ((c >> 2) & 1u); }
-
-__device__ __forceinline__ void ctx_counts(const unsigned long long *tab, uint32_t ctx, uint32_t c[4]) {
-  unsigned long long w = tab[ctx];
-  for (int b = 0; b < 4; ++b) c[b] = (uint32_t)(w >> (16 * b)) & 0xFFFFu;
-}
-
-__device__ __forceinline__ void ctx_update(unsigned long long *tab, uint32_t ctx, uint32_t c[4], uint32_t x) {
-  c[x] += 1;
-  if (c[x] >= kCountLimit)
-    for (int b = 0; b < 4; ++b) c[b] >>= 1;
-  tab[ctx] = (unsigned long long)c[0] | ((unsigned long long)c[1] << 16) | ((unsigned long long)c[2] << 32) |
-             ((unsigned long long)c[3] << 48);
-}
-
-__global__ void count_encode_kernel(const uint8_t *__restrict__ seq, const unsigned long long *__restrict__ off, int m,
-                                    uint8_t *__restrict__ out, const unsigned long long *__restrict__ out_off,
-                                    const uint32_t *__restrict__ cap, uint32_t *__restrict__ len, int *err) {
-  extern __shared__ unsigned long long tab[];
-  const int b = blockIdx.x;
-  const uint32_t nctx = 1u << (2 * m);
-  for (uint32_t i = threadIdx.x; i < nctx; i += blockDim.x) tab[i] = 0ull;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  const uint8_t *s = seq + off[b];
-  const unsigned long long n = off[b + 1] - off[b];
-  uint8_t *o = out + out_off[b];
-  const uint32_t cp = cap[b];
-  EncState st;
-  enc_init(st);
-  const uint32_t mask = nctx - 1;
-  uint32_t ctx = 0;
-  for (unsigned long long i = 0; i < n; ++i) {
-    uint32_t ch = s[i];
-    if (!(ch == 'A' || ch == 'C' || ch == 'G' || ch == 'T')) {
-      atomicOr(err, kErrBadBase);
-      ch = 'A';
-    }
-    uint32_t x = code_of(ch);
-    uint32_t c[4];
-    ctx_counts(tab, ctx, c);
-    uint32_t cum = 0;
-    for (uint32_t q = 0; q < x; ++q) cum += 2 * c[q] + 1;
-    uint32_t total = 2 * (c[0] + c[1] + c[2] + c[3]) + 4;
-    enc_code(st, cum, 2 * c[x] + 1, total, o, cp, err);
-    ctx_update(tab, ctx, c, x);
-    ctx = ((ctx << 2) | x) & mask;
+__global__ void __launch_bounds__(1024) count_step_kernel(Plan p, CountPlan c, int T) {
+  __shared__ uint32_t sctx[1024];
+  const int g = blockIdx.x;
+  const int j = T - p.grp_start[g];
+  if (j < 0 || j >= p.grp_steps[g]) return;
+  const int cmode = c.grp_cmode[g];
+  if (cmode == 0) return;
+  const int r0 = p.grp_lane_off[g], M = p.grp_lane_off[g + 1] - r0;
+  const int li = threadIdx.x;
+  const int r = r0 + li;
+  const bool live = li < M && j < p.lane_len[r];
+  const int nb = j == 0 ? c.k : c.s;
+  uint32_t *tab = c.table + ((size_t)g << (2 * c.m)) * 4;
+  const uint32_t mask = (1u << (2 * c.m)) - 1u;
+  long long tpos = live ? p.lane_tok[r] + j : 0;
+  uint32_t tok = (live && cmode == 1) ? p.tokens[tpos] : 0u;
+  uint32_t ctx = live ? c.ctx[r] : 0u, digits = 0;
+  EncState es;
+  DecState ds;
+  uint8_t *buf = nullptr;
+  uint32_t cap = 0;
+  if (live) {
+    buf = c.buf + c.buf_off[r];
+    cap = c.buf_cap[r];
+    if (cmode == 1)
+      es = c.enc[r];
+    else
+      ds = c.dec[r];
   }
-  len[b] = enc_finish(st, o, cp, err);
-}
-
-__global__ void count_decode_kernel(const uint8_t *__restrict__ in, const unsigned long long *__restrict__ in_off,
-                                    const uint32_t *__restrict__ in_len, const unsigned long long *__restrict__ off,
-                                    const int *__restrict__ sel, int m, uint8_t *__restrict__ seq) {
-  extern __shared__ unsigned long long tab[];
-  const int b = blockIdx.x;
-  if (!sel[b]) return;
-  const uint32_t nctx = 1u << (2 * m);
-  for (uint32_t i = threadIdx.x; i < nctx; i += blockDim.x) tab[i] = 0ull;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  const uint8_t *src = in + in_off[b];
-  const uint32_t ln = in_len[b];
-  uint8_t *dst = seq + off[b];
-  const unsigned long long n = off[b + 1] - off[b];
-  DecState st;
-  dec_init(st, src, ln);
-  const uint32_t mask = nctx - 1;
-  uint32_t ctx = 0;
-  for (unsigned long long i = 0; i < n; ++i) {
-    uint32_t c[4];
-    ctx_counts(tab, ctx, c);
-    uint32_t total = 2 * (c[0] + c[1] + c[2] + c[3]) + 4;
-    unsigned long long r;
-    uint32_t v = dec_target(st, total, r);
-    uint32_t x = 3, cum = 0;
-    for (uint32_t q = 0; q < 4; ++q) {
-      uint32_t f = 2 * c[q] + 1;
-      if (v < cum + f) {
-        x = q;
-        break;
+  for (int q = 0; q < nb; ++q) {
+    uint32_t x = 0;
+    if (li < 1024) sctx[li] = live ? ctx : 0xFFFFFFFFu;
+    if (live) {  // phase A
+      uint4 cw = __ldcg(reinterpret_cast<const uint4 *>(tab) + ctx);
+      uint32_t cnt[4] = {cw.x, cw.y, cw.z, cw.w};
+      uint32_t total = 2 * (cnt[0] + cnt[1] + cnt[2] + cnt[3]) + 4;
+      if (cmode == 1) {
+        x = (tok >> (2 * (nb - 1 - q))) & 3u;
+        uint32_t cum = 0;
+        for (uint32_t b = 0; b < x; ++b) cum += 2 * cnt[b] + 1;
+        enc_code(es, cum, 2 * cnt[x] + 1, total, buf, cap, p.err);
+      } else {
+        unsigned long long rr;
+        uint32_t v = dec_target(ds, total, rr);
+        uint32_t cum = 0;
+        x = 3;
+        for (uint32_t b = 0; b < 4; ++b) {
+          uint32_t f = 2 * cnt[b] + 1;
+          if (v < cum + f) {
+            x = b;
+            break;
+          }
+          cum += f;
+        }
+        if (x == 3) cum = total - (2 * cnt[3] + 1);
+        dec_consume(ds, rr, cum, 2 * cnt[x] + 1, buf, cap);
+        digits = (digits << 2) | x;
       }
-      cum += f;
     }
-    if (x == 3) cum = total - (2 * c[3] + 1);
-    dec_consume(st, r, cum, 2 * c[x] + 1, src, ln);
-    dst[i] = (uint8_t)"ACGT"[x];
-    ctx_update(tab, ctx, c, x);
-    ctx = ((ctx << 2) | x) & mask;
+    __syncthreads();
+    if (live) atomicAdd(tab + (size_t)ctx * 4 + x, 1u);  // phase B
+    __syncthreads();
+    if (live) {  // phase C
+      uint4 cw = __ldcg(reinterpret_cast<const uint4 *>(tab) + ctx);
+      uint32_t mx = max(max(cw.x, cw.y), max(cw.z, cw.w));
+      if (mx >= kCountLimit) {
+        bool first = true;
+        for (int o = 0; o < li && first; ++o) first = sctx[o] != ctx;
+        if (first) {
+          uint4 h = make_uint4(cw.x >> 1, cw.y >> 1, cw.z >> 1, cw.w >> 1);
+          __stcg(reinterpret_cast<uint4 *>(tab) + ctx, h);
+        }
+      }
+      ctx = ((ctx << 2) | x) & mask;
+    }
+    __syncthreads();
+  }
+  if (!live) return;
+  c.ctx[r] = ctx;
+  if (cmode == 1) {
+    c.enc[r] = es;
+  } else {
+    c.dec[r] = ds;
+    uint32_t t = digits;
+    if (j > 0) {  // keep the k - s digits shared with the previous token
+      uint32_t prev = p.tokens[tpos - 1];
+      t = ((prev & ((1u << (2 * (c.k - c.s))) - 1u)) << (2 * c.s)) | digits;
+    }
+    p.tokens[tpos] = (uint16_t)t;
   }
 }
 
-int smem_for(int m) { return (int)(sizeof(unsigned long long) << (2 * m)); }
+__global__ void count_init_kernel(Plan p, CountPlan c, int encode) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p.NL) return;
+  c.ctx[r] = 0;
+  if (encode) {
+    EncState s;
+    enc_init(s);
+    c.enc[r] = s;
+  } else {
+    DecState s;
+    dec_init(s, c.buf + c.buf_off[r], c.buf_cap[r]);
+    c.dec[r] = s;
+  }
+}
+
+__global__ void count_finish_kernel(Plan p, CountPlan c, uint32_t *lane_len) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p.NL) return;
+  EncState s = c.enc[r];
+  lane_len[r] = enc_finish(s, c.buf + c.buf_off[r], c.buf_cap[r], p.err);
+  c.enc[r] = s;
+}
 
 }  // namespace
 
-int launch_count_encode(const uint8_t *d_seq, const unsigned long long *d_off, int n_blocks, int m, uint8_t *d_out,
-                        const unsigned long long *d_out_off, const uint32_t *d_cap, uint32_t *d_len, int *d_err,
-                        cudaStream_t st) {
-  if (m < 0 || m > 7) return PMKLC_EINVAL;
-  if (n_blocks <= 0) return PMKLC_OK;
-  int smem = smem_for(m);
-  PMKLC_CUDA_TRY(cudaFuncSetAttribute(count_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  count_encode_kernel<<<n_blocks, 128, smem, st>>>(d_seq, d_off, m, d_out, d_out_off, d_cap, d_len, d_err);
-  PMKLC_CUDA_TRY(cudaGetLastError());
-  return PMKLC_OK;
+void launch_count_step(const Plan &p, const CountPlan &c, int T, cudaStream_t st) {
+  if (p.G <= 0 || p.Mmax <= 0) return;
+  int threads = ((p.Mmax + 31) / 32) * 32;
+  ProfScope ps("count_step", 0, 0, st);
+  count_step_kernel<<<p.G, threads, 0, st>>>(p, c, T);
 }
 
-int launch_count_decode(const uint8_t *d_in, const unsigned long long *d_in_off, const uint32_t *d_len,
-                        const unsigned long long *d_off, const int *d_sel, int n_blocks, int m, uint8_t *d_seq,
-                        cudaStream_t st) {
-  if (m < 0 || m > 7) return PMKLC_EINVAL;
-  if (n_blocks <= 0) return PMKLC_OK;
-  int smem = smem_for(m);
-  PMKLC_CUDA_TRY(cudaFuncSetAttribute(count_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  count_decode_kernel<<<n_blocks, 128, smem, st>>>(d_in, d_in_off, d_len, d_off, d_sel, m, d_seq);
-  PMKLC_CUDA_TRY(cudaGetLastError());
-  return PMKLC_OK;
+void launch_count_init(const Plan &p, const CountPlan &c, int encode, cudaStream_t st) {
+  if (p.NL <= 0) return;
+  count_init_kernel<<<(p.NL + 127) / 128, 128, 0, st>>>(p, c, encode);
+}
+
+void launch_count_finish(const Plan &p, const CountPlan &c, uint32_t *d_lane_len, cudaStream_t st) {
+  if (p.NL <= 0) return;
+  count_finish_kernel<<<(p.NL + 127) / 128, 128, 0, st>>>(p, c, d_lane_len);
 }
 
 }  // namespace pmklc
-
-using namespace pmklc;
-
-extern "C" int pmklc_count_encode(const uint8_t *d_seq, const uint64_t *d_off, uint32_t n_blocks, uint32_t m,
-                                  uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream) {
-  if (m > 7 || (n_blocks && (!d_off || !d_out || !d_len))) return PMKLC_EINVAL;
-  if (n_blocks == 0) return PMKLC_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  unsigned long long *d_oo = nullptr;
-  uint32_t *d_cap = nullptr;
-  int *d_err = nullptr;
-  size_t bytes = sizeof(unsigned long long) * n_blocks + sizeof(uint32_t) * n_blocks + sizeof(int) + 16;
-  char *blob = nullptr;
-  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&blob, bytes, st));
-  d_oo = (unsigned long long *)blob;
-  d_cap = (uint32_t *)(blob + sizeof(unsigned long long) * n_blocks);
-  d_err = (int *)(blob + sizeof(unsigned long long) * n_blocks + sizeof(uint32_t) * n_blocks);
-  unsigned long long *h_oo = new unsigned long long[n_blocks];
-  uint32_t *h_cap = new uint32_t[n_blocks];
-  for (uint32_t b = 0; b < n_blocks; ++b) {
-    h_oo[b] = (unsigned long long)b * cap;
-    h_cap[b] = cap;
-  }
-  cudaMemcpyAsync(d_oo, h_oo, sizeof(unsigned long long) * n_blocks, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_cap, h_cap, sizeof(uint32_t) * n_blocks, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(d_err, 0, sizeof(int), st);
-  int rc = launch_count_encode(d_seq, (const unsigned long long *)d_off, (int)n_blocks, (int)m, d_out, d_oo, d_cap,
-                               d_len, d_err, st);
-  int h_err = 0;
-  cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  cudaFreeAsync(blob, st);
-  delete[] h_oo;
-  delete[] h_cap;
-  if (rc) return rc;
-  if (e != cudaSuccess) return PMKLC_ECUDA;
-  if (h_err & kErrBadBase) return PMKLC_EINVAL;
-  if (h_err & kErrOverflow) return PMKLC_ENOSPC;
-  return PMKLC_OK;
-}
-
-extern "C" int pmklc_count_decode(const uint8_t *d_in, const uint32_t *d_len, uint32_t cap, const uint64_t *d_off,
-                                  uint32_t n_blocks, uint32_t m, uint8_t *d_seq, void *stream) {
-  if (m > 7 || (n_blocks && (!d_in || !d_len || !d_off || !d_seq))) return PMKLC_EINVAL;
-  if (n_blocks == 0) return PMKLC_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  char *blob = nullptr;
-  size_t bytes = sizeof(unsigned long long) * n_blocks + sizeof(int) * n_blocks;
-  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&blob, bytes, st));
-  unsigned long long *d_io = (unsigned long long *)blob;
-  int *d_sel = (int *)(blob + sizeof(unsigned long long) * n_blocks);
-  unsigned long long *h_io = new unsigned long long[n_blocks];
-  int *h_sel = new int[n_blocks];
-  for (uint32_t b = 0; b < n_blocks; ++b) {
-    h_io[b] = (unsigned long long)b * cap;
-    h_sel[b] = 1;
-  }
-  cudaMemcpyAsync(d_io, h_io, sizeof(unsigned long long) * n_blocks, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_sel, h_sel, sizeof(int) * n_blocks, cudaMemcpyHostToDevice, st);
-  int rc = launch_count_decode(d_in, d_io, d_len, (const unsigned long long *)d_off, d_sel, (int)n_blocks, (int)m,
-                               d_seq, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  cudaFreeAsync(blob, st);
-  delete[] h_io;
-  delete[] h_sel;
-  if (rc) return rc;
-  return e == cudaSuccess ? PMKLC_OK : PMKLC_ECUDA;
-}

@@ -48,12 +48,9 @@ void launch_detokenize(const uint16_t *d_tokens, const uint8_t *d_tail, const lo
 int crc32_device(const uint8_t *d_data, size_t n, uint32_t *crc, cudaStream_t st);
 
 // countmodel.cu --------------------------------------------------------------
-int launch_count_encode(const uint8_t *d_seq, const unsigned long long *d_off, int n_blocks, int m, uint8_t *d_out,
-                        const unsigned long long *d_out_off, const uint32_t *d_cap, uint32_t *d_len, int *d_err,
-                        cudaStream_t st);
-int launch_count_decode(const uint8_t *d_in, const unsigned long long *d_in_off, const uint32_t *d_len,
-                        const unsigned long long *d_off, const int *d_sel, int n_blocks, int m, uint8_t *d_seq,
-                        cudaStream_t st);
+void launch_count_step(const Plan &p, const CountPlan &c, int T, cudaStream_t st);
+void launch_count_init(const Plan &p, const CountPlan &c, int encode, cudaStream_t st);
+void launch_count_finish(const Plan &p, const CountPlan &c, uint32_t *d_lane_len, cudaStream_t st);
 
 // mixcode.cu -----------------------------------------------------------------
 void launch_mixcode(const Plan &p, int T, cudaStream_t st);

@@ -19,56 +19,149 @@ namespace pmklc {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BM = 64, BN = 64, BK = 32;
+__device__ const float kOneF = 1.0f;  // the "ones" entry that turns a bias gradient into a GEMM row
 
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Register fragments of one K-chunk (each of the 256 threads holds two float4).
+struct Frag {
+  float4 v[2];
+};
+
+// Operand with k contiguous (A rows, or B^T rows): element e = tid + 256q covers row e/8 and
+// k = 4*(e%8) .. +3 of the chunk.  ptr(rl, r, k) -> address of element (r, k), nullptr = 0.
+template <class F>
+__device__ __forceinline__ void fetch_kc(Frag &f, int r0, int k0, int R, int K, F ptr, bool vec_ok = true) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + 256 * q, rl = e >> 3, r = r0 + rl, k = k0 + (e & 7) * 4;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < R && k < K) {
+      const float *p = ptr(rl, r, k);
+      if (p) {
+        if (vec_ok && k + 3 < K && aligned16(p)) {
+          float4 v = *reinterpret_cast<const float4 *>(p);
+          t[0] = v.x, t[1] = v.y, t[2] = v.z, t[3] = v.w;
+        } else {
+          for (int i = 0; i < 4; ++i)
+            if (k + i < K) {
+              const float *pi = ptr(rl, r, k + i);
+              t[i] = pi ? *pi : 0.f;
+            }
+        }
+      }
+    }
+    f.v[q] = make_float4(t[0], t[1], t[2], t[3]);
+  }
+}
+template <int W>
+__device__ __forceinline__ void store_kc(float (*S)[W], const Frag &f) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + 256 * q, rl = e >> 3, kk = (e & 7) * 4;
+    S[kk][rl] = f.v[q].x;
+    S[kk + 1][rl] = f.v[q].y;
+    S[kk + 2][rl] = f.v[q].z;
+    S[kk + 3][rl] = f.v[q].w;
+  }
+}
+
+// Operand with its column index contiguous: element e covers k = e/16 and c = 4*(e%16) .. +3.
+// Vector loads only when c + 3 < Cv (the extent that is contiguous in memory).
+template <class F>
+__device__ __forceinline__ void fetch_cc(Frag &f, int c0, int k0, int C, int Cv, int K, F ptr) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + 256 * q, kl = e >> 4, k = k0 + kl, c = c0 + (e & 15) * 4;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k < K && c < C) {
+      const float *p = ptr(kl, k, c);
+      if (c + 3 < Cv && p && aligned16(p)) {
+        float4 v = *reinterpret_cast<const float4 *>(p);
+        t[0] = v.x, t[1] = v.y, t[2] = v.z, t[3] = v.w;
+      } else {
+        for (int i = 0; i < 4; ++i)
+          if (c + i < C) {
+            const float *pi = ptr(kl, k, c + i);
+            t[i] = pi ? *pi : 0.f;
+          }
+      }
+    }
+    f.v[q] = make_float4(t[0], t[1], t[2], t[3]);
+  }
+}
+template <int W>
+__device__ __forceinline__ void store_cc(float (*S)[W], const Frag &f) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + 256 * q, kl = e >> 4, cc = (e & 15) * 4;
+    *reinterpret_cast<float4 *>(&S[kl][cc]) = f.v[q];
+  }
+}
+
+// Shared engine: C[M x N] = sum_k A[m][k] B[k][n] for group g = blockIdx.z, tiles 64 x 64,
+// K-chunks of 32 staged in shared memory as As[k][m], Bs[k][n]; the next chunk is fetched into
+// registers while the current one is multiplied.  Each thread owns a 4x4 block of C and
+// accumulates its K products in increasing k with fmaf (the order never depends on the tile,
+// so every output equals the same sequential sum whatever the launch shape).
 template <class Op>
 __global__ void __launch_bounds__(256) ggemm_kernel(Op op) {
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ long long mbase[BM];
   const int g = blockIdx.z;
   if (!op.active(g)) return;
   const int M = op.M(g), N = op.N(), K = op.K(g);
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (m0 >= M || n0 >= N) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < BM) mbase[tid] = m0 + tid < M ? op.mrow_base(g, m0 + tid) : -1;
+  __syncthreads();
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  Frag fa, fb;
+  op.fetch_a(mbase, g, m0, 0, M, K, fa);
+  op.fetch_b(g, 0, n0, K, N, fb);
   for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-    for (int q = 0; q < (BM * BK) / 256; ++q) {
-      int e = tid + q * 256, kk = e % BK, rr = e / BK;
-      As[kk][rr] = (m0 + rr < M && k0 + kk < K) ? op.a(g, m0 + rr, k0 + kk) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < (BK * BN) / 256; ++q) {
-      int e = tid + q * 256, cc = e % BN, kk = e / BN;
-      Bs[kk][cc] = (k0 + kk < K && n0 + cc < N) ? op.b(g, k0 + kk, n0 + cc) : 0.f;
-    }
+    if (Op::kAKc)
+      store_kc(As, fa);
+    else
+      store_cc(As, fa);
+    if (Op::kBKc)
+      store_kc(Bs, fb);
+    else
+      store_cc(Bs, fb);
     __syncthreads();
+    if (k0 + BK < K) {
+      op.fetch_a(mbase, g, m0, k0 + BK, M, K, fa);
+      op.fetch_b(g, k0 + BK, n0, K, N, fb);
+    }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+      float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+      float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    int r = m0 + ty * 4 + i;
+    if (r >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int r = m0 + ty * 4 + i, c = n0 + tx * 4 + j;
-      if (r < M && c < N) op.epi(g, r, c, acc[i][j]);
+      int c = n0 + tx * 4 + j;
+      if (c < N) op.epi(mbase, g, r, ty * 4 + i, c, acc[i][j]);
     }
+  }
 }
 
 template <class Op>
@@ -84,33 +177,49 @@ struct RowBase {
   int T;
   __device__ int nrows(int g) const { return p.grp_lane_off[g + 1] - p.grp_lane_off[g]; }
   __device__ int row(int g, int r) const { return p.grp_lane_off[g] + r; }
-  __device__ bool pred(int g, int row) const { return row_pred(p, T, row, g); }
   __device__ bool active(int g) const { return group_trains(p, T, g); }
-  // token at context position pos (0 = oldest) of a model with context t
-  __device__ int ctx_token(int g, int row, int pos, int t) const {
-    int j = T - p.grp_start[g];
-    return p.tokens[p.lane_tok[row] + j - t + pos];
+  // absolute index of the row's target token (its context ends just before), or -1 if the
+  // row does not predict at this step
+  __device__ long long target_pos(int g, int r) const {
+    int rw = row(g, r);
+    if (!row_pred(p, T, rw, g)) return -1;
+    return p.lane_tok[rw] + (T - p.grp_start[g]);
+  }
+  __device__ long long mrow_base(int g, int r) const { return target_pos(g, r); }
+  // pointer to X[row][k] = Emb[token at context position k / E][k % E]
+  __device__ const float *xptr(const float *w, const Dims &D, long long tpos, int k) const {
+    int pos = k / D.E, e = k - pos * D.E;
+    int tok = p.tokens[tpos - D.t + pos];
+    return w + D.off_emb() + (size_t)tok * D.E + e;
   }
 };
 
 // h = relu(X W1 + b1) for the dynamic (stat = 0) or static (stat = 1) model
 struct HiddenOp : RowBase {
+  static constexpr bool kAKc = true, kBKc = false;
   int stat;
   __device__ const float *w(int g) const { return stat ? p.static_params : p.params + (size_t)g * p.P; }
   __device__ const Dims &d() const { return stat ? p.st : p.dm; }
   __device__ int M(int g) const { return nrows(g); }
   __device__ int N() const { return d().H; }
   __device__ int K(int) const { return d().K1(); }
-  __device__ float a(int g, int r, int k) const {
-    int rw = row(g, r);
-    if (!pred(g, rw)) return 0.f;
+  __device__ void fetch_a(const long long *mb, int g, int m0, int k0, int M, int K, Frag &f) const {
+    const float *wg = w(g);
     const Dims &D = d();
-    int pos = k / D.E, e = k - pos * D.E;
-    int tok = ctx_token(g, rw, pos, D.t);
-    return w(g)[D.off_emb() + (size_t)tok * D.E + e];
+    // four consecutive k lie in one embedding row only when E is a multiple of 4
+    fetch_kc(
+        f, m0, k0, M, K,
+        [&](int rl, int, int k) -> const float * {
+          long long b = mb[rl];
+          return b < 0 ? nullptr : xptr(wg, D, b, k);
+        },
+        D.E % 4 == 0);
   }
-  __device__ float b(int g, int k, int n) const { return w(g)[d().off_w1() + (size_t)k * d().H + n]; }
-  __device__ void epi(int g, int r, int n, float acc) const {
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    const float *w1 = w(g) + d().off_w1();
+    fetch_cc(f, n0, k0, N, N, K, [&](int, int k, int c) -> const float * { return w1 + (size_t)k * N + c; });
+  }
+  __device__ void epi(const long long *, int g, int r, int, int n, float acc) const {
     float h = fmaxf(acc + w(g)[d().off_b1() + n], 0.f);
     (stat ? p.hs : p.hd)[(size_t)row(g, r) * d().H + n] = h;
   }
@@ -118,123 +227,132 @@ struct HiddenOp : RowBase {
 
 // L = h W2 + b2
 struct LogitsOp : RowBase {
+  static constexpr bool kAKc = true, kBKc = false;
   int stat;
   __device__ const float *w(int g) const { return stat ? p.static_params : p.params + (size_t)g * p.P; }
   __device__ const Dims &d() const { return stat ? p.st : p.dm; }
   __device__ int M(int g) const { return nrows(g); }
   __device__ int N() const { return d().A; }
   __device__ int K(int) const { return d().H; }
-  __device__ float a(int g, int r, int k) const {
-    return (stat ? p.hs : p.hd)[(size_t)row(g, r) * d().H + k];
+  __device__ void fetch_a(const long long *mb, int g, int m0, int k0, int M, int K, Frag &f) const {
+    const float *h = stat ? p.hs : p.hd;
+    fetch_kc(f, m0, k0, M, K, [&](int rl, int m, int k) -> const float * {
+      return mb[rl] < 0 ? nullptr : h + (size_t)row(g, m) * K + k;
+    });
   }
-  __device__ float b(int g, int k, int n) const { return w(g)[d().off_w2() + (size_t)k * d().A + n]; }
-  __device__ void epi(int g, int r, int n, float acc) const {
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    const float *w2 = w(g) + d().off_w2();
+    fetch_cc(f, n0, k0, N, N, K, [&](int, int k, int c) -> const float * { return w2 + (size_t)k * N + c; });
+  }
+  __device__ void epi(const long long *mb, int g, int r, int rl, int n, float acc) const {
+    if (mb[rl] < 0) return;
     (stat ? p.zu : p.zm)[(size_t)row(g, r) * d().A + n] = acc + w(g)[d().off_b2() + n];
   }
 };
 
 // dh = (dz W2^T) * [h > 0]
 struct DhOp : RowBase {
+  static constexpr bool kAKc = true, kBKc = true;
   __device__ int M(int g) const { return nrows(g); }
   __device__ int N() const { return p.dm.H; }
   __device__ int K(int) const { return p.dm.A; }
-  __device__ float a(int g, int r, int k) const {
-    int rw = row(g, r);
-    return pred(g, rw) ? p.dz[(size_t)rw * p.dm.A + k] : 0.f;
+  __device__ void fetch_a(const long long *mb, int g, int m0, int k0, int M, int K, Frag &f) const {
+    fetch_kc(f, m0, k0, M, K, [&](int rl, int m, int k) -> const float * {
+      return mb[rl] < 0 ? nullptr : p.dz + (size_t)row(g, m) * K + k;
+    });
   }
-  __device__ float b(int g, int k, int n) const {
-    return p.params[(size_t)g * p.P + p.dm.off_w2() + (size_t)n * p.dm.A + k];
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    const float *w2 = p.params + (size_t)g * p.P + p.dm.off_w2();  // B[k][n] = W2[n][k]
+    fetch_kc(f, n0, k0, N, K, [&](int, int n, int k) -> const float * { return w2 + (size_t)n * K + k; });
   }
-  __device__ void epi(int g, int r, int n, float acc) const {
+  __device__ void epi(const long long *mb, int g, int r, int rl, int n, float acc) const {
     size_t i = (size_t)row(g, r) * p.dm.H + n;
-    p.dh[i] = p.hd[i] > 0.f ? acc : 0.f;
+    p.dh[i] = (mb[rl] >= 0 && p.hd[i] > 0.f) ? acc : 0.f;
   }
 };
 
-// dW2 = h^T dz   (K = rows of the group)
+// [dW2; db2] = [h 1]^T dz   (K = rows of the group; row H of the result is the bias gradient)
 struct DW2Op : RowBase {
-  __device__ int M(int) const { return p.dm.H; }
+  static constexpr bool kAKc = false, kBKc = false;
+  __device__ int M(int) const { return p.dm.H + 1; }
   __device__ int N() const { return p.dm.A; }
   __device__ int K(int g) const { return nrows(g); }
-  __device__ float a(int g, int i, int r) const {
-    int rw = row(g, r);
-    return pred(g, rw) ? p.hd[(size_t)rw * p.dm.H + i] : 0.f;
+  __device__ void fetch_a(const long long *, int g, int m0, int k0, int M, int K, Frag &f) const {
+    const int H = p.dm.H;
+    fetch_cc(f, m0, k0, M, H, K, [&](int, int r, int i) -> const float * {
+      if (target_pos(g, r) < 0) return nullptr;
+      return i < H ? p.hd + (size_t)row(g, r) * H + i : &kOneF;
+    });
   }
-  __device__ float b(int g, int r, int n) const {
-    int rw = row(g, r);
-    return pred(g, rw) ? p.dz[(size_t)rw * p.dm.A + n] : 0.f;
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    fetch_cc(f, n0, k0, N, N, K, [&](int, int r, int c) -> const float * {
+      return target_pos(g, r) < 0 ? nullptr : p.dz + (size_t)row(g, r) * N + c;
+    });
   }
-  __device__ void epi(int g, int i, int n, float acc) const {
-    p.grad[(size_t)g * p.P + p.dm.off_w2() + (size_t)i * p.dm.A + n] = acc;
+  __device__ void epi(const long long *, int g, int i, int, int n, float acc) const {
+    float *gr = p.grad + (size_t)g * p.P;
+    if (i < p.dm.H)
+      gr[p.dm.off_w2() + (size_t)i * p.dm.A + n] = acc;
+    else
+      gr[p.dm.off_b2() + n] = acc;
   }
 };
 
-// dW1 = X^T dh   (K = rows of the group)
+// [dW1; db1] = [X 1]^T dh   (K = rows of the group; row t*E of the result is the bias gradient)
 struct DW1Op : RowBase {
-  __device__ int M(int) const { return p.dm.K1(); }
+  static constexpr bool kAKc = false, kBKc = false;
+  __device__ int M(int) const { return p.dm.K1() + 1; }
   __device__ int N() const { return p.dm.H; }
   __device__ int K(int g) const { return nrows(g); }
-  __device__ float a(int g, int i, int r) const {
-    int rw = row(g, r);
-    if (!pred(g, rw)) return 0.f;
-    int pos = i / p.dm.E, e = i - pos * p.dm.E;
-    int tok = ctx_token(g, rw, pos, p.dm.t);
-    return p.params[(size_t)g * p.P + p.dm.off_emb() + (size_t)tok * p.dm.E + e];
+  __device__ void fetch_a(const long long *, int g, int m0, int k0, int M, int K, Frag &f) const {
+    // A[i][r] = X[r][i]: contiguous along i within one embedding row (E consecutive values)
+    const float *wg = p.params + (size_t)g * p.P;
+    const int KX = p.dm.K1(), E = p.dm.E;
+    fetch_cc(f, m0, k0, M, (E % 4 == 0) ? KX : 0, K, [&](int, int r, int i) -> const float * {
+      long long b = target_pos(g, r);
+      if (b < 0) return nullptr;
+      return i < KX ? xptr(wg, p.dm, b, i) : &kOneF;
+    });
   }
-  __device__ float b(int g, int r, int n) const {
-    int rw = row(g, r);
-    return pred(g, rw) ? p.dh[(size_t)rw * p.dm.H + n] : 0.f;
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    fetch_cc(f, n0, k0, N, N, K, [&](int, int r, int c) -> const float * {
+      return target_pos(g, r) < 0 ? nullptr : p.dh + (size_t)row(g, r) * N + c;
+    });
   }
-  __device__ void epi(int g, int i, int n, float acc) const {
-    p.grad[(size_t)g * p.P + p.dm.off_w1() + (size_t)i * p.dm.H + n] = acc;
+  __device__ void epi(const long long *, int g, int i, int, int n, float acc) const {
+    float *gr = p.grad + (size_t)g * p.P;
+    if (i < p.dm.K1())
+      gr[p.dm.off_w1() + (size_t)i * p.dm.H + n] = acc;
+    else
+      gr[p.dm.off_b1() + n] = acc;
   }
 };
 
 // dX = dh W1^T, scattered into the embedding rows of the context tokens
 struct DXOp : RowBase {
+  static constexpr bool kAKc = true, kBKc = true;
   __device__ int M(int g) const { return nrows(g); }
   __device__ int N() const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
-  __device__ float a(int g, int r, int k) const { return p.dh[(size_t)row(g, r) * p.dm.H + k]; }
-  __device__ float b(int g, int k, int i) const {
-    return p.params[(size_t)g * p.P + p.dm.off_w1() + (size_t)i * p.dm.H + k];
+  __device__ void fetch_a(const long long *mb, int g, int m0, int k0, int M, int K, Frag &f) const {
+    fetch_kc(f, m0, k0, M, K, [&](int rl, int m, int k) -> const float * {
+      return mb[rl] < 0 ? nullptr : p.dh + (size_t)row(g, m) * K + k;
+    });
   }
-  __device__ void epi(int g, int r, int i, float acc) const {
-    int rw = row(g, r);
-    if (!pred(g, rw)) return;
+  __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
+    const float *w1 = p.params + (size_t)g * p.P + p.dm.off_w1();  // B[k][i] = W1[i][k]
+    fetch_kc(f, n0, k0, N, K, [&](int, int i, int k) -> const float * { return w1 + (size_t)i * K + k; });
+  }
+  __device__ void epi(const long long *mb, int g, int r, int rl, int i, float acc) const {
+    long long b = mb[rl];
+    if (b < 0) return;
     int pos = i / p.dm.E, e = i - pos * p.dm.E;
-    int tok = ctx_token(g, rw, pos, p.dm.t);
+    int tok = p.tokens[b - p.dm.t + pos];
     long long q = __double2ll_rn((double)acc * kEmbFix);
     atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc + ((size_t)g * p.dm.A + tok) * p.dm.E + e),
               (unsigned long long)q);
   }
 };
-
-// db2 = sum dz, db1 = sum dh, dalpha = sum dalpha_row over the predicted rows, in row order
-__global__ void bias_grad_kernel(Plan p, int T) {
-  int g = blockIdx.y;
-  if (!group_trains(p, T, g)) return;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int A = p.dm.A, H = p.dm.H;
-  if (c > A + H) return;
-  int r0 = p.grp_lane_off[g], r1 = p.grp_lane_off[g + 1];
-  float s = 0.f;
-  for (int r = r0; r < r1; ++r) {
-    if (!row_pred(p, T, r, g)) continue;
-    if (c < A)
-      s += p.dz[(size_t)r * A + c];
-    else if (c < A + H)
-      s += p.dh[(size_t)r * H + (c - A)];
-    else
-      s += p.dalpha_row[r];
-  }
-  if (c < A)
-    p.grad[(size_t)g * p.P + p.dm.off_b2() + c] = s;
-  else if (c < A + H)
-    p.grad[(size_t)g * p.P + p.dm.off_b1() + (c - A)] = s;
-  else
-    p.dalpha_grp[g] = s;
-}
 
 __device__ __forceinline__ void adam_one(float &th, float &m, float &v, float gr, float lr, float bc1, float bc2) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -273,7 +391,11 @@ __global__ void update_kernel(Plan p, int T) {
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    float ga = p.dalpha_grp[g];
+    // dalpha = sum of the predicted rows' contributions, in row order
+    float ga = 0.f;
+    for (int r = p.grp_lane_off[g]; r < p.grp_lane_off[g + 1]; ++r)
+      if (row_pred(p, T, r, g)) ga += p.dalpha_row[r];
+    p.dalpha_grp[g] = ga;
     if (p.optimizer == PMKLC_ADAM) {
       float t = p.alpha[g], mm = p.alpha_m[g], vv = p.alpha_v[g];
       adam_one(t, mm, vv, ga, p.lr, bc1, bc2);
@@ -348,19 +470,16 @@ void launch_backward(const Plan &p, int T, cudaStream_t st) {
   }
   {
     ProfScope ps("bwd_dw2", 2.0 * R * p.dm.A * p.dm.H, 0, st);
-    run_ggemm(DW2Op{{p, T}}, p.dm.H, p.dm.A, p.G, st);
+    run_ggemm(DW2Op{{p, T}}, p.dm.H + 1, p.dm.A, p.G, st);
   }
   {
     ProfScope ps("bwd_dw1", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
-    run_ggemm(DW1Op{{p, T}}, p.dm.K1(), p.dm.H, p.G, st);
+    run_ggemm(DW1Op{{p, T}}, p.dm.K1() + 1, p.dm.H, p.G, st);
   }
   {
     ProfScope ps("bwd_dx_demb", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
     run_ggemm(DXOp{{p, T}}, p.Mmax, p.dm.K1(), p.G, st);
   }
-  int cols = p.dm.A + p.dm.H + 1;
-  ProfScope ps("bias_grad", 0, 0, st);
-  bias_grad_kernel<<<dim3((cols + 127) / 128, p.G), 128, 0, st>>>(p, T);
 }
 
 void launch_update(const Plan &p, int T, cudaStream_t st) {

@@ -28,11 +28,12 @@ CASES = [
     dict(s=1, k=1, ctx_s=2, ctx_d=2),
     dict(s=3, k=3),
     dict(use_static=False, smp_mode=1),
-    dict(smp_mode=0, fallback=False),
+    dict(smp_mode=0, fallback=0),
+    dict(fallback=2, smp_mode=1),
     dict(optimizer=1, lr=0.05),
     dict(s=4, k=5, lanes_per_block=1),
     dict(lanes_per_block=50),
-    dict(s=3, k=6, emb_d=8, ctx_d=6, hid_d=24, lanes_per_block=7, fallback=False),
+    dict(s=3, k=6, emb_d=8, ctx_d=6, hid_d=24, lanes_per_block=7, fallback=0),
 ]
 
 
@@ -71,14 +72,14 @@ def test_empty_and_tiny_inputs(P):
 def test_uniform_prefix_bytes_equal_oracle(P):
     # every token inside the uniform prefix: no floating point decides anything,
     # so the whole container must equal the oracle's byte for byte
-    kw = _cfg(P, use_static=False, ctx_d=50, lanes_per_block=4, fallback=False)
+    kw = _cfg(P, use_static=False, ctx_d=50, lanes_per_block=4, fallback=0)
     seq = synth.markov(800, 2, 0.4, 4).tobytes()  # (s,k)=(2,3): 200 + 198 tokens, 4 lanes of <= 50
     out = P.pmklc_compress(seq, [402, 398], P.ModelConfig(**kw))
     assert out == ocodec.compress(seq, [402, 398], ocodec.Config(**kw))
 
 
 def test_count_model_fallback_bytes_equal_oracle(P):
-    kw = _cfg(P, use_static=False, count_order=6, fallback=True)
+    kw = _cfg(P, use_static=False, count_order=6, fallback=1)
     seq = (b"ACGTTGCAAC" * 200) + synth.markov(300, 2, 0.4, 2).tobytes()
     out = P.pmklc_compress(seq, [2000, 300], P.ModelConfig(**kw))
     ref = ocodec.compress(seq, [2000, 300], ocodec.Config(**kw))
@@ -142,7 +143,7 @@ def test_tiny_workload_size_within_half_percent_of_oracle(P):
     """The 100,000-base tiny workload, one lane, dynamic model only: the full oracle run."""
     w = synth.workload("tiny")
     kw = dict(s=1, k=3, use_static=False, emb_d=16, ctx_d=16, hid_d=32, lanes_per_block=1, smp_mode=0,
-              count_order=6, fallback=True)
+              count_order=6, fallback=1)
     out = P.pmklc_compress(w.seq, w.block_lens, P.ModelConfig(**kw))
     assert P.pmklc_decompress(out)[0] == w.seq.tobytes()
     ref = ocodec.compress(w.seq.tobytes(), w.block_lens, ocodec.Config(**kw))

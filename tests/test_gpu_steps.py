@@ -10,7 +10,6 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import countmodel
 from oracle.mixer import loss_grads, mix, softmax
 from oracle.model import Shape, adam_step, backward, forward, init_params
 from oracle.quantize import TOTAL, cumulative, quantize
@@ -231,24 +230,18 @@ def test_train_step_within_tolerance(P, torch, use_static):
 
 # ---------------------------------------------------------------- count model, CRC
 
-@pytest.mark.parametrize("m", [0, 2, 6, 7])
-def test_count_model_bit_exact(P, torch, m):
-    seqs = [synth.markov(n, 3, 0.4, 40 + n) for n in (0, 1, 700, 20_000)]
-    seq = np.concatenate(seqs)
-    off = np.concatenate([[0], np.cumsum([len(s) for s in seqs])]).astype(np.uint64)
-    cap = 2 * 20_000 + 8
-    nb = len(seqs)
-    d_out = torch.zeros(nb * cap, dtype=torch.uint8, device="cuda")
-    d_len = torch.zeros(nb, dtype=torch.int32, device="cuda")
-    d_off = dev(torch, off.view(np.int64))
-    P.pmklc_count_encode(dev(torch, seq), d_off, nb, m, d_out, cap, d_len)
-    out, lens = d_out.cpu().numpy().reshape(nb, cap), d_len.cpu().numpy()
-    for b, s in enumerate(seqs):
-        want = countmodel.encode(base_codes(s.tobytes()), m)
-        assert out[b, :lens[b]].tobytes() == want
-    d_back = torch.zeros(len(seq), dtype=torch.uint8, device="cuda")
-    P.pmklc_count_decode(d_out, d_len, cap, d_off, nb, m, d_back)
-    assert d_back.cpu().numpy().tobytes() == seq.tobytes()
+@pytest.mark.parametrize("s,k,M,m", [(1, 1, 1, 0), (1, 1, 1, 6), (2, 4, 16, 6), (3, 6, 64, 7), (1, 3, 200, 2)])
+def test_count_model_bytes_equal_oracle(P, s, k, M, m):
+    """Count model only (fallback 2): integer arithmetic end to end, so the whole container
+    must equal the oracle's byte for byte, including lanes that share a context."""
+    from oracle import codec as ocodec
+    seq = np.concatenate([synth.markov(n, 3, 0.4, 40 + n) for n in (1, 700, 20_000, 3)]).tobytes()
+    lens = [1, 700, 20_000, 3]
+    kw = dict(s=s, k=k, emb_d=2, ctx_d=2, hid_d=2, lanes_per_block=M, count_order=m, fallback=2)
+    out = P.pmklc_compress(seq, lens, P.ModelConfig(**kw))
+    assert out == ocodec.compress(seq, lens, ocodec.Config(**kw))
+    back, bl = P.pmklc_decompress(out)
+    assert back == seq and list(bl) == lens
 
 
 def test_crc32_matches_zlib(P, torch):

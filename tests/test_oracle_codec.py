@@ -23,7 +23,8 @@ CASES = [
     dict(s=1, k=1, ctx_s=2, ctx_d=2),
     dict(s=3, k=3),
     dict(use_static=False, smp_mode=SMP_CHAIN),
-    dict(smp_mode=SMP_NONE, fallback=False),
+    dict(smp_mode=SMP_NONE, fallback=0),
+    dict(fallback=2),
     dict(optimizer=1, lr=0.05),
     dict(s=4, k=5, lanes_per_block=1),
     dict(lanes_per_block=50),
@@ -68,7 +69,7 @@ def test_lanes_partition():
 
 
 def test_smp_child_starts_from_parent_state():
-    cfg = _small(smp_mode=SMP_CHAIN, smp_fraction=0.25, fallback=False)
+    cfg = _small(smp_mode=SMP_CHAIN, smp_fraction=0.25, fallback=0)
     sw = init_params(cfg.static_shape, 5)
     seq = synth.markov(2000, 2, 0.4, 3).tobytes()
     snaps = {}
@@ -89,7 +90,7 @@ def test_smp_child_starts_from_parent_state():
 def test_f_zero_smp_equals_no_smp():
     sw = init_params(_small().static_shape, 5)
     seq = synth.markov(1200, 2, 0.4, 8).tobytes()
-    outs = {mode: codec.compress(seq, [400, 400, 400], _small(smp_mode=mode, smp_fraction=0.0, fallback=False), sw)
+    outs = {mode: codec.compress(seq, [400, 400, 400], _small(smp_mode=mode, smp_fraction=0.0, fallback=0), sw)
             for mode in (SMP_NONE, SMP_CHAIN, SMP_TREE)}
     strip = lambda b: b[:10] + b[11:]  # the smp-mode byte differs
     assert strip(outs[SMP_NONE]) == strip(outs[SMP_CHAIN]) == strip(outs[SMP_TREE])
@@ -97,7 +98,7 @@ def test_f_zero_smp_equals_no_smp():
 
 def test_uniform_prefix_costs_2k_bits_per_token():
     # context longer than every lane: every token is coded with the uniform table
-    cfg = _small(use_static=False, ctx_d=50, lanes_per_block=4, fallback=False)
+    cfg = _small(use_static=False, ctx_d=50, lanes_per_block=4, fallback=0)
     seq = synth.markov(402, 2, 0.4, 4).tobytes()  # (s,k)=(2,3): 200 tokens, 4 lanes of 50
     out = codec.compress(seq, [402], cfg)
     hdr = 80 + 2 + 1 + 1 + 4  # varint(402) + mode + tail byte + 4 one-byte lane lengths
@@ -131,14 +132,15 @@ def test_header_and_errors():
 def test_judge_picks_the_smaller_coding():
     # a periodic block is cheap for the order-6 count model and a fresh network
     # cannot match it; a short random block is not
-    cfg = _small(use_static=False, count_order=6, fallback=True)
+    cfg = _small(use_static=False, count_order=6, fallback=1)
     seq = (b"ACGTTGCAAC" * 200) + synth.markov(300, 2, 0.4, 2).tobytes()
     out = codec.compress(seq, [2000, 300], cfg)
     blocks = _modes(out)
     assert blocks[0] == 1
     assert codec.decompress(out) == seq
-    off = codec.compress(seq, [2000, 300], _small(use_static=False, fallback=False))
-    assert len(out) < len(off)
+    off = codec.compress(seq, [2000, 300], _small(use_static=False, fallback=0))
+    only = codec.compress(seq, [2000, 300], _small(use_static=False, fallback=2))
+    assert len(out) <= min(len(off), len(only)) + 2  # never worse than either coder alone (flag bytes aside)
 
 
 def _modes(data):
@@ -147,12 +149,8 @@ def _modes(data):
     for _ in range(meta["n_blocks"]):
         n, pos = codec.read_varint(data, pos)
         modes.append(data[pos])
-        pos += 1
-        if modes[-1] == 0:
-            pos += (codec.tail_len(n, cfg.s, cfg.k) * 2 + 7) // 8
-            for _ in codec.lanes(codec.n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0]:
-                _, pos = codec.read_varint(data, pos)
-        else:
+        pos += 1 + (codec.tail_len(n, cfg.s, cfg.k) * 2 + 7) // 8
+        for _ in codec.lanes(codec.n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0]:
             _, pos = codec.read_varint(data, pos)
     return modes
 
@@ -162,7 +160,7 @@ def test_online_learning_beats_uniform():
     table = np.array([[0.85, 0.05, 0.05, 0.05], [0.05, 0.85, 0.05, 0.05],
                       [0.05, 0.05, 0.85, 0.05], [0.05, 0.05, 0.05, 0.85]])
     seq = synth.sample(6000, table, 9).tobytes()
-    cfg = Config(s=1, k=1, emb_d=4, ctx_d=4, hid_d=16, lanes_per_block=1, fallback=False, lr=1e-2)
+    cfg = Config(s=1, k=1, emb_d=4, ctx_d=4, hid_d=16, lanes_per_block=1, fallback=0, lr=1e-2)
     out = codec.compress(seq, [6000], cfg)
     entropy = -(0.85 * math.log2(0.85) + 3 * 0.05 * math.log2(0.05))
     bpb = 8 * len(out) / 6000

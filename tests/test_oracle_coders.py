@@ -105,23 +105,43 @@ def test_count_model_hand_worked():
         if line.startswith("#") or not line.strip():
             continue
         s, m, *qs = line.split()
-        probs = countmodel.probabilities(base_codes(s.encode()), int(m))
+        probs = countmodel.sequential_probabilities(base_codes(s.encode()), int(m))
         want = [Fraction(q) for q in qs]
         assert [Fraction(f, t) for f, t in probs] == want
 
 
 @pytest.mark.parametrize("m", [0, 1, 3, 6])
-def test_count_model_round_trip_and_length(m):
+def test_count_model_one_lane_is_the_sequential_model(m):
+    """With one lane and (s,k) = (1,1) the lane coder codes every base in order with the
+    plain sequential adaptive model: its length obeys that model's bound, and it round-trips."""
     import synth
-    codes = base_codes(synth.markov(4000, 2, 0.45, 17 + m).tobytes())
-    data = countmodel.encode(codes, m)
-    assert np.array_equal(countmodel.decode(data, codes.size, m), codes)
-    ideal = sum(-math.log2(f / t) for f, t in countmodel.probabilities(codes, m))
-    assert 8 * len(data) <= ideal + 8 + 1e-3
+    from oracle import codec
+    seq = synth.markov(4000, 2, 0.45, 17 + m).tobytes()
+    cfg = codec.Config(s=1, k=1, emb_d=2, ctx_d=2, hid_d=2, lanes_per_block=1, fallback=2, count_order=m)
+    out = codec.compress(seq, [len(seq)], cfg)
+    assert codec.decompress(out) == seq
+    ideal = sum(-math.log2(f / t) for f, t in countmodel.sequential_probabilities(base_codes(seq), m))
+    payload = len(out) - 80 - len(codec.varint(len(seq))) - 1 - len(codec.varint(len(out) - 80 - 5))
+    assert 8 * payload <= ideal + 8 + 1e-3
+    assert 8 * payload >= ideal - 56
+
+
+def test_count_model_lanes_share_one_table():
+    import synth
+    from oracle import codec
+    seq = synth.markov(6000, 2, 0.45, 5).tobytes()
+    for s_, k_, M in [(1, 1, 7), (2, 4, 16), (3, 6, 5)]:
+        cfg = codec.Config(s=s_, k=k_, emb_d=2, ctx_d=2, hid_d=2, lanes_per_block=M, fallback=2, count_order=4)
+        out = codec.compress(seq, [3000, 3000], cfg)
+        assert codec.decompress(out) == seq
 
 
 def test_count_model_halving():
     codes = np.zeros(5000, dtype=np.uint8)  # one context, counts hit the limit repeatedly
-    probs = countmodel.probabilities(codes, 2)
+    probs = countmodel.sequential_probabilities(codes, 2)
     assert max(t for _, t in probs) <= 2 * 4 * countmodel.LIMIT + 4
-    assert np.array_equal(countmodel.decode(countmodel.encode(codes, 2), 5000, 2), codes)
+    t = countmodel.Table(2, 3)  # three lanes in one context: increments land together, halving once
+    for _ in range(400):
+        t.finish_substep([0, 1, 2], [0, 0, 0])
+        t.ctx = [0, 0, 0]
+    assert t.c[0].max() < countmodel.LIMIT and t.c[0, 0] > 0
