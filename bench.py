@@ -170,26 +170,86 @@ SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 
 def roofline(prof: dict, pk: dict, pk_kind: str):
-    """Achieved vs peak of the kernel with the largest sampled time."""
+    """Achieved vs peak of the kernel with the largest sampled time, against the bound that its
+    algorithmic work reaches first (tensor/ALU FLOPs or HBM bytes)."""
     if not prof:
         return None, {}
+    tot = sum(x["ms"] for x in prof.values())
+    per = {k: {"launches": v["launches"], "ms_avg": v["ms"] / max(v["launches"], 1), "share": v["ms"] / tot,
+               "work_flops_per_launch": v["flops"] / max(v["launches"], 1),
+               "work_bytes_per_launch": v["bytes"] / max(v["launches"], 1)} for k, v in prof.items()}
     name = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[name]
-    per = {k: {"launches": v["launches"], "ms_avg": v["ms"] / max(v["launches"], 1),
-               "share": v["ms"] / sum(x["ms"] for x in prof.values())} for k, v in prof.items()}
-    if d["flops"] > 0:
-        # FP32 FMA on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x max SM clock
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = d["flops"] / (d["ms"] / 1e3) / 1e12
-        r = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock", "traffic": None,
-             "work_per_launch": d["flops"] / d["launches"]}
+    sec = d["ms"] / 1e3
+    tensor = name.endswith("_bf16")
+    if tensor:  # BF16 mma on the tensor cores; the kernel runs inside a long step: sustained peak
+        fpeak, fsrc = pk.get("bf16_tflops_sustained", 1700.0), f"{pk_kind} bf16_tflops_sustained"
+    else:  # FP32 FMA on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+        fpeak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        fsrc = "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"
+    t_flop = d["flops"] / (fpeak * 1e12) if d["flops"] else 0.0
+    t_byte = d["bytes"] / (pk["hbm_gbs"] * 1e9) if d["bytes"] else 0.0
+    if t_flop >= t_byte and d["flops"]:
+        ach = d["flops"] / sec / 1e12
+        r = {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": ach, "peak": fpeak,
+             "unit": "TFLOP/s", "frac": ach / fpeak, "peak_source": fsrc, "traffic": None,
+             "work_per_launch": d["flops"] / d["launches"], "work_unit": "FLOP"}
     else:
-        peak = pk["hbm_gbs"]
-        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-             "peak_source": f"{pk_kind} hbm_gbs", "traffic": None, "work_per_launch": d["bytes"] / d["launches"]}
+        ach = d["bytes"] / sec / 1e9
+        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+             "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs", "traffic": None,
+             "work_per_launch": d["bytes"] / max(d["launches"], 1), "work_unit": "byte"}
     return r, per
+
+
+FORMS = {"bf16": 1, "fp32": 0}
+
+
+def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True):
+    """Device-resident compress+decompress of the workload: per-step times (CUDA events) + stats."""
+    cfg = P.ModelConfig(**kw, static_weights=sw, precision=FORMS[form])
+    n = int(w.seq.size)
+    stream = torch.cuda.current_stream()
+    d_seq = torch.from_numpy(w.seq).to(dev)
+    cap = P.pmklc_compress_bound(n, w.block_lens, cfg)
+    d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    d_back = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step():
+        clen = P.pmklc_compress_dev(d_seq, w.block_lens, cfg, d_out)
+        s1 = P.pmklc_last_stats()
+        P.pmklc_decompress_dev(d_out, clen, d_back, sw)
+        s2 = P.pmklc_last_stats()
+        return clen, s1["kernel_launches"] + s2["kernel_launches"], s1
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    assert torch.equal(d_back, d_seq), "round trip failed"
+    times, launches = [], 0
+    P.pmklc_profile_read()
+    if profile:
+        P.pmklc_profile_enable(PROFILE_EVERY)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        clen, nl, st1 = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches += nl
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    P.pmklc_profile_enable(0)
+    prof = P.pmklc_profile_read()
+    del flush
+    return {"cfg": cfg, "times": times, "launches": launches, "clen": clen, "stats": st1, "prof": prof}
 
 
 def main():
@@ -200,6 +260,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="both", choices=["both", "bf16", "fp32"])
     args = ap.parse_args()
     rank, world = _dist()
 
@@ -221,49 +282,14 @@ def main():
     dev = torch.cuda.current_device()
     w, kw = load_workload(args.workload)
     sw = static_weights(P, kw)
-    cfg = P.ModelConfig(**kw, static_weights=sw)
     n = int(w.seq.size)
-    stream = torch.cuda.current_stream()
-    d_seq = torch.from_numpy(w.seq).to(dev)
-    cap = P.pmklc_compress_bound(n, w.block_lens, cfg)
-    d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
-    d_back = torch.empty(n, dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    def step():
-        clen = P.pmklc_compress_dev(d_seq, w.block_lens, cfg, d_out)
-        s1 = P.pmklc_last_stats()
-        m = P.pmklc_decompress_dev(d_out, clen, d_back, sw)
-        s2 = P.pmklc_last_stats()
-        return clen, m, s1["kernel_launches"] + s2["kernel_launches"], s1
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    assert torch.equal(d_back, d_seq), "round trip failed"
-
-    times, launches, clen, st1 = [], 0, 0, None
-    P.pmklc_profile_read()  # drop anything recorded during warm-up
-    P.pmklc_profile_enable(PROFILE_EVERY)
+    results = {}
     with ClockSampler(dev) as clk:
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            clen, m, nl, st1 = step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            launches += nl
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-    P.pmklc_profile_enable(0)
-    prof = P.pmklc_profile_read()
-    ms = statistics.mean(times)
+        for form in ([args.form] if args.form != "both" else ["fp32", "bf16"]):
+            results[form] = measure(P, torch, w, kw, sw, form, args.steps, args.warmup, dev, world)
+    head = results["bf16"] if "bf16" in results else results[args.form]
+    form = "bf16" if "bf16" in results else args.form
+    ms = statistics.mean(head["times"])
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -276,7 +302,7 @@ def main():
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        blob = P.pmklc_compress(host, w.block_lens, cfg)
+        blob = P.pmklc_compress(host, w.block_lens, head["cfg"])
         back, _ = P.pmklc_decompress(blob, sw)
         e2e_times.append(time.perf_counter() - t0)
         assert back == host.tobytes()
@@ -286,19 +312,27 @@ def main():
     if rank != 0:
         return
     pk, pk_kind = peaks()
+    st1 = head["stats"]
     line = {
         "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16" if form == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w.recipe}, {n} bases, {len(w.block_lens)} blocks, "
-                               f"(s,k)=({kw['s']},{kw['k']})", "model": kw, "form": "FP32 plain",
-                   "bits_per_base": 8 * clen / n, "compressed_bytes": clen,
+                               f"(s,k)=({kw['s']},{kw['k']})", "model": kw,
+                   "form": {"bf16": "BF16 batched", "fp32": "FP32 plain"}[form],
+                   "bits_per_base": 8 * head["clen"] / n, "compressed_bytes": head["clen"],
                    "net_blocks": st1["net_blocks"], "count_blocks": st1["count_blocks"],
                    "global_steps": st1["global_steps"], "l2": "flushed (256 MB write) before every step",
                    "static_model": f"seeded random (init seed {STATIC_SEED})"},
-        "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "peaks": pk_kind,
+        "e2e": e2e, "gpu_launches": head["launches"], "clocks": clk.summary(), "peaks": pk_kind,
     }
-    line["roofline"], line["kernels"] = roofline(prof, pk, pk_kind)
+    if "fp32" in results and form != "fp32":
+        f = results["fp32"]
+        fms = statistics.mean(f["times"])
+        line["fp32_plain"] = {"value": world * n / 1e6 / (fms / 1e3), "unit": "MB/s", "ms_per_step": fms,
+                              "bits_per_base": 8 * f["clen"] / n, "gpu_launches": f["launches"]}
+        line["bits_per_base_rel_diff_vs_fp32"] = (head["clen"] - f["clen"]) / f["clen"]
+    line["roofline"], line["kernels"] = roofline(head["prof"], pk, pk_kind)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, kw, sw)
     print(json.dumps(line))

@@ -156,7 +156,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (c->use_static && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
                         c->hid_s > 65535 || !c->static_weights))
     return PMKLC_EINVAL;
-  if (c->precision != PMKLC_FP32_PLAIN) return PMKLC_EINVAL;
+  if (c->precision != PMKLC_FP32_PLAIN && c->precision != PMKLC_BF16_BATCHED) return PMKLC_EINVAL;
   if (c->optimizer > PMKLC_SGD || c->smp_mode > PMKLC_SMP_TREE || c->count_order > 7) return PMKLC_EINVAL;
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
@@ -342,6 +342,17 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.alpha_v = ar.alloc<float>(G);
   p.dalpha_grp = ar.alloc<float>(G);
   p.static_params = d_static;
+  p.precision = c.precision;
+  p.wbf = nullptr;
+  p.static_bf = nullptr;
+  if (c.precision == PMKLC_BF16_BATCHED) {
+    p.wbf = ar.alloc<__nv_bfloat16>(G * p.P);
+    if (c.use_static && d_static) {
+      __nv_bfloat16 *sb = ar.alloc<__nv_bfloat16>(c.st.count());
+      if (sb) launch_to_bf16(d_static, sb, c.st.count(), ar.st);
+      p.static_bf = sb;
+    }
+  }
   int A = c.A();
   p.hd = ar.alloc<float>(NL * c.dm.H);
   p.hs = c.use_static ? ar.alloc<float>(NL * c.st.H) : nullptr;
@@ -351,6 +362,13 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.dh = ar.alloc<float>(NL * c.dm.H);
   p.dalpha_row = ar.alloc<float>(NL);
   p.out_P = nullptr;
+  p.hd_b = p.hs_b = p.dz_b = p.dh_b = nullptr;
+  if (c.precision == PMKLC_BF16_BATCHED) {
+    p.hd_b = ar.alloc<__nv_bfloat16>(NL * c.dm.H);
+    p.hs_b = c.use_static ? ar.alloc<__nv_bfloat16>(NL * c.st.H) : nullptr;
+    p.dz_b = ar.alloc<__nv_bfloat16>(NL * A);
+    p.dh_b = ar.alloc<__nv_bfloat16>(NL * c.dm.H);
+  }
   p.demb_acc = ar.alloc<long long>(G * A * c.dm.E);
   p.err = ar.alloc<int>(1);
   std::vector<float> bc1(R.S.max_tau + 2), bc2(R.S.max_tau + 2);
@@ -377,6 +395,7 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   float *d_init = ar.upload(init);
   if (ar.failed) return PMKLC_ENOMEM;
   launch_init_groups(p, d_init, c.alpha0, ar.st);
+  if (p.wbf) launch_to_bf16(p.params, p.wbf, G * p.P, ar.st);
   return PMKLC_OK;
 }
 
@@ -411,16 +430,23 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     if (!R.net) continue;
+    const bool bf = R.p.precision == PMKLC_BF16_BATCHED;
     if (any_pred) {
-      launch_forward(R.p, T, st);
-      R.launches += R.c.use_static ? 4 : 2;
+      if (bf)
+        launch_forward_bf16(R.p, T, st);
+      else
+        launch_forward(R.p, T, st);
+      R.launches += bf ? 2 : (R.c.use_static ? 4 : 2);
     }
     if (any_pred || any_code) {
       launch_mixcode(R.p, T, st);
       R.launches++;
     }
     if (any_pred) {
-      launch_backward_update(R.p, T, st);
+      if (bf)
+        launch_backward_update_bf16(R.p, T, st);
+      else
+        launch_backward_update(R.p, T, st);
       R.launches += 5;
     }
   }
@@ -659,8 +685,8 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.smp_mode = h[10];
   c.count_order = h[11];
   c.fallback = (h[7] >> 1) & 3;
-  if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 || c.precision != 0 ||
-      c.fallback > 2)
+  if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 ||
+      c.fallback > 2 || c.precision > PMKLC_BF16_BATCHED)
     return PMKLC_ECORRUPT;
   int A = 1 << (2 * c.k);
   c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
@@ -1142,9 +1168,28 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
   R.p.alpha_m = d_alpha_m;
   R.p.alpha_v = d_alpha_v;
   const int T = te;
+  const bool bf = c.precision == PMKLC_BF16_BATCHED;
+  if (bf) launch_to_bf16(d_params, R.p.wbf, (size_t)G * R.p.P, st);
   if (d_logits_only) {
-    launch_forward(R.p, T, st);
+    if (bf)
+      launch_forward_bf16(R.p, T, st);
+    else
+      launch_forward(R.p, T, st);
     cudaMemcpyAsync(d_logits_only, R.p.zm, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
+  } else if (bf) {
+    // the BF16 form applies the optimiser inside the gradient GEMMs: no gradient to export
+    if (d_grad) return PMKLC_EINVAL;
+    std::vector<unsigned long long> off(rows, 0);
+    std::vector<uint32_t> cap(rows, 0);
+    R.p.lane_buf_off = ar.upload(off);
+    R.p.lane_buf_cap = ar.upload(cap);
+    R.p.lane_buf = ar.alloc<uint8_t>(16);
+    R.p.out_P = d_P;
+    if (ar.failed) return PMKLC_ENOMEM;
+    launch_forward_bf16(R.p, T, st);
+    launch_mixcode(R.p, T, st);
+    launch_backward_update_bf16(R.p, T, st);
+    if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
   } else {
     std::vector<unsigned long long> off(rows, 0);
     std::vector<uint32_t> cap(rows, 0);
@@ -1167,11 +1212,13 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
 
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,
                   size_t rows, uint32_t precision, float *d_logits, void *stream) {
-  if (k < 1 || k > 8 || !E || !t || !H || precision != PMKLC_FP32_PLAIN || (rows && (!d_params || !d_ctx || !d_logits)))
+  if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_BATCHED ||
+      (rows && (!d_params || !d_ctx || !d_logits)))
     return PMKLC_EINVAL;
   if (rows == 0) return PMKLC_OK;
   pmklc_model_cfg mc;
   pmklc_default_cfg(&mc, 1, k, E, t, H);
+  mc.precision = precision;
   Cfg c;
   int rc = check_cfg(&mc, c);
   if (rc) return rc;

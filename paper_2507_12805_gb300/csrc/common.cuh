@@ -1,5 +1,6 @@
 // Shared device-side definitions of libpmklc (sm_103a).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,10 +58,14 @@ struct Plan {
   // model state
   float *params, *m, *v, *grad, *alpha, *alpha_m, *alpha_v;
   const float *static_params;
+  __nv_bfloat16 *wbf;               // BF16 copy of every group's parameters (BF16 form), G x P
+  const __nv_bfloat16 *static_bf;   // BF16 copy of the static parameters (BF16 form)
+  int precision;                    // PMKLC_FP32_PLAIN / PMKLC_BF16_BATCHED
   const float *bc1, *bc2;      // Adam bias corrections 1 - beta^tau, indexed by tau
   // activations (NL rows)
   float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
   float *out_P;                // optional: mixed probabilities of predicted rows (tests)
+  __nv_bfloat16 *hd_b, *hs_b, *dz_b, *dh_b;  // BF16 activations of the BF16 form (else nullptr)
   long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
   // coders
   EncState *enc;
@@ -103,6 +108,18 @@ __device__ __forceinline__ bool row_pred(const Plan &p, int T, int r, int g) {
 __device__ __forceinline__ bool group_trains(const Plan &p, int T, int g) {
   int j = T - p.grp_start[g];
   return j >= p.t_eff && j < p.grp_steps[g];
+}
+
+// d loss / d alpha of group g: the predicted rows' contributions, summed by one warp in a fixed
+// order (each lane takes rows lane, lane+32, ... in turn, then a butterfly whose lane-0 value is
+// broadcast).  All 32 lanes must call it.
+__device__ __forceinline__ float alpha_grad(const Plan &p, int T, int g) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  for (int r = p.grp_lane_off[g] + lane; r < p.grp_lane_off[g + 1]; r += 32)
+    if (row_pred(p, T, r, g)) s += p.dalpha_row[r];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
 }
 
 // Fixed point scale of the embedding gradient accumulators (integer adds are order-free,

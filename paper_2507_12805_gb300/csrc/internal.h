@@ -64,6 +64,10 @@ void launch_update(const Plan &p, int T, cudaStream_t st);
 void launch_backward_update(const Plan &p, int T, cudaStream_t st);
 // gradient of every group (embedding part from the fixed-point accumulators) into d_out (G x P)
 void launch_export_grad(const Plan &p, float *d_out, cudaStream_t st);
+// predictor_bf16.cu
+void launch_forward_bf16(const Plan &p, int T, cudaStream_t st);
+void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st);
+void launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st);
 void launch_smp_copy(const Plan &p, const int *d_pairs, int n_pairs, cudaStream_t st);
 void launch_init_groups(const Plan &p, const float *d_init, float alpha0, cudaStream_t st);
 

@@ -234,12 +234,16 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
   lane_chunk(A, lane, a0, n);
   float da = 0.f;
   float *dz = p.dz + (size_t)r * A;
+  __nv_bfloat16 *dzb = p.dz_b ? p.dz_b + (size_t)r * A : nullptr;
   float *outP = p.out_P ? p.out_P + (size_t)r * A : nullptr;
   for (int a = a0; a < a0 + n; ++a) {
     float P = t.prob(v, a);
     if (outP) outP[a] = P;
     float d = (P - (a == e ? 1.f : 0.f)) * inv_n;
-    dz[a] = v.oma * d;
+    if (dzb)
+      dzb[a] = __float2bfloat16_rn(v.oma * d);
+    else
+      dz[a] = v.oma * d;
     float diff = p.use_static ? v.zu[a] - v.zm[a] : -v.zm[a];
     da = fmaf(d, diff, da);
   }
@@ -369,7 +373,8 @@ __global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, con
 
 void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
   if (p.NL <= 0) return;
-  ProfScope ps("mix_cdf_code", 0, 0, st);
+  // reads L^u and L^m, writes dL^m: 12 bytes per predicted row and symbol
+  ProfScope ps("mix_cdf_code", 0, 12.0 * prof_work().pred_rows * p.dm.A, st);
   mixcode_kernel<<<(p.NL * 32 + 255) / 256, 256, 0, st>>>(p, T);
 }
 

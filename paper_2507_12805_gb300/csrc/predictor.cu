@@ -390,11 +390,9 @@ __global__ void update_kernel(Plan p, int T) {
       th[i] -= p.lr * gi;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // dalpha = sum of the predicted rows' contributions, in row order
-    float ga = 0.f;
-    for (int r = p.grp_lane_off[g]; r < p.grp_lane_off[g + 1]; ++r)
-      if (row_pred(p, T, r, g)) ga += p.dalpha_row[r];
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    float ga = alpha_grad(p, T, g);
+    if (threadIdx.x != 0) return;
     p.dalpha_grp[g] = ga;
     if (p.optimizer == PMKLC_ADAM) {
       float t = p.alpha[g], mm = p.alpha_m[g], vv = p.alpha_v[g];
@@ -417,6 +415,7 @@ __global__ void smp_copy_kernel(Plan p, const int *pairs, int n_pairs) {
     p.params[child * P + i] = p.params[parent * P + i];
     p.m[child * P + i] = p.m[parent * P + i];
     p.v[child * P + i] = p.v[parent * P + i];
+    if (p.wbf) p.wbf[child * P + i] = p.wbf[parent * P + i];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.alpha[child] = p.alpha[parent];

@@ -1,0 +1,117 @@
+"""BF16 batched form: tensor-core predictor GEMMs with the optimiser fused into the
+weight-gradient epilogues.  Bars: probabilities within 2e-2 of the FP64 oracle for a
+single step from identical state; exact round trips; bits/base within 0.5 % of the
+FP32 plain form on the same input."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.mixer import mix, softmax
+from oracle.model import Shape, forward, init_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2507_12805_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("k,E,t,H,rows", [(3, 16, 16, 32, 70), (4, 32, 32, 128, 130), (6, 32, 8, 256, 65),
+                                          (2, 3, 5, 20, 9)])
+def test_predict_bf16_within_tolerance(P, torch, k, E, t, H, rows):
+    rng = np.random.default_rng(k * 101 + rows)
+    sh = Shape(4 ** k, E, t, H)
+    params = (init_params(sh, 3).astype(np.float64) + rng.normal(0, 0.05, sh.count)).astype(np.float32)
+    ctx = rng.integers(0, sh.A, (rows, t))
+    want = forward(params, sh, ctx)[3]
+    d_out = torch.zeros((rows, sh.A), dtype=torch.float32, device="cuda")
+    P.pmklc_predict(dev(torch, params), k, E, t, H, dev(torch, ctx.astype(np.uint16).view(np.int16)), d_out,
+                    precision=P.PMKLC_BF16_BATCHED)
+    got = d_out.cpu().numpy()
+    # the probabilities are what the coder uses: compare softmax(logits) at the 2e-2 bar
+    assert np.abs(softmax(got) - softmax(want)).max() < 2e-2
+    assert np.abs(got - want).max() < 2e-2 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("use_static", [0, 1])
+def test_train_step_bf16_within_tolerance(P, torch, use_static):
+    from oracle.codec import Config
+    from tests.test_gpu_steps import _model, _oracle_step
+    rng = np.random.default_rng(21 + use_static)
+    cfg_o = Config(s=2, k=4, use_static=bool(use_static), emb_s=16, ctx_s=12, hid_s=48, emb_d=32, ctx_d=8,
+                   hid_d=64, lr=1e-3)
+    G, M = 3, 37
+    dsh = cfg_o.dm_shape
+    params = np.stack([_model(rng, dsh, 5 + g, 0.05) for g in range(G)])
+    m = (rng.normal(0, 1e-3, params.shape)).astype(np.float32)
+    v = (1e-6 + rng.random(params.shape) * 1e-5).astype(np.float32)
+    alpha = np.array([0.5, 0.25, 0.8], np.float32)
+    am = np.array([1e-3, 0, -1e-3], np.float32)
+    av = np.array([1e-6, 1e-7, 2e-6], np.float32)
+    static = _model(rng, cfg_o.static_shape, 77, 0.05) if use_static else None
+    ctx = rng.integers(0, dsh.A, (G * M, cfg_o.t_eff))
+    tgt = rng.integers(0, dsh.A, G * M)
+    tau = 5
+    want = _oracle_step(cfg_o, params, m, v, alpha, am, av, static, ctx, tgt, tau, G, M)
+    cfg = P.ModelConfig(s=2, k=4, use_static=bool(use_static), emb_s=16, ctx_s=12, hid_s=48, emb_d=32, ctx_d=8,
+                        hid_d=64, lr=1e-3, static_weights=static, precision=P.PMKLC_BF16_BATCHED)
+    d = {k: dev(torch, x) for k, x in dict(params=params, m=m, v=v, alpha=alpha, am=am, av=av).items()}
+    d_P = torch.zeros((G * M, dsh.A), dtype=torch.float32, device="cuda")
+    d_da = torch.zeros(G, dtype=torch.float32, device="cuda")
+    P.pmklc_train_step(cfg, G, M, d["params"], d["m"], d["v"], d["alpha"], d["am"], d["av"],
+                       dev(torch, static) if use_static else None,
+                       dev(torch, ctx.astype(np.uint16).view(np.int16)), dev(torch, tgt.astype(np.uint16).view(np.int16)),
+                       tau, d_P, None, d_da)
+    gP, gth, gal = d_P.cpu().numpy(), d["params"].cpu().numpy(), d["alpha"].cpu().numpy()
+    for g in range(G):
+        Pr, gr, dal, th, mm, vv, al = want[g]
+        assert np.abs(gP[g * M:(g + 1) * M] - Pr).max() < 2e-2
+        step_err = np.abs((gth[g] - params[g]) - (th - params[g].astype(np.float64)))
+        assert np.quantile(step_err, 0.999) <= 0.1 * cfg.lr and step_err.max() <= 2 * cfg.lr
+        assert abs(gal[g] - al) <= 0.1 * cfg.lr
+
+
+def _cfg(P, **kw):
+    base = dict(s=2, k=3, use_static=True, emb_s=8, ctx_s=3, hid_s=16, emb_d=8, ctx_d=4, hid_d=16,
+                lanes_per_block=3, count_order=3, smp_mode=P.PMKLC_SMP_TREE, smp_fraction=0.2,
+                precision=P.PMKLC_BF16_BATCHED)
+    base.update(kw)
+    return base
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(use_static=False, smp_mode=1), dict(optimizer=1, lr=0.05, fallback=0),
+                                dict(s=3, k=6, emb_d=8, ctx_d=6, hid_d=24, lanes_per_block=7, fallback=0),
+                                dict(emb_d=5, emb_s=3, fallback=0)])
+def test_bf16_round_trip_and_determinism(P, kw):
+    kw = _cfg(P, **kw)
+    sw = init_params(Shape(4 ** kw["k"], kw["emb_s"], kw["ctx_s"], kw["hid_s"]), 5) if kw["use_static"] else None
+    seq = synth.markov(3000, 2, 0.4, 31).tobytes()
+    lens = [1400, 1000, 2, 0, 598]
+    cfg = P.ModelConfig(**kw, static_weights=sw)
+    out = P.pmklc_compress(seq, lens, cfg)
+    assert out == P.pmklc_compress(seq, lens, cfg)
+    back, bl = P.pmklc_decompress(out, sw)
+    assert back == seq and list(bl) == lens
+
+
+def test_bf16_bits_per_base_close_to_fp32(P):
+    w = synth.workload("plain", scale=1 / 16)
+    kw = dict(s=2, k=4, use_static=True, emb_s=32, ctx_s=32, hid_s=128, emb_d=32, ctx_d=32, hid_d=128,
+              lanes_per_block=16, smp_mode=2, fallback=0)
+    sw = P.pmklc_init_model(4, 32, 32, 128, 2001)
+    a = P.pmklc_compress(w.seq, w.block_lens, P.ModelConfig(**kw, static_weights=sw))
+    b = P.pmklc_compress(w.seq, w.block_lens, P.ModelConfig(**kw, static_weights=sw, precision=1))
+    assert P.pmklc_decompress(b, sw)[0] == w.seq.tobytes()
+    assert abs(len(b) - len(a)) <= 0.005 * len(a), (len(a), len(b))
