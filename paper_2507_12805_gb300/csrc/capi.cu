@@ -363,7 +363,10 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.dalpha_row = ar.alloc<float>(NL);
   p.out_P = nullptr;
   p.hd_b = p.hs_b = p.dz_b = p.dh_b = nullptr;
+  p.hpart = nullptr;
   if (c.precision == PMKLC_BF16_BATCHED) {
+    int hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
+    p.hpart = ar.alloc<float>((size_t)2 * kHiddenSplit * NL * hmax);  // 2 models x K-slices
     p.hd_b = ar.alloc<__nv_bfloat16>(NL * c.dm.H);
     p.hs_b = c.use_static ? ar.alloc<__nv_bfloat16>(NL * c.st.H) : nullptr;
     p.dz_b = ar.alloc<__nv_bfloat16>(NL * A);
@@ -1169,6 +1172,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
   R.p.alpha_v = d_alpha_v;
   const int T = te;
   const bool bf = c.precision == PMKLC_BF16_BATCHED;
+  prof_step(0, StepWork{(double)rows, (double)G});  // sampled when profiling is enabled
   if (bf) launch_to_bf16(d_params, R.p.wbf, (size_t)G * R.p.P, st);
   if (d_logits_only) {
     if (bf)
@@ -1190,6 +1194,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     launch_mixcode(R.p, T, st);
     launch_backward_update_bf16(R.p, T, st);
     if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
+    prof_stop_sampling();
   } else {
     std::vector<unsigned long long> off(rows, 0);
     std::vector<uint32_t> cap(rows, 0);
@@ -1205,6 +1210,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     launch_update(R.p, T, st);  // also forms dalpha of every group
     if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
   }
+  prof_stop_sampling();
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
   PMKLC_CUDA_TRY(cudaGetLastError());
   return PMKLC_OK;

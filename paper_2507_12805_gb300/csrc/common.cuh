@@ -4,12 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/pmklc.h"
+#include "pmklc.h"
 
 namespace pmklc {
 
 constexpr int kTotalBits = 24;             // frequency tables sum to 2^24 (reading R10)
 constexpr uint32_t kTotal = 1u << kTotalBits;
+
+// K-slices of the BF16 hidden-layer GEMM (split-K; the slices are summed in a fixed order)
+constexpr int kHiddenSplit = 4;
 
 enum GroupMode : int { kEncode = 0, kDecode = 1, kReplay = 2 };
 
@@ -66,6 +69,7 @@ struct Plan {
   float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
   float *out_P;                // optional: mixed probabilities of predicted rows (tests)
   __nv_bfloat16 *hd_b, *hs_b, *dz_b, *dh_b;  // BF16 activations of the BF16 form (else nullptr)
+  float *hpart;                // split-K partial sums of the hidden layer (BF16 form)
   long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
   // coders
   EncState *enc;

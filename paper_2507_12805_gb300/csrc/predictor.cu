@@ -354,56 +354,104 @@ struct DXOp : RowBase {
   }
 };
 
-__device__ __forceinline__ void adam_one(float &th, float &m, float &v, float gr, float lr, float bc1, float bc2) {
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  m = b1 * m + (1.f - b1) * gr;
-  v = b2 * v + (1.f - b2) * gr * gr;
-  float mh = m / bc1, vh = v / bc2;
-  th -= lr * mh / (sqrtf(vh) + eps);
+// Optimiser over every parameter of every training group, streamed in float4 groups: the
+// gradient comes from `grad` (W1, b1, W2, b2) or from the fixed-point embedding accumulators
+// (Emb, zeroed on the way); all loads of a group are issued before its stores.  The FP32
+// master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.
+__device__ __forceinline__ void adam4(float (&t)[4], float (&m)[4], float (&v)[4], const float (&g)[4], float lr,
+                                      float bc1, float bc2, bool adam) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (adam) {
+      m[e] = 0.9f * m[e] + 0.1f * g[e];
+      v[e] = 0.999f * v[e] + 0.001f * g[e] * g[e];
+      t[e] -= lr * (m[e] / bc1) / (sqrtf(v[e] / bc2) + 1e-8f);
+    } else {
+      t[e] -= lr * g[e];
+    }
+  }
 }
 
-__global__ void update_kernel(Plan p, int T) {
-  int g = blockIdx.y;
+__global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
+  const size_t P = p.P, nq = (P + 3) / 4, nemb = (size_t)p.dm.A * p.dm.E;
+  const bool adam = p.optimizer == PMKLC_ADAM;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < (size_t)p.G * nq;
+       w += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(w / nq);
+    if (!group_trains(p, T, g)) continue;
+    const size_t i0 = (w - (size_t)g * nq) * 4, base = (size_t)g * P;
+    const int j = T - p.grp_start[g];
+    const int tau = p.grp_tau0[g] + (j - p.t_eff) + 1;
+    const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
+    float *__restrict__ th = p.params + base;
+    float *__restrict__ mm = p.m + base;
+    float *__restrict__ vv = p.v + base;
+    const float *__restrict__ gr = p.grad + base;
+    long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
+    float t[4], m[4], v[4], gg[4];
+    const bool vec = i0 + 3 < P && (base & 3) == 0;
+    if (vec) {
+      float4 a = *reinterpret_cast<const float4 *>(th + i0), b = *reinterpret_cast<const float4 *>(mm + i0),
+             c = *reinterpret_cast<const float4 *>(vv + i0);
+      t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
+      m[0] = b.x, m[1] = b.y, m[2] = b.z, m[3] = b.w;
+      v[0] = c.x, v[1] = c.y, v[2] = c.z, v[3] = c.w;
+      if (i0 < nemb) {  // A*E is a multiple of 4: a group never straddles the embedding boundary
+        longlong2 q0 = *reinterpret_cast<const longlong2 *>(acc + i0),
+                  q1 = *reinterpret_cast<const longlong2 *>(acc + i0 + 2);
+        gg[0] = (float)((double)q0.x * (1.0 / kEmbFix)), gg[1] = (float)((double)q0.y * (1.0 / kEmbFix));
+        gg[2] = (float)((double)q1.x * (1.0 / kEmbFix)), gg[3] = (float)((double)q1.y * (1.0 / kEmbFix));
+        *reinterpret_cast<longlong2 *>(acc + i0) = make_longlong2(0, 0);
+        *reinterpret_cast<longlong2 *>(acc + i0 + 2) = make_longlong2(0, 0);
+      } else {
+        float4 d = *reinterpret_cast<const float4 *>(gr + i0);
+        gg[0] = d.x, gg[1] = d.y, gg[2] = d.z, gg[3] = d.w;
+      }
+      adam4(t, m, v, gg, p.lr, bc1, bc2, adam);
+      *reinterpret_cast<float4 *>(th + i0) = make_float4(t[0], t[1], t[2], t[3]);
+      if (adam) {
+        *reinterpret_cast<float4 *>(mm + i0) = make_float4(m[0], m[1], m[2], m[3]);
+        *reinterpret_cast<float4 *>(vv + i0) = make_float4(v[0], v[1], v[2], v[3]);
+      }
+      if (p.wbf) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(t[0], t[1]), hi = __floats2bfloat162_rn(t[2], t[3]);
+        *reinterpret_cast<uint2 *>(p.wbf + base + i0) =
+            make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+      }
+    } else {
+      for (size_t i = i0; i < i0 + 4 && i < P; ++i) {
+        float t1[4] = {th[i], 0, 0, 0}, m1[4] = {mm[i], 0, 0, 0}, v1[4] = {vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
+        if (i < nemb) {
+          g1[0] = (float)((double)acc[i] * (1.0 / kEmbFix));
+          acc[i] = 0;
+        } else {
+          g1[0] = gr[i];
+        }
+        adam4(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
+        th[i] = t1[0];
+        if (adam) mm[i] = m1[0], vv[i] = v1[0];
+        if (p.wbf) p.wbf[base + i] = __float2bfloat16_rn(t1[0]);
+      }
+    }
+  }
+}
+
+// alpha of every training group (one warp per group)
+__global__ void alpha_update_kernel(Plan p, int T) {
+  int g = blockIdx.x;
   if (!group_trains(p, T, g)) return;
+  float ga = alpha_grad(p, T, g);
+  if (threadIdx.x != 0) return;
   int j = T - p.grp_start[g];
   int tau = p.grp_tau0[g] + (j - p.t_eff) + 1;
   float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
-  size_t nemb = (size_t)p.dm.A * p.dm.E;
-  float *th = p.params + (size_t)g * p.P, *m = p.m + (size_t)g * p.P, *v = p.v + (size_t)g * p.P;
-  const float *gr = p.grad + (size_t)g * p.P;
-  long long *acc = p.demb_acc + (size_t)g * nemb;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < p.P; i += (size_t)gridDim.x * blockDim.x) {
-    float gi;
-    if (i < nemb) {
-      gi = (float)((double)acc[i] * (1.0 / kEmbFix));
-      acc[i] = 0;
-    } else {
-      gi = gr[i];
-    }
-    if (p.optimizer == PMKLC_ADAM) {
-      float t = th[i], mm = m[i], vv = v[i];
-      adam_one(t, mm, vv, gi, p.lr, bc1, bc2);
-      th[i] = t;
-      m[i] = mm;
-      v[i] = vv;
-    } else {
-      th[i] -= p.lr * gi;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    float ga = alpha_grad(p, T, g);
-    if (threadIdx.x != 0) return;
-    p.dalpha_grp[g] = ga;
-    if (p.optimizer == PMKLC_ADAM) {
-      float t = p.alpha[g], mm = p.alpha_m[g], vv = p.alpha_v[g];
-      adam_one(t, mm, vv, ga, p.lr, bc1, bc2);
-      p.alpha[g] = t;
-      p.alpha_m[g] = mm;
-      p.alpha_v[g] = vv;
-    } else {
-      p.alpha[g] -= p.lr * ga;
-    }
-  }
+  p.dalpha_grp[g] = ga;
+  float t[4] = {p.alpha[g], 0, 0, 0}, m[4] = {p.alpha_m[g], 0, 0, 0}, v[4] = {p.alpha_v[g], 0, 0, 0},
+        gg[4] = {ga, 0, 0, 0};
+  adam4(t, m, v, gg, p.lr, bc1, bc2, p.optimizer == PMKLC_ADAM);
+  p.alpha[g] = t[0];
+  p.alpha_m[g] = m[0];
+  p.alpha_v[g] = v[0];
 }
 
 __global__ void smp_copy_kernel(Plan p, const int *pairs, int n_pairs) {
@@ -482,12 +530,18 @@ void launch_backward(const Plan &p, int T, cudaStream_t st) {
 }
 
 void launch_update(const Plan &p, int T, cudaStream_t st) {
-  unsigned gx = (unsigned)((p.P + 1023) / 1024);
-  if (gx > 64) gx = 64;
-  // Adam: read w, m, v, grad (16 B) and write w, m, v (12 B) per parameter of every training group
+  // Adam: read w, m, v, grad (16 B) and write w, m, v (12 B) per parameter of every training
+  // group (+2 B for the BF16 copy); the embedding part reads/clears 8-byte accumulators instead
   const double nemb = (double)p.dm.A * p.dm.E;
-  ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * 28.0 + nemb * 12.0), st);
-  update_kernel<<<dim3(gx, p.G), 256, 0, st>>>(p, T);
+  const double per = p.wbf ? 30.0 : 28.0;
+  {
+    ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * per + nemb * 12.0), st);
+    size_t nq = (size_t)p.G * ((p.P + 3) / 4);
+    size_t grid = (nq + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    opt_stream_kernel<<<(unsigned)grid, 256, 0, st>>>(p, T);
+  }
+  alpha_update_kernel<<<p.G, 32, 0, st>>>(p, T);
 }
 
 void launch_backward_update(const Plan &p, int T, cudaStream_t st) {

@@ -46,9 +46,30 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 
 __device__ __forceinline__ bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-constexpr int STG = 3;  // cp.async pipeline depth
 constexpr int ASZ = TBM * SKC > TBK * SMC ? TBM * SKC : TBK * SMC;
 constexpr int BSZ = TBN * SKC > TBK * SMC ? TBN * SKC : TBK * SMC;
+constexpr int kMaxCtxStaged = 128;
+constexpr bool kPrefetchEpi = false;  // pull the epilogue's optimiser state into L2 during the GEMM
+// true: the optimiser runs inside the weight-gradient GEMM epilogues; false: they store the
+// gradient and one streaming optimiser kernel updates every parameter afterwards
+constexpr bool kFuseOpt = false;  // measured: the streaming optimiser is faster
+
+// Gradient tile (staged in shared memory) to the gradient buffer, four columns per store.
+template <class RowOff>
+__device__ __forceinline__ void store_grad_tile(const Plan &p, int g, int m0, int n0, int M, int N, const float *Cs,
+                                                int ld, RowOff rowoff) {
+  float *gr = p.grad + (size_t)g * p.P;
+  for (int q = threadIdx.x; q < TBM * (TBN / 4); q += TTH) {
+    int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
+    if (r >= M || c >= N) continue;
+    size_t o = rowoff(r) + c;
+    const float *src = Cs + rl * ld + cl;
+    if (c + 3 < N && (((size_t)g * p.P + o) & 3) == 0)
+      *reinterpret_cast<float4 *>(gr + o) = make_float4(src[0], src[1], src[2], src[3]);
+    else
+      for (int e = 0; e < 4 && c + e < N; ++e) gr[o + e] = src[e];
+  }
+}  // context tokens per row staged in shared memory (HiddenB)
 __device__ const unsigned short kOneBfBits = 0x3F80;  // BF16 1.0: the "ones" entry of a bias-gradient row
 __device__ const uint4 kZero16 = {0u, 0u, 0u, 0u};  // source of zero-filled async copies
 
@@ -113,13 +134,20 @@ __device__ __forceinline__ void stage_cc(bf16 *S, int c0, int k0, int C, int Cv,
 // 32x32 block of the 64x64 tile (2 x 4 mma.sync m16n8k16 per 16 of K).  The accumulation order
 // of an output element does not depend on its tile position.
 template <class Op>
+constexpr int tgemm_smem() {
+  constexpr int stage = Op::kStages * (ASZ + BSZ) * 2, tile = TBM * (TBN + 4) * 4;
+  return (stage > tile ? stage : tile) + TBM * Op::kTokSlots * 2;
+}
+
+template <class Op>
 __global__ void __launch_bounds__(TTH) tgemm_kernel(Op op) {
-  constexpr int STAGE_BYTES = STG * (ASZ + BSZ) * 2;
-  constexpr int TILE_BYTES = TBM * (TBN + 4) * 4;
-  __shared__ __align__(128) unsigned char smem[STAGE_BYTES > TILE_BYTES ? STAGE_BYTES : TILE_BYTES];
+  constexpr int STG = Op::kStages;
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ long long mbase[TBM];
   bf16 *As = reinterpret_cast<bf16 *>(smem);
   bf16 *Bs = As + STG * ASZ;
+  constexpr int stage_bytes = STG * (ASZ + BSZ) * 2, tile_bytes = TBM * (TBN + 4) * 4;
+  uint16_t *toks = reinterpret_cast<uint16_t *>(smem + (stage_bytes > tile_bytes ? stage_bytes : tile_bytes));
   const int z = blockIdx.z;
   if (!op.active(z)) return;
   const int M = op.M(z), N = op.N(z), K = op.K(z);
@@ -129,6 +157,11 @@ __global__ void __launch_bounds__(TTH) tgemm_kernel(Op op) {
   const int mw = (warp >> 1) * 32, nw = (warp & 1) * 32;
   if (tid < TBM) mbase[tid] = m0 + tid < M ? op.mrow_base(z, m0 + tid) : -1;
   __syncthreads();
+  if constexpr (Op::kTokSlots > 0) {  // context tokens of the tile's rows, staged once
+    op.stage_tokens(toks, mbase, z);
+    __syncthreads();
+  }
+  if constexpr (Op::kTileEpi && kPrefetchEpi) op.prefetch_epi(z, m0, n0, M, N);  // overlap with the GEMM
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -136,12 +169,13 @@ __global__ void __launch_bounds__(TTH) tgemm_kernel(Op op) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  const int nk = (K + TBK - 1) / TBK;
+  const int kb = op.kbeg(z);  // first K of this CTA (split-K ops), a multiple of TBK
+  const int nk = (K - kb + TBK - 1) / TBK;
 #pragma unroll
   for (int s = 0; s < STG - 1; ++s) {
     if (s < nk) {
-      op.stage_a(As + s * ASZ, mbase, z, m0, s * TBK, M, K);
-      op.stage_b(Bs + s * BSZ, z, s * TBK, n0, K, N);
+      op.stage_a(As + s * ASZ, mbase, toks, z, m0, kb + s * TBK, M, K);
+      op.stage_b(Bs + s * BSZ, z, kb + s * TBK, n0, K, N);
     }
     cp_commit();
   }
@@ -150,8 +184,8 @@ __global__ void __launch_bounds__(TTH) tgemm_kernel(Op op) {
     __syncthreads();
     const int nxt = kt + STG - 1;
     if (nxt < nk) {
-      op.stage_a(As + (nxt % STG) * ASZ, mbase, z, m0, nxt * TBK, M, K);
-      op.stage_b(Bs + (nxt % STG) * BSZ, z, nxt * TBK, n0, K, N);
+      op.stage_a(As + (nxt % STG) * ASZ, mbase, toks, z, m0, kb + nxt * TBK, M, K);
+      op.stage_b(Bs + (nxt % STG) * BSZ, z, kb + nxt * TBK, n0, K, N);
     }
     cp_commit();
     const bf16 *Ak = As + (kt % STG) * ASZ, *Bk = Bs + (kt % STG) * BSZ;
@@ -222,15 +256,25 @@ template <class Op>
 void run_tgemm(const Op &op, int Mmax, int Nmax, int Z, cudaStream_t st) {
   if (Mmax <= 0 || Nmax <= 0 || Z <= 0) return;
   dim3 grid((Mmax + TBM - 1) / TBM, (Nmax + TBN - 1) / TBN, Z);
-  tgemm_kernel<Op><<<grid, TTH, 0, st>>>(op);
+  constexpr int smem = tgemm_smem<Op>();
+  static bool attr = false;  // one attribute call per kernel instantiation and process
+  if (!attr) {
+    cudaFuncSetAttribute(tgemm_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  tgemm_kernel<Op><<<grid, TTH, smem, st>>>(op);
 }
 
 // ---- ops -----------------------------------------------------------------------------------
 struct BBase {
   static constexpr bool kTileEpi = false;
+  static constexpr int kStages = 3, kTokSlots = 0;
   Plan p;
   int T;
   __device__ void epi_tile(int, int, int, int, int, const float *, int) const {}
+  __device__ void prefetch_epi(int, int, int, int, int) const {}
+  __device__ int kbeg(int) const { return 0; }
+  __device__ void stage_tokens(uint16_t *, const long long *, int) const {}
   __device__ int nrows(int g) const { return p.grp_lane_off[g + 1] - p.grp_lane_off[g]; }
   __device__ int row(int g, int r) const { return p.grp_lane_off[g] + r; }
   __device__ long long target_pos(int g, int r) const {
@@ -247,17 +291,31 @@ struct BBase {
   __device__ const bf16 *wb(int g) const { return p.wbf + (size_t)g * p.P; }
 };
 
-// h = relu(X W1 + b1); z < G: dynamic model of group z, z >= G: static model for group z - G
+// Partial sums of h = X W1 over K-slices: z = (model*G + g)*S + slice (model 0 dynamic, 1 static);
+// the slices are summed in order by hidden_reduce_kernel, which adds b1, applies relu and stores
+// BF16 h.  Splitting K gives enough CTAs to hide the gather and weight-stream latency.
 struct HiddenB : BBase {
   static constexpr bool kAKc = true, kBKc = false;
-  __device__ bool stat(int z) const { return z >= p.G; }
+  float *part;  // [2][S][NL][Hmax] partial sums
+  int hmax;
+  __device__ int zz(int z) const { return z / kHiddenSplit; }
+  __device__ int slice(int z) const { return z % kHiddenSplit; }
+  __device__ bool stat(int z) const { return zz(z) >= p.G; }
+  __device__ int grp(int z) const { return zz(z) % p.G; }
   __device__ const Dims &d(int z) const { return stat(z) ? p.st : p.dm; }
-  __device__ const bf16 *w(int z) const { return stat(z) ? p.static_bf : wb(z); }
-  __device__ bool active(int z) const { return group_trains(p, T, z % p.G); }
-  __device__ int M(int z) const { return nrows(z % p.G); }
+  __device__ const bf16 *w(int z) const { return stat(z) ? p.static_bf : wb(grp(z)); }
+  __device__ bool active(int z) const { return group_trains(p, T, grp(z)); }
+  __device__ int M(int z) const { return nrows(grp(z)); }
   __device__ int N(int z) const { return d(z).H; }
-  __device__ int K(int z) const { return d(z).K1(); }
-  __device__ void stage_a(bf16 *S, const long long *mb, int z, int m0, int k0, int M, int K) const {
+  __device__ int kper(int z) const {
+    int k = d(z).K1();
+    return ((k + kHiddenSplit - 1) / kHiddenSplit + TBK - 1) / TBK * TBK;
+  }
+  __device__ int kbeg(int z) const { return min(d(z).K1(), slice(z) * kper(z)); }
+  __device__ int K(int z) const { return min(d(z).K1(), (slice(z) + 1) * kper(z)); }
+  __device__ long long mrow_base(int z, int r) const { return target_pos(grp(z), r); }
+  __device__ void stage_a(bf16 *S, const long long *mb, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     const bf16 *wz = w(z);
     const Dims &D = d(z);
     stage_kc(
@@ -273,12 +331,30 @@ struct HiddenB : BBase {
     stage_cc(S, n0, k0, N, N, K, [&](int, int k, int c) -> const bf16 * { return w1 + (size_t)k * N + c; });
   }
   __device__ void epi2(const long long *, int z, int r, int, int c, float a0, float a1, int N) const {
-    const float *b1 = (stat(z) ? p.static_params : p.params + (size_t)z * p.P) + d(z).off_b1();
-    bf16 *h = (stat(z) ? p.hs_b : p.hd_b) + (size_t)row(z % p.G, r) * N;
-    if (c < N) h[c] = __float2bfloat16_rn(fmaxf(a0 + b1[c], 0.f));
-    if (c + 1 < N) h[c + 1] = __float2bfloat16_rn(fmaxf(a1 + b1[c + 1], 0.f));
+    float *o = part + (((size_t)(stat(z) ? 1 : 0) * kHiddenSplit + slice(z)) * p.NL + row(grp(z), r)) * hmax;
+    if (c < N) o[c] = a0;
+    if (c + 1 < N) o[c + 1] = a1;
   }
 };
+
+// h = relu(sum_slices + b1) -> BF16, for the predicted rows of every active group and model.
+__global__ void hidden_reduce_kernel(Plan p, int T, const float *part, int hmax) {
+  const int model = blockIdx.y;  // 0 dynamic, 1 static
+  const Dims &D = model ? p.st : p.dm;
+  const int H = D.H;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < (size_t)p.NL * H;
+       w += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(w / H), c = (int)(w - (size_t)r * H);
+    const int g = p.lane_grp[r];
+    if (!row_pred(p, T, r, g)) continue;
+    float acc = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < kHiddenSplit; ++sl)
+      acc += part[(((size_t)model * kHiddenSplit + sl) * p.NL + r) * hmax + c];
+    const float *b1 = (model ? p.static_params : p.params + (size_t)g * p.P) + D.off_b1();
+    (model ? p.hs_b : p.hd_b)[(size_t)r * H + c] = __float2bfloat16_rn(fmaxf(acc + b1[c], 0.f));
+  }
+}
 
 struct LogitsB : BBase {
   static constexpr bool kAKc = true, kBKc = false;
@@ -288,7 +364,8 @@ struct LogitsB : BBase {
   __device__ int M(int z) const { return nrows(z % p.G); }
   __device__ int N(int z) const { return d(z).A; }
   __device__ int K(int z) const { return d(z).H; }
-  __device__ void stage_a(bf16 *S, const long long *mb, int z, int m0, int k0, int M, int K) const {
+  __device__ void stage_a(bf16 *S, const long long *mb, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     const bf16 *h = stat(z) ? p.hs_b : p.hd_b;
     const int g = z % p.G;
     stage_kc(
@@ -316,7 +393,8 @@ struct DhB : BBase {
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.H; }
   __device__ int K(int) const { return p.dm.A; }
-  __device__ void stage_a(bf16 *S, const long long *mb, int z, int m0, int k0, int M, int K) const {
+  __device__ void stage_a(bf16 *S, const long long *mb, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     stage_kc(
         S, m0, k0, M, K,
         [&](int rl, int m, int k) -> const bf16 * {
@@ -359,21 +437,48 @@ __device__ __forceinline__ void opt_apply(const Plan &p, int g, size_t i, float 
 template <class RowOff>
 __device__ __forceinline__ void opt_tile(const Plan &p, int g, int m0, int n0, int M, int N, const float *Cs, int ld,
                                          float bc1, float bc2, RowOff rowoff) {
-  float *th = p.params + (size_t)g * p.P, *mm = p.m + (size_t)g * p.P, *vv = p.v + (size_t)g * p.P;
-  __nv_bfloat16 *wb = p.wbf + (size_t)g * p.P;
-  for (int q = threadIdx.x; q < TBM * (TBN / 4); q += TTH) {
-    int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
-    if (r >= M || c >= N) continue;
-    size_t o = rowoff(r) + c;
-    const float *gr = Cs + rl * ld + cl;
-    if (c + 3 < N && (((size_t)g * p.P + o) & 3) == 0) {
-      float4 t = *reinterpret_cast<const float4 *>(th + o);
-      float4 a = *reinterpret_cast<const float4 *>(mm + o);
-      float4 b = *reinterpret_cast<const float4 *>(vv + o);
-      float tt[4] = {t.x, t.y, t.z, t.w}, ma[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
+  float *__restrict__ th = p.params + (size_t)g * p.P;
+  float *__restrict__ mm = p.m + (size_t)g * p.P;
+  float *__restrict__ vv = p.v + (size_t)g * p.P;
+  __nv_bfloat16 *__restrict__ wb = p.wbf + (size_t)g * p.P;
+  const bool adam = p.optimizer == PMKLC_ADAM;
+  constexpr int NQ = TBM * (TBN / 4) / TTH;  // float4 groups per thread (8)
+  constexpr int BATCH = 4;                   // loads of 4 groups issued before any store
+#pragma unroll
+  for (int q0 = 0; q0 < NQ; q0 += BATCH) {
+    float4 t4[BATCH], m4[BATCH], v4[BATCH];
+    size_t off[BATCH];
+    bool vec[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      int q = threadIdx.x + TTH * (q0 + u);
+      int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
+      bool in = r < M && c < N;
+      off[u] = in ? rowoff(r) + c : 0;
+      vec[u] = in && c + 3 < N && (((size_t)g * p.P + off[u]) & 3) == 0;
+      if (vec[u]) {
+        t4[u] = *reinterpret_cast<const float4 *>(th + off[u]);
+        if (adam) {
+          m4[u] = *reinterpret_cast<const float4 *>(mm + off[u]);
+          v4[u] = *reinterpret_cast<const float4 *>(vv + off[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      int q = threadIdx.x + TTH * (q0 + u);
+      int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
+      if (r >= M || c >= N) continue;
+      const float *gr = Cs + rl * ld + cl;
+      if (!vec[u]) {
+        for (int e = 0; e < 4 && c + e < N; ++e) opt_apply(p, g, off[u] + e, gr[e], bc1, bc2);
+        continue;
+      }
+      float tt[4] = {t4[u].x, t4[u].y, t4[u].z, t4[u].w};
+      float ma[4] = {m4[u].x, m4[u].y, m4[u].z, m4[u].w}, vb[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        if (p.optimizer == PMKLC_ADAM) {
+        if (adam) {
           ma[e] = 0.9f * ma[e] + 0.1f * gr[e];
           vb[e] = 0.999f * vb[e] + 0.001f * gr[e] * gr[e];
           tt[e] -= p.lr * (ma[e] / bc1) / (sqrtf(vb[e] / bc2) + 1e-8f);
@@ -381,17 +486,29 @@ __device__ __forceinline__ void opt_tile(const Plan &p, int g, int m0, int n0, i
           tt[e] -= p.lr * gr[e];
         }
       }
-      *reinterpret_cast<float4 *>(th + o) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-      if (p.optimizer == PMKLC_ADAM) {
-        *reinterpret_cast<float4 *>(mm + o) = make_float4(ma[0], ma[1], ma[2], ma[3]);
-        *reinterpret_cast<float4 *>(vv + o) = make_float4(vb[0], vb[1], vb[2], vb[3]);
+      *reinterpret_cast<float4 *>(th + off[u]) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+      if (adam) {
+        *reinterpret_cast<float4 *>(mm + off[u]) = make_float4(ma[0], ma[1], ma[2], ma[3]);
+        *reinterpret_cast<float4 *>(vv + off[u]) = make_float4(vb[0], vb[1], vb[2], vb[3]);
       }
       __nv_bfloat162 lo = __floats2bfloat162_rn(tt[0], tt[1]), hi = __floats2bfloat162_rn(tt[2], tt[3]);
-      uint2 pk = make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
-      *reinterpret_cast<uint2 *>(wb + o) = pk;
-    } else {
-      for (int e = 0; e < 4 && c + e < N; ++e) opt_apply(p, g, o + e, gr[e], bc1, bc2);
+      *reinterpret_cast<uint2 *>(wb + off[u]) =
+          make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
     }
+  }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
+
+// L2 prefetch of the optimiser state (w, m, v) under a 64 x 64 parameter tile: one 128-byte line
+// per (row, half row, array), i.e. 3 per thread.
+template <class RowOff>
+__device__ __forceinline__ void prefetch_tile(const Plan &p, int g, int m0, int n0, int M, int N, RowOff rowoff) {
+  const float *arr[3] = {p.params + (size_t)g * p.P, p.m + (size_t)g * p.P, p.v + (size_t)g * p.P};
+  for (int q = threadIdx.x; q < TBM * 2 * 3; q += TTH) {
+    int a = q / (TBM * 2), rem = q - a * TBM * 2, rl = rem >> 1, half = rem & 1;
+    int r = m0 + rl, c = n0 + half * 32;
+    if (r < M && c < N) prefetch_l2(arr[a] + rowoff(r) + c);
   }
 }
 
@@ -409,7 +526,8 @@ struct DW2B : BBase {
   __device__ int N(int) const { return p.dm.A; }
   __device__ int K(int z) const { return nrows(z); }
   __device__ long long mrow_base(int, int) const { return 0; }
-  __device__ void stage_a(bf16 *S, const long long *, int z, int m0, int k0, int M, int K) const {
+  __device__ void stage_a(bf16 *S, const long long *, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     const int H = p.dm.H;
     stage_cc(S, m0, k0, M, H, K, [&](int, int r, int i) -> const bf16 * {
       if (target_pos(z, r) < 0) return nullptr;
@@ -422,13 +540,19 @@ struct DW2B : BBase {
     });
   }
   __device__ void epi2(const long long *, int, int, int, int, float, float, int) const {}
+  __device__ size_t rowoff(int i, int N) const { return i < p.dm.H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2(); }
+  __device__ void prefetch_epi(int z, int m0, int n0, int M, int N) const {
+    prefetch_tile(p, z, m0, n0, M, N, [&](int i) { return rowoff(i, N); });
+  }
   __device__ void epi_tile(int z, int m0, int n0, int M, int N, const float *Cs, int ld) const {
     float bc1, bc2;
     tau_bc(p, T, z, bc1, bc2);
     const int H = p.dm.H;
-    opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, [&](int i) -> size_t {
-      return i < H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2();
-    });
+    auto ro = [&](int i) -> size_t { return i < H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2(); };
+    if (kFuseOpt)
+      opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, ro);
+    else
+      store_grad_tile(p, z, m0, n0, M, N, Cs, ld, ro);
   }
 };
 
@@ -439,7 +563,8 @@ struct DXB : BBase {
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
-  __device__ void stage_a(bf16 *S, const long long *mb, int z, int m0, int k0, int M, int K) const {
+  __device__ void stage_a(bf16 *S, const long long *mb, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     stage_kc(
         S, m0, k0, M, K,
         [&](int rl, int m, int k) -> const bf16 * {
@@ -475,7 +600,8 @@ struct DW1B : BBase {
   __device__ int N(int) const { return p.dm.H; }
   __device__ int K(int z) const { return nrows(z); }
   __device__ long long mrow_base(int, int) const { return 0; }
-  __device__ void stage_a(bf16 *S, const long long *, int z, int m0, int k0, int M, int K) const {
+  __device__ void stage_a(bf16 *S, const long long *, const uint16_t *, int z, int m0, int k0, int M,
+                          int K) const {
     const int KX = p.dm.K1(), E = p.dm.E;
     const bf16 *wz = wb(z);
     stage_cc(S, m0, k0, M, (E % 8 == 0) ? KX : 0, K, [&](int, int r, int i) -> const bf16 * {
@@ -490,40 +616,75 @@ struct DW1B : BBase {
     });
   }
   __device__ void epi2(const long long *, int, int, int, int, float, float, int) const {}
+  __device__ size_t rowoff(int i, int N) const {
+    return i < p.dm.K1() ? p.dm.off_w1() + (size_t)i * N : p.dm.off_b1();
+  }
+  __device__ void prefetch_epi(int z, int m0, int n0, int M, int N) const {
+    prefetch_tile(p, z, m0, n0, M, N, [&](int i) { return rowoff(i, N); });
+  }
   __device__ void epi_tile(int z, int m0, int n0, int M, int N, const float *Cs, int ld) const {
     float bc1, bc2;
     tau_bc(p, T, z, bc1, bc2);
     const int KX = p.dm.K1();
-    opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, [&](int i) -> size_t {
-      return i < KX ? p.dm.off_w1() + (size_t)i * N : p.dm.off_b1();
-    });
+    auto ro = [&](int i) -> size_t { return i < KX ? p.dm.off_w1() + (size_t)i * N : p.dm.off_b1(); };
+    if (kFuseOpt)
+      opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, ro);
+    else
+      store_grad_tile(p, z, m0, n0, M, N, Cs, ld, ro);
   }
 };
 
-// Embedding rows and alpha: optimiser step from the fixed-point embedding gradient.
+// Embedding rows and alpha: optimiser step from the fixed-point embedding gradient.  Each thread
+// owns up to two consecutive parameters and issues all its loads before any store.
 __global__ void emb_update_kernel(Plan p, int T) {
   int g = blockIdx.y;
   if (!group_trains(p, T, g)) return;
   float bc1, bc2;
   tau_bc(p, T, g, bc1, bc2);
-  size_t nemb = (size_t)p.dm.A * p.dm.E;
-  long long *acc = p.demb_acc + (size_t)g * nemb;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nemb; i += (size_t)gridDim.x * blockDim.x) {
-    float gi = (float)((double)acc[i] * (1.0 / kEmbFix));
-    acc[i] = 0;
-    opt_apply(p, g, p.dm.off_emb() + i, gi, bc1, bc2);
+  const size_t nemb = (size_t)p.dm.A * p.dm.E;
+  long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
+  const float *__restrict__ th = p.params + (size_t)g * p.P + p.dm.off_emb();
+  const float *__restrict__ mm = p.m + (size_t)g * p.P + p.dm.off_emb();
+  const float *__restrict__ vv = p.v + (size_t)g * p.P + p.dm.off_emb();
+  for (size_t i0 = 2 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i0 < nemb;
+       i0 += 2 * (size_t)gridDim.x * blockDim.x) {
+    int n = i0 + 1 < nemb ? 2 : 1;
+    long long a[2];
+    float t[2], m[2], v[2];
+    for (int u = 0; u < n; ++u) {
+      a[u] = acc[i0 + u];
+      t[u] = th[i0 + u];
+      m[u] = mm[i0 + u];
+      v[u] = vv[i0 + u];
+    }
+    for (int u = 0; u < n; ++u) {
+      acc[i0 + u] = 0;
+      float gi = (float)((double)a[u] * (1.0 / kEmbFix));
+      size_t o = (size_t)g * p.P + p.dm.off_emb() + i0 + u;
+      float tt = t[u];
+      if (p.optimizer == PMKLC_ADAM) {
+        float m2 = 0.9f * m[u] + 0.1f * gi;
+        float v2 = 0.999f * v[u] + 0.001f * gi * gi;
+        p.m[o] = m2;
+        p.v[o] = v2;
+        tt -= p.lr * (m2 / bc1) / (sqrtf(v2 / bc2) + 1e-8f);
+      } else {
+        tt -= p.lr * gi;
+      }
+      p.params[o] = tt;
+      p.wbf[o] = __float2bfloat16_rn(tt);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {
     float ga = alpha_grad(p, T, g);
     if (threadIdx.x != 0) return;
     p.dalpha_grp[g] = ga;
     if (p.optimizer == PMKLC_ADAM) {
-      const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-      float mm = b1 * p.alpha_m[g] + (1.f - b1) * ga;
-      float vv = b2 * p.alpha_v[g] + (1.f - b2) * ga * ga;
-      p.alpha_m[g] = mm;
-      p.alpha_v[g] = vv;
-      p.alpha[g] -= p.lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+      float m2 = 0.9f * p.alpha_m[g] + 0.1f * ga;
+      float v2 = 0.999f * p.alpha_v[g] + 0.001f * ga * ga;
+      p.alpha_m[g] = m2;
+      p.alpha_v[g] = v2;
+      p.alpha[g] -= p.lr * (m2 / bc1) / (sqrtf(v2 / bc2) + 1e-8f);
     } else {
       p.alpha[g] -= p.lr * ga;
     }
@@ -551,7 +712,11 @@ void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
   {
     double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
     ProfScope ps("fwd_hidden_bf16", fl, 0, st);
-    run_tgemm(HiddenB{{p, T}}, p.Mmax, Hmax, Z, st);
+    HiddenB op{{p, T}, p.hpart, Hmax};
+    run_tgemm(op, p.Mmax, Hmax, Z * kHiddenSplit, st);
+    size_t n = (size_t)p.NL * Hmax, grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    hidden_reduce_kernel<<<dim3((unsigned)grid, p.use_static ? 2 : 1), 256, 0, st>>>(p, T, p.hpart, Hmax);
   }
   double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static ? 2.0 * R * p.st.H * p.st.A : 0.0);
   ProfScope ps("fwd_logits_bf16", fl, 0, st);
@@ -577,8 +742,12 @@ void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st) {
     ProfScope ps("bwd_dw1_adam_bf16", 2.0 * R * p.dm.K1() * p.dm.H, Gt * (p.dm.K1() + 1.0) * p.dm.H * 26.0, st);
     run_tgemm(DW1B{{p, T}}, p.dm.K1() + 1, p.dm.H, p.G, st);
   }
-  unsigned gx = (unsigned)(((size_t)p.dm.A * p.dm.E + 1023) / 1024);
-  if (gx > 32) gx = 32;
+  if (!kFuseOpt) {
+    launch_update(p, T, st);
+    return;
+  }
+  unsigned gx = (unsigned)(((size_t)p.dm.A * p.dm.E + 511) / 512);
+  if (gx > 256) gx = 256;
   ProfScope ps("emb_update_bf16", 0, Gt * (double)p.dm.A * p.dm.E * 30.0, st);
   emb_update_kernel<<<dim3(gx, p.G), 256, 0, st>>>(p, T);
 }
