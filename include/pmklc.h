@@ -217,6 +217,23 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
 /* CRC-32 (IEEE 802.3, reflected, as zlib) of n device bytes. */
 int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
 
+/*
+ * The same CRC-32 computed without allocating any device memory (the paper has
+ * no counterpart: this is a library service).  For callers that cannot call
+ * cudaMalloc: processes whose device memory is handed out entirely by another
+ * framework's pool allocator, and latency-sensitive loops that must not pay for
+ * an allocation.  Its scratch is a fixed array in the library's device memory
+ * (about 256 KiB, kept on every device that loads the library until the
+ * process exits), so n is limited to 256 MiB plus up to 4110 bytes of unaligned
+ * head and ragged tail; larger inputs return PMKLC_EINVAL before touching any
+ * memory.  The first call on a device looks up the array's device address once
+ * (with that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; nothing in it
+ * must start at zero, but calls that overlap on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller.
+ */
+int pmklc_crc32_noalloc(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
+
 /* Last run's statistics (per thread): compressed payload split and timings. */
 typedef struct {
   uint64_t net_blocks, count_blocks;

@@ -79,6 +79,7 @@ _sigs = {
     "pmklc_train_step": ([_cfgp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
                           _vp], _i),
     "pmklc_crc32": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
+    "pmklc_crc32_noalloc": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
     "pmklc_init_model": ([_u32, _u32, _u32, _u32, _u64, _vp], _i),
     "pmklc_train_model": ([_vp, _sz, _cfgp, _u32, _vp, _vp], _i),
@@ -269,6 +270,14 @@ def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:
     crc = ctypes.c_uint32()
     _check(lib.pmklc_crc32(_ptr(d_data), d_data.numel() if n is None else n, ctypes.byref(crc), _stream(stream)),
            "pmklc_crc32")
+    return crc.value
+
+
+def pmklc_crc32_noalloc(d_data, n: int | None = None, stream=None) -> int:
+    """CRC-32 of device bytes without any device allocation (fixed library scratch, inputs up to 256 MiB)."""
+    crc = ctypes.c_uint32()
+    _check(lib.pmklc_crc32_noalloc(_ptr(d_data), d_data.numel() if n is None else n, ctypes.byref(crc),
+                                   _stream(stream)), "pmklc_crc32_noalloc")
     return crc.value
 
 

@@ -7,6 +7,7 @@
 // bases are read as bytes (they are HBM-bound streams of <= 8 bytes per token).
 #include <stdio.h>
 
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -275,3 +276,79 @@ int crc32_device(const uint8_t *d_all, size_t n_all, uint32_t *crc, cudaStream_t
 }
 
 }  // namespace pmklc
+
+namespace pmklc {
+
+// ---------------------------------------------------------------------------
+// CRC-32 without any device allocation.
+//
+// Its scratch (one register per 4 KiB chunk, the three zero-byte matrices and the result word)
+// lives in a file-scope device array of fixed size instead of cudaMallocAsync memory, for
+// callers that cannot allocate: a process whose device memory is handed out entirely by another
+// framework's pool allocator, or a latency-sensitive loop that must not pay for an allocation.
+// The array holds kNoAllocCrcChunks chunk registers, i.e. inputs up to 256 MiB (+ 15 head bytes
+// and up to 4095 tail bytes); every device that loads the library keeps it (about 256 KiB) until
+// the process exits.  All calls share it and it keeps the last call's contents; nothing in it
+// needs to start at zero (each call writes every slot it reads), but calls that overlap on the
+// GPU (different streams, or host threads) race on it and must be serialised by the caller.
+
+namespace {
+constexpr long long kNoAllocCrcChunks = 65536;
+__device__ __align__(256) uint32_t g_crc_scratch[kNoAllocCrcChunks + 96 + 1];
+
+constexpr int kMaxDevices = 64;
+uint32_t *g_crc_scratch_addr[kMaxDevices];  // device address of g_crc_scratch, per device
+std::mutex g_crc_scratch_mu;
+
+// Set-up, once per device with that device current: the host-side name of the array is a
+// stand-in, not a device address, so the kernels get the address cudaGetSymbolAddress returns.
+int crc_scratch_addr(uint32_t **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PMKLC_ECUDA;
+  std::lock_guard<std::mutex> lock(g_crc_scratch_mu);
+  if (!g_crc_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_crc_scratch) != cudaSuccess || !p) return PMKLC_ECUDA;
+    g_crc_scratch_addr[dev] = static_cast<uint32_t *>(p);
+  }
+  *out = g_crc_scratch_addr[dev];
+  return PMKLC_OK;
+}
+}  // namespace
+
+}  // namespace pmklc
+
+extern "C" int pmklc_crc32_noalloc(const uint8_t *d_all, size_t n_all, uint32_t *crc, void *stream) {
+  using namespace pmklc;
+  if (!crc || (n_all && !d_all)) return PMKLC_EINVAL;
+  size_t head = (16 - (reinterpret_cast<uintptr_t>(d_all) & 15)) & 15;
+  if (head > n_all) head = n_all;
+  const uint8_t *d_data = d_all + head;
+  size_t n = n_all - head;
+  long long n_chunks = (long long)(n / kCrcChunk);
+  if (n_chunks > kNoAllocCrcChunks) return PMKLC_EINVAL;  // larger than the fixed scratch
+  uint32_t *scratch = nullptr;
+  int rc = crc_scratch_addr(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  long long per = (n_chunks + kCrcFold - 1) / kCrcFold;
+  if (per == 0) per = 1;
+  long long last = n_chunks - (n_chunks > 0 ? ((n_chunks - 1) / per) * per : 0);
+  uint32_t mats[96];
+  zero_bytes_matrix(kCrcChunk, mats);
+  zero_bytes_matrix((unsigned long long)kCrcChunk * per, mats + 32);
+  zero_bytes_matrix((unsigned long long)kCrcChunk * (last > 0 ? last : 1), mats + 64);
+  uint32_t *d_regs = scratch, *d_mats = scratch + kNoAllocCrcChunks, *d_out = d_mats + 96;
+  PMKLC_CUDA_TRY(cudaMemcpyAsync(d_mats, mats, sizeof(mats), cudaMemcpyHostToDevice, st));
+  if (n_chunks > 0)
+    crc_chunks_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, st>>>(d_data, n_chunks, d_regs);
+  int rest_len = (int)(n - (size_t)n_chunks * kCrcChunk);
+  crc_fold_kernel<<<1, kCrcFold, 0, st>>>(d_all, (int)head, d_regs, n_chunks, per, d_mats,
+                                          d_data + (size_t)n_chunks * kCrcChunk, rest_len, d_out);
+  uint32_t h = 0;
+  PMKLC_CUDA_TRY(cudaMemcpyAsync(&h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  *crc = h;
+  return PMKLC_OK;
+}
