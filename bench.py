@@ -205,10 +205,22 @@ def roofline(prof: dict, pk: dict, pk_kind: str):
 FORMS = {"bf16": 1, "fp32": 0}
 
 
+AUTOTUNE_LANES = (64, 128, 192, 256, 320)  # candidates; the first is the FP32 plain form's setting
+
+
 def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True):
     """Device-resident compress+decompress of the workload: per-step times (CUDA events) + stats."""
     cfg = P.ModelConfig(**kw, static_weights=sw, precision=FORMS[form])
     n = int(w.seq.size)
+    tune = None
+    if form == "bf16":  # the batched form picks its batch size (lanes per block) on a sample, untimed
+        d = torch.from_numpy(w.seq).to(dev)
+        chosen, sizes, tms = P.pmklc_autotune_lanes(d, w.block_lens, cfg, AUTOTUNE_LANES, sample_blocks=8,
+                                                    max_rel_size=0.005)
+        tune = {"lanes_per_block": chosen, "candidates": list(AUTOTUNE_LANES), "sample_bytes": [int(x) for x in sizes],
+                "sample_ms": [round(float(x), 2) for x in tms], "sample": "first 8 blocks, compress only",
+                "rule": "fastest with coded size <= 1.005 x the first candidate's"}
+        del d
     stream = torch.cuda.current_stream()
     d_seq = torch.from_numpy(w.seq).to(dev)
     cap = P.pmklc_compress_bound(n, w.block_lens, cfg)
@@ -249,7 +261,7 @@ def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True):
     P.pmklc_profile_enable(0)
     prof = P.pmklc_profile_read()
     del flush
-    return {"cfg": cfg, "times": times, "launches": launches, "clen": clen, "stats": st1, "prof": prof}
+    return {"cfg": cfg, "times": times, "launches": launches, "clen": clen, "stats": st1, "prof": prof, "tune": tune}
 
 
 def main():
@@ -323,7 +335,8 @@ def main():
                    "bits_per_base": 8 * head["clen"] / n, "compressed_bytes": head["clen"],
                    "net_blocks": st1["net_blocks"], "count_blocks": st1["count_blocks"],
                    "global_steps": st1["global_steps"], "l2": "flushed (256 MB write) before every step",
-                   "static_model": f"seeded random (init seed {STATIC_SEED})"},
+                   "static_model": f"seeded random (init seed {STATIC_SEED})",
+                   "lanes_per_block": head["cfg"].lanes_per_block, "autotune": head["tune"]},
         "e2e": e2e, "gpu_launches": head["launches"], "clocks": clk.summary(), "peaks": pk_kind,
     }
     if "fp32" in results and form != "fp32":

@@ -72,6 +72,9 @@ typedef struct {
                                   (needs lanes_per_block <= 1024); 2: count model only */
   uint64_t seed;               /* seed of the dynamic model's initialisation */
   const float *static_weights; /* host FP32 static parameters (layout above); NULL if unused */
+  uint32_t lane_tokens;        /* 0: a block of l tokens gets min(lanes_per_block, l) lanes; else
+                                  min(lanes_per_block, l, ceil(l / lane_tokens)), so lanes of uneven
+                                  blocks take about the same number of steps */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);
@@ -126,6 +129,19 @@ int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, siz
  */
 int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weights, size_t static_count,
                      void *stream, uint8_t **seq, size_t *n, uint64_t **block_lens, size_t *n_blocks);
+
+/*
+ * Autotuner of the batch size (lanes per block; the paper's bs, §5.8): compresses
+ * the first `sample_blocks` blocks of the device input once per candidate value
+ * (after one untimed warm-up), timing each on `stream`, and picks the fastest
+ * candidate whose coded size is at most (1 + max_rel_size) times the size
+ * coded with candidates[0] (the reference).  cfg->lanes_per_block is set to the
+ * choice; sizes (bytes) and times (ms) per candidate go to the optional arrays.
+ * Errors as pmklc_compress_dev.
+ */
+int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                         size_t sample_blocks, pmklc_model_cfg *cfg, const uint32_t *candidates,
+                         size_t n_candidates, float max_rel_size, void *stream, uint64_t *sizes, float *ms);
 
 /* Upper bound of the container size of pmklc_compress_dev for this input. */
 size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg);

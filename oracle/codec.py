@@ -7,9 +7,11 @@ mixed by Eq. (1), cross-entropy updates by the Backward Controller (Eq. 2),
 data-block partitioning and Step-wise Model Passing (§4.3, Fig. 5).
 
 Readings where the paper is silent (each listed in the design doc):
-  lanes    a block's l tokens are cut into M_b = min(M, l) contiguous lanes,
-           the first (l mod M_b) one token longer (the paper's batch of
-           bs parallel sub-streams, §5.1.4); each lane has its own coder.
+  lanes    a block's l tokens are cut into M_b contiguous lanes, the first
+           (l mod M_b) one token longer (the paper's batch of bs parallel
+           sub-streams, §5.1.4); each lane has its own coder.  M_b = min(M, l),
+           or with a lane length target L: M_b = min(M, l, max(1, ceil(l/L))),
+           so lanes of uneven blocks take about the same number of steps.
   steps    all lanes of a block advance together; at local step j lane r codes
            its j-th token.  Positions j < t_eff (t_eff = the largest context in
            use) are coded with the uniform table and not trained on (§2).
@@ -84,6 +86,7 @@ class Config:
     fallback: int = 1
     seed: int = 42
     variant: int = 0
+    lane_tokens: int = 0
 
     def f32(self, name: str) -> float:
         return float(np.float32(getattr(self, name)))
@@ -108,11 +111,11 @@ class Config:
 # ---------------------------------------------------------------------------
 # lanes and schedule
 
-def lanes(l: int, M: int):
-    """(starts, lengths) of the lanes of a block with l tokens."""
+def lanes(l: int, M: int, L: int = 0):
+    """(starts, lengths) of the lanes of a block with l tokens (M lanes at most, L target tokens per lane)."""
     if l == 0:
         return [], []
-    Mb = min(M, l)
+    Mb = min(M, l) if L <= 0 else min(M, l, max(1, -(-l // L)))
     base, extra = divmod(l, Mb)
     lens = [base + (1 if r < extra else 0) for r in range(Mb)]
     starts = [r * base + min(r, extra) for r in range(Mb)]
@@ -348,7 +351,7 @@ def _prepare(cfg: Config, codes_blocks):
     blocks, tails = [], []
     for codes in codes_blocks:
         tok, tail = tokenize(codes, cfg.s, cfg.k)
-        starts, lens = lanes(tok.size, cfg.lanes_per_block)
+        starts, lens = lanes(tok.size, cfg.lanes_per_block, cfg.lane_tokens)
         blocks.append(_Block(codes.size, tok, starts, lens))
         tails.append(tail)
     return blocks, tails
@@ -398,7 +401,7 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> byte
                        cfg.lanes_per_block, cfg.lr, cfg.alpha_init, cfg.smp_fraction, cfg.seed,
                        static_hash(static_w if cfg.use_static else None), codes.size, len(block_lens),
                        zlib.crc32(bytes(np.asarray(seq, dtype=np.uint8) if isinstance(seq, np.ndarray) else seq)),
-                       cfg.variant, 0)
+                       cfg.variant, cfg.lane_tokens)
     return bytes(head) + bytes(out_hdr) + bytes(payload)
 
 
@@ -411,7 +414,7 @@ def parse_header(data: bytes):
     cfg = Config(s=f[2], k=f[3], use_static=bool(f[4] & 1), fallback=(f[4] >> 1) & 3, precision=f[5],
                  optimizer=f[6], smp_mode=f[7], count_order=f[8], emb_d=f[9], ctx_d=f[10], hid_d=f[11],
                  emb_s=f[12], ctx_s=f[13], hid_s=f[14], lanes_per_block=f[15], lr=f[16], alpha_init=f[17],
-                 smp_fraction=f[18], seed=f[19], variant=f[24])
+                 smp_fraction=f[18], seed=f[19], variant=f[24], lane_tokens=f[25])
     return cfg, {"static_hash": f[20], "n": f[21], "n_blocks": f[22], "crc": f[23]}
 
 
@@ -438,14 +441,14 @@ def decompress(data: bytes, static_w=None) -> bytes:
         tail = unpack_tail(data[pos:pos + nb], tl)
         pos += nb
         sizes = []
-        for _ in range(len(lanes(n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0])):
+        for _ in range(len(lanes(n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block, cfg.lane_tokens)[0])):
             x, pos = read_varint(data, pos)
             sizes.append(x)
         recs.append((n, mode, tail, sizes))
     blocks = []
     for n, mode, tail, sizes in recs:
         l = n_tokens(n, cfg.s, cfg.k)
-        starts, lens = lanes(l, cfg.lanes_per_block)
+        starts, lens = lanes(l, cfg.lanes_per_block, cfg.lane_tokens)
         b = _Block(n, np.zeros(l, dtype=np.int64), starts, lens)
         streams = []
         for x in sizes:

@@ -42,7 +42,7 @@ class CModelCfg(ctypes.Structure):
                 ("optimizer", ctypes.c_uint32), ("lr", ctypes.c_float), ("alpha_init", ctypes.c_float),
                 ("smp_mode", ctypes.c_uint32), ("smp_fraction", ctypes.c_float), ("count_order", ctypes.c_uint32),
                 ("fallback", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("static_weights", ctypes.POINTER(ctypes.c_float))]
+                ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -83,6 +83,7 @@ _sigs = {
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
     "pmklc_init_model": ([_u32, _u32, _u32, _u32, _u64, _vp], _i),
     "pmklc_train_model": ([_vp, _sz, _cfgp, _u32, _vp, _vp], _i),
+    "pmklc_autotune_lanes": ([_vp, _sz, _vp, _sz, _sz, _cfgp, _vp, _sz, ctypes.c_float, _vp, _vp, _vp], _i),
     "pmklc_profile_enable": ([_i], _i),
     "pmklc_profile_read": ([ctypes.POINTER(CKernelProf), _i, ctypes.POINTER(_i)], _i),
 }
@@ -121,6 +122,7 @@ class ModelConfig:
     fallback: int = 1
     seed: int = 42
     static_weights: np.ndarray | None = field(default=None, repr=False)
+    lane_tokens: int = 0
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()
@@ -302,6 +304,23 @@ def pmklc_profile_read() -> dict:
 
 def pmklc_abi_version() -> int:
     return int(lib.pmklc_abi_version())
+
+
+def pmklc_autotune_lanes(d_seq, block_lens, cfg: ModelConfig, candidates, sample_blocks: int = 8,
+                         max_rel_size: float = 0.005, stream=None):
+    """Pick lanes per block (batch size) for `cfg` on a sample of the device input; returns
+    (chosen, sizes, ms) and sets cfg.lanes_per_block."""
+    bl = np.ascontiguousarray(block_lens, dtype=np.uint64)
+    cand = np.ascontiguousarray(candidates, dtype=np.uint32)
+    c = cfg.to_c()
+    sizes = np.zeros(cand.size, dtype=np.uint64)
+    ms = np.zeros(cand.size, dtype=np.float32)
+    _check(lib.pmklc_autotune_lanes(_ptr(d_seq), d_seq.numel(), bl.ctypes.data_as(_vp), bl.size, sample_blocks,
+                                    ctypes.byref(c), cand.ctypes.data_as(_vp), cand.size, max_rel_size,
+                                    _stream(stream), sizes.ctypes.data_as(_vp), ms.ctypes.data_as(_vp)),
+           "pmklc_autotune_lanes")
+    cfg.lanes_per_block = int(c.lanes_per_block)
+    return cfg.lanes_per_block, sizes, ms
 
 
 def pmklc_train_model(seq, cfg: ModelConfig, epochs: int = 1, stream=None) -> np.ndarray:

@@ -142,6 +142,7 @@ struct Cfg {
   int s, k, use_static, precision, optimizer, smp_mode, count_order, fallback;
   Dims dm, st;
   int lanes;
+  int lane_tokens;  // 0: every block gets min(lanes, l) lanes; else min(lanes, l, ceil(l / lane_tokens))
   float lr, alpha0, smp_f;
   uint64_t seed;
   int A() const { return 1 << (2 * k); }
@@ -173,6 +174,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
   o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
   o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
+  o.lane_tokens = (int)c->lane_tokens;
   o.lr = c->lr;
   o.alpha0 = c->alpha_init;
   o.smp_f = c->smp_fraction;
@@ -191,7 +193,14 @@ struct Layout {
   long long n_tok = 0;
 };
 
-void make_layout(const std::vector<unsigned long long> &lens, int s, int k, int M, Layout &L) {
+long long lanes_of(long long l, int M, int lane_tokens) {
+  if (l == 0) return 0;
+  long long m = std::min<long long>(M, l);
+  if (lane_tokens > 0) m = std::min(m, std::max(1LL, (l + lane_tokens - 1) / lane_tokens));
+  return m;
+}
+
+void make_layout(const std::vector<unsigned long long> &lens, int s, int k, int M, int lane_tokens, Layout &L) {
   L.G = (int)lens.size();
   L.base_off.assign(L.G + 1, 0);
   L.tok_off.assign(L.G + 1, 0);
@@ -204,7 +213,7 @@ void make_layout(const std::vector<unsigned long long> &lens, int s, int k, int 
     long long l = n_tokens_of(n, s, k);
     L.base_off[g + 1] = L.base_off[g] + n;
     L.tok_off[g + 1] = L.tok_off[g] + l;
-    int Mb = (int)std::min<long long>(M, l);
+    int Mb = (int)lanes_of(l, M, lane_tokens);
     L.lane_off[g + 1] = L.lane_off[g] + Mb;
     if (Mb > 0) {
       long long base = l / Mb, extra = l % Mb;
@@ -483,7 +492,7 @@ size_t bound_of(const std::vector<unsigned long long> &lens, const Cfg &c) {
   size_t b = kHeader;
   for (unsigned long long n : lens) {
     long long l = n_tokens_of((long long)n, c.s, c.k);
-    long long Mb = std::min<long long>(c.lanes, l);
+    long long Mb = lanes_of(l, c.lanes, c.lane_tokens);
     b += 10 + 1 + 2 + (size_t)Mb * 10 + (size_t)l * 3 + (size_t)Mb * 8;
   }
   return b;
@@ -505,7 +514,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   for (auto x : lens) sum += x;
   if (sum != n) return PMKLC_EINVAL;
   if (out_cap < bound_of(lens, c)) return PMKLC_ENOSPC;
-  make_layout(lens, c.s, c.k, c.lanes, R.L);
+  make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
   make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
   const Layout &L = R.L;
   Arena ar(st);
@@ -616,7 +625,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   put_le<uint32_t>(H, (uint32_t)n_blocks);
   put_le<uint32_t>(H, crc);
   put_le<uint32_t>(H, 0u);  // kernel variant
-  put_le<uint32_t>(H, 0u);
+  put_le<uint32_t>(H, (uint32_t)c.lane_tokens);
   std::vector<unsigned long long> seg;  // (src, dst-relative, len, which)
   unsigned long long pay = 0;
   uint64_t n_net = 0, n_cnt = 0;
@@ -706,6 +715,8 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   P.n = get_le<uint64_t>(h + 56);
   P.n_blocks = get_le<uint32_t>(h + 64);
   P.crc = get_le<uint32_t>(h + 68);
+  c.lane_tokens = (int)get_le<uint32_t>(h + 76);
+  if (c.lane_tokens < 0) return PMKLC_ECORRUPT;
   if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !isfinite(c.lr)) return PMKLC_ECORRUPT;
   return PMKLC_OK;
 }
@@ -733,7 +744,7 @@ int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
     for (long long i = 0; i < tl; ++i) P.tails[(size_t)b * 8 + i] = (h[pos + (i >> 2)] >> (2 * (i & 3))) & 3;
     pos += tbytes;
     long long l = n_tokens_of((long long)nb, c.s, c.k);
-    long long Mb = std::min<long long>(c.lanes, l);
+    long long Mb = lanes_of(l, c.lanes, c.lane_tokens);
     for (long long r = 0; r < Mb; ++r) {
       uint64_t x;
       if (!get_varint(h, len, pos, x) || x > 0xFFFFFFFFull) return PMKLC_ECORRUPT;
@@ -776,7 +787,7 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
     if (!static_weights || static_count != c.st.count()) return PMKLC_EMODEL;
     if (fnv1a(static_weights, static_count * sizeof(float)) != P.shash) return PMKLC_EMODEL;
   }
-  make_layout(P.lens, c.s, c.k, c.lanes, R.L);
+  make_layout(P.lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
   make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
   const Layout &L = R.L;
   Arena ar(st);
@@ -913,6 +924,60 @@ int pmklc_compress_dev(const uint8_t *d_seq, size_t n, const uint64_t *block_len
   return compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, (cudaStream_t)stream, d_out, out_cap, out_len);
 }
 
+int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                         size_t sample_blocks, pmklc_model_cfg *cfg, const uint32_t *candidates, size_t n_candidates,
+                         float max_rel_size, void *stream, uint64_t *sizes, float *ms) {
+  if (!cfg || !candidates || n_candidates == 0 || (n_blocks && !block_lens) || !(max_rel_size >= 0.f))
+    return PMKLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t nb = std::min(n_blocks, std::max<size_t>(sample_blocks, 1));
+  size_t ns = 0;
+  for (size_t b = 0; b < nb; ++b) ns += block_lens[b];
+  if (ns > n) return PMKLC_EINVAL;
+  pmklc_model_cfg trial = *cfg;
+  size_t cap = 0;
+  for (size_t i = 0; i < n_candidates; ++i) {
+    trial.lanes_per_block = candidates[i];
+    cap = std::max(cap, pmklc_compress_bound(ns, block_lens, nb, &trial));
+  }
+  if (cap == 0) return PMKLC_EINVAL;
+  uint8_t *d_out = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_out, cap, st));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = PMKLC_OK, best = -1;
+  std::vector<uint64_t> sz(n_candidates, 0);
+  std::vector<float> tm(n_candidates, 0.f);
+  for (size_t i = 0; i < n_candidates && rc == PMKLC_OK; ++i) {
+    trial.lanes_per_block = candidates[i];
+    size_t len = 0;
+    rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);  // warm-up
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&tm[i], e0, e1);
+    sz[i] = len;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(d_out, st);
+  cudaStreamSynchronize(st);
+  if (rc) return rc;
+  for (size_t i = 0; i < n_candidates; ++i) {
+    bool ok = (double)sz[i] <= (double)sz[0] * (1.0 + (double)max_rel_size);
+    if (ok && (best < 0 || tm[i] < tm[best])) best = (int)i;
+  }
+  cfg->lanes_per_block = candidates[best < 0 ? 0 : best];
+  for (size_t i = 0; i < n_candidates; ++i) {
+    if (sizes) sizes[i] = sz[i];
+    if (ms) ms[i] = tm[i];
+  }
+  return PMKLC_OK;
+}
+
 int pmklc_decompress_dev(const uint8_t *d_in, size_t in_len, const float *static_weights, size_t static_count,
                          void *stream, uint8_t *d_seq, size_t seq_cap, size_t *n) {
   return decompress_dev_impl(d_in, in_len, static_weights, static_count, (cudaStream_t)stream, d_seq, seq_cap, n,
@@ -1015,7 +1080,7 @@ int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, 
   R.c = c;
   // one group holding all training tokens; epochs are consecutive groups chained with f = 1
   std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
-  make_layout(lens, c.s, c.k, c.lanes, R.L);
+  make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
   make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
   Arena ar(st);
   uint8_t *d_seq = ar.alloc<uint8_t>(n);

@@ -34,6 +34,7 @@ CASES = [
     dict(s=4, k=5, lanes_per_block=1),
     dict(lanes_per_block=50),
     dict(s=3, k=6, emb_d=8, ctx_d=6, hid_d=24, lanes_per_block=7, fallback=0),
+    dict(lanes_per_block=40, lane_tokens=30),
 ]
 
 

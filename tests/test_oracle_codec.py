@@ -28,6 +28,7 @@ CASES = [
     dict(optimizer=1, lr=0.05),
     dict(s=4, k=5, lanes_per_block=1),
     dict(lanes_per_block=50),
+    dict(lanes_per_block=40, lane_tokens=30),
 ]
 
 
@@ -66,6 +67,9 @@ def test_lanes_partition():
             assert sum(lens) == l and len(lens) == min(M, l)
             assert all(starts[i] + lens[i] == (starts[i + 1] if i + 1 < len(lens) else l) for i in range(len(lens)))
             assert (max(lens) - min(lens) <= 1) if lens else True
+            for L in [1, 7, 1000]:
+                starts, lens = codec.lanes(l, M, L)
+                assert sum(lens) == l and len(lens) == (0 if l == 0 else min(M, l, max(1, -(-l // L))))
 
 
 def test_smp_child_starts_from_parent_state():
@@ -150,7 +154,7 @@ def _modes(data):
         n, pos = codec.read_varint(data, pos)
         modes.append(data[pos])
         pos += 1 + (codec.tail_len(n, cfg.s, cfg.k) * 2 + 7) // 8
-        for _ in codec.lanes(codec.n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block)[0]:
+        for _ in codec.lanes(codec.n_tokens(n, cfg.s, cfg.k), cfg.lanes_per_block, cfg.lane_tokens)[0]:
             _, pos = codec.read_varint(data, pos)
     return modes
 
