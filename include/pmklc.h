@@ -14,8 +14,9 @@
  *   - Sizes are element counts unless the name says bytes.
  *   - Token arrays are uint16 (k <= 8, so 4^k <= 65536 symbols).
  *   - A model's parameters are one FP32 array in the layout
- *         Emb[A][E] | W1[t*E][H] | b1[H] | W2[H][A] | b2[A]     (A = 4^k)
- *     (row-major), see pmklc_model_count().
+ *         Emb[A][E] | W1t[H][t*E] | b1[H] | W2[H][A] | b2[A]     (A = 4^k)
+ *     (row-major; W1 is stored transposed, row j holding the weights into
+ *     hidden unit j), see pmklc_model_count().
  */
 #ifndef PMKLC_H
 #define PMKLC_H

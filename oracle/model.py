@@ -7,7 +7,8 @@ is the one the measured configurations fix (embedding E, context t, one ReLU
 hidden layer H, 4^k output logits), in place of the paper's BiGRU/Transformer.
 
 Flat parameter layout (float32 storage, one model):
-    Emb [A][E] | W1 [t*E][H] | b1 [H] | W2 [H][A] | b2 [A]
+    Emb [A][E] | W1^T [H][t*E] | b1 [H] | W2 [H][A] | b2 [A]
+(W1 is stored transposed: row j holds the t*E weights into hidden unit j.)
 For a row with context tokens c_0..c_{t-1} (oldest first):
     X   = [Emb[c_0], ..., Emb[c_{t-1}]]            (t*E)
     a   = X W1 + b1,   h = relu(a)                 (H)
@@ -71,7 +72,7 @@ def views(flat: np.ndarray, shape: Shape):
     off = shape.offsets()
     A, E, t, H = shape.A, shape.E, shape.t, shape.H
     get = lambda n: flat[off[n][0]:off[n][1]]
-    return (get("emb").reshape(A, E), get("w1").reshape(t * E, H), get("b1"),
+    return (get("emb").reshape(A, E), get("w1").reshape(H, t * E).T, get("b1"),
             get("w2").reshape(H, A), get("b2"))
 
 

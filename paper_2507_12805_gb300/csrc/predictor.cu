@@ -196,7 +196,7 @@ struct RowBase {
 
 // h = relu(X W1 + b1) for the dynamic (stat = 0) or static (stat = 1) model
 struct HiddenOp : RowBase {
-  static constexpr bool kAKc = true, kBKc = false;
+  static constexpr bool kAKc = true, kBKc = true;
   int stat;
   __device__ const float *w(int g) const { return stat ? p.static_params : p.params + (size_t)g * p.P; }
   __device__ const Dims &d() const { return stat ? p.st : p.dm; }
@@ -216,8 +216,8 @@ struct HiddenOp : RowBase {
         D.E % 4 == 0);
   }
   __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
-    const float *w1 = w(g) + d().off_w1();
-    fetch_cc(f, n0, k0, N, N, K, [&](int, int k, int c) -> const float * { return w1 + (size_t)k * N + c; });
+    const float *w1t = w(g) + d().off_w1();  // B[k][n] = W1t[n][k]
+    fetch_kc(f, n0, k0, N, K, [&](int, int n, int k) -> const float * { return w1t + (size_t)n * K + k; });
   }
   __device__ void epi(const long long *, int g, int r, int, int n, float acc) const {
     float h = fmaxf(acc + w(g)[d().off_b1() + n], 0.f);
@@ -322,7 +322,7 @@ struct DW1Op : RowBase {
   __device__ void epi(const long long *, int g, int i, int, int n, float acc) const {
     float *gr = p.grad + (size_t)g * p.P;
     if (i < p.dm.K1())
-      gr[p.dm.off_w1() + (size_t)i * p.dm.H + n] = acc;
+      gr[p.dm.off_w1() + (size_t)n * p.dm.K1() + i] = acc;  // W1 is stored transposed
     else
       gr[p.dm.off_b1() + n] = acc;
   }
@@ -330,7 +330,7 @@ struct DW1Op : RowBase {
 
 // dX = dh W1^T, scattered into the embedding rows of the context tokens
 struct DXOp : RowBase {
-  static constexpr bool kAKc = true, kBKc = true;
+  static constexpr bool kAKc = true, kBKc = false;
   __device__ int M(int g) const { return nrows(g); }
   __device__ int N() const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
@@ -340,8 +340,8 @@ struct DXOp : RowBase {
     });
   }
   __device__ void fetch_b(int g, int k0, int n0, int K, int N, Frag &f) const {
-    const float *w1 = p.params + (size_t)g * p.P + p.dm.off_w1();  // B[k][i] = W1[i][k]
-    fetch_kc(f, n0, k0, N, K, [&](int, int i, int k) -> const float * { return w1 + (size_t)i * K + k; });
+    const float *w1t = p.params + (size_t)g * p.P + p.dm.off_w1();  // B[h][i] = W1[i][h] = W1t[h][i]
+    fetch_cc(f, n0, k0, N, N, K, [&](int, int h, int i) -> const float * { return w1t + (size_t)h * N + i; });
   }
   __device__ void epi(const long long *mb, int g, int r, int rl, int i, float acc) const {
     long long b = mb[rl];

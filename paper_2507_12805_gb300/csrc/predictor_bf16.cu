@@ -1,16 +1,13 @@
-// Predictor forward/backward/update: the "BF16 batched" form.
+// Predictor forward and backward: the "BF16 batched" form.
 //
 // Same mathematics as predictor.cu (paper §2 steps (3)-(4); MLP predictor
 // X -> relu(X W1 + b1) -> W2, Eq. (1) mixing, Eq. (2) loss), with the
-// contractions on the tensor cores: operands are staged in shared memory as
-// BF16 (weights from per-group BF16 copies of the FP32 master weights,
-// activations converted on load), multiplied with mma.sync m16n8k16 into FP32
-// accumulators.  The optimiser is fused into the weight-gradient epilogues: a
-// CTA owns a complete dW tile (its K runs over all rows of the group), applies
-// Adam/SGD to the FP32 master weight and moments in place and refreshes the
-// BF16 copy, so gradients of W1/b1/W2/b2 never reach memory.  Kernel order within
-// a step (dh, dW2+update, dX, dW1+update, embedding update) guarantees every
-// reader sees the pre-update weights, so one BF16 copy suffices.
+// contractions on the tensor cores: operands are BF16 (weights from per-group
+// BF16 copies of the FP32 master weights, activations stored in BF16 by their
+// producers) streamed into shared memory by a cp.async pipeline and multiplied
+// with mma.sync m16n8k16 into FP32 accumulators.  The weight-gradient GEMMs
+// store FP32 gradient tiles; the shared streaming optimiser (predictor.cu) then
+// updates the FP32 master weights, moments and BF16 copies.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -49,12 +46,9 @@ __device__ __forceinline__ bool al16(const void *p) { return (reinterpret_cast<u
 constexpr int ASZ = TBM * SKC > TBK * SMC ? TBM * SKC : TBK * SMC;
 constexpr int BSZ = TBN * SKC > TBK * SMC ? TBN * SKC : TBK * SMC;
 constexpr int kMaxCtxStaged = 128;
-constexpr bool kPrefetchEpi = false;  // pull the epilogue's optimiser state into L2 during the GEMM
-// true: the optimiser runs inside the weight-gradient GEMM epilogues; false: they store the
-// gradient and one streaming optimiser kernel updates every parameter afterwards
-constexpr bool kFuseOpt = false;  // measured: the streaming optimiser is faster
 
-// Gradient tile (staged in shared memory) to the gradient buffer, four columns per store.
+// Gradient tile [rows m0.. x cols n0..] (staged in shared memory, leading dimension ld) to the
+// gradient buffer: row r of the tile starts at parameter offset rowoff(r); four columns per store.
 template <class RowOff>
 __device__ __forceinline__ void store_grad_tile(const Plan &p, int g, int m0, int n0, int M, int N, const float *Cs,
                                                 int ld, RowOff rowoff) {
@@ -161,7 +155,6 @@ __global__ void __launch_bounds__(TTH) tgemm_kernel(Op op) {
     op.stage_tokens(toks, mbase, z);
     __syncthreads();
   }
-  if constexpr (Op::kTileEpi && kPrefetchEpi) op.prefetch_epi(z, m0, n0, M, N);  // overlap with the GEMM
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -272,7 +265,6 @@ struct BBase {
   Plan p;
   int T;
   __device__ void epi_tile(int, int, int, int, int, const float *, int) const {}
-  __device__ void prefetch_epi(int, int, int, int, int) const {}
   __device__ int kbeg(int) const { return 0; }
   __device__ void stage_tokens(uint16_t *, const long long *, int) const {}
   __device__ int nrows(int g) const { return p.grp_lane_off[g + 1] - p.grp_lane_off[g]; }
@@ -295,7 +287,7 @@ struct BBase {
 // the slices are summed in order by hidden_reduce_kernel, which adds b1, applies relu and stores
 // BF16 h.  Splitting K gives enough CTAs to hide the gather and weight-stream latency.
 struct HiddenB : BBase {
-  static constexpr bool kAKc = true, kBKc = false;
+  static constexpr bool kAKc = true, kBKc = true;
   float *part;  // [2][S][NL][Hmax] partial sums
   int hmax;
   __device__ int zz(int z) const { return z / kHiddenSplit; }
@@ -327,8 +319,10 @@ struct HiddenB : BBase {
         D.E % 8 == 0);
   }
   __device__ void stage_b(bf16 *S, int z, int k0, int n0, int K, int N) const {
-    const bf16 *w1 = w(z) + d(z).off_w1();
-    stage_cc(S, n0, k0, N, N, K, [&](int, int k, int c) -> const bf16 * { return w1 + (size_t)k * N + c; });
+    const bf16 *w1t = w(z) + d(z).off_w1();  // B[k][n] = W1t[n][k]; the row stride is the full K
+    const int KX = d(z).K1();
+    stage_kc(
+        S, n0, k0, N, K, [&](int, int n, int k) -> const bf16 * { return w1t + (size_t)n * KX + k; }, true);
   }
   __device__ void epi2(const long long *, int z, int r, int, int c, float a0, float a1, int N) const {
     float *o = part + (((size_t)(stat(z) ? 1 : 0) * kHiddenSplit + slice(z)) * p.NL + row(grp(z), r)) * hmax;
@@ -415,110 +409,7 @@ struct DhB : BBase {
   }
 };
 
-// Optimiser step on one parameter from its gradient (FP32 master, moments), BF16 copy refreshed.
-__device__ __forceinline__ void opt_apply(const Plan &p, int g, size_t i, float gr, float bc1, float bc2) {
-  float *th = p.params + (size_t)g * p.P, *m = p.m + (size_t)g * p.P, *v = p.v + (size_t)g * p.P;
-  float t = th[i];
-  if (p.optimizer == PMKLC_ADAM) {
-    float mm = 0.9f * m[i] + 0.1f * gr;
-    float vv = 0.999f * v[i] + 0.001f * gr * gr;
-    m[i] = mm;
-    v[i] = vv;
-    t -= p.lr * (mm / bc1) / (sqrtf(vv / bc2) + 1e-8f);
-  } else {
-    t -= p.lr * gr;
-  }
-  th[i] = t;
-  p.wbf[(size_t)g * p.P + i] = __float2bfloat16_rn(t);
-}
-
-// Optimiser over a staged gradient tile: rows m0.. of the parameter matrix whose row i starts at
-// param offset rowoff(i), columns n0..n0+63 (< N).  Four consecutive columns per access.
-template <class RowOff>
-__device__ __forceinline__ void opt_tile(const Plan &p, int g, int m0, int n0, int M, int N, const float *Cs, int ld,
-                                         float bc1, float bc2, RowOff rowoff) {
-  float *__restrict__ th = p.params + (size_t)g * p.P;
-  float *__restrict__ mm = p.m + (size_t)g * p.P;
-  float *__restrict__ vv = p.v + (size_t)g * p.P;
-  __nv_bfloat16 *__restrict__ wb = p.wbf + (size_t)g * p.P;
-  const bool adam = p.optimizer == PMKLC_ADAM;
-  constexpr int NQ = TBM * (TBN / 4) / TTH;  // float4 groups per thread (8)
-  constexpr int BATCH = 4;                   // loads of 4 groups issued before any store
-#pragma unroll
-  for (int q0 = 0; q0 < NQ; q0 += BATCH) {
-    float4 t4[BATCH], m4[BATCH], v4[BATCH];
-    size_t off[BATCH];
-    bool vec[BATCH];
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      int q = threadIdx.x + TTH * (q0 + u);
-      int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
-      bool in = r < M && c < N;
-      off[u] = in ? rowoff(r) + c : 0;
-      vec[u] = in && c + 3 < N && (((size_t)g * p.P + off[u]) & 3) == 0;
-      if (vec[u]) {
-        t4[u] = *reinterpret_cast<const float4 *>(th + off[u]);
-        if (adam) {
-          m4[u] = *reinterpret_cast<const float4 *>(mm + off[u]);
-          v4[u] = *reinterpret_cast<const float4 *>(vv + off[u]);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      int q = threadIdx.x + TTH * (q0 + u);
-      int rl = q / (TBN / 4), cl = (q % (TBN / 4)) * 4, r = m0 + rl, c = n0 + cl;
-      if (r >= M || c >= N) continue;
-      const float *gr = Cs + rl * ld + cl;
-      if (!vec[u]) {
-        for (int e = 0; e < 4 && c + e < N; ++e) opt_apply(p, g, off[u] + e, gr[e], bc1, bc2);
-        continue;
-      }
-      float tt[4] = {t4[u].x, t4[u].y, t4[u].z, t4[u].w};
-      float ma[4] = {m4[u].x, m4[u].y, m4[u].z, m4[u].w}, vb[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (adam) {
-          ma[e] = 0.9f * ma[e] + 0.1f * gr[e];
-          vb[e] = 0.999f * vb[e] + 0.001f * gr[e] * gr[e];
-          tt[e] -= p.lr * (ma[e] / bc1) / (sqrtf(vb[e] / bc2) + 1e-8f);
-        } else {
-          tt[e] -= p.lr * gr[e];
-        }
-      }
-      *reinterpret_cast<float4 *>(th + off[u]) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-      if (adam) {
-        *reinterpret_cast<float4 *>(mm + off[u]) = make_float4(ma[0], ma[1], ma[2], ma[3]);
-        *reinterpret_cast<float4 *>(vv + off[u]) = make_float4(vb[0], vb[1], vb[2], vb[3]);
-      }
-      __nv_bfloat162 lo = __floats2bfloat162_rn(tt[0], tt[1]), hi = __floats2bfloat162_rn(tt[2], tt[3]);
-      *reinterpret_cast<uint2 *>(wb + off[u]) =
-          make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
-    }
-  }
-}
-
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
-
-// L2 prefetch of the optimiser state (w, m, v) under a 64 x 64 parameter tile: one 128-byte line
-// per (row, half row, array), i.e. 3 per thread.
-template <class RowOff>
-__device__ __forceinline__ void prefetch_tile(const Plan &p, int g, int m0, int n0, int M, int N, RowOff rowoff) {
-  const float *arr[3] = {p.params + (size_t)g * p.P, p.m + (size_t)g * p.P, p.v + (size_t)g * p.P};
-  for (int q = threadIdx.x; q < TBM * 2 * 3; q += TTH) {
-    int a = q / (TBM * 2), rem = q - a * TBM * 2, rl = rem >> 1, half = rem & 1;
-    int r = m0 + rl, c = n0 + half * 32;
-    if (r < M && c < N) prefetch_l2(arr[a] + rowoff(r) + c);
-  }
-}
-
-__device__ __forceinline__ void tau_bc(const Plan &p, int T, int g, float &bc1, float &bc2) {
-  int tau = p.grp_tau0[g] + (T - p.grp_start[g] - p.t_eff) + 1;
-  bc1 = p.bc1[tau];
-  bc2 = p.bc2[tau];
-}
-
-// [dW2; db2] = [h 1]^T dz, applied to W2/b2 in the epilogue
+// [dW2; db2] = [h 1]^T dz -> gradient buffer (row H of the tile is the bias gradient)
 struct DW2B : BBase {
   static constexpr bool kAKc = false, kBKc = false, kTileEpi = true;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
@@ -540,25 +431,16 @@ struct DW2B : BBase {
     });
   }
   __device__ void epi2(const long long *, int, int, int, int, float, float, int) const {}
-  __device__ size_t rowoff(int i, int N) const { return i < p.dm.H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2(); }
-  __device__ void prefetch_epi(int z, int m0, int n0, int M, int N) const {
-    prefetch_tile(p, z, m0, n0, M, N, [&](int i) { return rowoff(i, N); });
-  }
   __device__ void epi_tile(int z, int m0, int n0, int M, int N, const float *Cs, int ld) const {
-    float bc1, bc2;
-    tau_bc(p, T, z, bc1, bc2);
     const int H = p.dm.H;
-    auto ro = [&](int i) -> size_t { return i < H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2(); };
-    if (kFuseOpt)
-      opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, ro);
-    else
-      store_grad_tile(p, z, m0, n0, M, N, Cs, ld, ro);
+    store_grad_tile(p, z, m0, n0, M, N, Cs, ld,
+                    [&](int i) -> size_t { return i < H ? p.dm.off_w2() + (size_t)i * N : p.dm.off_b2(); });
   }
 };
 
 // dX = dh W1^T scattered into the embedding rows (fixed-point atomics)
 struct DXB : BBase {
-  static constexpr bool kAKc = true, kBKc = true;
+  static constexpr bool kAKc = true, kBKc = false;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.K1(); }
@@ -573,9 +455,8 @@ struct DXB : BBase {
         true);
   }
   __device__ void stage_b(bf16 *S, int z, int k0, int n0, int K, int N) const {
-    const bf16 *w1 = wb(z) + p.dm.off_w1();  // row i of B^T = W1[i][.]
-    stage_kc(
-        S, n0, k0, N, K, [&](int, int i, int k) -> const bf16 * { return w1 + (size_t)i * K + k; }, true);
+    const bf16 *w1t = wb(z) + p.dm.off_w1();  // B[h][i] = W1[i][h] = W1t[h][i]
+    stage_cc(S, n0, k0, N, N, K, [&](int, int h, int i) -> const bf16 * { return w1t + (size_t)h * N + i; });
   }
   __device__ void one(long long b, int z, int i, float acc) const {
     int pos = i / p.dm.E, e = i - pos * p.dm.E;
@@ -592,7 +473,8 @@ struct DXB : BBase {
   }
 };
 
-// [dW1; db1] = [X 1]^T dh, applied to W1/b1 in the epilogue
+// [dW1; db1] = [X 1]^T dh -> gradient buffer; W1 is stored transposed (W1t[h][i]), so the tile is
+// written column-wise: four consecutive i of one h per store.
 struct DW1B : BBase {
   static constexpr bool kAKc = false, kBKc = false, kTileEpi = true;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
@@ -616,80 +498,29 @@ struct DW1B : BBase {
     });
   }
   __device__ void epi2(const long long *, int, int, int, int, float, float, int) const {}
-  __device__ size_t rowoff(int i, int N) const {
-    return i < p.dm.K1() ? p.dm.off_w1() + (size_t)i * N : p.dm.off_b1();
-  }
-  __device__ void prefetch_epi(int z, int m0, int n0, int M, int N) const {
-    prefetch_tile(p, z, m0, n0, M, N, [&](int i) { return rowoff(i, N); });
-  }
   __device__ void epi_tile(int z, int m0, int n0, int M, int N, const float *Cs, int ld) const {
-    float bc1, bc2;
-    tau_bc(p, T, z, bc1, bc2);
     const int KX = p.dm.K1();
-    auto ro = [&](int i) -> size_t { return i < KX ? p.dm.off_w1() + (size_t)i * N : p.dm.off_b1(); };
-    if (kFuseOpt)
-      opt_tile(p, z, m0, n0, M, N, Cs, ld, bc1, bc2, ro);
-    else
-      store_grad_tile(p, z, m0, n0, M, N, Cs, ld, ro);
+    float *gr = p.grad + (size_t)z * p.P;
+    float *g1t = gr + p.dm.off_w1();
+    for (int q = threadIdx.x; q < TBN * (TBM / 4); q += TTH) {
+      int cl = q / (TBM / 4), rl = (q % (TBM / 4)) * 4, c = n0 + cl, i = m0 + rl;
+      if (c >= N || i >= M) continue;
+      float v[4];
+      for (int e = 0; e < 4; ++e) v[e] = Cs[(rl + e) * ld + cl];
+      float *dst = g1t + (size_t)c * KX + i;
+      if (i + 3 < KX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        for (int e = 0; e < 4 && i + e < M; ++e) {
+          if (i + e < KX)
+            dst[e] = v[e];
+          else
+            gr[p.dm.off_b1() + c] = v[e];  // the bias row
+        }
+      }
+    }
   }
 };
-
-// Embedding rows and alpha: optimiser step from the fixed-point embedding gradient.  Each thread
-// owns up to two consecutive parameters and issues all its loads before any store.
-__global__ void emb_update_kernel(Plan p, int T) {
-  int g = blockIdx.y;
-  if (!group_trains(p, T, g)) return;
-  float bc1, bc2;
-  tau_bc(p, T, g, bc1, bc2);
-  const size_t nemb = (size_t)p.dm.A * p.dm.E;
-  long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
-  const float *__restrict__ th = p.params + (size_t)g * p.P + p.dm.off_emb();
-  const float *__restrict__ mm = p.m + (size_t)g * p.P + p.dm.off_emb();
-  const float *__restrict__ vv = p.v + (size_t)g * p.P + p.dm.off_emb();
-  for (size_t i0 = 2 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i0 < nemb;
-       i0 += 2 * (size_t)gridDim.x * blockDim.x) {
-    int n = i0 + 1 < nemb ? 2 : 1;
-    long long a[2];
-    float t[2], m[2], v[2];
-    for (int u = 0; u < n; ++u) {
-      a[u] = acc[i0 + u];
-      t[u] = th[i0 + u];
-      m[u] = mm[i0 + u];
-      v[u] = vv[i0 + u];
-    }
-    for (int u = 0; u < n; ++u) {
-      acc[i0 + u] = 0;
-      float gi = (float)((double)a[u] * (1.0 / kEmbFix));
-      size_t o = (size_t)g * p.P + p.dm.off_emb() + i0 + u;
-      float tt = t[u];
-      if (p.optimizer == PMKLC_ADAM) {
-        float m2 = 0.9f * m[u] + 0.1f * gi;
-        float v2 = 0.999f * v[u] + 0.001f * gi * gi;
-        p.m[o] = m2;
-        p.v[o] = v2;
-        tt -= p.lr * (m2 / bc1) / (sqrtf(v2 / bc2) + 1e-8f);
-      } else {
-        tt -= p.lr * gi;
-      }
-      p.params[o] = tt;
-      p.wbf[o] = __float2bfloat16_rn(tt);
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    float ga = alpha_grad(p, T, g);
-    if (threadIdx.x != 0) return;
-    p.dalpha_grp[g] = ga;
-    if (p.optimizer == PMKLC_ADAM) {
-      float m2 = 0.9f * p.alpha_m[g] + 0.1f * ga;
-      float v2 = 0.999f * p.alpha_v[g] + 0.001f * ga * ga;
-      p.alpha_m[g] = m2;
-      p.alpha_v[g] = v2;
-      p.alpha[g] -= p.lr * (m2 / bc1) / (sqrtf(v2 / bc2) + 1e-8f);
-    } else {
-      p.alpha[g] -= p.lr * ga;
-    }
-  }
-}
 
 __global__ void to_bf16_kernel(const float *src, bf16 *dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -724,14 +555,13 @@ void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
 }
 
 void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st) {
-  const double R = prof_work().pred_rows, Gt = prof_work().train_groups;
+  const double R = prof_work().pred_rows;
   {
     ProfScope ps("bwd_dh_bf16", 2.0 * R * p.dm.A * p.dm.H, 0, st);
     run_tgemm(DhB{{p, T}}, p.Mmax, p.dm.H, p.G, st);
   }
-  // fused optimiser: read w, m, v (12 B) and write w, m, v, BF16 copy (14 B) per parameter
   {
-    ProfScope ps("bwd_dw2_adam_bf16", 2.0 * R * p.dm.A * p.dm.H, Gt * (p.dm.H + 1.0) * p.dm.A * 26.0, st);
+    ProfScope ps("bwd_dw2_bf16", 2.0 * R * p.dm.A * p.dm.H, 0, st);
     run_tgemm(DW2B{{p, T}}, p.dm.H + 1, p.dm.A, p.G, st);
   }
   {
@@ -739,17 +569,10 @@ void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st) {
     run_tgemm(DXB{{p, T}}, p.Mmax, p.dm.K1(), p.G, st);
   }
   {
-    ProfScope ps("bwd_dw1_adam_bf16", 2.0 * R * p.dm.K1() * p.dm.H, Gt * (p.dm.K1() + 1.0) * p.dm.H * 26.0, st);
+    ProfScope ps("bwd_dw1_bf16", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
     run_tgemm(DW1B{{p, T}}, p.dm.K1() + 1, p.dm.H, p.G, st);
   }
-  if (!kFuseOpt) {
-    launch_update(p, T, st);
-    return;
-  }
-  unsigned gx = (unsigned)(((size_t)p.dm.A * p.dm.E + 511) / 512);
-  if (gx > 256) gx = 256;
-  ProfScope ps("emb_update_bf16", 0, Gt * (double)p.dm.A * p.dm.E * 30.0, st);
-  emb_update_kernel<<<dim3(gx, p.G), 256, 0, st>>>(p, T);
+  launch_update(p, T, st);  // streaming optimiser over every parameter (also refreshes the BF16 copy)
 }
 
 }  // namespace pmklc
