@@ -456,7 +456,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
     }
     if (any_pred) {
       if (bf)
-        launch_backward_update_bf16(R.p, T, st);
+        launch_backward_bf16(R.p, T, st), launch_update(R.p, T, st);
       else
         launch_backward_update(R.p, T, st);
       R.launches += 5;
@@ -1246,8 +1246,6 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
       launch_forward(R.p, T, st);
     cudaMemcpyAsync(d_logits_only, R.p.zm, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
   } else if (bf) {
-    // the BF16 form applies the optimiser inside the gradient GEMMs: no gradient to export
-    if (d_grad) return PMKLC_EINVAL;
     std::vector<unsigned long long> off(rows, 0);
     std::vector<uint32_t> cap(rows, 0);
     R.p.lane_buf_off = ar.upload(off);
@@ -1257,7 +1255,9 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     if (ar.failed) return PMKLC_ENOMEM;
     launch_forward_bf16(R.p, T, st);
     launch_mixcode(R.p, T, st);
-    launch_backward_update_bf16(R.p, T, st);
+    launch_backward_bf16(R.p, T, st);
+    if (d_grad) launch_export_grad(R.p, d_grad, st);
+    launch_update(R.p, T, st);  // also forms dalpha of every group
     if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
     prof_stop_sampling();
   } else {
@@ -1276,9 +1276,11 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     if (d_dalpha) cudaMemcpyAsync(d_dalpha, R.p.dalpha_grp, sizeof(float) * G, cudaMemcpyDeviceToDevice, st);
   }
   prof_stop_sampling();
+  int h_err = 0;
+  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
   PMKLC_CUDA_TRY(cudaGetLastError());
-  return PMKLC_OK;
+  return h_err ? err_to_rc(h_err) : PMKLC_OK;
 }
 
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,

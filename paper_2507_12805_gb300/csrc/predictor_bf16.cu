@@ -537,6 +537,10 @@ void launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st) {
 }
 
 void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
+  if (tc_supported(p)) {
+    launch_forward_tc(p, T, st);
+    return;
+  }
   const double R = prof_work().pred_rows;
   const int Z = p.use_static ? 2 * p.G : p.G;
   const int Hmax = p.use_static ? max(p.dm.H, p.st.H) : p.dm.H;
@@ -554,7 +558,11 @@ void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
   run_tgemm(LogitsB{{p, T}}, p.Mmax, p.dm.A, Z, st);
 }
 
-void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st) {
+void launch_backward_bf16(const Plan &p, int T, cudaStream_t st) {
+  if (tc_supported(p)) {
+    launch_backward_tc(p, T, st);
+    return;
+  }
   const double R = prof_work().pred_rows;
   {
     ProfScope ps("bwd_dh_bf16", 2.0 * R * p.dm.A * p.dm.H, 0, st);
@@ -572,7 +580,6 @@ void launch_backward_update_bf16(const Plan &p, int T, cudaStream_t st) {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * p.dm.K1() * p.dm.H, 0, st);
     run_tgemm(DW1B{{p, T}}, p.dm.K1() + 1, p.dm.H, p.G, st);
   }
-  launch_update(p, T, st);  // streaming optimiser over every parameter (also refreshes the BF16 copy)
 }
 
 }  // namespace pmklc
