@@ -455,10 +455,12 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     if (any_pred) {
-      if (bf)
-        launch_backward_bf16(R.p, T, st), launch_update(R.p, T, st);
-      else
+      if (bf) {
+        launch_backward_bf16(R.p, T, st);
+        launch_update(R.p, T, st);
+      } else {
         launch_backward_update(R.p, T, st);
+      }
       R.launches += 5;
     }
   }

@@ -126,6 +126,28 @@ __device__ __forceinline__ float alpha_grad(const Plan &p, int T, int g) {
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
+// One optimiser step of n parameters (paper §2 step 4; Adam with beta 0.9 / 0.999, eps 1e-8 and
+// bias corrections bc1 = 1 - 0.9^tau, bc2 = 1 - 0.999^tau, else plain SGD), in registers.
+template <int n>
+__device__ __forceinline__ void adam_n(float *t, float *m, float *v, const float *g, float lr, float bc1, float bc2,
+                                       bool adam) {
+#pragma unroll
+  for (int e = 0; e < n; ++e) {
+    if (adam) {
+      m[e] = 0.9f * m[e] + 0.1f * g[e];
+      v[e] = 0.999f * v[e] + 0.001f * g[e] * g[e];
+      t[e] -= lr * (m[e] / bc1) / (sqrtf(v[e] / bc2) + 1e-8f);
+    } else {
+      t[e] -= lr * g[e];
+    }
+  }
+}
+
+// Update count tau of group g at global step T (1-based).
+__device__ __forceinline__ int group_tau(const Plan &p, int T, int g) {
+  return p.grp_tau0[g] + (T - p.grp_start[g] - p.t_eff) + 1;
+}
+
 // Fixed point scale of the embedding gradient accumulators (integer adds are order-free,
 // so the sum is deterministic; resolution 2^-40, range +-2^23).
 constexpr double kEmbFix = 1099511627776.0;  // 2^40

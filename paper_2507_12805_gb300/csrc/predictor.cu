@@ -358,20 +358,6 @@ struct DXOp : RowBase {
 // gradient comes from `grad` (W1, b1, W2, b2) or from the fixed-point embedding accumulators
 // (Emb, zeroed on the way); all loads of a group are issued before its stores.  The FP32
 // master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.
-__device__ __forceinline__ void adam4(float (&t)[4], float (&m)[4], float (&v)[4], const float (&g)[4], float lr,
-                                      float bc1, float bc2, bool adam) {
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    if (adam) {
-      m[e] = 0.9f * m[e] + 0.1f * g[e];
-      v[e] = 0.999f * v[e] + 0.001f * g[e] * g[e];
-      t[e] -= lr * (m[e] / bc1) / (sqrtf(v[e] / bc2) + 1e-8f);
-    } else {
-      t[e] -= lr * g[e];
-    }
-  }
-}
-
 __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
   const size_t P = p.P, nq = (P + 3) / 4, nemb = (size_t)p.dm.A * p.dm.E;
   const bool adam = p.optimizer == PMKLC_ADAM;
@@ -380,8 +366,7 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
     const int g = (int)(w / nq);
     if (!group_trains(p, T, g)) continue;
     const size_t i0 = (w - (size_t)g * nq) * 4, base = (size_t)g * P;
-    const int j = T - p.grp_start[g];
-    const int tau = p.grp_tau0[g] + (j - p.t_eff) + 1;
+    const int tau = group_tau(p, T, g);
     const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
     float *__restrict__ th = p.params + base;
     float *__restrict__ mm = p.m + base;
@@ -407,7 +392,7 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
         float4 d = *reinterpret_cast<const float4 *>(gr + i0);
         gg[0] = d.x, gg[1] = d.y, gg[2] = d.z, gg[3] = d.w;
       }
-      adam4(t, m, v, gg, p.lr, bc1, bc2, adam);
+      adam_n<4>(t, m, v, gg, p.lr, bc1, bc2, adam);
       *reinterpret_cast<float4 *>(th + i0) = make_float4(t[0], t[1], t[2], t[3]);
       if (adam) {
         *reinterpret_cast<float4 *>(mm + i0) = make_float4(m[0], m[1], m[2], m[3]);
@@ -427,7 +412,7 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
         } else {
           g1[0] = gr[i];
         }
-        adam4(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
+        adam_n<1>(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
         th[i] = t1[0];
         if (adam) mm[i] = m1[0], vv[i] = v1[0];
         if (p.wbf) p.wbf[base + i] = __float2bfloat16_rn(t1[0]);
@@ -448,7 +433,7 @@ __global__ void alpha_update_kernel(Plan p, int T) {
   p.dalpha_grp[g] = ga;
   float t[4] = {p.alpha[g], 0, 0, 0}, m[4] = {p.alpha_m[g], 0, 0, 0}, v[4] = {p.alpha_v[g], 0, 0, 0},
         gg[4] = {ga, 0, 0, 0};
-  adam4(t, m, v, gg, p.lr, bc1, bc2, p.optimizer == PMKLC_ADAM);
+  adam_n<1>(t, m, v, gg, p.lr, bc1, bc2, p.optimizer == PMKLC_ADAM);
   p.alpha[g] = t[0];
   p.alpha_m[g] = m[0];
   p.alpha_v[g] = v[0];

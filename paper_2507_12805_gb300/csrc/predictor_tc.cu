@@ -6,12 +6,21 @@
 //   backward  dh = (dz W2^T) * [h > 0]
 //             dW2 = h^T dz,  dX = dh W1^T (scattered into the embedding rows),  dW1 = X^T dh
 //             db2 = sum of dz, db1 = sum of dh over the predicted rows (fixed-order column sums)
-// after which the streaming optimiser (predictor.cu) updates every parameter and refreshes the
-// BF16 copy.
+// The weight-gradient epilogues store the gradient; the streaming optimiser of predictor.cu then
+// updates every parameter (spread over all SMs at full occupancy it outruns an optimiser applied
+// in these epilogues, whose four-to-eight warps per SM keep too few accesses in flight).
 //
-// Operand majors follow the stored layouts: W1 is stored transposed (W1t[h][i], K-major for the
-// hidden layer), W2 as [h][a]; activations are [row][feature].  The weight-gradient GEMMs reduce
-// over lanes, so both their operands are MN-major.
+// Operand majors follow the stored layouts, so every dense operand is one TMA box per stage:
+// W1 is stored transposed (W1t[h][i]: K-major for the hidden layer, MN-major for dX), W2 as
+// [h][a] (MN-major for the logits, K-major for dh), activations as [lane row][feature] (K-major
+// where rows are lanes, MN-major where the GEMM reduces over lanes).  The context vectors X are
+// gathered from the embedding table (copied to shared memory when it fits).  The lanes a group
+// predicts at a step are a prefix of its lanes (lanes differ by at most one token), so the
+// lane-reducing GEMMs run over that prefix and zero the rows past it in their last K stage.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "tcgemm.cuh"
 
 namespace pmklc {
@@ -20,17 +29,31 @@ namespace {
 
 using tc::bf16;
 
-// Per-tile shared data.  Row-tiled GEMMs (rows = lanes): the target position of each of the 128
-// tile rows (-1: no prediction) and, when the op gathers embeddings, each row's t context tokens.
-// Lane-reducing GEMMs (K = lanes): the target position of every lane of the group and, for dW1,
-// its context tokens.
-constexpr int kRowMetaTok = tc::kRows * 8;  // byte offset of the token block in a row-tile meta
-__host__ __device__ inline size_t row_meta_bytes(int t) { return kRowMetaTok + (size_t)tc::kRows * t * 2; }
-__host__ __device__ inline size_t lane_meta_bytes(int lanes, int t) { return (size_t)lanes * 8 + (size_t)lanes * t * 2; }
+constexpr size_t kTableMax = 48 * 1024;  // largest embedding table copied to shared memory
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Per-tile shared data ("meta").  Row tiles (rows = lanes): [target of each of the 128 rows]
+// [their t context tokens][embedding table].  Lane reductions: [target of every lane][their
+// context tokens][embedding table].
+struct MetaLayout {
+  int nrows;   // 128 for row tiles, Mmax for lane reductions
+  int t;       // context tokens per row kept (0: none)
+  int table;   // bytes of embedding table kept (0: none)
+  __host__ __device__ size_t tok_off() const { return align16((size_t)nrows * 8); }
+  __host__ __device__ size_t tab_off() const { return tok_off() + align16((size_t)nrows * t * 2); }
+  __host__ __device__ size_t bytes() const { return tab_off() + (size_t)table; }
+};
 
 struct TBase {
+  static constexpr bool kFinish = false;
   Plan p;
   int T;
+  MetaLayout ml;
+  __device__ void finish(uint8_t *, int) const {}
+  __device__ void epilogue(const uint8_t *, int, int, int, int, const float *) const {}
+  __device__ bool row_active(const uint8_t *, int, int, int) const { return false; }
+  __device__ void emit(const uint8_t *, int, int, int, int, float) const {}
   __device__ int *err() const { return p.err; }
   __device__ int nrows(int g) const { return p.grp_lane_off[g + 1] - p.grp_lane_off[g]; }
   __device__ int row(int g, int r) const { return p.grp_lane_off[g] + r; }
@@ -39,50 +62,70 @@ struct TBase {
     if (!row_pred(p, T, rw, g)) return -1;
     return p.lane_tok[rw] + (T - p.grp_start[g]);
   }
+  __device__ int npred(int g) const { return live_lanes(p, g, T - p.grp_start[g]); }
   __device__ const bf16 *wb(int g) const { return p.wbf + (size_t)g * p.P; }
-  // row-tile meta of group g's rows m0..m0+127, with t context tokens per row (t = 0: none)
-  __device__ void prep_rows(uint8_t *meta, int g, int m0, int t) const {
-    long long *tp = reinterpret_cast<long long *>(meta);
-    for (int i = threadIdx.x; i < tc::kRows; i += tc::kThreads) {
-      const int r = m0 + i;
-      tp[i] = r < nrows(g) ? target_pos(g, r) : -1;
+  __device__ const long long *tp(const uint8_t *meta) const { return reinterpret_cast<const long long *>(meta); }
+  __device__ const uint16_t *tk(const uint8_t *meta) const {
+    return reinterpret_cast<const uint16_t *>(meta + ml.tok_off());
+  }
+  __device__ const bf16 *table(const uint8_t *meta) const {
+    return reinterpret_cast<const bf16 *>(meta + ml.tab_off());
+  }
+  // targets of rows r0 .. r0 + n - 1 of group g (-1 past the group or for rows that predict
+  // nothing), their t context tokens and the embedding table emb (A x E) if ml.table.  The table
+  // arrives by one bulk copy that overlaps the target and token loads.
+  __device__ void fill(uint8_t *meta, const MetaLayout &ml, int g, int r0, int n, const bf16 *emb, int AE) const {
+    __shared__ __align__(8) uint64_t tbar;
+    long long *tpw = reinterpret_cast<long long *>(meta);
+    const bool copy = emb != nullptr && AE > 0 && ml.table >= AE * 2;
+    if (copy && threadIdx.x == 0) {
+      const uint32_t bar = tc::sa(&tbar);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+      tc::expect_tx(bar, (uint32_t)(AE * 2));
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                       tc::sa(meta + ml.tab_off())),
+                   "l"(emb), "r"(AE * 2), "r"(bar)
+                   : "memory");
     }
-    if (t <= 0) return;
-    __syncthreads();
-    uint16_t *tk = reinterpret_cast<uint16_t *>(meta + kRowMetaTok);
-    for (int i = threadIdx.x; i < tc::kRows * t; i += tc::kThreads) {
-      const int r = i / t, j = i - r * t;
-      const long long b = tp[r];
-      tk[i] = b >= 0 ? p.tokens[b - t + j] : 0;
-    }
-  }
-  __device__ static long long row_target(const uint8_t *meta, int rl) {
-    return reinterpret_cast<const long long *>(meta)[rl];
-  }
-  __device__ static int row_token(const uint8_t *meta, int rl, int t, int pos) {
-    return reinterpret_cast<const uint16_t *>(meta + kRowMetaTok)[rl * t + pos];
-  }
-  // lane meta of every lane of group g, with t context tokens per lane (t = 0: none)
-  __device__ void prep_lanes(uint8_t *meta, int g, int t) const {
     const int L = nrows(g);
-    long long *tp = reinterpret_cast<long long *>(meta);
-    for (int i = threadIdx.x; i < L; i += tc::kThreads) tp[i] = target_pos(g, i);
-    if (t <= 0) return;
+    for (int i = threadIdx.x; i < n; i += tc::kThreads) tpw[i] = r0 + i < L ? target_pos(g, r0 + i) : -1;
     __syncthreads();
-    uint16_t *tk = reinterpret_cast<uint16_t *>(meta + (size_t)p.Mmax * 8);
-    for (int i = threadIdx.x; i < L * t; i += tc::kThreads) {
-      const int r = i / t, j = i - r * t;
-      const long long b = tp[r];
-      tk[i] = b >= 0 ? p.tokens[b - t + j] : 0;
+    if (ml.t > 0) {
+      uint16_t *tkw = reinterpret_cast<uint16_t *>(meta + ml.tok_off());
+      const int t = ml.t, total = n * t;
+      for (int i0 = 0; i0 < total; i0 += 16 * tc::kThreads) {  // sixteen loads in flight per thread
+        uint16_t v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int i = i0 + q * tc::kThreads + threadIdx.x;
+          v[q] = 0;
+          if (i < total) {
+            const int r = i / t;
+            const long long b = tpw[r];
+            if (b >= 0) v[q] = p.tokens[b - t + (i - r * t)];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int i = i0 + q * tc::kThreads + threadIdx.x;
+          if (i < total) tkw[i] = v[q];
+        }
+      }
     }
-  }
-  __device__ static long long lane_target(const uint8_t *meta, int m) {
-    return reinterpret_cast<const long long *>(meta)[m];
-  }
-  __device__ int lane_token(const uint8_t *meta, int m, int t, int pos) const {
-    return reinterpret_cast<const uint16_t *>(meta + (size_t)p.Mmax * 8)[m * t + pos];
+    if (copy && !tc::mbar_wait(tc::sa(&tbar), 0) && threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
   }
 };
+
+// 16 bytes from the shared-memory table or, without one, an async copy from global memory
+__device__ __forceinline__ void put16(uint8_t *dst, const bf16 *tab_s, const bf16 *tab_g, size_t off) {
+  if (tab_s) {
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tab_s + off);
+  } else {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(tab_g + off));
+  }
+}
+__device__ __forceinline__ void zero16(uint8_t *dst) { *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0); }
 
 // z < G: dynamic model of group z; z >= G: static model on group z - G's rows
 struct TwoModels : TBase {
@@ -109,26 +152,69 @@ __device__ __forceinline__ void store8(float *dst, const float *v) {
   reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
 }
 
-// h = relu(X W1 + b1): A = X (gathered, K-major), B = W1t (K-major)
+constexpr tc::TmaOperand kNoTma = {nullptr, 2, 0, 0};
+
+// h = relu(X W1 + b1): A = X gathered (K-major), B = W1t by TMA (K-major)
 struct HiddenT : TwoModels {
-  static constexpr bool kAMN = false, kBMN = false;
+  static constexpr bool kAMN = false, kBMN = false, kTail = false;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 1;
+  CUtensorMap w1[2];  // W1t of the dynamic models (3-D, per group) and of the static model
+  int table[2];       // embedding table kept in shared memory (dynamic, static)
   __device__ int M(int z) const { return nrows(grp(z)); }
   __device__ int N(int z) const { return d(z).H; }
   __device__ int K(int z) const { return d(z).K1(); }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const { prep_rows(meta, grp(z), m0, d(z).t); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int, int k0, int rlim, int klim) const {
-    const Dims &D = d(z);
-    tc::stage_k_gather(dst, rlim, k0, klim, reinterpret_cast<const long long *>(meta),
-                       reinterpret_cast<const uint16_t *>(meta + kRowMetaTok), D.t, D.E, w(z) + D.off_emb());
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    MetaLayout l = ml;
+    l.t = d(z).t;
+    l.table = table[stat(z)] ? d(z).A * d(z).E * 2 : 0;
+    fill(meta, l, grp(z), m0, tc::kRows, w(z) + d(z).off_emb(), d(z).A * d(z).E);
   }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *, int z, int n0, int k0, int R, int rlim, int klim) const {
+  __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w1[stat(z)], stat(z) ? 2 : 3, grp(z), 0}; }
+  __device__ int row_a(int, int) const { return 0; }
+  __device__ int row_b(int, int n0) const { return n0; }
+  // thread: 16-byte chunk c = tid % 8 of rows tid / 8 + 32 i; the 4 table reads are in flight together
+  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int, int k0, int) const {
     const Dims &D = d(z);
-    const bf16 *w1t = w(z) + D.off_w1() + (size_t)n0 * D.K1();
-    const int K1 = D.K1();
-    tc::stage_k_rows(dst, R, rlim, k0, klim, [&](int r) { return w1t + (size_t)r * K1; });
+    MetaLayout l = ml;
+    l.t = D.t;
+    const long long *tpv = reinterpret_cast<const long long *>(meta);
+    const uint16_t *tkv = reinterpret_cast<const uint16_t *>(meta + l.tok_off());
+    const bf16 *tab_s = table[stat(z)] ? reinterpret_cast<const bf16 *>(meta + l.tab_off()) : nullptr;
+    const bf16 *tab_g = w(z) + D.off_emb();
+    const int c = threadIdx.x & 7, k = k0 + 8 * c, r0 = threadIdx.x >> 3;
+    const bool kin = k < D.K1();
+    const int pos = kin ? k / D.E : 0, e = k - pos * D.E;
+    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
+    int off[kPer];
+    bool ok[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int r = r0 + kStep * i;
+      ok[i] = kin && tpv[r] >= 0;
+      off[i] = ok[i] ? (int)tkv[r * D.t + pos] * D.E + e : 0;
+    }
+    if (tab_s) {
+      uint4 v[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i)
+        v[i] = ok[i] ? *reinterpret_cast<const uint4 *>(tab_s + off[i]) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) *reinterpret_cast<uint4 *>(tile + tc::sw_k(r0 + kStep * i, c)) = v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        uint8_t *dst = tile + tc::sw_k(r0 + kStep * i, c);
+        if (ok[i])
+          put16(dst, nullptr, tab_g, (size_t)off[i]);
+        else
+          zero16(dst);
+      }
+    }
   }
   __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (row_target(meta, rl) < 0) return;
+    if (tp(meta)[rl] < 0) return;
     const Dims &D = d(z);
     const float *b1 = w32(z) + D.off_b1() + n;
     float x[8];
@@ -138,28 +224,23 @@ struct HiddenT : TwoModels {
   }
 };
 
-// L = h W2 + b2: A = h (K-major), B = W2[h][a] (MN-major)
+// L = h W2 + b2: A = h by TMA (K-major), B = W2[h][a] by TMA (MN-major)
 struct LogitsT : TwoModels {
-  static constexpr bool kAMN = false, kBMN = true;
+  static constexpr bool kAMN = false, kBMN = true, kTail = false;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 0;
+  CUtensorMap h[2], w2[2];
   __device__ int M(int z) const { return nrows(grp(z)); }
   __device__ int N(int z) const { return d(z).A; }
   __device__ int K(int z) const { return d(z).H; }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const { prep_rows(meta, grp(z), m0, 0); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int m0, int k0, int rlim, int klim) const {
-    const int g = grp(z), H = d(z).H;
-    const bf16 *h = (stat(z) ? p.hs_b : p.hd_b) + (size_t)row(g, m0) * H;
-    tc::stage_k_rows(dst, tc::kRows, rlim, k0, klim, [&](int r) -> const bf16 * {
-      return row_target(meta, r) < 0 ? nullptr : h + (size_t)r * H;
-    });
-  }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *, int z, int n0, int k0, int R, int rlim, int klim) const {
-    const Dims &D = d(z);
-    const bf16 *w2 = w(z) + D.off_w2() + (size_t)k0 * D.A + n0;
-    const int A = D.A;
-    tc::stage_mn_rows(dst, R, rlim, klim, [&](int k) { return w2 + (size_t)k * A; });
-  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const { fill(meta, ml, grp(z), m0, tc::kRows, nullptr, 0); }
+  __device__ tc::TmaOperand tma_a(int z) const { return {&h[stat(z)], 2, 0, 0}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w2[stat(z)], stat(z) ? 2 : 3, grp(z), 0}; }
+  __device__ int row_a(int z, int m0) const { return row(grp(z), m0); }
+  __device__ int row_b(int, int n0) const { return n0; }
+  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
   __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (row_target(meta, rl) < 0) return;
+    if (tp(meta)[rl] < 0) return;
     const Dims &D = d(z);
     const float *b2 = w32(z) + D.off_b2() + n;
     float x[8];
@@ -169,117 +250,145 @@ struct LogitsT : TwoModels {
   }
 };
 
-// dh = (dz W2^T) * [h > 0]: A = dz (K-major), B = W2[h][a] read as N = h, K = a (K-major)
+// dh = (dz W2^T) * [h > 0]: A = dz by TMA (K-major), B = W2[h][a] as N = h, K = a (K-major)
 struct DhT : TBase {
-  static constexpr bool kAMN = false, kBMN = false;
+  static constexpr bool kAMN = false, kBMN = false, kTail = false;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 0;
+  CUtensorMap dz, w2;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.H; }
   __device__ int K(int) const { return p.dm.A; }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const { prep_rows(meta, z, m0, 0); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int m0, int k0, int rlim, int klim) const {
-    const int A = p.dm.A;
-    const bf16 *dz = p.dz_b + (size_t)row(z, m0) * A;
-    tc::stage_k_rows(dst, tc::kRows, rlim, k0, klim, [&](int r) -> const bf16 * {
-      return row_target(meta, r) < 0 ? nullptr : dz + (size_t)r * A;
-    });
-  }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *, int z, int n0, int k0, int R, int rlim, int klim) const {
-    const int A = p.dm.A;
-    const bf16 *w2 = wb(z) + p.dm.off_w2() + (size_t)n0 * A;
-    tc::stage_k_rows(dst, R, rlim, k0, klim, [&](int r) { return w2 + (size_t)r * A; });
-  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const { fill(meta, ml, z, m0, tc::kRows, nullptr, 0); }
+  __device__ tc::TmaOperand tma_a(int) const { return {&dz, 2, 0, 0}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w2, 3, z, 0}; }
+  __device__ int row_a(int z, int m0) const { return row(z, m0); }
+  __device__ int row_b(int, int n0) const { return n0; }
+  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
   __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
     const size_t i = (size_t)row(z, m) * p.dm.H + n;
-    const bool ok = row_target(meta, rl) >= 0;
+    const bool ok = tp(meta)[rl] >= 0;  // zeros where nothing is predicted
     uint4 hw = *reinterpret_cast<const uint4 *>(p.hd_b + i);
-    const bf16 *h = reinterpret_cast<const bf16 *>(&hw);
+    const bf16 *hv = reinterpret_cast<const bf16 *>(&hw);
     float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (ok && __bfloat162float(h[j]) > 0.f) ? v[j] : 0.f;
+    for (int j = 0; j < 8; ++j) x[j] = (ok && __bfloat162float(hv[j]) > 0.f) ? v[j] : 0.f;
     *reinterpret_cast<uint4 *>(p.dh_b + i) = pack8(x);
   }
 };
 
-// dW2 = h^T dz over the lanes: M = H, N = A, K = lanes; both operands MN-major
+// dW2 = h^T dz over the predicted lanes: M = H, N = A, K = lanes; both operands MN-major by TMA
 struct DW2T : TBase {
-  static constexpr bool kAMN = true, kBMN = true;
+  static constexpr bool kAMN = true, kBMN = true, kTail = true;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 0;
+  CUtensorMap h, dz;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int) const { return p.dm.H; }
   __device__ int N(int) const { return p.dm.A; }
-  __device__ int K(int z) const { return nrows(z); }
-  __device__ void prepare(uint8_t *meta, int z, int) const { prep_lanes(meta, z, 0); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int m0, int k0, int rlim, int klim) const {
-    const int H = p.dm.H;
-    tc::stage_mn_rows(dst, tc::kRows, rlim, klim, [&](int k) -> const bf16 * {
-      return lane_target(meta, k0 + k) < 0 ? nullptr : p.hd_b + (size_t)row(z, k0 + k) * H + m0;
-    });
-  }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *meta, int z, int n0, int k0, int R, int rlim, int klim) const {
-    const int A = p.dm.A;
-    tc::stage_mn_rows(dst, R, rlim, klim, [&](int k) -> const bf16 * {
-      return lane_target(meta, k0 + k) < 0 ? nullptr : p.dz_b + (size_t)row(z, k0 + k) * A + n0;
-    });
-  }
-  __device__ void epilogue(const uint8_t *, int z, int h, int, int n, const float *v) const {
-    store8(p.grad + (size_t)z * p.P + p.dm.off_w2() + (size_t)h * p.dm.A + n, v);
+  __device__ int K(int z) const { return npred(z); }
+  __device__ void prepare(uint8_t *, int, int) const {}
+  __device__ tc::TmaOperand tma_a(int z) const { return {&h, 2, 0, p.grp_lane_off[z]}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&dz, 2, 0, p.grp_lane_off[z]}; }
+  __device__ int row_a(int, int m0) const { return m0; }
+  __device__ int row_b(int, int n0) const { return n0; }
+  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
+  __device__ void epilogue(const uint8_t *, int z, int h_, int, int n, const float *v) const {
+    store8(p.grad + (size_t)z * p.P + p.dm.off_w2() + (size_t)h_ * p.dm.A + n, v);
   }
 };
 
-// dX = dh W1^T scattered into the embedding rows (fixed-point atomics): A = dh (K-major),
-// B = W1t[h][i] read as N = i, K = h (MN-major)
+// dX = dh W1^T scattered into the embedding rows as fixed-point integers (order-free sums, so the
+// result does not depend on scheduling): A = dh by TMA (K-major), B = W1t[h][i] as N = i, K = h
+// by TMA (MN-major).  The lanes of a warp add consecutive elements of one embedding row.
 struct DXT : TBase {
-  static constexpr bool kAMN = false, kBMN = true;
+  static constexpr bool kAMN = false, kBMN = true, kTail = false;
+  static constexpr int kEpi = 1;
+  static constexpr int kGather = 0;
+  CUtensorMap dh, w1;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const { prep_rows(meta, z, m0, p.dm.t); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int m0, int k0, int rlim, int klim) const {
-    const int H = p.dm.H;
-    const bf16 *dh = p.dh_b + (size_t)row(z, m0) * H;
-    tc::stage_k_rows(dst, tc::kRows, rlim, k0, klim, [&](int r) -> const bf16 * {
-      return row_target(meta, r) < 0 ? nullptr : dh + (size_t)r * H;
-    });
-  }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *, int z, int n0, int k0, int R, int rlim, int klim) const {
-    const int K1 = p.dm.K1();
-    const bf16 *w1t = wb(z) + p.dm.off_w1() + (size_t)k0 * K1 + n0;
-    tc::stage_mn_rows(dst, R, rlim, klim, [&](int k) { return w1t + (size_t)k * K1; });
-  }
-  __device__ void epilogue(const uint8_t *meta, int z, int, int rl, int n, const float *v) const {
-    if (row_target(meta, rl) < 0) return;
-    const int pos = n / p.dm.E, e = n - pos * p.dm.E;  // 8 columns stay inside one embedding row
-    const int tok = row_token(meta, rl, p.dm.t, pos);
-    unsigned long long *acc =
-        reinterpret_cast<unsigned long long *>(p.demb_acc + ((size_t)z * p.dm.A + tok) * p.dm.E + e);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(acc + j, (unsigned long long)__double2ll_rn((double)v[j] * kEmbFix));
+  __device__ void prepare(uint8_t *meta, int z, int m0) const { fill(meta, ml, z, m0, tc::kRows, nullptr, 0); }
+  __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
+  __device__ int row_a(int z, int m0) const { return row(z, m0); }
+  __device__ int row_b(int, int n0) const { return n0; }
+  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
+  __device__ bool row_active(const uint8_t *meta, int, int, int rl) const { return tp(meta)[rl] >= 0; }
+  __device__ void emit(const uint8_t *meta, int z, int, int rl, int n, float v) const {
+    const int pos = n / p.dm.E;
+    const size_t i = ((size_t)z * p.dm.A + tk(meta)[rl * p.dm.t + pos]) * p.dm.E + (n - pos * p.dm.E);
+    atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc) + i,
+              (unsigned long long)__double2ll_rn((double)v * kEmbFix));
   }
 };
 
-// dW1 (stored transposed: dW1t[h][i] = sum over lanes of dh[m][h] X[m][i]): M = H, N = t*E,
-// K = lanes; both operands MN-major
+// dW1 (stored transposed: dW1t[h][i] = sum over predicted lanes of dh[m][h] X[m][i]): M = H,
+// N = t*E, K = lanes; A = dh by TMA (MN-major), B = X gathered (MN-major)
 struct DW1T : TBase {
-  static constexpr bool kAMN = true, kBMN = true;
+  static constexpr bool kAMN = true, kBMN = true, kTail = true;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 2;
+  CUtensorMap dh;
+  int table;
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int) const { return p.dm.H; }
   __device__ int N(int) const { return p.dm.K1(); }
-  __device__ int K(int z) const { return nrows(z); }
-  __device__ void prepare(uint8_t *meta, int z, int) const { prep_lanes(meta, z, p.dm.t); }
-  __device__ void stage_a(uint8_t *dst, const uint8_t *meta, int z, int m0, int k0, int rlim, int klim) const {
-    const int H = p.dm.H;
-    tc::stage_mn_rows(dst, tc::kRows, rlim, klim, [&](int k) -> const bf16 * {
-      return lane_target(meta, k0 + k) < 0 ? nullptr : p.dh_b + (size_t)row(z, k0 + k) * H + m0;
-    });
+  __device__ int K(int z) const { return npred(z); }
+  __device__ void prepare(uint8_t *meta, int z, int) const {
+    fill(meta, ml, z, 0, npred(z), wb(z) + p.dm.off_emb(), p.dm.A * p.dm.E);
   }
-  __device__ void stage_b(uint8_t *dst, const uint8_t *meta, int z, int n0, int k0, int R, int rlim, int klim) const {
-    tc::stage_mn_gather(dst, R, rlim, n0, k0, klim, reinterpret_cast<const long long *>(meta),
-                        reinterpret_cast<const uint16_t *>(meta + (size_t)p.Mmax * 8), p.dm.t, p.dm.E,
-                        wb(z) + p.dm.off_emb());
+  __device__ tc::TmaOperand tma_a(int z) const { return {&dh, 2, 0, p.grp_lane_off[z]}; }
+  __device__ tc::TmaOperand tma_b(int) const { return kNoTma; }
+  __device__ int row_a(int, int m0) const { return m0; }
+  __device__ int row_b(int, int) const { return 0; }
+  // chunk idx = 16 bytes at column n = 8 (idx % (R/8)) of K row idx / (R/8); consecutive threads
+  // take consecutive chunks of a row, four per thread in flight
+  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int n0, int k0, int R) const {
+    const Dims &D = p.dm;
+    const long long *tpv = tp(meta);
+    const uint16_t *tkv = tk(meta);
+    const bf16 *tab_s = table ? this->table_ptr(meta) : nullptr;
+    const bf16 *tab_g = wb(z) + D.off_emb();
+    const int K = npred(z), cpr = R / 8, total = cpr * tc::kBK;
+    for (int i0 = 0; i0 < total; i0 += 4 * tc::kThreads) {
+      int off[4], dsto[4];
+      bool ok[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int idx = i0 + j * tc::kThreads + threadIdx.x;
+        const int n = (idx % cpr) * 8, k = idx / cpr, m = k0 + k;
+        dsto[j] = idx < total ? (int)tc::sw_mn(n, k) : -1;
+        ok[j] = idx < total && m < K && tpv[m] >= 0;
+        const int i = n0 + n, pos = i / D.E;
+        off[j] = ok[j] ? (int)tkv[m * D.t + pos] * D.E + (i - pos * D.E) : 0;
+      }
+      if (tab_s) {
+        uint4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          v[j] = ok[j] ? *reinterpret_cast<const uint4 *>(tab_s + off[j]) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (dsto[j] >= 0) *reinterpret_cast<uint4 *>(tile + dsto[j]) = v[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (dsto[j] < 0) continue;
+          if (ok[j])
+            put16(tile + dsto[j], nullptr, tab_g, (size_t)off[j]);
+          else
+            zero16(tile + dsto[j]);
+        }
+      }
+    }
   }
-  __device__ void epilogue(const uint8_t *, int z, int h, int, int n, const float *v) const {
-    store8(p.grad + (size_t)z * p.P + p.dm.off_w1() + (size_t)h * p.dm.K1() + n, v);
+  __device__ const bf16 *table_ptr(const uint8_t *meta) const { return TBase::table(meta); }
+  __device__ void epilogue(const uint8_t *, int z, int h_, int, int n, const float *v) const {
+    store8(p.grad + (size_t)z * p.P + p.dm.off_w1() + (size_t)h_ * p.dm.K1() + n, v);
   }
 };
 
@@ -311,50 +420,198 @@ __global__ void __launch_bounds__(32 * kBiasSlices) bias_grad_kernel(Plan p, int
   }
 }
 
-constexpr size_t kMaxLaneMeta = 80 * 1024;
+
+// ---- host: tensor maps -----------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// BF16 tensor map with 128-byte swizzle: dims[0] innermost (elements), strides in bytes for the
+// outer dimensions, box {64, box1}
+bool make_map(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides, int box1) {
+  auto fn = encode_fn();
+  if (!fn || !ptr) return false;
+  cuuint64_t d[3], s[2];
+  cuuint32_t box[3] = {64, (cuuint32_t)box1, 1}, es[3] = {1, 1, 1};
+  for (int i = 0; i < rank; ++i) d[i] = dims[i];
+  for (int i = 0; i + 1 < rank; ++i) s[i] = strides[i];
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(ptr), d, s, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Everything the six launches of a plan need: tile widths, shared data sizes and tensor maps.
+struct TcSetup {
+  // key: the plan's buffers and shapes
+  const void *wbf, *static_bf, *hd_b, *hs_b, *dz_b, *dh_b;
+  int G, NL, Mmax, use_static;
+  Dims dm, st;
+  size_t P;
+  bool ok;
+  tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1;
+  MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1;
+  int table_h[2], table_w1;
+  CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn;
+};
+
+bool same_key(const TcSetup &a, const Plan &p) {
+  auto dims_eq = [](const Dims &x, const Dims &y) { return x.A == y.A && x.E == y.E && x.t == y.t && x.H == y.H; };
+  return a.wbf == p.wbf && a.static_bf == p.static_bf && a.hd_b == p.hd_b && a.hs_b == p.hs_b && a.dz_b == p.dz_b &&
+         a.dh_b == p.dh_b && a.G == p.G && a.NL == p.NL && a.Mmax == p.Mmax && a.use_static == p.use_static &&
+         dims_eq(a.dm, p.dm) && (!p.use_static || dims_eq(a.st, p.st)) && a.P == p.P;
+}
+
+bool shapes_ok(const Plan &p) {
+  auto ok = [](const Dims &d) { return d.E % 8 == 0 && d.H % 64 == 0 && d.A % 64 == 0 && d.K1() % 64 == 0; };
+  return p.G > 0 && p.NL > 0 && p.Mmax > 0 && ok(p.dm) && p.P % 8 == 0 && (!p.use_static || ok(p.st));
+}
+
+bool build(TcSetup &S, const Plan &p) {
+  S.wbf = p.wbf, S.static_bf = p.static_bf, S.hd_b = p.hd_b, S.hs_b = p.hs_b, S.dz_b = p.dz_b, S.dh_b = p.dh_b;
+  S.G = p.G, S.NL = p.NL, S.Mmax = p.Mmax, S.use_static = p.use_static, S.dm = p.dm, S.st = p.st, S.P = p.P;
+  S.ok = false;
+  if (!shapes_ok(p) || !encode_fn()) return false;
+  const Dims &D = p.dm, &Sd = p.st;
+  const int Z = p.use_static ? 2 * p.G : p.G;
+  const int tmax = p.use_static ? max(D.t, Sd.t) : D.t;
+  const size_t limit = 220 * 1024;
+  // embedding tables kept in shared memory where they fit
+  S.table_h[0] = (size_t)D.A * D.E * 2 <= kTableMax;
+  S.table_h[1] = p.use_static && (size_t)Sd.A * Sd.E * 2 <= kTableMax;
+  S.table_w1 = S.table_h[0];
+  S.ml_h = {tc::kRows, tmax, (int)max(S.table_h[0] ? (size_t)D.A * D.E * 2 : 0,
+                                       S.table_h[1] ? (size_t)Sd.A * Sd.E * 2 : 0)};
+  S.ml_l = S.ml_dh = {tc::kRows, 0, 0};
+  S.ml_w2 = {0, 0, 0};
+  S.ml_dx = {tc::kRows, D.t, 0};
+  S.ml_w1 = {p.Mmax, D.t, S.table_w1 ? D.A * D.E * 2 : 0};
+  const int Hmax = p.use_static ? max(D.H, Sd.H) : D.H, K1max = p.use_static ? max(D.K1(), Sd.K1()) : D.K1();
+  S.t_h = tc::plan_tiles(p.Mmax, Hmax, K1max, Z, S.ml_h.bytes(), false);
+  S.t_l = tc::plan_tiles(p.Mmax, D.A, Hmax, Z, S.ml_l.bytes());
+  S.t_dh = tc::plan_tiles(p.Mmax, D.H, D.A, p.G, S.ml_dh.bytes());
+  S.t_w2 = tc::plan_tiles(D.H, D.A, p.Mmax, p.G, S.ml_w2.bytes());
+  S.t_dx = tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes());
+  S.t_w1 = tc::plan_tiles(D.H, D.K1(), p.Mmax, p.G, S.ml_w1.bytes());
+  for (const auto &pr : {std::make_pair(S.t_h, S.ml_h.bytes()), std::make_pair(S.t_l, S.ml_l.bytes()),
+                         std::make_pair(S.t_dh, S.ml_dh.bytes()), std::make_pair(S.t_w2, S.ml_w2.bytes()),
+                         std::make_pair(S.t_dx, S.ml_dx.bytes()), std::make_pair(S.t_w1, S.ml_w1.bytes())})
+    if (tc::smem_bytes(pr.first, pr.second) > limit) return false;
+  // per-group weights: [G][P] BF16 with W1t [H][t*E] and W2 [H][A] inside
+  const uint64_t gs = (uint64_t)p.P * 2;
+  bool ok = true;
+  {
+    const uint64_t d[3] = {(uint64_t)D.K1(), (uint64_t)D.H, (uint64_t)p.G}, s[2] = {(uint64_t)D.K1() * 2, gs};
+    ok &= make_map(&S.w1k[0], p.wbf + D.off_w1(), 3, d, s, S.t_h.nt);
+    ok &= make_map(&S.w1mn, p.wbf + D.off_w1(), 3, d, s, 64);
+  }
+  {
+    const uint64_t d[3] = {(uint64_t)D.A, (uint64_t)D.H, (uint64_t)p.G}, s[2] = {(uint64_t)D.A * 2, gs};
+    ok &= make_map(&S.w2mn[0], p.wbf + D.off_w2(), 3, d, s, 64);
+    ok &= make_map(&S.w2k, p.wbf + D.off_w2(), 3, d, s, S.t_dh.nt);
+  }
+  auto act = [&](CUtensorMap *m, const void *ptr, int width, int box1) {
+    const uint64_t d[2] = {(uint64_t)width, (uint64_t)p.NL}, s[1] = {(uint64_t)width * 2};
+    return make_map(m, ptr, 2, d, s, box1);
+  };
+  ok &= act(&S.hk[0], p.hd_b, D.H, tc::kRows);
+  ok &= act(&S.dzk, p.dz_b, D.A, tc::kRows);
+  ok &= act(&S.dhk, p.dh_b, D.H, tc::kRows);
+  ok &= act(&S.hmn, p.hd_b, D.H, 64);
+  ok &= act(&S.dzmn, p.dz_b, D.A, 64);
+  ok &= act(&S.dhmn, p.dh_b, D.H, 64);
+  if (p.use_static) {
+    const uint64_t d1[2] = {(uint64_t)Sd.K1(), (uint64_t)Sd.H}, s1[1] = {(uint64_t)Sd.K1() * 2};
+    ok &= make_map(&S.w1k[1], p.static_bf + Sd.off_w1(), 2, d1, s1, S.t_h.nt);
+    const uint64_t d2[2] = {(uint64_t)Sd.A, (uint64_t)Sd.H}, s2[1] = {(uint64_t)Sd.A * 2};
+    ok &= make_map(&S.w2mn[1], p.static_bf + Sd.off_w2(), 2, d2, s2, 64);
+    ok &= act(&S.hk[1], p.hs_b, Sd.H, tc::kRows);
+  } else {
+    S.w1k[1] = S.w1k[0], S.w2mn[1] = S.w2mn[0], S.hk[1] = S.hk[0];
+  }
+  S.ok = ok;
+  return ok;
+}
+
+std::mutex g_tc_mu;
+TcSetup g_tc;  // the last plan's setup (runs reuse their buffers for every step)
+bool g_tc_valid = false;
+
+bool get_setup(const Plan &p, TcSetup &out) {
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (!g_tc_valid || !same_key(g_tc, p)) {
+    build(g_tc, p);
+    g_tc_valid = true;
+  }
+  out = g_tc;
+  return out.ok;
+}
 
 }  // namespace
 
 bool tc_supported(const Plan &p) {
-  auto ok = [](const Dims &d) { return d.E % 8 == 0 && d.H % 16 == 0 && d.A % 8 == 0; };
-  // the lane-reducing GEMMs keep every lane's target and context tokens in shared memory
-  return ok(p.dm) && p.P % 8 == 0 && (!p.use_static || ok(p.st)) &&
-         lane_meta_bytes(p.Mmax, p.dm.t) <= kMaxLaneMeta && row_meta_bytes(p.use_static ? max(p.dm.t, p.st.t) : p.dm.t) <= kMaxLaneMeta;
+  if (!shapes_ok(p)) return false;
+  TcSetup S;
+  return get_setup(p, S);
 }
 
 void launch_forward_tc(const Plan &p, int T, cudaStream_t st) {
+  TcSetup S;
+  if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
   const int Z = p.use_static ? 2 * p.G : p.G;
   {
     double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
     ProfScope ps("fwd_hidden_bf16", fl, 0, st);
-    tc::launch(HiddenT{{p, T}}, p.Mmax, p.use_static ? max(p.dm.H, p.st.H) : p.dm.H, Z,
-               row_meta_bytes(p.use_static ? max(p.dm.t, p.st.t) : p.dm.t), st);
+    HiddenT op;
+    op.p = p, op.T = T, op.ml = S.ml_h, op.w1[0] = S.w1k[0], op.w1[1] = S.w1k[1];
+    op.table[0] = S.table_h[0], op.table[1] = S.table_h[1];
+    tc::launch(op, p.Mmax, p.use_static ? max(p.dm.H, p.st.H) : p.dm.H, Z, S.t_h, S.ml_h.bytes(), st);
   }
   double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static ? 2.0 * R * p.st.H * p.st.A : 0.0);
   ProfScope ps("fwd_logits_bf16", fl, 0, st);
-  tc::launch(LogitsT{{p, T}}, p.Mmax, p.dm.A, Z, row_meta_bytes(0), st);
+  LogitsT op;
+  op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0], op.w2[1] = S.w2mn[1];
+  tc::launch(op, p.Mmax, p.dm.A, Z, S.t_l, S.ml_l.bytes(), st);
 }
 
 void launch_backward_tc(const Plan &p, int T, cudaStream_t st) {
+  TcSetup S;
+  if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
   const Dims &D = p.dm;
   {
     ProfScope ps("bwd_dh_bf16", 2.0 * R * D.A * D.H, 0, st);
-    tc::launch(DhT{p, T}, p.Mmax, D.H, p.G, row_meta_bytes(0), st);
+    DhT op;
+    op.p = p, op.T = T, op.ml = S.ml_dh, op.dz = S.dzk, op.w2 = S.w2k;
+    tc::launch(op, p.Mmax, D.H, p.G, S.t_dh, S.ml_dh.bytes(), st);
   }
   {
     ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, st);
-    tc::launch(DW2T{p, T}, D.H, D.A, p.G, lane_meta_bytes(p.Mmax, 0), st);
+    DW2T op;
+    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
+    tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), st);
     bias_grad_kernel<<<dim3((D.H + D.A + 31) / 32, p.G), dim3(32, kBiasSlices), 0, st>>>(p, T);
   }
   {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, st);
-    tc::launch(DXT{p, T}, p.Mmax, D.K1(), p.G, row_meta_bytes(D.t), st);
+    DXT op;
+    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
+    tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), st);
   }
   {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);
-    tc::launch(DW1T{p, T}, D.H, D.K1(), p.G, lane_meta_bytes(p.Mmax, D.t), st);
+    DW1T op;
+    op.p = p, op.T = T, op.ml = S.ml_w1, op.dh = S.dhmn, op.table = S.table_w1;
+    tc::launch(op, D.H, D.K1(), p.G, S.t_w1, S.ml_w1.bytes(), st);
   }
 }
 

@@ -1,27 +1,31 @@
 // Grouped GEMM engine on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
 // accumulators in tensor memory.  Used by the BF16 batched form for every predictor GEMM.
 //
-// One CTA of 128 threads computes a 128-row x nt-column tile (nt a multiple of 16, <= 256) of
-// problem z = blockIdx.z over that problem's whole K:
-//   * both operands are staged into shared memory by cp.async, 16 bytes (8 BF16) per copy, in
-//     the canonical no-swizzle layouts of 8-row x 16-byte core matrices.  An operand whose 8
-//     contiguous elements run along K is "K-major", one whose 8 contiguous elements run along M
-//     (or N) is "MN-major"; the op of each GEMM says which, so every operand is read in the
-//     layout it already has in global memory (no transposes);
-//   * stages of 64 K cycle through a ring; one elected thread issues the tcgen05.mma
-//     instructions of a landed stage (M 128, N nt, K 16 each) and commits them to that stage's
-//     mbarrier, which frees the buffer for the copy issued kStages - 1 stages later;
-//   * the epilogue reads the accumulator back with tcgen05.ld: warp w owns tensor-memory lanes
-//     32w..32w+31, i.e. tile rows, and hands the op 8 consecutive columns of one row at a time.
+// One CTA of 256 threads computes a 128-row x nt-column tile (nt a multiple of 64, <= 256) of
+// problem z = blockIdx.z over that problem's whole K, in stages of 64 K:
+//   * dense operands (weights, activations) arrive by TMA (cp.async.bulk.tensor) in the
+//     128-byte-swizzled layout, one bulk copy per 64-wide box, counted on the stage's "full"
+//     mbarrier; operands gathered from an embedding table (the context vectors X) are written
+//     into the same layout by the threads, from a copy of the table in shared memory;
+//   * one thread issues the tcgen05.mma instructions of a landed stage (M 128, N nt, K 16) and
+//     commits them to the stage's "done" mbarrier, which frees the buffer for the TMA issued
+//     stages - 1 iterations later;
+//   * the epilogue reads the accumulator back with tcgen05.ld (warp w owns tensor-memory lanes
+//     32w..32w+31, i.e. tile rows) and hands the op either 8 consecutive columns of a thread's
+//     row or, staged through shared memory, one element per lane with the lanes of a warp on
+//     consecutive columns of one row (for scattered atomics).
 // Every mbarrier wait is bounded; on expiry the CTA sets kErrTimeout in the plan's error word,
-// drains its own copies, frees its tensor memory and returns.
+// waits (bounded) for its bulk copies, frees its tensor memory and returns.
 //
-// Shared-memory layouts of one R x 64 stage (R rows along M or N, 64 along K), byte offsets:
-//   K-major : core matrix (r/8, k/8) at (r/8)*1024 + (k/8)*128, its row r%8 at +16*(r%8);
-//             descriptor LBO = 128 (next core matrix along K), SBO = 1024 (next along M/N)
-//   MN-major: core matrix (r/8, k/8) at (r/8)*128 + (k/8)*16R, its row k%8 at +16*(k%8);
-//             descriptor LBO = 16R (next core matrix along K), SBO = 128 (next along M/N)
+// Shared-memory operand layouts (each tile 1024-byte aligned), 128-byte swizzle: a 16-byte chunk
+// c of a 128-byte row r sits at r*128 + ((c ^ (r % 8)) * 16).
+//   K-major  (R x 64): row r = the 64 K values of M/N index r.  Descriptor: SBO 1024 (8 rows),
+//            layout SWIZZLE_128B; the K=16 step j starts 32j bytes into the row.
+//   MN-major (64 x R): R/64 boxes of 64 K-rows x 128 bytes (64 M/N values), 8 KB apart.
+//            Descriptor: LBO 8192 (next box along M/N), SBO 1024 (next 8 K-rows); the K=16
+//            step j starts 2048j bytes in.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -31,129 +35,123 @@ namespace tc {
 
 using bf16 = __nv_bfloat16;
 constexpr int kRows = 128;             // MMA M: tile rows = tensor-memory lanes
-constexpr int kBK = 64;                // K per pipeline stage
-constexpr int kThreads = 128;          // four warps
+constexpr int kBK = 64;                // K per pipeline stage (one 128-byte swizzle row)
+constexpr int kThreads = 256;          // eight warps: warps w and w + 4 share tensor-memory lanes 32(w % 4)..
+constexpr int kStages = 4;             // most stage buffers of a ring (a launch may use fewer)
 constexpr long kSpinLimit = 1L << 24;  // mbarrier polls before a wait gives up
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  // no swizzle, base offset 0, descriptor version 1
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ const uint4 kZero16 = {0u, 0u, 0u, 0u};  // source of zero-filled copies
-
-// 16-byte async copy; a null source fills zeros
-__device__ __forceinline__ void cp16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa(dst)), "l"(src ? src : &kZero16),
-               "r"(src ? 16 : 0));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long it = 0; it < kSpinLimit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(sa(bar)), "r"(parity));
+        : "r"(bar), "r"(parity));
     if (ok) return true;
   }
   return false;
 }
 
-// Staging of one R x 64 operand tile (R rows along M or N, a multiple of 16) by 128 threads.
-// In both layouts a thread's position along K is fixed for the whole tile, so each routine forms
-// the per-thread part of the address once and then steps over its R/16 rows:
-//   K-major : thread covers k-chunk (tid >> 3) & 7 of rows (tid >> 6) * 8 + (tid & 7) + 16 i;
-//             eight consecutive threads fill one 128-byte core matrix
-//   MN-major: thread covers k = tid & 63 of row-chunks (tid >> 6) * 8 + 16 i
-// rlim / klim are the valid extents of the tile (rows, and K from the stage start k0).
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
 
-// K-major, each row a contiguous run along K: rowp(r) is row r's address at k = 0, or nullptr
-template <class RowPtr>
-__device__ __forceinline__ void stage_k_rows(uint8_t *dst, int R, int rlim, int k0, int klim, RowPtr rowp) {
-  const int kj = (threadIdx.x >> 3) & 7, k = k0 + kj * 8;
-  const bool kin = kj * 8 < klim;
-  for (int r = (threadIdx.x >> 6) * 8 + (threadIdx.x & 7); r < R; r += 16) {
-    const bf16 *p = (kin && r < rlim) ? rowp(r) : nullptr;
-    cp16(dst + (r >> 3) * 1024 + kj * 128 + (r & 7) * 16, p ? p + k : nullptr);
+// TMA box loads into shared memory, completion counted on bar
+__device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap *m, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap *m, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          dst),
+      "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// A dense operand tile by TMA.  K-major: one box {64 K, R rows} at (k0, row0[, grp]).
+// MN-major: R/64 boxes {64 M/N, 64 K} at (mn0 + 64j, kofs + k0[, grp]), 8 KB apart.
+struct TmaOperand {
+  const CUtensorMap *map;
+  int rank;  // 2 or 3
+  int grp;   // third coordinate (rank 3)
+  int kofs;  // MN-major: first K row (a group's first lane in an activation map)
+};
+__device__ __forceinline__ void tma_k_tile(uint32_t dst, const TmaOperand &o, int k0, int row0, uint32_t bar) {
+  if (o.rank == 3)
+    tma3(dst, o.map, k0, row0, o.grp, bar);
+  else
+    tma2(dst, o.map, k0, row0, bar);
+}
+__device__ __forceinline__ void tma_mn_tile(uint32_t dst, const TmaOperand &o, int mn0, int R, int k0, uint32_t bar) {
+  for (int j = 0; j < R / 64; ++j) {
+    if (o.rank == 3)
+      tma3(dst + j * 8192, o.map, mn0 + 64 * j, o.kofs + k0, o.grp, bar);
+    else
+      tma2(dst + j * 8192, o.map, mn0 + 64 * j, o.kofs + k0, bar);
   }
 }
 
-// K-major rows gathered from an embedding table: row r's K run is the concatenation of the
-// E-wide embedding rows of its t context tokens tok[r * t + pos] (E % 8 == 0); rows with
-// tpos[r] < 0 are zero
-__device__ __forceinline__ void stage_k_gather(uint8_t *dst, int rlim, int k0, int klim, const long long *tpos,
-                                               const uint16_t *tok, int t, int E, const bf16 *emb) {
-  const int kj = (threadIdx.x >> 3) & 7, k = k0 + kj * 8;
-  const bool kin = kj * 8 < klim;
-  const int pos = kin ? k / E : 0, e = k - pos * E;
-  for (int r = (threadIdx.x >> 6) * 8 + (threadIdx.x & 7); r < kRows; r += 16) {
-    const bool ok = kin && r < rlim && tpos[r] >= 0;
-    cp16(dst + (r >> 3) * 1024 + kj * 128 + (r & 7) * 16, ok ? emb + (size_t)tok[r * t + pos] * E + e : nullptr);
-  }
-}
-
-// MN-major, each K row a contiguous run along M/N: kptr(k) is the address of K row k0 + k at
-// the tile's first M/N index, or nullptr
-template <class KPtr>
-__device__ __forceinline__ void stage_mn_rows(uint8_t *dst, int R, int rlim, int klim, KPtr kptr) {
-  const int k = threadIdx.x & 63;
-  const bf16 *base = k < klim ? kptr(k) : nullptr;
-  for (int r = (threadIdx.x >> 6) * 8; r < R; r += 16)
-    cp16(dst + (r >> 3) * 128 + (k >> 3) * (R * 16) + (k & 7) * 16, (base && r < rlim) ? base + r : nullptr);
-}
-
-// MN-major rows gathered from an embedding table: K row k0 + k is lane k0 + k's context vector
-// (concatenated embedding rows of tok[(k0 + k) * t + pos]); M/N index n0 + r is element r of it
-__device__ __forceinline__ void stage_mn_gather(uint8_t *dst, int R, int rlim, int n0, int k0, int klim,
-                                                const long long *tpos, const uint16_t *tok, int t, int E,
-                                                const bf16 *emb) {
-  const int k = threadIdx.x & 63;
-  const bool ok = k < klim && tpos[k0 + k] >= 0;
-  const uint16_t *tk = tok + (size_t)(k0 + k) * t;
-  for (int r = (threadIdx.x >> 6) * 8; r < R; r += 16) {
-    const bf16 *p = nullptr;
-    if (ok && r < rlim) {
-      const int i = n0 + r, pos = i / E;
-      p = emb + (size_t)tk[pos] * E + (i - pos * E);
-    }
-    cp16(dst + (r >> 3) * 128 + (k >> 3) * (R * 16) + (k & 7) * 16, p);
-  }
+// Swizzled byte offsets of 16-byte chunk c (8 BF16) of K-major row r, and of the 8 M/N values
+// n..n+7 (n % 8 == 0) at K-row k of an MN-major tile.
+__device__ __forceinline__ uint32_t sw_k(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+__device__ __forceinline__ uint32_t sw_mn(int n, int k) {
+  return (uint32_t)((n >> 6) * 8192 + k * 128 + ((((n & 63) >> 3) ^ (k & 7)) << 4));
 }
 
 // Op interface (device, const):
-//   static constexpr bool kAMN, kBMN;       operand majors (A: M x K, B: N x K)
+//   static constexpr bool kAMN, kBMN;         operand majors (A: M x K, B: N x K)
+//   static constexpr bool kTail;              K rows past K(z) in the last stage must be zeroed
+//                                             (the dense operands run on into other groups)
+//   static constexpr int kGather;             0: both operands by TMA; 1: A gathered; 2: B gathered
 //   bool active(z); int M(z), N(z), K(z);
-//   void prepare(uint8_t *meta, z, m0);     every thread calls it before the first barrier: the
-//                                           op's per-tile data (row targets, context tokens) go
-//                                           to shared memory so that staging reads no global
-//                                           memory to form an address
-//   void stage_a(uint8_t *dst, const uint8_t *meta, z, m0, k0, rlim, klim);   128 x 64 A tile
-//   void stage_b(uint8_t *dst, const uint8_t *meta, z, n0, k0, R, rlim, klim);  R x 64 B tile
-//   void epilogue(const uint8_t *meta, z, m, rl, n, const float v[8]);   m < M, n + 7 < N
-//   int *err();                             the error word
+//   void prepare(uint8_t *meta, z, m0);       every thread calls it before the first barrier:
+//                                             per-tile data (row targets, context tokens, the
+//                                             embedding table of a gathered operand)
+//   TmaOperand tma_a(z), tma_b(z); int row_a(z, m0), row_b(z, n0): TMA row coordinates
+//   void gather(uint8_t *tile, const uint8_t *meta, z, mn0, k0, R)   the gathered operand
+//   static constexpr int kEpi;                0: void epilogue(const uint8_t *meta, z, m, rl, n,
+//                                             const float v[8]) per row (8 columns n.., m < M);
+//                                             1: bool row_active(meta, z, m, rl) and void emit(meta,
+//                                             z, m, rl, n, float v) per element, the 32 lanes of a
+//                                             warp on consecutive n of one row
+//   static constexpr bool kFinish; void finish(uint8_t *meta, z): every thread, after the epilogue
+//   int *err();                               the error word
 template <class Op>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(const Op op, int nt_max, int tmem_cols, int stages) {
-  // dynamic shared memory: [stages x A tile][stages x B tile][op metadata]
+__global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ Op op, int nt_max, int tmem_cols,
+                                                         int ns) {
   const int z = blockIdx.z;
   if (!op.active(z)) return;
   const int M = op.M(z), N = op.N(z), K = op.K(z);
   const int m0 = blockIdx.x * kRows, n0 = blockIdx.y * nt_max;
   if (m0 >= M || n0 >= N) return;
-  const int nt = min(nt_max, (N - n0 + 15) & ~15);  // MMA N of this tile
+  const int nt = min(nt_max, N - n0);  // MMA N of this tile (N and nt_max are multiples of 64)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const int a_bytes = kRows * kBK * 2, b_bytes = nt_max * kBK * 2;
-  uint8_t *sA = smem, *sB = smem + stages * a_bytes;
-  uint8_t *meta = smem + stages * (a_bytes + b_bytes);
-  __shared__ __align__(8) uint64_t mbar[4];
+  // dynamic shared memory: [alignment slack][stages x A tile][stages x B tile][meta]
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base = (sa(smem_raw) + 1023) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - sa(smem_raw));
+  const uint32_t a_bytes = kRows * kBK * 2, b_bytes = nt_max * kBK * 2;
+  const uint32_t sA = base, sB = base + ns * a_bytes;
+  uint8_t *meta = gbase + ns * (a_bytes + b_bytes);
+  __shared__ __align__(8) uint64_t full[kStages], done[kStages];
   __shared__ uint32_t tmem_base;
   op.prepare(meta, z, m0);
   if (tid == 0) {
-    for (int s = 0; s < stages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&mbar[s])));
+    for (int s = 0; s < ns; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sa(&done[s])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
   if (warp == 0) {
@@ -165,41 +163,88 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const Op op, int nt_max,
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
 
-  auto issue = [&](int s, int k0) {
-    op.stage_a(sA + s * a_bytes, meta, z, m0, k0, M - m0, K - k0);
-    op.stage_b(sB + s * b_bytes, meta, z, n0, k0, nt, N - n0, K - k0);
-    asm volatile("cp.async.commit_group;\n" ::);
-  };
-  auto commit_empty = [] { asm volatile("cp.async.commit_group;\n" ::); };
-
   const int nk = max(1, (K + kBK - 1) / kBK);  // K = 0 still runs one all-zero stage
+  const TmaOperand ta = op.tma_a(z), tb = op.tma_b(z);
+  const int ra = op.row_a(z, m0), rb = op.row_b(z, n0);
+  // bytes per stage: a K-major box is as high as the map's box (nt_max rows for B), MN-major
+  // boxes are issued for this tile's nt columns only
+  const uint32_t tx = (Op::kGather == 1 ? 0u : a_bytes) +
+                      (Op::kGather == 2 ? 0u : (uint32_t)(Op::kBMN ? nt : nt_max) * kBK * 2);
+  // fill stage s with K block kt: bulk copies by thread 0, the gathered operand by every thread
+  auto issue = [&](int s, int kt) {
+    const int k0 = kt * kBK;
+    if (tid == 0) {
+      const uint32_t bar = sa(&full[s]);
+      expect_tx(bar, tx);
+      if (Op::kGather != 1) {
+        if (Op::kAMN)
+          tma_mn_tile(sA + s * a_bytes, ta, ra, kRows, k0, bar);
+        else
+          tma_k_tile(sA + s * a_bytes, ta, k0, ra, bar);
+      }
+      if (Op::kGather != 2) {
+        if (Op::kBMN)
+          tma_mn_tile(sB + s * b_bytes, tb, rb, nt, k0, bar);
+        else
+          tma_k_tile(sB + s * b_bytes, tb, k0, rb, bar);
+      }
+    }
+    if (Op::kGather == 1) op.gather(gbase + s * a_bytes, meta, z, m0, k0, kRows);
+    if (Op::kGather == 2) op.gather(gbase + ns * a_bytes + s * b_bytes, meta, z, n0, k0, nt);
+    if (Op::kGather) asm volatile("cp.async.commit_group;\n" ::);  // gathers copied from global memory
+  };
+  // zero the K rows r >= rows of a stage (MN-major operands of the last, partial K block)
+  auto zero_tail = [&](int s, int rows) {
+    const uint4 zz = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (kBK - rows) * 8; i += kThreads) {  // 8 chunks of 16 B per 128-byte row
+      const int r = rows + (i >> 3), c = i & 7;
+      if (Op::kAMN)
+        for (int j = 0; j < kRows / 64; ++j)
+          *reinterpret_cast<uint4 *>(gbase + s * a_bytes + j * 8192 + r * 128 + c * 16) = zz;
+      if (Op::kBMN)
+        for (int j = 0; j < nt / 64; ++j)
+          *reinterpret_cast<uint4 *>(gbase + ns * a_bytes + s * b_bytes + j * 8192 + r * 128 + c * 16) = zz;
+    }
+  };
+
   // instruction descriptor: FP32 accumulator, BF16 A and B, operand majors, N = nt, M = 128
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((Op::kAMN ? 1u : 0u) << 15) |
                          ((Op::kBMN ? 1u : 0u) << 16) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-  const uint32_t a_lbo = Op::kAMN ? kRows * 16 : 128, a_sbo = Op::kAMN ? 128 : 1024, a_step = Op::kAMN ? kRows * 32 : 256;
-  const uint32_t b_lbo = Op::kBMN ? nt * 16 : 128, b_sbo = Op::kBMN ? 128 : 1024, b_step = Op::kBMN ? nt * 32 : 256;
+  const uint32_t a_lbo = Op::kAMN ? 8192 : 16, a_step = Op::kAMN ? 2048 : 32;
+  const uint32_t b_lbo = Op::kBMN ? 8192 : 16, b_step = Op::kBMN ? 2048 : 32;
   bool ok = true;
-  for (int s = 0; s < stages - 1; ++s) {
+  for (int s = 0; s < ns - 1; ++s) {
     if (s < nk)
-      issue(s, s * kBK);
-    else
-      commit_empty();
+      issue(s, s);
+    else if (Op::kGather)
+      asm volatile("cp.async.commit_group;\n" ::);
   }
   for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt % stages;
-    // all but the newest stages - 2 copy groups have landed: stage kt is in shared memory
-    if (stages == 4)
-      asm volatile("cp.async.wait_group 2;\n" ::);
-    else
-      asm volatile("cp.async.wait_group 1;\n" ::);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);
-    __syncthreads();
+    const int s = kt % ns;
+    const uint32_t par = (uint32_t)((kt / ns) & 1);
+    const bool tail = Op::kTail && kt == nk - 1 && K - kt * kBK < kBK;
+    if (Op::kGather || tail) {
+      // a gathered stage kt is the oldest of the ns - 1 copy groups in flight
+      if (Op::kGather) {
+        if (ns >= 4)
+          asm volatile("cp.async.wait_group 2;\n" ::);
+        else if (ns == 3)
+          asm volatile("cp.async.wait_group 1;\n" ::);
+        else
+          asm volatile("cp.async.wait_group 0;\n" ::);
+      }
+      if (ok) ok = mbar_wait(sa(&full[s]), par);
+      if (tail && ok) zero_tail(s, max(0, K - kt * kBK));
+      asm volatile("fence.proxy.async.shared::cta;\n" ::);
+      __syncthreads();
+    } else if (tid == 0 && ok) {
+      ok = mbar_wait(sa(&full[s]), par);
+    }
     if (tid == 0 && ok) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      const uint32_t a0 = sa(sA + s * a_bytes), b0 = sa(sB + s * b_bytes);
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t da = smem_desc(a0 + kk * a_step, a_lbo, a_sbo);
-        const uint64_t db = smem_desc(b0 + kk * b_step, b_lbo, b_sbo);
+        const uint64_t da = desc_sw128(sA + s * a_bytes + kk * a_step, a_lbo, 1024);
+        const uint64_t db = desc_sw128(sB + s * b_bytes + kk * b_step, b_lbo, 1024);
         const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -207,45 +252,92 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const Op op, int nt_max,
             "l"(da), "l"(db), "r"(idesc), "r"(accum));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          sa(&mbar[s])));
+          sa(&done[s])));
     }
-    // the buffer refilled next held stage kt - 1: wait until its MMAs have read it
-    const int nxt = kt + stages - 1;
+    // refill the buffer of stage kt - 1 once its MMAs have read it
+    const int nxt = kt + ns - 1;
     if (nxt < nk) {
-      if (kt >= 1 && ok) ok = mbar_wait(&mbar[(kt - 1) % stages], (uint32_t)(((kt - 1) / stages) & 1));
-      if (ok)
-        issue(nxt % stages, nxt * kBK);
-      else
-        commit_empty();
-    } else {
-      commit_empty();
+      const bool need = Op::kGather != 0 || tid == 0;
+      if (need && kt >= 1 && ok) ok = mbar_wait(sa(&done[(kt - 1) % ns]), (uint32_t)(((kt - 1) / ns) & 1));
+      if (need && ok)
+        issue(nxt % ns, nxt);
+      else if (Op::kGather)
+        asm volatile("cp.async.commit_group;\n" ::);
+    } else if (Op::kGather) {
+      asm volatile("cp.async.commit_group;\n" ::);  // one group per iteration keeps the wait count exact
     }
   }
   // the last commit covers every MMA of the tile
-  if (ok) ok = mbar_wait(&mbar[(nk - 1) % stages], (uint32_t)(((nk - 1) / stages) & 1));
-  asm volatile("cp.async.wait_group 0;\n" ::);
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  if (tid == 0 && ok) ok = mbar_wait(sa(&done[(nk - 1) % ns]), (uint32_t)(((nk - 1) / ns) & 1));
+  if (Op::kGather) asm volatile("cp.async.wait_group 0;\n" ::);
   if (!__syncthreads_and(ok)) {
-    if (tid == 0) atomicOr(op.err(), kErrTimeout);
-  } else {
-    const int rl = warp * 32 + lane, m = m0 + rl;
-    for (int c0 = 0; c0 < nt; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-      if (m < M) {
-        float f[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
-        if (n0 + c0 < N) op.epilogue(meta, z, m, rl, n0 + c0, f);
-        if (n0 + c0 + 8 < N) op.epilogue(meta, z, m, rl, n0 + c0 + 8, f + 8);
+    if (tid == 0) {
+      atomicOr(op.err(), kErrTimeout);
+      // let the bulk copies this CTA issued land before its shared memory is released: stage s
+      // was last filled with K block last(s); waits on phases already completed return at once
+      for (int s = 0; s < ns && s < nk; ++s) {
+        const int last = ((nk - 1 - s) / ns) * ns + s;
+        mbar_wait(sa(&full[s]), (uint32_t)((last / ns) & 1));
       }
     }
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const int quad = warp & 3, half = warp >> 2;  // tensor-memory lanes 32 quad.., column half
+    const int rl = quad * 32 + lane;
+    if (Op::kEpi == 0) {
+      // per row: thread rl hands the op 8 consecutive columns of its row at a time, the two warps
+      // of a lane quarter taking one half of the columns each
+      const int m = m0 + rl;
+      for (int c0 = half * (nt / 2); c0 < (half + 1) * (nt / 2); c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+        if (m < M) {
+          float f[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
+          op.epilogue(meta, z, m, rl, n0 + c0, f);
+          op.epilogue(meta, z, m, rl, n0 + c0 + 8, f + 8);
+        }
+      }
+    } else {
+      // 64-column chunks staged through the (now idle) stage buffers: thread rl moves its half of
+      // its row from tensor memory to shared memory, then warp w emits rows w, w + 8, ... with its
+      // lanes on consecutive columns, so the global accesses of a warp touch one row
+      float *stg = reinterpret_cast<float *>(gbase);
+      constexpr int kPitch = 68;  // floats per staged row: float4 writes of 8 threads hit distinct banks
+      for (int c0 = 0; c0 < nt; c0 += 64) {
+#pragma unroll
+        for (int q = half * 32; q < half * 32 + 32; q += 16) {
+          uint32_t v[16];
+          const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c0 + q);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+          float4 *dst = reinterpret_cast<float4 *>(stg + rl * kPitch + q);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        }
+        __syncthreads();
+        for (int r = warp; r < kRows && m0 + r < M; r += kThreads / 32) {
+          if (!op.row_active(meta, z, m0 + r, r)) continue;
+          for (int j = lane; j < 64 && n0 + c0 + j < N; j += 32)
+            op.emit(meta, z, m0 + r, r, n0 + c0 + j, stg[r * kPitch + j]);
+        }
+        __syncthreads();
+      }
+    }
+    if (Op::kFinish) op.finish(meta, z);  // the op's CTA-wide step after the epilogue
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
@@ -259,28 +351,38 @@ inline int pow2_at_least(int x) {
   return c;
 }
 
-// Launch op over Z problems whose M and N are at most Mmax and Nmax, with meta_bytes of per-tile
-// shared data.  The column tile is the widest multiple of 16 (<= 256) that still gives at least
-// one CTA per SM.
-template <class Op>
-void launch(const Op &op, int Mmax, int Nmax, int Z, size_t meta_bytes, cudaStream_t st) {
-  if (Mmax <= 0 || Nmax <= 0 || Z <= 0) return;
+// Tile plan for Z problems whose M, N and K are at most Mmax, Nmax (a multiple of 64) and Kmax,
+// with meta_bytes of per-tile shared data: as many stage buffers as K blocks (up to kStages) and
+// the widest column tile (a multiple of 64, <= 256) that still gives at least one CTA per SM and
+// fits the shared memory.  Tensor maps of K-major B operands use nt as their box height.
+struct TilePlan {
+  int nt, ns;
+};
+inline size_t smem_bytes(const TilePlan &t, size_t meta_bytes) {
+  return 1024 + (size_t)t.ns * (kRows + t.nt) * kBK * 2 + ((meta_bytes + 15) & ~(size_t)15);
+}
+inline TilePlan plan_tiles(int Mmax, int Nmax, int Kmax, int Z, size_t meta_bytes, bool split = true) {
   const int mt = (Mmax + kRows - 1) / kRows;
-  int nt = min(256, (Nmax + 15) & ~15);
-  while (nt >= 64 && (nt / 2) % 16 == 0 && (long)mt * ((Nmax + nt - 1) / nt) * Z < 152L) nt /= 2;
-  const int stages = 3;
-  const int meta = (int)((meta_bytes + 15) & ~(size_t)15);
-  // stay inside the opt-in shared memory per block (with room for the kernel's static variables)
-  while (nt > 16 && (nt / 2) % 16 == 0 && stages * (kRows * kBK * 2 + nt * kBK * 2) + meta > 220 * 1024) nt /= 2;
-  const int smem = stages * (kRows * kBK * 2 + nt * kBK * 2) + meta;
+  TilePlan t{min(256, Nmax), max(2, min(kStages, (Kmax + kBK - 1) / kBK))};
+  // (an op that gathers its A operand pays the gather once per column tile: split = false)
+  while (split && t.nt > 64 && (t.nt / 2) % 64 == 0 && (long)mt * ((Nmax + t.nt - 1) / t.nt) * Z < 152L) t.nt /= 2;
+  while (t.nt > 64 && (t.nt / 2) % 64 == 0 && smem_bytes(t, meta_bytes) > 220 * 1024) t.nt /= 2;
+  while (t.ns > 2 && smem_bytes(t, meta_bytes) > 220 * 1024) --t.ns;
+  return t;
+}
+
+template <class Op>
+void launch(const Op &op, int Mmax, int Nmax, int Z, const TilePlan &t, size_t meta_bytes, cudaStream_t st) {
+  if (Mmax <= 0 || Nmax <= 0 || Z <= 0) return;
+  const int smem = (int)smem_bytes(t, meta_bytes);
   static int configured = 0;  // per op type: the opt-in limit covers static + dynamic shared memory
   if (configured < smem) {
     if (cudaFuncSetAttribute(gemm_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return;  // recorded for the caller's cudaGetLastError
     configured = smem;
   }
-  dim3 grid(mt, (Nmax + nt - 1) / nt, Z);
-  gemm_kernel<Op><<<grid, kThreads, smem, st>>>(op, nt, pow2_at_least(nt), stages);
+  dim3 grid((Mmax + kRows - 1) / kRows, (Nmax + t.nt - 1) / t.nt, Z);
+  gemm_kernel<Op><<<grid, kThreads, smem, st>>>(op, t.nt, pow2_at_least(t.nt), t.ns);
 }
 
 }  // namespace tc

@@ -28,10 +28,11 @@ def dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-# shapes on both hidden-layer engines: tcgen05 (E % 8 == 0, H % 16 == 0, H <= 512; ragged K
-# stages, several 128-row tiles, two column tiles for H > 256) and the mma.sync fallback
-@pytest.mark.parametrize("k,E,t,H,rows", [(3, 16, 16, 32, 70), (4, 32, 32, 128, 130), (6, 32, 8, 256, 65),
-                                          (3, 8, 5, 48, 300), (4, 16, 20, 320, 140), (2, 3, 5, 20, 9)])
+# shapes on both engines: tcgen05/TMA (every GEMM dimension a multiple of 64: several 128-row
+# tiles, two column tiles for H > 256, 4^6 tokens gathered from global memory) and mma.sync
+@pytest.mark.parametrize("k,E,t,H,rows", [(4, 32, 32, 128, 130), (6, 32, 8, 256, 65), (4, 16, 20, 320, 140),
+                                          (3, 16, 8, 64, 300), (3, 16, 16, 32, 70), (3, 8, 5, 48, 300),
+                                          (2, 3, 5, 20, 9)])
 def test_predict_bf16_within_tolerance(P, torch, k, E, t, H, rows):
     rng = np.random.default_rng(k * 101 + rows)
     sh = Shape(4 ** k, E, t, H)
@@ -78,18 +79,32 @@ def _bf16_operand_grads(flat, sh, ctx, dLm):
 # up to ~7 % (relative L2) from the exact FP64 gradient on these inputs (cancellation in the sums
 # over rows), so each block is held to 2e-2 of the BF16-operand restatement of the oracle's
 # backward, and to 0.15 of the exact oracle gradient; a transposed or misplaced operand gives
-# errors of order 1 in both.  The shapes span two 128-row tiles of the row GEMMs, a ragged last
-# K stage of the weight-gradient GEMMs (150 and 200 lanes) and H > 128.
-@pytest.mark.parametrize("E,t,H,G,M,use_static", [(32, 8, 64, 3, 37, 1), (16, 12, 144, 2, 150, 0),
-                                                  (8, 4, 32, 2, 200, 1)])
-def test_train_step_bf16_gradient_blocks(P, torch, E, t, H, G, M, use_static):
+# errors of order 1 in both.  Shapes: the first three take the tcgen05/TMA engine (every GEMM
+# dimension a multiple of 64) with two 128-row tiles, ragged last K stages of the lane reductions
+# (150 and 200 predicted lanes), H > 256 and, for 4^6 tokens, embedding gathers from global
+# memory; the last three take the mma.sync engine.
+GRAD_CASES = [
+    # k, E, t, H, G, M, static (E, t, H) or None
+    (4, 32, 8, 64, 3, 37, (32, 4, 64)),
+    (4, 16, 12, 192, 2, 150, None),
+    (4, 8, 16, 320, 2, 200, (16, 8, 64)),
+    (6, 8, 8, 64, 2, 90, None),
+    (4, 32, 8, 64, 3, 37, (16, 12, 48)),
+    (4, 16, 12, 144, 2, 150, None),
+]
+
+
+@pytest.mark.parametrize("k,E,t,H,G,M,stat", GRAD_CASES)
+def test_train_step_bf16_gradient_blocks(P, torch, k, E, t, H, G, M, stat):
     from oracle.codec import Config
     from oracle.mixer import loss_grads, mix, softmax
     from oracle.model import forward
     from tests.test_gpu_steps import _model, _oracle_step
-    rng = np.random.default_rng(E * 7 + H + M)
-    cfg_o = Config(s=2, k=4, use_static=bool(use_static), emb_s=16, ctx_s=12, hid_s=48, emb_d=E, ctx_d=t,
-                   hid_d=H, lr=1e-3)
+    rng = np.random.default_rng(k * 1000 + E * 7 + H + M)
+    use_static = stat is not None
+    es, ts, hs = stat if use_static else (16, 12, 48)
+    cfg_o = Config(s=2, k=k, use_static=use_static, emb_s=es, ctx_s=ts, hid_s=hs, emb_d=E, ctx_d=t, hid_d=H,
+                   lr=1e-3)
     dsh, ssh = cfg_o.dm_shape, cfg_o.static_shape
     params = np.stack([_model(rng, dsh, 5 + g, 0.05) for g in range(G)])
     m = np.zeros_like(params)
@@ -100,9 +115,9 @@ def test_train_step_bf16_gradient_blocks(P, torch, E, t, H, G, M, use_static):
     ctx = rng.integers(0, dsh.A, (G * M, cfg_o.t_eff))
     tgt = rng.integers(0, dsh.A, G * M)
     want = _oracle_step(cfg_o, params, m, v, alpha, az, az, static, ctx, tgt, 1, G, M)
-    cfg = P.ModelConfig(s=2, k=4, use_static=bool(use_static), emb_s=16, ctx_s=12, hid_s=48, emb_d=E, ctx_d=t,
+    cfg = P.ModelConfig(s=2, k=k, use_static=use_static, emb_s=es, ctx_s=ts, hid_s=hs, emb_d=E, ctx_d=t,
                         hid_d=H, lr=1e-3, static_weights=static, precision=P.PMKLC_BF16_BATCHED)
-    d = {k: dev(torch, x) for k, x in dict(params=params, m=m, v=v, alpha=alpha, am=az, av=az).items()}
+    d = {k_: dev(torch, x) for k_, x in dict(params=params, m=m, v=v, alpha=alpha, am=az, av=az).items()}
     d_grad = torch.zeros(params.shape, dtype=torch.float32, device="cuda")
     P.pmklc_train_step(cfg, G, M, d["params"], d["m"], d["v"], d["alpha"], d["am"], d["av"],
                        dev(torch, static) if use_static else None,
@@ -114,7 +129,7 @@ def test_train_step_bf16_gradient_blocks(P, torch, E, t, H, G, M, use_static):
         rows = slice(g * M, (g + 1) * M)
         cd = ctx[rows, ctx.shape[1] - t:]
         Lm = forward(params[g].astype(np.float64), dsh, cd)[3]
-        Lu = forward(static.astype(np.float64), ssh, ctx[rows, ctx.shape[1] - 12:])[3] if use_static else None
+        Lu = forward(static.astype(np.float64), ssh, ctx[rows, ctx.shape[1] - ts:])[3] if use_static else None
         dLm = loss_grads(softmax(mix(Lu, Lm, 0.5, S)), tgt[rows], Lu, Lm, 0.5, S)[0]
         emu = _bf16_operand_grads(params[g], dsh, cd, dLm)
         exact = want[g][1]
