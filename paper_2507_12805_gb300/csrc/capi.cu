@@ -416,6 +416,14 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
   const Layout &L = R.L;
   const Schedule &S = R.S;
   const int t_eff = R.p.t_eff;
+  // auxiliary streams: the count model beside the network's forward, and the three gradient
+  // GEMMs side by side (joined by events before the kernels that read their results)
+  StepStreams ss;
+  bool use_ss = true;
+  for (auto &a : ss.aux) use_ss = use_ss && cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t *e : {&ss.fork, &ss.join[0], &ss.join[1], &ss.count_done})
+    use_ss = use_ss && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  if (!use_ss) cudaGetLastError();  // fall back to the caller's stream alone
   for (int T = 0; T < S.T_total; ++T) {
     int np = R.pair_off[T + 1] - R.pair_off[T];
     if (np > 0) {
@@ -437,8 +445,17 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       if (!R.cmode.empty() && R.cmode[g]) any_count = true;
     }
     prof_step(T, w);
-    if (any_count) {  // before the network: a count-decoded token is the network's target and context
-      launch_count_step(R.p, R.cp, T, st);
+    const bool net = R.net && (any_pred || any_code);
+    if (any_count) {
+      // a count-decoded token is the network's target at this step: joined before the mixer
+      cudaStream_t cs = st;
+      if (use_ss && net) {
+        cudaEventRecord(ss.fork, st);
+        cudaStreamWaitEvent(ss.aux[0], ss.fork, 0);
+        cs = ss.aux[0];
+      }
+      launch_count_step(R.p, R.cp, T, cs);
+      if (cs != st) cudaEventRecord(ss.count_done, cs);
       R.launches++;
     }
     if (!R.net) continue;
@@ -450,13 +467,14 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
         launch_forward(R.p, T, st);
       R.launches += bf ? 2 : (R.c.use_static ? 4 : 2);
     }
+    if (any_count && use_ss && net) cudaStreamWaitEvent(st, ss.count_done, 0);
     if (any_pred || any_code) {
       launch_mixcode(R.p, T, st);
       R.launches++;
     }
     if (any_pred) {
       if (bf) {
-        launch_backward_bf16(R.p, T, st);
+        launch_backward_bf16(R.p, T, st, use_ss ? &ss : nullptr);
         launch_update(R.p, T, st);
       } else {
         launch_backward_update(R.p, T, st);
@@ -465,6 +483,14 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
     }
   }
   prof_stop_sampling();
+  if (use_ss) {
+    cudaStreamSynchronize(ss.aux[0]);
+    cudaStreamSynchronize(ss.aux[1]);
+  }
+  for (auto &a : ss.aux)
+    if (use_ss) cudaStreamDestroy(a);
+  if (use_ss)
+    for (cudaEvent_t e : {ss.fork, ss.join[0], ss.join[1], ss.count_done}) cudaEventDestroy(e);
 }
 
 __global__ void gather_kernel(const unsigned long long *seg, int n_seg, const uint8_t *src0, const uint8_t *src1,

@@ -69,7 +69,7 @@ struct Plan {
   float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
   float *out_P;                // optional: mixed probabilities of predicted rows (tests)
   __nv_bfloat16 *hd_b, *hs_b, *dz_b, *dh_b;  // BF16 activations of the BF16 form (else nullptr)
-  float *hpart;                // split-K partial sums of the hidden layer (BF16 form)
+  float *hpart;                // split-K partial sums of the hidden layer (BF16 form, mma.sync engine)
   long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
   // coders
   EncState *enc;

@@ -64,15 +64,23 @@ void launch_update(const Plan &p, int T, cudaStream_t st);
 void launch_backward_update(const Plan &p, int T, cudaStream_t st);
 // gradient of every group (embedding part from the fixed-point accumulators) into d_out (G x P)
 void launch_export_grad(const Plan &p, float *d_out, cudaStream_t st);
+// Auxiliary streams of a run's step loop: independent kernels of a step are forked onto them and
+// joined back by events (fork/join events reused every step).
+struct StepStreams {
+  cudaStream_t aux[2];
+  cudaEvent_t fork, join[2], count_done;
+};
+
 // predictor_tc.cu: the BF16 form's GEMMs on tcgen05, for shapes with E % 8 == 0, H % 16 == 0,
 // 4^k % 8 == 0 and a parameter count divisible by 8 (16-byte aligned per-group BF16 copies)
 bool tc_supported(const Plan &p);
 void launch_forward_tc(const Plan &p, int T, cudaStream_t st);
-void launch_backward_tc(const Plan &p, int T, cudaStream_t st);
+// ss (optional): run dW2, dX and dW1 concurrently on st and ss->aux
+void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss);
 // predictor_bf16.cu: the BF16 form (tcgen05 engine where tc_supported, else mma.sync)
 void launch_forward_bf16(const Plan &p, int T, cudaStream_t st);
 // gradient GEMMs into the gradient buffer (the optimiser is launch_update)
-void launch_backward_bf16(const Plan &p, int T, cudaStream_t st);
+void launch_backward_bf16(const Plan &p, int T, cudaStream_t st, const StepStreams *ss = nullptr);
 void launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st);
 void launch_smp_copy(const Plan &p, const int *d_pairs, int n_pairs, cudaStream_t st);
 void launch_init_groups(const Plan &p, const float *d_init, float alpha0, cudaStream_t st);

@@ -558,9 +558,9 @@ void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
   run_tgemm(LogitsB{{p, T}}, p.Mmax, p.dm.A, Z, st);
 }
 
-void launch_backward_bf16(const Plan &p, int T, cudaStream_t st) {
+void launch_backward_bf16(const Plan &p, int T, cudaStream_t st, const StepStreams *ss) {
   if (tc_supported(p)) {
-    launch_backward_tc(p, T, st);
+    launch_backward_tc(p, T, st, ss);
     return;
   }
   const double R = prof_work().pred_rows;

@@ -583,7 +583,7 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st) {
   tc::launch(op, p.Mmax, p.dm.A, Z, S.t_l, S.ml_l.bytes(), st);
 }
 
-void launch_backward_tc(const Plan &p, int T, cudaStream_t st) {
+void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss) {
   TcSetup S;
   if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
@@ -594,24 +594,39 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st) {
     op.p = p, op.T = T, op.ml = S.ml_dh, op.dz = S.dzk, op.w2 = S.w2k;
     tc::launch(op, p.Mmax, D.H, p.G, S.t_dh, S.ml_dh.bytes(), st);
   }
-  {
-    ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, st);
-    DW2T op;
-    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
-    tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), st);
-    bias_grad_kernel<<<dim3((D.H + D.A + 31) / 32, p.G), dim3(32, kBiasSlices), 0, st>>>(p, T);
+  // dW2 (+ bias sums), dX and dW1 only read dh, dz, h and the weights
+  // and write disjoint buffers: with auxiliary streams they run side by side
+  cudaStream_t s1 = st, s2 = st;
+  if (ss) {
+    cudaEventRecord(ss->fork, st);
+    cudaStreamWaitEvent(ss->aux[0], ss->fork, 0);
+    cudaStreamWaitEvent(ss->aux[1], ss->fork, 0);
+    s1 = ss->aux[0], s2 = ss->aux[1];
   }
   {
-    ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, st);
+    ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXT op;
     op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
-    tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), st);
+    tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
+  }
+  {
+    ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, s1);
+    DW2T op;
+    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
+    tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
+    bias_grad_kernel<<<dim3((D.H + D.A + 31) / 32, p.G), dim3(32, kBiasSlices), 0, s1>>>(p, T);
   }
   {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);
     DW1T op;
     op.p = p, op.T = T, op.ml = S.ml_w1, op.dh = S.dhmn, op.table = S.table_w1;
     tc::launch(op, D.H, D.K1(), p.G, S.t_w1, S.ml_w1.bytes(), st);
+  }
+  if (ss) {
+    cudaEventRecord(ss->join[0], s1);
+    cudaEventRecord(ss->join[1], s2);
+    cudaStreamWaitEvent(st, ss->join[0], 0);
+    cudaStreamWaitEvent(st, ss->join[1], 0);
   }
 }
 
