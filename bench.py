@@ -92,10 +92,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def load_workload(name: str):
+def load_workload(name: str, block_bases: int = 0):
+    """The named workload; block_bases > 0 keeps its number of blocks but cuts every block to that
+    many bases (same per-step shapes and model state, fewer steps: the small case for profiling)."""
+    import dataclasses
     import synth
     wname, kw = WORKLOADS[name]
     w = synth.workload(wname)
+    if block_bases > 0:
+        nb = len(w.block_lens)
+        w = dataclasses.replace(w, seq=np.ascontiguousarray(w.seq[: nb * block_bases]),
+                                block_lens=np.full(nb, block_bases, dtype=np.uint64),
+                                recipe=f"{w.recipe}, first {nb} x {block_bases} bases")
     return w, kw
 
 
@@ -208,12 +216,15 @@ FORMS = {"bf16": 1, "fp32": 0}
 AUTOTUNE_LANES = (64, 128, 192, 256, 320)  # candidates; the first is the FP32 plain form's setting
 
 
-def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True):
+def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, lanes=0):
     """Device-resident compress+decompress of the workload: per-step times (CUDA events) + stats."""
     cfg = P.ModelConfig(**kw, static_weights=sw, precision=FORMS[form])
     n = int(w.seq.size)
     tune = None
-    if form == "bf16":  # the batched form picks its batch size (lanes per block) on a sample, untimed
+    if form == "bf16" and lanes > 0:  # fixed batch size (profiling runs): no autotuner launches
+        cfg.lanes_per_block = lanes
+        tune = {"lanes_per_block": lanes, "rule": "fixed by --lanes"}
+    elif form == "bf16":  # the batched form picks its batch size (lanes per block) on a sample, untimed
         d = torch.from_numpy(w.seq).to(dev)
         chosen, sizes, tms = P.pmklc_autotune_lanes(d, w.block_lens, cfg, AUTOTUNE_LANES, sample_blocks=8,
                                                     max_rel_size=0.005)
@@ -273,6 +284,9 @@ def main():
     ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "bf16", "fp32"])
+    ap.add_argument("--lanes", type=int, default=0, help="BF16 lanes per block (0: autotune)")
+    ap.add_argument("--block-bases", type=int, default=0,
+                    help="cut every block to this many bases (profiling: same per-step shapes, fewer steps)")
     args = ap.parse_args()
     rank, world = _dist()
 
@@ -280,7 +294,7 @@ def main():
         if rank != 0:
             return
         import paper_2507_12805_gb300 as P
-        w, kw = load_workload(args.workload)
+        w, kw = load_workload(args.workload, args.block_bases)
         sw = static_weights(P, kw)
         print(json.dumps(run_reference(args, w, kw, sw)))
         return
@@ -292,13 +306,14 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    w, kw = load_workload(args.workload)
+    w, kw = load_workload(args.workload, args.block_bases)
     sw = static_weights(P, kw)
     n = int(w.seq.size)
     results = {}
     with ClockSampler(dev) as clk:
         for form in ([args.form] if args.form != "both" else ["fp32", "bf16"]):
-            results[form] = measure(P, torch, w, kw, sw, form, args.steps, args.warmup, dev, world)
+            results[form] = measure(P, torch, w, kw, sw, form, args.steps, args.warmup, dev, world,
+                                    lanes=args.lanes)
     head = results["bf16"] if "bf16" in results else results[args.form]
     form = "bf16" if "bf16" in results else args.form
     ms = statistics.mean(head["times"])

@@ -43,6 +43,9 @@ extern "C" {
 /* precision forms */
 #define PMKLC_FP32_PLAIN 0
 #define PMKLC_BF16_BATCHED 1
+/* BF16 batched, with the frozen static predictor in FP8 (E4M3 weights with one scale per
+   channel, E4M3 activations): see pmklc_quantize_static_fp8 */
+#define PMKLC_BF16_FP8STATIC 2
 /* optimisers */
 #define PMKLC_ADAM 0
 #define PMKLC_SGD 1
@@ -62,7 +65,7 @@ typedef struct {
   uint32_t emb_s, ctx_s, hid_s;/* static predictor: embedding E, context t, hidden H */
   uint32_t emb_d, ctx_d, hid_d;/* dynamic predictor (trained online, §4.2.4) */
   uint32_t lanes_per_block;    /* M: parallel sub-streams per block (bs, §5.8); 0 = default */
-  uint32_t precision;          /* PMKLC_FP32_PLAIN or PMKLC_BF16_BATCHED */
+  uint32_t precision;          /* PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED or PMKLC_BF16_FP8STATIC */
   uint32_t optimizer;          /* PMKLC_ADAM or PMKLC_SGD */
   float lr;                    /* learning rate of the Backward Controller (§4.2.6) */
   float alpha_init;            /* initial mixing weight alpha of Eq. (1) */
@@ -113,7 +116,7 @@ void pmklc_default_cfg(pmklc_model_cfg *cfg, uint32_t s, uint32_t k, uint32_t em
 /*
  * Compress n ASCII bases (A, C, G, T only) split into n_blocks blocks
  * (block_lens sums to n; the paper's Data Chunker, §4.3) into a container
- * (format in the design doc §3).  The static weights are not stored, only their
+ * (format: an 80-byte header, per-block records, then the lane payloads).  The static weights are not stored, only their
  * hash (§4.2.2: the public static model is part of the compressor).
  * Output: *out (library-allocated, pmklc_free) of *out_len bytes.
  * Errors: EINVAL (bad cfg, non-ACGT byte, block lengths), ENOMEM, ECUDA.
@@ -230,6 +233,24 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
                      float *d_v, float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static,
                      const uint16_t *d_ctx, const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad,
                      float *d_dalpha, void *stream);
+
+/*
+ * FP8 (E4M3) form of a frozen static predictor (the paper's static public model
+ * is frozen, §4.2.2 and Fig. 2(a); its precision is not stated): one scale per
+ * channel, s = amax / 448 (1 for an all-zero channel), code = E4M3(w / s)
+ * rounded to nearest even and saturated at 448, both divisions in FP32.
+ * Channels: the whole embedding table; each hidden unit (a row of W1t); each
+ * logit (a column of W2).  The compressor applies this to the static weights
+ * when cfg->precision is PMKLC_BF16_FP8STATIC; the entry point exposes it.
+ *   d_params: device FP32 parameters (layout above) of shape (k, E, t, H);
+ *     E must be a multiple of 16 for the FP8 forward (not checked here).
+ *   d_codes: device, 4^k*E + H*t*E + 4^k*H bytes: Emb codes [A][E], W1t codes
+ *     [H][t*E], W2 codes transposed [A][H].
+ *   d_scales: device, 1 + H + 4^k floats: s_emb, s_w1[H], s_w2[A].
+ * Errors: EINVAL (shape, NULL pointers), ECUDA.
+ */
+int pmklc_quantize_static_fp8(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H,
+                              uint8_t *d_codes, float *d_scales, void *stream);
 
 /* CRC-32 (IEEE 802.3, reflected, as zlib) of n device bytes. */
 int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);

@@ -6,7 +6,7 @@ as organised by PMKLC: (s,k)-mer tokens (§4.1), static + dynamic predictors
 mixed by Eq. (1), cross-entropy updates by the Backward Controller (Eq. 2),
 data-block partitioning and Step-wise Model Passing (§4.3, Fig. 5).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   lanes    a block's l tokens are cut into M_b contiguous lanes, the first
            (l mod M_b) one token longer (the paper's batch of bs parallel
            sub-streams, §5.1.4); each lane has its own coder.  M_b = min(M, l),
@@ -23,6 +23,9 @@ Readings where the paper is silent (each listed in the design doc):
            from the seeded init; CHAIN: parent g-1, start[g] = start[g-1] +
            ceil(f*L_{g-1}) (the paper's GPU-0 -> GPU-1 passing); TREE: parent
            g - 2^floor(log2 g), start[g] = (floor(log2 g)+1)*ceil(f*max L).
+  FP8      precision 2: the frozen static predictor runs in its FP8 form
+           (fp8.py: E4M3 weights with per-channel scales, E4M3 activations with
+           a per-row scale); the dynamic predictor is unchanged.
   judge    fallback 1: the count model (countmodel.py) codes every block in the
            same lanes alongside the network, and a block is stored with it when
            that costs fewer bytes (flag in the container); fallback 2: the count
@@ -41,7 +44,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-from . import countmodel
+from . import countmodel, fp8
 from .mixer import loss_grads, mix, softmax
 from .model import Shape, adam_step, backward, forward, init_params, sgd_step
 from .quantize import TOTAL, cumulative, quantize
@@ -270,6 +273,8 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
     """Run the lockstep loop over all blocks (groups) in compress or decompress mode."""
     dshape, sshape = cfg.dm_shape, cfg.static_shape
     S = (1 if cfg.use_static else 0, 0, 1)
+    # precision 2: the frozen static model in its FP8 form (fp8.py), else as stored
+    fq = fp8.quantize_model(static_w, sshape) if cfg.use_static and cfg.precision == 2 else None
     t_eff, A = cfg.t_eff, cfg.A
     lr = cfg.f32("lr")
     uni = TOTAL // A
@@ -314,7 +319,7 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
             Lu = None
             if cfg.use_static:
                 cs = np.stack([_ctx(b.tokens, b.starts[r], j, cfg.ctx_s) for r in pred])
-                Lu = forward(static_w, sshape, cs)[3]
+                Lu = fp8.forward(fq, cs) if fq is not None else forward(static_w, sshape, cs)[3]
             P = softmax(mix(Lu, Lm, st.alpha, S))
             if on_probs is not None:
                 on_probs(g, j, P)

@@ -2,7 +2,7 @@
 
 Test infrastructure only.  Not a component of the paper's compressor: it is
 the integer, exact fallback that guards the learned path, coding a block
-whenever the network would spend more bytes on it.  Reading (R15):
+whenever the network would spend more bytes on it.  Reading (the paper has no count model):
 
 Estimator.  Counts c[ctx][b] start at 0; the Krichevsky-Trofimov estimate
 freq_b = 2 c_b + 1, total = 2 sum(c) + 4 is range coded; the context is the

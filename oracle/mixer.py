@@ -3,7 +3,7 @@
 Test infrastructure only.
 Eq. (1):  P = softmax( alpha*(S0*L^u + S1*L^r) + (1 - alpha)*S2*L^m )
 Eq. (2):  loss = sum_i sum_j E_ij * log(1/P_ij)   (E one-hot of the target)
-Readings (DESIGN.md): the mix acts on logits exactly as written; alpha is an
+Readings: the mix acts on logits exactly as written; alpha is an
 unconstrained scalar per dynamic model, learned with the model's optimiser;
 S1 = 0 (no private static model on this path), S2 = 1; the loss of one update
 is the mean over the rows trained in that step.

@@ -17,7 +17,7 @@ Backward from dL (rows x A): dW2 = h^T dL, db2 = sum dL, dh = dL W2^T,
 da = dh * [a > 0], dW1 = X^T da, db1 = sum da, dX = da W1^T, and dEmb[c] adds
 the slice of dX of every context position holding token c.
 
-Optimiser (paper silent; reading in the design doc): Adam with beta1 0.9,
+Optimiser (paper silent; the reading used): Adam with beta1 0.9,
 beta2 0.999, eps 1e-8 and bias correction by the update count tau, or plain
 SGD.  Pins: central finite differences of the loss (tests), closed-form Adam
 first step (|update| = lr for every parameter with nonzero gradient).

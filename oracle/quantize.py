@@ -1,7 +1,7 @@
 """Probabilities -> integer frequency table for the entropy coder.
 
 Test infrastructure only.  The paper passes P to its entropy encoder (§2 step 3)
-without saying how P becomes integers; the reading used here (DESIGN.md):
+without saying how P becomes integers; the reading used here:
 
     T = 2^24 (total), A = alphabet size
     freq_j = 1 + floor(P_j * (T - A))      the product rounded in the working

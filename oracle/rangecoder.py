@@ -2,7 +2,7 @@
 
 Test infrastructure only.  The paper's entropy encoder (§2 step 3, "EE" in
 Fig. 2) turns each predicted distribution and target symbol into bits but is
-not specified; the reading used here (DESIGN.md) is range encoding (G. N. N.
+not specified; the reading used here is range encoding (G. N. N.
 Martin, 1979) with a 56-bit window and byte output, written with Python
 integers so no intermediate can overflow:
 
@@ -26,7 +26,8 @@ code -= r*cum_s, range = r*freq_s, then shift in bytes while range < 2^48.
 
 Pins (tests): round trip on random tables; exact byte equality with the CUDA
 coder given the same tables; length bound 8*bytes <= sum(-log2 q) +
-N*2^-24/ln2 + 8 (derived in the design doc), checked against the exact rational
+N*2^-24/ln2 + 8 (per symbol: the truncation of range / 2^24;
+at the end: the flush), checked against the exact rational
 coder below, whose output length obeys ceil(-log2 W) + 1 <= sum(-log2 q) + 2.
 """
 from __future__ import annotations

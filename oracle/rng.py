@@ -2,7 +2,7 @@
 
 Test infrastructure only.  The paper initialises the dynamic model from
 "randomly initialized parameters" (§4.3) without naming a generator; the
-reading used here (listed in the design doc) is splitmix64 (Steele, Lea & Flood,
+reading used here is splitmix64 (Steele, Lea & Flood,
 2014) as a counter-based stream: draw i of seed S is mix(S + (i+1)*gamma).
 
 Initial value of parameter i of a tensor with bound B:

@@ -4,7 +4,7 @@ Bases map to numbers A:0 C:1 G:2 T:3; a window of k bases starting every s
 bases is read as a base-4 number with the first base most significant (the
 paper's example: "CGG" = 4^2*1 + 4^1*2 + 4^0*2 = 26).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * only 1 <= s <= k <= 8 is lossless, so only that is accepted;
   * l = floor((n-k)/s) + 1 windows for n >= k, none for n < k;
   * the n - ((l-1)s + k) bases after the last window (fewer than s) form the

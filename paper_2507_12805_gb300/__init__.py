@@ -23,7 +23,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 PMKLC_OK, PMKLC_EINVAL, PMKLC_ENOMEM, PMKLC_ECUDA = 0, -1, -2, -3
 PMKLC_ECORRUPT, PMKLC_EMODEL, PMKLC_ETIMEOUT, PMKLC_ENOSPC = -4, -5, -6, -7
-PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED = 0, 1
+PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED, PMKLC_BF16_FP8STATIC = 0, 1, 2
 PMKLC_ADAM, PMKLC_SGD = 0, 1
 PMKLC_SMP_NONE, PMKLC_SMP_CHAIN, PMKLC_SMP_TREE = 0, 1, 2
 
@@ -78,6 +78,7 @@ _sigs = {
     "pmklc_predict": ([_vp, _u32, _u32, _u32, _u32, _vp, _sz, _u32, _vp, _vp], _i),
     "pmklc_train_step": ([_cfgp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
                           _vp], _i),
+    "pmklc_quantize_static_fp8": ([_vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp], _i),
     "pmklc_crc32": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_crc32_noalloc": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
@@ -266,6 +267,12 @@ def pmklc_train_step(cfg: ModelConfig, G: int, M: int, d_params, d_m, d_v, d_alp
     _check(lib.pmklc_train_step(ctypes.byref(c), G, M, _ptr(d_params), _ptr(d_m), _ptr(d_v), _ptr(d_alpha),
                                 _ptr(d_alpha_m), _ptr(d_alpha_v), _ptr(d_static), _ptr(d_ctx), _ptr(d_target), tau,
                                 _ptr(d_P), _ptr(d_grad), _ptr(d_dalpha), _stream(stream)), "pmklc_train_step")
+
+
+def pmklc_quantize_static_fp8(d_params, k: int, E: int, t: int, H: int, d_codes, d_scales, stream=None):
+    """FP8 (E4M3) codes [Emb | W1t | W2 transposed] and scales [s_emb | s_w1 | s_w2] of a frozen model."""
+    _check(lib.pmklc_quantize_static_fp8(_ptr(d_params), k, E, t, H, _ptr(d_codes), _ptr(d_scales),
+                                         _stream(stream)), "pmklc_quantize_static_fp8")
 
 
 def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:

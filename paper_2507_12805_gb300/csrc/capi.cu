@@ -149,6 +149,9 @@ struct Cfg {
   int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
 };
 
+// the BF16 batched forms (the static model in BF16 or in FP8)
+bool bf_form(int precision) { return precision == PMKLC_BF16_BATCHED || precision == PMKLC_BF16_FP8STATIC; }
+
 int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!c || c->struct_size != sizeof(pmklc_model_cfg)) return PMKLC_EINVAL;
   if (c->s < 1 || c->s > c->k || c->k > 8) return PMKLC_EINVAL;
@@ -157,7 +160,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (c->use_static && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
                         c->hid_s > 65535 || !c->static_weights))
     return PMKLC_EINVAL;
-  if (c->precision != PMKLC_FP32_PLAIN && c->precision != PMKLC_BF16_BATCHED) return PMKLC_EINVAL;
+  if (c->precision > PMKLC_BF16_FP8STATIC) return PMKLC_EINVAL;
   if (c->optimizer > PMKLC_SGD || c->smp_mode > PMKLC_SMP_TREE || c->count_order > 7) return PMKLC_EINVAL;
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
@@ -354,9 +357,26 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.precision = c.precision;
   p.wbf = nullptr;
   p.static_bf = nullptr;
-  if (c.precision == PMKLC_BF16_BATCHED) {
+  p.st8 = nullptr;
+  p.st8_c1 = p.st8_s2 = nullptr;
+  p.hs_rowmax = nullptr;
+  if (bf_form(c.precision)) {
     p.wbf = ar.alloc<__nv_bfloat16>(G * p.P);
-    if (c.use_static && d_static) {
+    if (c.use_static && d_static && c.precision == PMKLC_BF16_FP8STATIC) {
+      // the frozen static model in E4M3 with per-channel scales (fp8static.cu)
+      uint8_t *codes = ar.alloc<uint8_t>(fp8_code_bytes(c.st));
+      float *scales = ar.alloc<float>(fp8_scale_count(c.st));
+      float *c1 = ar.alloc<float>(c.st.H);
+      unsigned *rmax = ar.alloc<unsigned>(NL);
+      if (ar.failed) return PMKLC_ENOMEM;
+      launch_quantize_fp8(d_static, c.st, codes, scales, ar.st);
+      launch_fp8_hidden_scale(scales, c.st, c1, ar.st);
+      cudaMemsetAsync(rmax, 0, sizeof(unsigned) * NL, ar.st);
+      p.st8 = codes;
+      p.st8_c1 = c1;
+      p.st8_s2 = scales + 1 + c.st.H;
+      p.hs_rowmax = rmax;
+    } else if (c.use_static && d_static) {
       __nv_bfloat16 *sb = ar.alloc<__nv_bfloat16>(c.st.count());
       if (sb) launch_to_bf16(d_static, sb, c.st.count(), ar.st);
       p.static_bf = sb;
@@ -373,7 +393,7 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.out_P = nullptr;
   p.hd_b = p.hs_b = p.dz_b = p.dh_b = nullptr;
   p.hpart = nullptr;
-  if (c.precision == PMKLC_BF16_BATCHED) {
+  if (bf_form(c.precision)) {
     int hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
     p.hpart = ar.alloc<float>((size_t)2 * kHiddenSplit * NL * hmax);  // 2 models x K-slices
     p.hd_b = ar.alloc<__nv_bfloat16>(NL * c.dm.H);
@@ -400,6 +420,8 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   R.pair_off[R.S.T_total + 1] = (int)flat.size() / 2;
   R.d_pairs = ar.upload(flat);
   if (ar.failed) return PMKLC_ENOMEM;
+  // the FP8 static model runs on the tcgen05 engine only (no mma.sync form of it)
+  if (p.st8 && !tc_supported(p)) return PMKLC_EINVAL;
   cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
   cudaMemsetAsync(p.err, 0, sizeof(int), ar.st);
   std::vector<float> init;
@@ -459,7 +481,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     if (!R.net) continue;
-    const bool bf = R.p.precision == PMKLC_BF16_BATCHED;
+    const bool bf = bf_form(R.p.precision);
     if (any_pred) {
       if (bf)
         launch_forward_bf16(R.p, T, st);
@@ -726,7 +748,7 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.count_order = h[11];
   c.fallback = (h[7] >> 1) & 3;
   if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 ||
-      c.fallback > 2 || c.precision > PMKLC_BF16_BATCHED)
+      c.fallback > 2 || c.precision > PMKLC_BF16_FP8STATIC)
     return PMKLC_ECORRUPT;
   int A = 1 << (2 * c.k);
   c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
@@ -1264,7 +1286,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
   R.p.alpha_m = d_alpha_m;
   R.p.alpha_v = d_alpha_v;
   const int T = te;
-  const bool bf = c.precision == PMKLC_BF16_BATCHED;
+  const bool bf = bf_form(c.precision);
   prof_step(0, StepWork{(double)rows, (double)G});  // sampled when profiling is enabled
   if (bf) launch_to_bf16(d_params, R.p.wbf, (size_t)G * R.p.P, st);
   if (d_logits_only) {
@@ -1272,7 +1294,9 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
       launch_forward_bf16(R.p, T, st);
     else
       launch_forward(R.p, T, st);
-    cudaMemcpyAsync(d_logits_only, R.p.zm, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
+    // the FP8 form returns the static model's logits (pmklc_predict runs the model as the static one)
+    const float *src = c.precision == PMKLC_BF16_FP8STATIC ? R.p.zu : R.p.zm;
+    cudaMemcpyAsync(d_logits_only, src, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
   } else if (bf) {
     std::vector<unsigned long long> off(rows, 0);
     std::vector<uint32_t> cap(rows, 0);
@@ -1313,16 +1337,24 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
 
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,
                   size_t rows, uint32_t precision, float *d_logits, void *stream) {
-  if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_BATCHED ||
+  if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_FP8STATIC ||
       (rows && (!d_params || !d_ctx || !d_logits)))
     return PMKLC_EINVAL;
   if (rows == 0) return PMKLC_OK;
   pmklc_model_cfg mc;
   pmklc_default_cfg(&mc, 1, k, E, t, H);
   mc.precision = precision;
+  if (precision == PMKLC_BF16_FP8STATIC) {  // the model runs as the frozen static predictor in FP8
+    mc.use_static = 1;
+    mc.emb_s = E, mc.ctx_s = t, mc.hid_s = H;
+    mc.static_weights = d_params;  // only checked non-null
+  }
   Cfg c;
   int rc = check_cfg(&mc, c);
   if (rc) return rc;
+  if (precision == PMKLC_BF16_FP8STATIC)
+    return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
+                    d_params, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
   // a throw-away copy of the parameters: the forward never writes them, but the plan wants a mutable pointer
   return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);

@@ -63,7 +63,14 @@ struct Plan {
   const float *static_params;
   __nv_bfloat16 *wbf;               // BF16 copy of every group's parameters (BF16 form), G x P
   const __nv_bfloat16 *static_bf;   // BF16 copy of the static parameters (BF16 form)
-  int precision;                    // PMKLC_FP32_PLAIN / PMKLC_BF16_BATCHED
+  // FP8 static form (PMKLC_BF16_FP8STATIC with a static model; else nullptr): E4M3 codes
+  // [Emb A x E][W1t H x tE][W2t A x H], the hidden scales c1[h] = s_emb s_w1[h], the logit scales
+  // s_w2[a], and per lane row the largest static hidden activation of the step (float bits,
+  // raised by integer atomicMax; reset by the mixer once the logits are formed)
+  const uint8_t *st8;
+  const float *st8_c1, *st8_s2;
+  unsigned *hs_rowmax;
+  int precision;                    // PMKLC_FP32_PLAIN / PMKLC_BF16_BATCHED / PMKLC_BF16_FP8STATIC
   const float *bc1, *bc2;      // Adam bias corrections 1 - beta^tau, indexed by tau
   // activations (NL rows)
   float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
@@ -151,6 +158,50 @@ __device__ __forceinline__ int group_tau(const Plan &p, int T, int g) {
 // Fixed point scale of the embedding gradient accumulators (integer adds are order-free,
 // so the sum is deterministic; resolution 2^-40, range +-2^23).
 constexpr double kEmbFix = 1099511627776.0;  // 2^40
+
+// v * 2^40 rounded to the nearest integer (ties to even), saturated to the int64 range (NaN -> 0),
+// in integer arithmetic: the product is exact in binary floating point, so this equals the
+// conversion of the exact product; no FP64 instruction is issued (GB300 has little FP64 rate).
+__device__ __forceinline__ long long fix40(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xFFu);
+  const bool neg = (b >> 31) != 0;
+  if (e == 0xFF) return (b & 0x7FFFFFu) ? 0ll : (neg ? (long long)(1ull << 63) : (long long)((1ull << 63) - 1));
+  if (e == 0) return 0ll;  // subnormal: |v| 2^40 < 2^-86
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = e - 110;  // v 2^40 = m 2^(e - 150 + 40)
+  unsigned long long q;
+  if (sh >= 40) {  // |v| 2^40 >= 2^63
+    return neg ? (long long)(1ull << 63) : (long long)((1ull << 63) - 1);
+  } else if (sh >= 0) {
+    q = m << sh;
+  } else if (sh < -24) {
+    q = 0;  // below one half (m < 2^24)
+  } else {
+    const int r = -sh;
+    q = m >> r;
+    const unsigned long long rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return neg ? -(long long)q : (long long)q;
+}
+
+// q * 2^-40 rounded once to the nearest float (ties to even), in integer arithmetic.
+__device__ __forceinline__ float unfix40(long long q) {
+  if (q == 0) return 0.f;
+  const bool neg = q < 0;
+  unsigned long long u = neg ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  const int top = 63 - __clzll((long long)u);  // index of the leading one
+  int sh = 0;
+  if (top > 23) {
+    sh = top - 23;
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    u >>= sh;
+    if (rem > half || (rem == half && (u & 1ull))) ++u;  // may reach 2^24: still exact below
+  }
+  const float mag = __uint2float_rn((uint32_t)u) * __int_as_float((127 + sh - 40) << 23);
+  return neg ? -mag : mag;
+}
 
 }  // namespace pmklc
 

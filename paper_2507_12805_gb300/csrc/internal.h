@@ -47,6 +47,15 @@ void launch_detokenize(const uint16_t *d_tokens, const uint8_t *d_tail, const lo
                        uint8_t *d_seq, int *d_err, cudaStream_t st);
 int crc32_device(const uint8_t *d_data, size_t n, uint32_t *crc, cudaStream_t st);
 
+// fp8static.cu ---------------------------------------------------------------
+// FP8 (E4M3) form of a frozen model of shape d: codes [Emb A x E][W1t H x tE][W2 transposed A x H]
+// (fp8_code_bytes) and scales [s_emb][s_w1: H][s_w2: A] (fp8_scale_count).
+size_t fp8_code_bytes(const Dims &d);
+size_t fp8_scale_count(const Dims &d);
+void launch_quantize_fp8(const float *d_params, const Dims &d, uint8_t *d_codes, float *d_scales, cudaStream_t st);
+// c1[h] = s_emb * s_w1[h], the hidden layer's combined scale
+void launch_fp8_hidden_scale(const float *d_scales, const Dims &d, float *d_c1, cudaStream_t st);
+
 // countmodel.cu --------------------------------------------------------------
 void launch_count_step(const Plan &p, const CountPlan &c, int T, cudaStream_t st);
 void launch_count_init(const Plan &p, const CountPlan &c, int encode, cudaStream_t st);

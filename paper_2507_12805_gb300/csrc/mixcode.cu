@@ -162,10 +162,150 @@ __device__ __forceinline__ int symbol_of(const RowView &v, int A, const RowTable
   return sym;
 }
 
+// ---- register-resident rows (A = 32 NR, NR = 2, 8, 32) ----
+// Lane owns symbols [NR lane, NR lane + NR).  The row's logits are read once with vector loads
+// and every exponential, probability and frequency is computed once and kept in registers; the
+// operations and their order are those of the generic path above, so both give identical tables.
+template <int NR>
+struct RegRow {
+  static constexpr bool kKeep = NR <= 8;  // raw logits kept for the gradient pass
+  float u[kKeep ? NR : 1], m[kKeep ? NR : 1];
+  float ex[NR];    // exp(z - max)
+  uint32_t f[NR];  // final frequencies (remainder included)
+  float inv;
+  uint32_t cbase, csum;
+};
+
+template <int NR>
+__device__ __forceinline__ void load_chunk(const float *src, float (&x)[NR]) {
+  if constexpr (NR % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NR / 4; ++q) {
+      const float4 w = reinterpret_cast<const float4 *>(src)[q];
+      x[4 * q] = w.x, x[4 * q + 1] = w.y, x[4 * q + 2] = w.z, x[4 * q + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NR / 2; ++q) {
+      const float2 w = reinterpret_cast<const float2 *>(src)[q];
+      x[2 * q] = w.x, x[2 * q + 1] = w.y;
+    }
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ void reg_table(const RowView &v, int lane, RegRow<NR> &R) {
+  const int a0 = lane * NR;
+  float uu[NR], mm[NR], z[NR];
+  load_chunk<NR>(v.zm + a0, mm);
+  if (v.use_static) {
+    load_chunk<NR>(v.zu + a0, uu);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) uu[i] = 0.f;
+  }
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    z[i] = v.use_static ? __fadd_rn(__fmul_rn(v.alpha, uu[i]), __fmul_rn(v.oma, mm[i])) : __fmul_rn(v.oma, mm[i]);
+    mx = fmaxf(mx, z[i]);
+    if constexpr (RegRow<NR>::kKeep) R.u[i] = uu[i], R.m[i] = mm[i];
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    R.ex[i] = __expf(__fsub_rn(z[i], mx));
+    s = __fadd_rn(s, R.ex[i]);
+  }
+  for (int o = 16; o; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(kFull, s, o));
+  s = __shfl_sync(kFull, s, 0);
+  R.inv = __frcp_rn(s);
+  const float scale = (float)(kTotal - (uint32_t)(32 * NR));
+  uint32_t fs = 0, fmx = 0, amx = 0xffffffffu;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    R.f[i] = qfreq(__fmul_rn(R.ex[i], R.inv), scale);
+    fs += R.f[i];
+    if (R.f[i] > fmx) {
+      fmx = R.f[i];
+      amx = a0 + i;
+    }
+  }
+  uint32_t tot = fs;
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(kFull, tot, o);
+    uint32_t of = __shfl_xor_sync(kFull, fmx, o), oa = __shfl_xor_sync(kFull, amx, o);
+    if (of > fmx || (of == fmx && oa < amx)) {
+      fmx = of;
+      amx = oa;
+    }
+  }
+  const int rem = (int)(kTotal - tot);
+  const bool here = amx >= (uint32_t)a0 && amx < (uint32_t)(a0 + NR);
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+    if (here && amx == (uint32_t)(a0 + i)) R.f[i] = (uint32_t)((int)R.f[i] + rem);
+  const uint32_t cs = fs + (here ? (uint32_t)rem : 0u);
+  uint32_t inc = cs;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  R.csum = cs;
+  R.cbase = inc - cs;
+}
+
+// (cum, freq) of symbol e on every lane
+template <int NR>
+__device__ __forceinline__ void reg_interval(const RegRow<NR> &R, int e, uint32_t &cum, uint32_t &freq) {
+  const int owner = e / NR, idx = e - owner * NR;
+  uint32_t c = R.cbase, fr = 0;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    if (i < idx) c += R.f[i];
+    if (i == idx) fr = R.f[i];
+  }
+  cum = __shfl_sync(kFull, c, owner);
+  freq = __shfl_sync(kFull, fr, owner);
+}
+
+// symbol whose interval holds x, on every lane (every lane scans its own chunk; the owner's
+// result is broadcast)
+template <int NR>
+__device__ __forceinline__ int reg_symbol(const RegRow<NR> &R, int lane, uint32_t x, uint32_t &cum,
+                                          uint32_t &freq) {
+  const bool mine = x >= R.cbase && x - R.cbase < R.csum;
+  const unsigned bal = __ballot_sync(kFull, mine);
+  const int owner = bal ? __ffs(bal) - 1 : 0;
+  uint32_t c = R.cbase, fr = 0;
+  int sym = NR - 1;
+  bool found = false;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    if (!found) {
+      if (x < c + R.f[i]) {
+        sym = i;
+        fr = R.f[i];
+        found = true;
+      } else {
+        c += R.f[i];
+      }
+    }
+  }
+  if (!found) fr = R.f[NR - 1];  // corrupt input: clamp into the last symbol
+  sym = __shfl_sync(kFull, lane * NR + sym, owner);
+  cum = __shfl_sync(kFull, c, owner);
+  freq = __shfl_sync(kFull, fr, owner);
+  return sym;
+}
+
+template <int NR>
 __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
   const int lane = threadIdx.x & 31;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= p.NL) return;
+  if (p.hs_rowmax && lane == 0) p.hs_rowmax[r] = 0u;  // the FP8 static logits of this step are formed
   const int g = p.lane_grp[r];
   const int j = T - p.grp_start[g];
   if (j < 0 || j >= p.lane_len[r]) return;
@@ -196,56 +336,120 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
   }
   const float alpha = p.alpha[g];
   RowView v{p.zu + (size_t)r * A, p.zm + (size_t)r * A, alpha, __fsub_rn(1.f, alpha), p.use_static};
-  RowTable t;
-  row_table(v, A, t);
-  int e;
-  if (mode == kDecode) {
-    DecState s;
-    unsigned long long rr = 0;
-    uint32_t x = 0;
-    if (lane == 0) {
-      s = p.dec[r];
-      x = dec_target24(s, rr);
-    }
-    x = __shfl_sync(kFull, x, 0);
-    uint32_t cum, freq;
-    e = symbol_of(v, A, t, x, cum, freq);
-    if (lane == 0) {
-      dec_consume(s, rr, cum, freq, buf, cap);
-      p.dec[r] = s;
-      p.tokens[tpos] = (uint16_t)e;
-    }
-  } else {
-    e = p.tokens[tpos];
-    if (mode == kEncode) {
-      uint32_t cum, freq;
-      symbol_interval(v, A, t, e, cum, freq);
-      if (lane == 0) {
-        EncState s = p.enc[r];
-        enc_code24(s, cum, freq, buf, cap, p.err);
-        p.enc[r] = s;
-      }
-    }
-  }
-  // Backward Controller inputs: mean cross entropy over the group's predicted lanes
   const int n_pred = live_lanes(p, g, j);
   const float inv_n = 1.f / (float)n_pred;
-  int a0, n;
-  lane_chunk(A, lane, a0, n);
-  float da = 0.f;
-  float *dz = p.dz + (size_t)r * A;
-  __nv_bfloat16 *dzb = p.dz_b ? p.dz_b + (size_t)r * A : nullptr;
   float *outP = p.out_P ? p.out_P + (size_t)r * A : nullptr;
-  for (int a = a0; a < a0 + n; ++a) {
-    float P = t.prob(v, a);
-    if (outP) outP[a] = P;
-    float d = (P - (a == e ? 1.f : 0.f)) * inv_n;
-    if (dzb)
-      dzb[a] = __float2bfloat16_rn(v.oma * d);
-    else
-      dz[a] = v.oma * d;
-    float diff = p.use_static ? v.zu[a] - v.zm[a] : -v.zm[a];
-    da = fmaf(d, diff, da);
+  float da = 0.f;
+  if constexpr (NR > 0) {
+    RegRow<NR> R;
+    reg_table<NR>(v, lane, R);
+    int e;
+    if (mode == kDecode) {
+      DecState s;
+      unsigned long long rr = 0;
+      uint32_t x = 0;
+      if (lane == 0) {
+        s = p.dec[r];
+        x = dec_target24(s, rr);
+      }
+      x = __shfl_sync(kFull, x, 0);
+      uint32_t cum, freq;
+      e = reg_symbol<NR>(R, lane, x, cum, freq);
+      if (lane == 0) {
+        dec_consume(s, rr, cum, freq, buf, cap);
+        p.dec[r] = s;
+        p.tokens[tpos] = (uint16_t)e;
+      }
+    } else {
+      e = p.tokens[tpos];
+      if (mode == kEncode) {
+        uint32_t cum, freq;
+        reg_interval<NR>(R, e, cum, freq);
+        if (lane == 0) {
+          EncState s = p.enc[r];
+          enc_code24(s, cum, freq, buf, cap, p.err);
+          p.enc[r] = s;
+        }
+      }
+    }
+    // Backward Controller inputs (Eq. 2): the lane's chunk in registers, stored with vector writes
+    const int a0 = lane * NR;
+    float dv[NR], uu[NR], mm[NR];
+    if constexpr (RegRow<NR>::kKeep) {
+#pragma unroll
+      for (int i = 0; i < NR; ++i) uu[i] = R.u[i], mm[i] = R.m[i];
+    } else {
+      load_chunk<NR>(v.zm + a0, mm);
+      if (p.use_static) load_chunk<NR>(v.zu + a0, uu);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const float P = __fmul_rn(R.ex[i], R.inv);
+      if (outP) outP[a0 + i] = P;
+      const float d = (P - (a0 + i == e ? 1.f : 0.f)) * inv_n;
+      dv[i] = v.oma * d;
+      const float diff = p.use_static ? uu[i] - mm[i] : -mm[i];
+      da = fmaf(d, diff, da);
+    }
+    if (p.dz_b) {
+#pragma unroll
+      for (int q = 0; q < NR / 2; ++q) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(dv[2 * q], dv[2 * q + 1]);
+        reinterpret_cast<__nv_bfloat162 *>(p.dz_b + (size_t)r * A + a0)[q] = h;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NR / 2; ++q)
+        reinterpret_cast<float2 *>(p.dz + (size_t)r * A + a0)[q] = make_float2(dv[2 * q], dv[2 * q + 1]);
+    }
+  } else {
+    RowTable t;
+    row_table(v, A, t);
+    int e;
+    if (mode == kDecode) {
+      DecState s;
+      unsigned long long rr = 0;
+      uint32_t x = 0;
+      if (lane == 0) {
+        s = p.dec[r];
+        x = dec_target24(s, rr);
+      }
+      x = __shfl_sync(kFull, x, 0);
+      uint32_t cum, freq;
+      e = symbol_of(v, A, t, x, cum, freq);
+      if (lane == 0) {
+        dec_consume(s, rr, cum, freq, buf, cap);
+        p.dec[r] = s;
+        p.tokens[tpos] = (uint16_t)e;
+      }
+    } else {
+      e = p.tokens[tpos];
+      if (mode == kEncode) {
+        uint32_t cum, freq;
+        symbol_interval(v, A, t, e, cum, freq);
+        if (lane == 0) {
+          EncState s = p.enc[r];
+          enc_code24(s, cum, freq, buf, cap, p.err);
+          p.enc[r] = s;
+        }
+      }
+    }
+    // Backward Controller inputs: mean cross entropy over the group's predicted lanes
+    int a0, n;
+    lane_chunk(A, lane, a0, n);
+    float *dz = p.dz + (size_t)r * A;
+    __nv_bfloat16 *dzb = p.dz_b ? p.dz_b + (size_t)r * A : nullptr;
+    for (int a = a0; a < a0 + n; ++a) {
+      float P = t.prob(v, a);
+      if (outP) outP[a] = P;
+      float d = (P - (a == e ? 1.f : 0.f)) * inv_n;
+      if (dzb)
+        dzb[a] = __float2bfloat16_rn(v.oma * d);
+      else
+        dz[a] = v.oma * d;
+      float diff = p.use_static ? v.zu[a] - v.zm[a] : -v.zm[a];
+      da = fmaf(d, diff, da);
+    }
   }
   for (int o = 16; o; o >>= 1) da += __shfl_xor_sync(kFull, da, o);
   if (lane == 0) p.dalpha_row[r] = da;
@@ -375,7 +579,13 @@ void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
   if (p.NL <= 0) return;
   // reads L^u and L^m, writes dL^m: 12 bytes per predicted row and symbol
   ProfScope ps("mix_cdf_code", 0, 12.0 * prof_work().pred_rows * p.dm.A, st);
-  mixcode_kernel<<<(p.NL * 32 + 255) / 256, 256, 0, st>>>(p, T);
+  const unsigned grid = (unsigned)((p.NL * 32 + 255) / 256);
+  switch (p.dm.A) {  // register-resident rows where a lane's chunk fits in registers
+    case 64: mixcode_kernel<2><<<grid, 256, 0, st>>>(p, T); break;
+    case 256: mixcode_kernel<8><<<grid, 256, 0, st>>>(p, T); break;
+    case 1024: mixcode_kernel<32><<<grid, 256, 0, st>>>(p, T); break;
+    default: mixcode_kernel<0><<<grid, 256, 0, st>>>(p, T); break;
+  }
 }
 
 void launch_coder_init(const Plan &p, int encode, cudaStream_t st) {

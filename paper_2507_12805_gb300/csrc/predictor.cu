@@ -13,6 +13,8 @@
 // The embedding gradient is accumulated with 64-bit integer atomics on a
 // 2^-40 fixed-point grid: integer addition is associative, so the result does
 // not depend on the order of the atomics.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace pmklc {
@@ -348,7 +350,7 @@ struct DXOp : RowBase {
     if (b < 0) return;
     int pos = i / p.dm.E, e = i - pos * p.dm.E;
     int tok = p.tokens[b - p.dm.t + pos];
-    long long q = __double2ll_rn((double)acc * kEmbFix);
+    long long q = fix40(acc);
     atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc + ((size_t)g * p.dm.A + tok) * p.dm.E + e),
               (unsigned long long)q);
   }
@@ -357,25 +359,27 @@ struct DXOp : RowBase {
 // Optimiser over every parameter of every training group, streamed in float4 groups: the
 // gradient comes from `grad` (W1, b1, W2, b2) or from the fixed-point embedding accumulators
 // (Emb, zeroed on the way); all loads of a group are issued before its stores.  The FP32
-// master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.
+// master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.  Grid row
+// blockIdx.y is a group; its blocks stride over the group's float4 groups with 32-bit indices
+// (no 64-bit division, whose FP64-based code is slow on GB300).
 __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
-  const size_t P = p.P, nq = (P + 3) / 4, nemb = (size_t)p.dm.A * p.dm.E;
+  const int g = blockIdx.y;
+  if (!group_trains(p, T, g)) return;
+  const uint32_t P = (uint32_t)p.P, nq = (P + 3) / 4, nemb = (uint32_t)(p.dm.A * p.dm.E);
   const bool adam = p.optimizer == PMKLC_ADAM;
-  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < (size_t)p.G * nq;
-       w += (size_t)gridDim.x * blockDim.x) {
-    const int g = (int)(w / nq);
-    if (!group_trains(p, T, g)) continue;
-    const size_t i0 = (w - (size_t)g * nq) * 4, base = (size_t)g * P;
-    const int tau = group_tau(p, T, g);
-    const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
-    float *__restrict__ th = p.params + base;
-    float *__restrict__ mm = p.m + base;
-    float *__restrict__ vv = p.v + base;
-    const float *__restrict__ gr = p.grad + base;
-    long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
+  const size_t base = (size_t)g * p.P;
+  const int tau = group_tau(p, T, g);
+  const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
+  float *__restrict__ th = p.params + base;
+  float *__restrict__ mm = p.m + base;
+  float *__restrict__ vv = p.v + base;
+  const float *__restrict__ gr = p.grad + base;
+  long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
+  const bool aligned = (base & 3) == 0;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nq; w += gridDim.x * blockDim.x) {
+    const uint32_t i0 = w * 4;
     float t[4], m[4], v[4], gg[4];
-    const bool vec = i0 + 3 < P && (base & 3) == 0;
-    if (vec) {
+    if (aligned && i0 + 3 < P) {
       float4 a = *reinterpret_cast<const float4 *>(th + i0), b = *reinterpret_cast<const float4 *>(mm + i0),
              c = *reinterpret_cast<const float4 *>(vv + i0);
       t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
@@ -384,8 +388,7 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
       if (i0 < nemb) {  // A*E is a multiple of 4: a group never straddles the embedding boundary
         longlong2 q0 = *reinterpret_cast<const longlong2 *>(acc + i0),
                   q1 = *reinterpret_cast<const longlong2 *>(acc + i0 + 2);
-        gg[0] = (float)((double)q0.x * (1.0 / kEmbFix)), gg[1] = (float)((double)q0.y * (1.0 / kEmbFix));
-        gg[2] = (float)((double)q1.x * (1.0 / kEmbFix)), gg[3] = (float)((double)q1.y * (1.0 / kEmbFix));
+        gg[0] = unfix40(q0.x), gg[1] = unfix40(q0.y), gg[2] = unfix40(q1.x), gg[3] = unfix40(q1.y);
         *reinterpret_cast<longlong2 *>(acc + i0) = make_longlong2(0, 0);
         *reinterpret_cast<longlong2 *>(acc + i0 + 2) = make_longlong2(0, 0);
       } else {
@@ -404,10 +407,10 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
             make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
       }
     } else {
-      for (size_t i = i0; i < i0 + 4 && i < P; ++i) {
+      for (uint32_t i = i0; i < i0 + 4 && i < P; ++i) {
         float t1[4] = {th[i], 0, 0, 0}, m1[4] = {mm[i], 0, 0, 0}, v1[4] = {vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
         if (i < nemb) {
-          g1[0] = (float)((double)acc[i] * (1.0 / kEmbFix));
+          g1[0] = unfix40(acc[i]);
           acc[i] = 0;
         } else {
           g1[0] = gr[i];
@@ -521,10 +524,12 @@ void launch_update(const Plan &p, int T, cudaStream_t st) {
   const double per = p.wbf ? 30.0 : 28.0;
   {
     ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * per + nemb * 12.0), st);
-    size_t nq = (size_t)p.G * ((p.P + 3) / 4);
-    size_t grid = (nq + 255) / 256;
-    if (grid > 152 * 16) grid = 152 * 16;
-    opt_stream_kernel<<<(unsigned)grid, 256, 0, st>>>(p, T);
+    // about 16 blocks of 256 threads per SM over all groups; each grid row is one group
+    const size_t nq = (p.P + 3) / 4;
+    size_t gx = (nq + 255) / 256;
+    const size_t cap = std::max<size_t>(1, (size_t)152 * 16 / std::max(1, p.G));
+    if (gx > cap) gx = cap;
+    opt_stream_kernel<<<dim3((unsigned)gx, (unsigned)p.G), 256, 0, st>>>(p, T);
   }
   alpha_update_kernel<<<p.G, 32, 0, st>>>(p, T);
 }
@@ -539,7 +544,7 @@ __global__ void export_grad_kernel(Plan p, float *out) {
   int g = blockIdx.y;
   size_t nemb = (size_t)p.dm.A * p.dm.E;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < p.P; i += (size_t)gridDim.x * blockDim.x)
-    out[(size_t)g * p.P + i] = i < nemb ? (float)((double)p.demb_acc[(size_t)g * nemb + i] * (1.0 / kEmbFix))
+    out[(size_t)g * p.P + i] = i < nemb ? unfix40(p.demb_acc[(size_t)g * nemb + i])
                                         : p.grad[(size_t)g * p.P + i];
 }
 }  // namespace

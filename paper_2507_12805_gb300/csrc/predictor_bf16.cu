@@ -336,9 +336,9 @@ __global__ void hidden_reduce_kernel(Plan p, int T, const float *part, int hmax)
   const int model = blockIdx.y;  // 0 dynamic, 1 static
   const Dims &D = model ? p.st : p.dm;
   const int H = D.H;
-  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < (size_t)p.NL * H;
-       w += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(w / H), c = (int)(w - (size_t)r * H);
+  const uint32_t total = (uint32_t)p.NL * (uint32_t)H;  // 32-bit indices: no FP64-based 64-bit division
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+    const int r = (int)(w / (uint32_t)H), c = (int)(w - (uint32_t)r * (uint32_t)H);
     const int g = p.lane_grp[r];
     if (!row_pred(p, T, r, g)) continue;
     float acc = 0.f;
@@ -461,7 +461,7 @@ struct DXB : BBase {
   __device__ void one(long long b, int z, int i, float acc) const {
     int pos = i / p.dm.E, e = i - pos * p.dm.E;
     int tok = p.tokens[b - p.dm.t + pos];
-    long long q = __double2ll_rn((double)acc * kEmbFix);
+    long long q = fix40(acc);
     atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc + ((size_t)z * p.dm.A + tok) * p.dm.E + e),
               (unsigned long long)q);
   }

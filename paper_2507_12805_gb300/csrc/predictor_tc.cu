@@ -18,6 +18,7 @@
 // predicts at a step are a prefix of its lanes (lanes differ by at most one token), so the
 // lane-reducing GEMMs run over that prefix and zero the rows past it in their last K stage.
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <mutex>
 
@@ -30,6 +31,7 @@ namespace {
 using tc::bf16;
 
 constexpr size_t kTableMax = 48 * 1024;  // largest embedding table copied to shared memory
+constexpr size_t kAccMax = 96 * 1024;    // largest fixed-point gradient table summed in shared memory
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -47,6 +49,7 @@ struct MetaLayout {
 
 struct TBase {
   static constexpr bool kFinish = false;
+  static constexpr bool kFP8 = false;
   Plan p;
   int T;
   MetaLayout ml;
@@ -74,18 +77,18 @@ struct TBase {
   // targets of rows r0 .. r0 + n - 1 of group g (-1 past the group or for rows that predict
   // nothing), their t context tokens and the embedding table emb (A x E) if ml.table.  The table
   // arrives by one bulk copy that overlaps the target and token loads.
-  __device__ void fill(uint8_t *meta, const MetaLayout &ml, int g, int r0, int n, const bf16 *emb, int AE) const {
+  __device__ void fill(uint8_t *meta, const MetaLayout &ml, int g, int r0, int n, const void *emb, int bytes) const {
     __shared__ __align__(8) uint64_t tbar;
     long long *tpw = reinterpret_cast<long long *>(meta);
-    const bool copy = emb != nullptr && AE > 0 && ml.table >= AE * 2;
+    const bool copy = emb != nullptr && bytes > 0 && ml.table >= bytes;
     if (copy && threadIdx.x == 0) {
       const uint32_t bar = tc::sa(&tbar);
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-      tc::expect_tx(bar, (uint32_t)(AE * 2));
+      tc::expect_tx(bar, (uint32_t)bytes);
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                        tc::sa(meta + ml.tab_off())),
-                   "l"(emb), "r"(AE * 2), "r"(bar)
+                   "l"(emb), "r"(bytes), "r"(bar)
                    : "memory");
     }
     const int L = nrows(g);
@@ -168,7 +171,7 @@ struct HiddenT : TwoModels {
     MetaLayout l = ml;
     l.t = d(z).t;
     l.table = table[stat(z)] ? d(z).A * d(z).E * 2 : 0;
-    fill(meta, l, grp(z), m0, tc::kRows, w(z) + d(z).off_emb(), d(z).A * d(z).E);
+    fill(meta, l, grp(z), m0, tc::kRows, w(z) + d(z).off_emb(), d(z).A * d(z).E * 2);
   }
   __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
   __device__ tc::TmaOperand tma_b(int z) const { return {&w1[stat(z)], stat(z) ? 2 : 3, grp(z), 0}; }
@@ -301,17 +304,37 @@ struct DW2T : TBase {
 
 // dX = dh W1^T scattered into the embedding rows as fixed-point integers (order-free sums, so the
 // result does not depend on scheduling): A = dh by TMA (K-major), B = W1t[h][i] as N = i, K = h
-// by TMA (MN-major).  The lanes of a warp add consecutive elements of one embedding row.
+// by TMA (MN-major).  The lanes of a warp add consecutive elements of one embedding row.  Where
+// the group's fixed-point table (A x E x 8 bytes) fits in shared memory, the CTA first sums its
+// tile there and then adds each non-zero entry to global memory once, so a token that appears at
+// several (lane, position) pairs of the tile costs one global atomic per element instead of one
+// per pair.  A 64-bit shared-memory sum is kept as two 32-bit words updated by native 32-bit
+// atomics: the low word first, then the high word plus the carry out of the low word (the number
+// of wraps of the low word does not depend on the order of the adds, so the sum is exact).
 struct DXT : TBase {
   static constexpr bool kAMN = false, kBMN = true, kTail = false;
   static constexpr int kEpi = 1;
   static constexpr int kGather = 0;
+  static constexpr bool kFinish = true;
   CUtensorMap dh, w1;
+  int sacc;    // sum the tile in shared memory (ml.table bytes: low words [A*E] then high words [A*E])
+  int eshift;  // log2 E when E is a power of two, else -1
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const { fill(meta, ml, z, m0, tc::kRows, nullptr, 0); }
+  __device__ uint32_t *lo_s(const uint8_t *meta) const {
+    return reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(meta) + ml.tab_off());
+  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    MetaLayout l = ml;
+    l.table = 0;  // the accumulator region is not an embedding copy
+    fill(meta, l, z, m0, tc::kRows, nullptr, 0);
+    if (sacc) {
+      uint4 *a = reinterpret_cast<uint4 *>(lo_s(meta));
+      for (int i = threadIdx.x; i < p.dm.A * p.dm.E / 2; i += tc::kThreads) a[i] = make_uint4(0, 0, 0, 0);
+    }
+  }
   __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
   __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
   __device__ int row_a(int z, int m0) const { return row(z, m0); }
@@ -319,10 +342,30 @@ struct DXT : TBase {
   __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
   __device__ bool row_active(const uint8_t *meta, int, int, int rl) const { return tp(meta)[rl] >= 0; }
   __device__ void emit(const uint8_t *meta, int z, int, int rl, int n, float v) const {
-    const int pos = n / p.dm.E;
-    const size_t i = ((size_t)z * p.dm.A + tk(meta)[rl * p.dm.t + pos]) * p.dm.E + (n - pos * p.dm.E);
-    atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc) + i,
-              (unsigned long long)__double2ll_rn((double)v * kEmbFix));
+    const int pos = eshift >= 0 ? n >> eshift : n / p.dm.E;
+    const uint32_t i = (uint32_t)tk(meta)[rl * p.dm.t + pos] * (uint32_t)p.dm.E + (uint32_t)(n - pos * p.dm.E);
+    const long long q = fix40(v);
+    if (q == 0) return;
+    if (sacc) {
+      uint32_t *lo = lo_s(meta);
+      const uint32_t ql = (uint32_t)(unsigned long long)q, qh = (uint32_t)((unsigned long long)q >> 32);
+      const uint32_t old = atomicAdd(lo + i, ql);
+      const uint32_t up = qh + (old + ql < old ? 1u : 0u);  // high part plus the carry out of the low word
+      if (up) atomicAdd(lo + p.dm.A * p.dm.E + i, up);
+    } else {
+      atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * p.dm.A * p.dm.E + i,
+                (unsigned long long)q);
+    }
+  }
+  // every thread, after the epilogue's last barrier: the non-zero sums of the tile to global memory
+  __device__ void finish(uint8_t *meta, int z) const {
+    if (!sacc) return;
+    const uint32_t *lo = lo_s(meta), *hi = lo + p.dm.A * p.dm.E;
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * p.dm.A * p.dm.E;
+    for (int i = threadIdx.x; i < p.dm.A * p.dm.E; i += tc::kThreads) {
+      const unsigned long long q = ((unsigned long long)hi[i] << 32) | lo[i];
+      if (q) atomicAdd(dst + i, q);
+    }
   }
 };
 
@@ -339,7 +382,7 @@ struct DW1T : TBase {
   __device__ int N(int) const { return p.dm.K1(); }
   __device__ int K(int z) const { return npred(z); }
   __device__ void prepare(uint8_t *meta, int z, int) const {
-    fill(meta, ml, z, 0, npred(z), wb(z) + p.dm.off_emb(), p.dm.A * p.dm.E);
+    fill(meta, ml, z, 0, npred(z), wb(z) + p.dm.off_emb(), p.dm.A * p.dm.E * 2);
   }
   __device__ tc::TmaOperand tma_a(int z) const { return {&dh, 2, 0, p.grp_lane_off[z]}; }
   __device__ tc::TmaOperand tma_b(int) const { return kNoTma; }
@@ -392,31 +435,172 @@ struct DW1T : TBase {
   }
 };
 
-// db1 = sum of dh, db2 = sum of dz over the predicted rows of each group.  Block (32 columns x 8
-// row slices): slice y adds rows y, y+8, ... in order, then slice 0 adds the 8 partial sums in
-// order, so the result does not depend on scheduling.
-constexpr int kBiasSlices = 8;
-__global__ void __launch_bounds__(32 * kBiasSlices) bias_grad_kernel(Plan p, int T) {
-  __shared__ float part[kBiasSlices][32];
+// ---- the frozen static model in FP8 (E4M3): hidden layer and logits on kind::f8f6f4 ----
+// h = relu((X_q W1_q) c1[h] + b1) in FP32, X_q gathered from the E4M3 embedding codes (16 codes per
+// 16-byte chunk; E % 16 == 0), W1_q = the W1t codes by TMA (K-major).  The epilogue also raises the
+// row's largest activation (float bits: h >= 0, so integer order is float order).
+struct HiddenF8 : TBase {
+  static constexpr bool kAMN = false, kBMN = false, kTail = false, kFP8 = true;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 1;
+  CUtensorMap w1;  // W1t codes [H][t*E], box {128, nt}
+  int table;       // E4M3 embedding table kept in shared memory
+  __device__ bool active(int z) const { return group_trains(p, T, z); }
+  __device__ int M(int z) const { return nrows(z); }
+  __device__ int N(int) const { return p.st.H; }
+  __device__ int K(int) const { return p.st.K1(); }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    MetaLayout l = ml;
+    l.table = table ? p.st.A * p.st.E : 0;
+    fill(meta, l, z, m0, tc::kRows, p.st8, p.st.A * p.st.E);
+  }
+  __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
+  __device__ tc::TmaOperand tma_b(int) const { return {&w1, 2, 0, 0}; }
+  __device__ int row_a(int, int) const { return 0; }
+  __device__ int row_b(int, int n0) const { return n0; }
+  // thread: 16-byte chunk c = tid % 8 (16 codes) of rows tid / 8 + 32 i
+  __device__ void gather(uint8_t *tile, const uint8_t *meta, int, int, int k0, int) const {
+    const Dims &D = p.st;
+    const long long *tpv = tp(meta);
+    const uint16_t *tkv = tk(meta);
+    const uint8_t *tab_s = table ? meta + ml.tab_off() : nullptr;
+    const int c = threadIdx.x & 7, k = k0 + 16 * c, r0 = threadIdx.x >> 3;
+    const bool kin = k < D.K1();
+    const int pos = kin ? k / D.E : 0, e = k - pos * D.E;
+    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int r = r0 + kStep * i;
+      uint8_t *dst = tile + tc::sw_k(r, c);
+      const bool ok = kin && tpv[r] >= 0;
+      const int off = ok ? (int)tkv[r * D.t + pos] * D.E + e : 0;
+      if (!ok)
+        zero16(dst);
+      else if (tab_s)
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tab_s + off);
+      else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(p.st8 + off));
+    }
+  }
+  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
+    if (tp(meta)[rl] < 0) return;
+    const float *c1 = p.st8_c1 + n, *b1 = p.static_params + p.st.off_b1() + n;
+    const int rw = row(z, m);
+    float x[8], mx = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float a = fmaf(v[j], c1[j], b1[j]);
+      x[j] = a > 0.f ? a : 0.f;  // +0 below zero (its bits must order as a float)
+      mx = fmaxf(mx, x[j]);
+    }
+    store8(p.hs + (size_t)rw * p.st.H + n, x);
+    atomicMax(p.hs_rowmax + rw, __float_as_uint(mx));
+  }
+};
+
+// L = (h_q W2_q) s_r s_w2[a] + b2: A = the row's activations coded as E4M3 with the row scale
+// s_r = max h / 448 (gathered from the FP32 h), B = the transposed W2 codes [A][H] by TMA (K-major).
+struct LogitsF8 : TBase {
+  static constexpr bool kAMN = false, kBMN = false, kTail = false, kFP8 = true;
+  static constexpr int kEpi = 0;
+  static constexpr int kGather = 1;
+  CUtensorMap w2;  // W2t codes [A][H], box {128, nt}
+  __device__ bool active(int z) const { return group_trains(p, T, z); }
+  __device__ int M(int z) const { return nrows(z); }
+  __device__ int N(int) const { return p.st.A; }
+  __device__ int K(int) const { return p.st.H; }
+  // meta: targets | (no tokens) | per row: s_r and 448 / max h (0 for an all-zero row)
+  __device__ float *rs(const uint8_t *meta) const {
+    return reinterpret_cast<float *>(const_cast<uint8_t *>(meta) + ml.tab_off());
+  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    fill(meta, ml, z, m0, tc::kRows, nullptr, 0);
+    float *r = rs(meta);
+    for (int i = threadIdx.x; i < tc::kRows; i += tc::kThreads) {
+      const int m = m0 + i;
+      const float mx = m < nrows(z) ? __uint_as_float(p.hs_rowmax[row(z, m)]) : 0.f;
+      r[2 * i] = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
+      r[2 * i + 1] = mx > 0.f ? __fdiv_rn(448.f, mx) : 0.f;
+    }
+  }
+  __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
+  __device__ tc::TmaOperand tma_b(int) const { return {&w2, 2, 0, 0}; }
+  __device__ int row_a(int, int) const { return 0; }
+  __device__ int row_b(int, int n0) const { return n0; }
+  // thread: 16-byte chunk c = tid % 8 (16 activations) of rows tid / 8 + 32 i
+  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int m0, int k0, int) const {
+    const int H = p.st.H;
+    const long long *tpv = tp(meta);
+    const float *r = rs(meta);
+    const int c = threadIdx.x & 7, k = k0 + 16 * c, r0 = threadIdx.x >> 3;
+    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int rl = r0 + kStep * i;
+      uint4 out = make_uint4(0, 0, 0, 0);
+      if (k < H && tpv[rl] >= 0) {  // H % 16 == 0: a chunk is all in or all out
+        const float inv = r[2 * rl + 1];
+        const float4 *src = reinterpret_cast<const float4 *>(p.hs + (size_t)row(z, m0 + rl) * H + k);
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 f = src[q];
+          const __nv_fp8x4_e4m3 x(make_float4(f.x * inv, f.y * inv, f.z * inv, f.w * inv));
+          w[q] = *reinterpret_cast<const uint32_t *>(&x);
+        }
+        out = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      *reinterpret_cast<uint4 *>(tile + tc::sw_k(rl, c)) = out;
+    }
+  }
+  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
+    if (tp(meta)[rl] < 0) return;
+    const float sr = rs(meta)[2 * rl];
+    const float *s2 = p.st8_s2 + n, *b2 = p.static_params + p.st.off_b2() + n;
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fmaf(v[j], __fmul_rn(sr, s2[j]), b2[j]);
+    store8(p.zu + (size_t)row(z, m) * p.st.A + n, x);
+  }
+};
+
+// db1 = sum of dh, db2 = sum of dz over the predicted rows of each group (the predicted lanes are
+// a prefix of the group's lanes).  Block: 16 chunks of 8 columns x 16 row slices; slice y adds
+// rows y, y + 16, ... in order (16-byte loads), then slice 0 adds the 16 partial sums in order,
+// so the result does not depend on scheduling.
+constexpr int kBiasChunks = 16, kBiasSlices = 16;
+__global__ void __launch_bounds__(kBiasChunks * kBiasSlices) bias_grad_kernel(Plan p, int T) {
+  __shared__ float part[kBiasSlices][kBiasChunks * 8 + 4];
   const int g = blockIdx.y;
   if (!group_trains(p, T, g)) return;
   const int H = p.dm.H, A = p.dm.A;
-  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int cx = threadIdx.x % kBiasChunks, y = threadIdx.x / kBiasChunks;
+  const int c = (blockIdx.x * kBiasChunks + cx) * 8;  // first of 8 columns (H and A are multiples of 8)
   const bool in = c < H + A, is1 = c < H;
   const int w = is1 ? H : A, cc = is1 ? c : c - H;
   const bf16 *src = is1 ? p.dh_b : p.dz_b;
-  const int j = T - p.grp_start[g];
-  float s = 0.f;
-  if (in)
+  const int r0 = p.grp_lane_off[g], n = live_lanes(p, g, T - p.grp_start[g]);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (in) {
 #pragma unroll 4
-    for (int r = p.grp_lane_off[g] + threadIdx.y; r < p.grp_lane_off[g + 1]; r += kBiasSlices)
-      if (j >= p.t_eff && j < p.lane_len[r]) s += __bfloat162float(src[(size_t)r * w + cc]);
-  part[threadIdx.y][threadIdx.x] = s;
+    for (int r = y; r < n; r += kBiasSlices) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)(r0 + r) * w + cc);
+      const bf16 *b = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s[q] += __bfloat162float(b[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) part[y][cx * 8 + q] = s[q];
   __syncthreads();
-  if (threadIdx.y == 0 && in) {
-    float t = 0.f;
-    for (int y = 0; y < kBiasSlices; ++y) t += part[y][threadIdx.x];
-    p.grad[(size_t)g * p.P + (is1 ? p.dm.off_b1() : p.dm.off_b2()) + cc] = t;
+  if (threadIdx.x < kBiasChunks * 8) {
+    const int col = blockIdx.x * kBiasChunks * 8 + threadIdx.x;
+    if (col < H + A) {
+      float t = 0.f;
+      for (int yy = 0; yy < kBiasSlices; ++yy) t += part[yy][threadIdx.x];
+      const bool b1 = col < H;
+      p.grad[(size_t)g * p.P + (b1 ? p.dm.off_b1() + col : p.dm.off_b2() + (col - H))] = t;
+    }
   }
 }
 
@@ -435,16 +619,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// BF16 tensor map with 128-byte swizzle: dims[0] innermost (elements), strides in bytes for the
-// outer dimensions, box {64, box1}
-bool make_map(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides, int box1) {
+// BF16 (or, with u8, E4M3 code) tensor map with 128-byte swizzle: dims[0] innermost (elements),
+// strides in bytes for the outer dimensions, box {128 bytes of elements, box1}
+bool make_map(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides, int box1,
+              bool u8 = false) {
   auto fn = encode_fn();
   if (!fn || !ptr) return false;
   cuuint64_t d[3], s[2];
-  cuuint32_t box[3] = {64, (cuuint32_t)box1, 1}, es[3] = {1, 1, 1};
+  cuuint32_t box[3] = {u8 ? 128u : 64u, (cuuint32_t)box1, 1}, es[3] = {1, 1, 1};
   for (int i = 0; i < rank; ++i) d[i] = dims[i];
   for (int i = 0; i + 1 < rank; ++i) s[i] = strides[i];
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(ptr), d, s, box, es,
+  return fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
+            const_cast<void *>(ptr), d, s, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -452,31 +638,35 @@ bool make_map(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, c
 // Everything the six launches of a plan need: tile widths, shared data sizes and tensor maps.
 struct TcSetup {
   // key: the plan's buffers and shapes
-  const void *wbf, *static_bf, *hd_b, *hs_b, *dz_b, *dh_b;
+  const void *wbf, *static_bf, *hd_b, *hs_b, *dz_b, *dh_b, *st8;
   int G, NL, Mmax, use_static;
   Dims dm, st;
   size_t P;
   bool ok;
-  tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1;
-  MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1;
-  int table_h[2], table_w1;
-  CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn;
+  tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8;
+  MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
+  int table_h[2], table_w1, sacc_dx, table_h8;
+  CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
 };
 
 bool same_key(const TcSetup &a, const Plan &p) {
   auto dims_eq = [](const Dims &x, const Dims &y) { return x.A == y.A && x.E == y.E && x.t == y.t && x.H == y.H; };
   return a.wbf == p.wbf && a.static_bf == p.static_bf && a.hd_b == p.hd_b && a.hs_b == p.hs_b && a.dz_b == p.dz_b &&
-         a.dh_b == p.dh_b && a.G == p.G && a.NL == p.NL && a.Mmax == p.Mmax && a.use_static == p.use_static &&
+         a.dh_b == p.dh_b && a.st8 == p.st8 && a.G == p.G && a.NL == p.NL && a.Mmax == p.Mmax &&
+         a.use_static == p.use_static &&
          dims_eq(a.dm, p.dm) && (!p.use_static || dims_eq(a.st, p.st)) && a.P == p.P;
 }
 
 bool shapes_ok(const Plan &p) {
   auto ok = [](const Dims &d) { return d.E % 8 == 0 && d.H % 64 == 0 && d.A % 64 == 0 && d.K1() % 64 == 0; };
-  return p.G > 0 && p.NL > 0 && p.Mmax > 0 && ok(p.dm) && p.P % 8 == 0 && (!p.use_static || ok(p.st));
+  // the FP8 static model: 16 E4M3 codes per gathered chunk never straddle two embedding rows
+  const bool f8 = p.st8 == nullptr || p.st.E % 16 == 0;
+  return p.G > 0 && p.NL > 0 && p.Mmax > 0 && ok(p.dm) && p.P % 8 == 0 && (!p.use_static || ok(p.st)) && f8;
 }
 
 bool build(TcSetup &S, const Plan &p) {
   S.wbf = p.wbf, S.static_bf = p.static_bf, S.hd_b = p.hd_b, S.hs_b = p.hs_b, S.dz_b = p.dz_b, S.dh_b = p.dh_b;
+  S.st8 = p.st8;
   S.G = p.G, S.NL = p.NL, S.Mmax = p.Mmax, S.use_static = p.use_static, S.dm = p.dm, S.st = p.st, S.P = p.P;
   S.ok = false;
   if (!shapes_ok(p) || !encode_fn()) return false;
@@ -492,7 +682,8 @@ bool build(TcSetup &S, const Plan &p) {
                                        S.table_h[1] ? (size_t)Sd.A * Sd.E * 2 : 0)};
   S.ml_l = S.ml_dh = {tc::kRows, 0, 0};
   S.ml_w2 = {0, 0, 0};
-  S.ml_dx = {tc::kRows, D.t, 0};
+  S.sacc_dx = (size_t)D.A * D.E * 8 <= kAccMax;
+  S.ml_dx = {tc::kRows, D.t, S.sacc_dx ? D.A * D.E * 8 : 0};
   S.ml_w1 = {p.Mmax, D.t, S.table_w1 ? D.A * D.E * 2 : 0};
   const int Hmax = p.use_static ? max(D.H, Sd.H) : D.H, K1max = p.use_static ? max(D.K1(), Sd.K1()) : D.K1();
   S.t_h = tc::plan_tiles(p.Mmax, Hmax, K1max, Z, S.ml_h.bytes(), false);
@@ -528,7 +719,22 @@ bool build(TcSetup &S, const Plan &p) {
   ok &= act(&S.hmn, p.hd_b, D.H, 64);
   ok &= act(&S.dzmn, p.dz_b, D.A, 64);
   ok &= act(&S.dhmn, p.dh_b, D.H, 64);
-  if (p.use_static) {
+  const bool f8 = p.use_static && p.st8 != nullptr;
+  if (f8) {  // the static model in E4M3: its own tiles (128 K per stage) and code maps
+    S.table_h8 = (size_t)Sd.A * Sd.E <= kTableMax;
+    S.ml_h8 = {tc::kRows, Sd.t, S.table_h8 ? Sd.A * Sd.E : 0};
+    S.ml_l8 = {tc::kRows, 0, tc::kRows * 8};
+    S.t_h8 = tc::plan_tiles(p.Mmax, Sd.H, Sd.K1(), p.G, S.ml_h8.bytes(), false, 2 * tc::kBK);
+    S.t_l8 = tc::plan_tiles(p.Mmax, Sd.A, Sd.H, p.G, S.ml_l8.bytes(), false, 2 * tc::kBK);
+    if (tc::smem_bytes(S.t_h8, S.ml_h8.bytes()) > limit || tc::smem_bytes(S.t_l8, S.ml_l8.bytes()) > limit)
+      return false;
+    const uint8_t *w1c = p.st8 + (size_t)Sd.A * Sd.E, *w2c = w1c + (size_t)Sd.H * Sd.K1();
+    const uint64_t d1[2] = {(uint64_t)Sd.K1(), (uint64_t)Sd.H}, s1[1] = {(uint64_t)Sd.K1()};
+    ok &= make_map(&S.w1_8, w1c, 2, d1, s1, S.t_h8.nt, true);
+    const uint64_t d2[2] = {(uint64_t)Sd.H, (uint64_t)Sd.A}, s2[1] = {(uint64_t)Sd.H};
+    ok &= make_map(&S.w2_8, w2c, 2, d2, s2, S.t_l8.nt, true);
+  }
+  if (p.use_static && !f8) {
     const uint64_t d1[2] = {(uint64_t)Sd.K1(), (uint64_t)Sd.H}, s1[1] = {(uint64_t)Sd.K1() * 2};
     ok &= make_map(&S.w1k[1], p.static_bf + Sd.off_w1(), 2, d1, s1, S.t_h.nt);
     const uint64_t d2[2] = {(uint64_t)Sd.A, (uint64_t)Sd.H}, s2[1] = {(uint64_t)Sd.A * 2};
@@ -567,16 +773,29 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st) {
   TcSetup S;
   if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
-  const int Z = p.use_static ? 2 * p.G : p.G;
+  const bool f8 = p.use_static && p.st8 != nullptr;  // static model on its own E4M3 launches
+  const int Z = p.use_static && !f8 ? 2 * p.G : p.G;
+  if (f8) {
+    {
+      ProfScope ps("fwd_hidden_static_fp8", 2.0 * R * p.st.K1() * p.st.H, 0, st);
+      HiddenF8 op;
+      op.p = p, op.T = T, op.ml = S.ml_h8, op.w1 = S.w1_8, op.table = S.table_h8;
+      tc::launch(op, p.Mmax, p.st.H, p.G, S.t_h8, S.ml_h8.bytes(), st);
+    }
+    ProfScope ps("fwd_logits_static_fp8", 2.0 * R * p.st.H * p.st.A, 0, st);
+    LogitsF8 op;
+    op.p = p, op.T = T, op.ml = S.ml_l8, op.w2 = S.w2_8;
+    tc::launch(op, p.Mmax, p.st.A, p.G, S.t_l8, S.ml_l8.bytes(), st);
+  }
   {
-    double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
+    double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static && !f8 ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
     ProfScope ps("fwd_hidden_bf16", fl, 0, st);
     HiddenT op;
     op.p = p, op.T = T, op.ml = S.ml_h, op.w1[0] = S.w1k[0], op.w1[1] = S.w1k[1];
     op.table[0] = S.table_h[0], op.table[1] = S.table_h[1];
     tc::launch(op, p.Mmax, p.use_static ? max(p.dm.H, p.st.H) : p.dm.H, Z, S.t_h, S.ml_h.bytes(), st);
   }
-  double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static ? 2.0 * R * p.st.H * p.st.A : 0.0);
+  double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static && !f8 ? 2.0 * R * p.st.H * p.st.A : 0.0);
   ProfScope ps("fwd_logits_bf16", fl, 0, st);
   LogitsT op;
   op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0], op.w2[1] = S.w2mn[1];
@@ -606,7 +825,8 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
   {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXT op;
-    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
+    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn, op.sacc = S.sacc_dx;
+    op.eshift = (D.E & (D.E - 1)) == 0 ? __builtin_ctz((unsigned)D.E) : -1;
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
   }
   {
@@ -614,7 +834,8 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     DW2T op;
     op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
     tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
-    bias_grad_kernel<<<dim3((D.H + D.A + 31) / 32, p.G), dim3(32, kBiasSlices), 0, s1>>>(p, T);
+    bias_grad_kernel<<<dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G), kBiasChunks * kBiasSlices, 0,
+                       s1>>>(p, T);
   }
   {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);

@@ -35,9 +35,10 @@ namespace tc {
 
 using bf16 = __nv_bfloat16;
 constexpr int kRows = 128;             // MMA M: tile rows = tensor-memory lanes
-constexpr int kBK = 64;                // K per pipeline stage (one 128-byte swizzle row)
+constexpr int kBK = 64;                // BF16 K per pipeline stage (one 128-byte swizzle row)
+constexpr int kRowBytes = 128;         // bytes of K per operand row and stage (64 BF16 or 128 E4M3)
 constexpr int kThreads = 256;          // eight warps: warps w and w + 4 share tensor-memory lanes 32(w % 4)..
-constexpr int kStages = 4;             // most stage buffers of a ring (a launch may use fewer)
+constexpr int kStages = 6;             // most stage buffers of a ring (a launch may use fewer)
 constexpr long kSpinLimit = 1L << 24;  // mbarrier polls before a wait gives up
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -111,6 +112,8 @@ __device__ __forceinline__ uint32_t sw_mn(int n, int k) {
 
 // Op interface (device, const):
 //   static constexpr bool kAMN, kBMN;         operand majors (A: M x K, B: N x K)
+//   static constexpr bool kFP8;               E4M3 operands (kind::f8f6f4, K-major only, 128 K per
+//                                             stage, K = 32 per MMA) instead of BF16 (kind::f16)
 //   static constexpr bool kTail;              K rows past K(z) in the last stage must be zeroed
 //                                             (the dense operands run on into other groups)
 //   static constexpr int kGather;             0: both operands by TMA; 1: A gathered; 2: B gathered
@@ -141,7 +144,9 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (sa(smem_raw) + 1023) & ~1023u;
   uint8_t *gbase = smem_raw + (base - sa(smem_raw));
-  const uint32_t a_bytes = kRows * kBK * 2, b_bytes = nt_max * kBK * 2;
+  static_assert(!Op::kFP8 || (!Op::kAMN && !Op::kBMN && !Op::kTail), "E4M3 operands are K-major");
+  constexpr int BK = Op::kFP8 ? 2 * kBK : kBK;  // K elements per stage
+  const uint32_t a_bytes = kRows * kRowBytes, b_bytes = nt_max * kRowBytes;
   const uint32_t sA = base, sB = base + ns * a_bytes;
   uint8_t *meta = gbase + ns * (a_bytes + b_bytes);
   __shared__ __align__(8) uint64_t full[kStages], done[kStages];
@@ -163,16 +168,16 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
 
-  const int nk = max(1, (K + kBK - 1) / kBK);  // K = 0 still runs one all-zero stage
+  const int nk = max(1, (K + BK - 1) / BK);  // K = 0 still runs one all-zero stage
   const TmaOperand ta = op.tma_a(z), tb = op.tma_b(z);
   const int ra = op.row_a(z, m0), rb = op.row_b(z, n0);
   // bytes per stage: a K-major box is as high as the map's box (nt_max rows for B), MN-major
   // boxes are issued for this tile's nt columns only
   const uint32_t tx = (Op::kGather == 1 ? 0u : a_bytes) +
-                      (Op::kGather == 2 ? 0u : (uint32_t)(Op::kBMN ? nt : nt_max) * kBK * 2);
+                      (Op::kGather == 2 ? 0u : (uint32_t)(Op::kBMN ? nt : nt_max) * kRowBytes);
   // fill stage s with K block kt: bulk copies by thread 0, the gathered operand by every thread
   auto issue = [&](int s, int kt) {
-    const int k0 = kt * kBK;
+    const int k0 = kt * BK;
     if (tid == 0) {
       const uint32_t bar = sa(&full[s]);
       expect_tx(bar, tx);
@@ -207,13 +212,20 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
     }
   };
 
-  // instruction descriptor: FP32 accumulator, BF16 A and B, operand majors, N = nt, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((Op::kAMN ? 1u : 0u) << 15) |
+  // instruction descriptor: FP32 accumulator, A and B BF16 (format 1 of kind::f16) or E4M3 (format 0 of
+  // kind::f8f6f4), operand majors, N = nt, M = 128
+  const uint32_t fmt = Op::kFP8 ? 0u : 1u;
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((Op::kAMN ? 1u : 0u) << 15) |
                          ((Op::kBMN ? 1u : 0u) << 16) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
   const uint32_t a_lbo = Op::kAMN ? 8192 : 16, a_step = Op::kAMN ? 2048 : 32;
   const uint32_t b_lbo = Op::kBMN ? 8192 : 16, b_step = Op::kBMN ? 2048 : 32;
+  // Prefetch distance pf: K block kt + pf is staged while block kt is multiplied.  Its buffer was
+  // last read by the MMAs of block kt + pf - ns, i.e. kt - 2 (ns >= 3), which were committed two
+  // iterations earlier, so refilling it rarely waits on the tensor core; with ns = 2 the distance
+  // is one block and the refill waits for block kt - 1.
+  const int pf = ns >= 3 ? ns - 2 : 1;
   bool ok = true;
-  for (int s = 0; s < ns - 1; ++s) {
+  for (int s = 0; s < pf; ++s) {
     if (s < nk)
       issue(s, s);
     else if (Op::kGather)
@@ -222,19 +234,19 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt % ns;
     const uint32_t par = (uint32_t)((kt / ns) & 1);
-    const bool tail = Op::kTail && kt == nk - 1 && K - kt * kBK < kBK;
+    const bool tail = Op::kTail && kt == nk - 1 && K - kt * BK < BK;
     if (Op::kGather || tail) {
-      // a gathered stage kt is the oldest of the ns - 1 copy groups in flight
+      // a gathered stage kt is the oldest of the pf copy groups in flight
       if (Op::kGather) {
-        if (ns >= 4)
-          asm volatile("cp.async.wait_group 2;\n" ::);
-        else if (ns == 3)
-          asm volatile("cp.async.wait_group 1;\n" ::);
-        else
-          asm volatile("cp.async.wait_group 0;\n" ::);
+        switch (pf) {
+          case 1: asm volatile("cp.async.wait_group 0;\n" ::); break;
+          case 2: asm volatile("cp.async.wait_group 1;\n" ::); break;
+          case 3: asm volatile("cp.async.wait_group 2;\n" ::); break;
+          default: asm volatile("cp.async.wait_group 3;\n" ::); break;
+        }
       }
       if (ok) ok = mbar_wait(sa(&full[s]), par);
-      if (tail && ok) zero_tail(s, max(0, K - kt * kBK));
+      if (tail && ok) zero_tail(s, max(0, K - kt * BK));
       asm volatile("fence.proxy.async.shared::cta;\n" ::);
       __syncthreads();
     } else if (tid == 0 && ok) {
@@ -242,23 +254,29 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
     }
     if (tid == 0 && ok) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      for (int kk = 0; kk < kBK / 16; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {  // four MMAs of 32 bytes of K (K = 16 BF16 or 32 E4M3)
         const uint64_t da = desc_sw128(sA + s * a_bytes + kk * a_step, a_lbo, 1024);
         const uint64_t db = desc_sw128(sB + s * b_bytes + kk * b_step, b_lbo, 1024);
         const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(accum));
+        if constexpr (Op::kFP8)
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(accum));
+        else
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(accum));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           sa(&done[s])));
     }
-    // refill the buffer of stage kt - 1 once its MMAs have read it
-    const int nxt = kt + ns - 1;
+    // stage K block kt + pf once the MMAs that last read its buffer (block kt + pf - ns) are done
+    const int nxt = kt + pf, prev = nxt - ns;
     if (nxt < nk) {
       const bool need = Op::kGather != 0 || tid == 0;
-      if (need && kt >= 1 && ok) ok = mbar_wait(sa(&done[(kt - 1) % ns]), (uint32_t)(((kt - 1) / ns) & 1));
+      if (need && prev >= 0 && ok) ok = mbar_wait(sa(&done[prev % ns]), (uint32_t)((prev / ns) & 1));
       if (need && ok)
         issue(nxt % ns, nxt);
       else if (Op::kGather)
@@ -352,22 +370,23 @@ inline int pow2_at_least(int x) {
 }
 
 // Tile plan for Z problems whose M, N and K are at most Mmax, Nmax (a multiple of 64) and Kmax,
-// with meta_bytes of per-tile shared data: as many stage buffers as K blocks (up to kStages) and
+// with meta_bytes of per-tile shared data: K blocks + 2 stage buffers (up to kStages) and
 // the widest column tile (a multiple of 64, <= 256) that still gives at least one CTA per SM and
 // fits the shared memory.  Tensor maps of K-major B operands use nt as their box height.
 struct TilePlan {
   int nt, ns;
 };
 inline size_t smem_bytes(const TilePlan &t, size_t meta_bytes) {
-  return 1024 + (size_t)t.ns * (kRows + t.nt) * kBK * 2 + ((meta_bytes + 15) & ~(size_t)15);
+  return 1024 + (size_t)t.ns * (kRows + t.nt) * kRowBytes + ((meta_bytes + 15) & ~(size_t)15);
 }
-inline TilePlan plan_tiles(int Mmax, int Nmax, int Kmax, int Z, size_t meta_bytes, bool split = true) {
+inline TilePlan plan_tiles(int Mmax, int Nmax, int Kmax, int Z, size_t meta_bytes, bool split = true, int bk = kBK) {
   const int mt = (Mmax + kRows - 1) / kRows;
-  TilePlan t{min(256, Nmax), max(2, min(kStages, (Kmax + kBK - 1) / kBK))};
+  // K blocks + 2 buffers let every block be staged before the MMAs need it (prefetch ns - 2)
+  TilePlan t{min(256, Nmax), max(2, min(kStages, (Kmax + bk - 1) / bk + 2))};
   // (an op that gathers its A operand pays the gather once per column tile: split = false)
   while (split && t.nt > 64 && (t.nt / 2) % 64 == 0 && (long)mt * ((Nmax + t.nt - 1) / t.nt) * Z < 152L) t.nt /= 2;
+  while (t.ns > 2 && smem_bytes(t, meta_bytes) > 220 * 1024) --t.ns;  // fewer buffers before narrower tiles
   while (t.nt > 64 && (t.nt / 2) % 64 == 0 && smem_bytes(t, meta_bytes) > 220 * 1024) t.nt /= 2;
-  while (t.ns > 2 && smem_bytes(t, meta_bytes) > 220 * 1024) --t.ns;
   return t;
 }
 
