@@ -438,14 +438,35 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
   const Layout &L = R.L;
   const Schedule &S = R.S;
   const int t_eff = R.p.t_eff;
-  // auxiliary streams: the count model beside the network's forward, and the three gradient
-  // GEMMs side by side (joined by events before the kernels that read their results)
+  // auxiliary streams: the count model beside the network's forward, the three gradient GEMMs side
+  // by side, and (BF16 forms) the static model's forward of step T + 1 beside the backward and the
+  // optimiser of step T (it reads only tokens decoded by step T), joined by events before the
+  // kernels that read their results
   StepStreams ss;
   bool use_ss = true;
   for (auto &a : ss.aux) use_ss = use_ss && cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
-  for (cudaEvent_t *e : {&ss.fork, &ss.join[0], &ss.join[1], &ss.count_done})
+  for (cudaEvent_t *e : {&ss.fork, &ss.join[0], &ss.join[1], &ss.count_done, &ss.mix_done, &ss.static_done})
     use_ss = use_ss && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   if (!use_ss) cudaGetLastError();  // fall back to the caller's stream alone
+  // per global step: does any group predict (and so run the network's forward)?
+  std::vector<char> pred_at(S.T_total + 1, 0);
+  for (int g = 0; g < L.G; ++g)
+    for (int j = t_eff; j < L.steps[g]; ++j) pred_at[S.start[g] + j] = 1;
+  // rows predicted and groups trained at a global step (the profiler's work figures)
+  auto work_at = [&](int T) {
+    StepWork w{0.0, 0.0};
+    for (int g = 0; g < L.G; ++g) {
+      const int j = T - S.start[g];
+      if (j < t_eff || j >= L.steps[g]) continue;
+      const int M = L.lane_off[g + 1] - L.lane_off[g];
+      w.pred_rows += j < L.base_len[g] ? M : (j == L.base_len[g] ? L.extra[g] : 0);
+      w.train_groups += 1;
+    }
+    return w;
+  };
+  const bool bf = bf_form(R.p.precision);
+  const bool split_static = R.net && use_ss && bf && R.p.use_static && tc_supported(R.p);
+  int static_for = -1;  // the step whose static forward is already queued on ss.aux[2]
   for (int T = 0; T < S.T_total; ++T) {
     int np = R.pair_off[T + 1] - R.pair_off[T];
     if (np > 0) {
@@ -453,19 +474,14 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     bool any_pred = false, any_code = false, any_count = false;
-    StepWork w{0.0, 0.0};
     for (int g = 0; g < L.G; ++g) {
       int j = T - S.start[g];
       if (j < 0 || j >= L.steps[g]) continue;
-      if (j >= t_eff) {
-        any_pred = true;
-        int M = L.lane_off[g + 1] - L.lane_off[g];
-        w.pred_rows += j < L.base_len[g] ? M : (j == L.base_len[g] ? L.extra[g] : 0);
-        w.train_groups += 1;
-      }
+      if (j >= t_eff) any_pred = true;
       if (grp_mode[g] != kReplay) any_code = true;
       if (!R.cmode.empty() && R.cmode[g]) any_count = true;
     }
+    const StepWork w = work_at(T);
     prof_step(T, w);
     const bool net = R.net && (any_pred || any_code);
     if (any_count) {
@@ -481,18 +497,42 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       R.launches++;
     }
     if (!R.net) continue;
-    const bool bf = bf_form(R.p.precision);
     if (any_pred) {
-      if (bf)
+      if (split_static) {
+        if (static_for != T) {  // not queued by the previous step (the first predicting step)
+          cudaEventRecord(ss.fork, st);
+          cudaStreamWaitEvent(ss.aux[2], ss.fork, 0);
+          launch_forward_bf16(R.p, T, ss.aux[2], kFwdStatic);
+          cudaEventRecord(ss.static_done, ss.aux[2]);
+          R.launches += 2;
+        }
+        launch_forward_bf16(R.p, T, st, kFwdDynamic);
+        cudaStreamWaitEvent(st, ss.static_done, 0);
+        R.launches += 2;
+      } else if (bf) {
         launch_forward_bf16(R.p, T, st);
-      else
+        R.launches += 2;
+      } else {
         launch_forward(R.p, T, st);
-      R.launches += bf ? 2 : (R.c.use_static ? 4 : 2);
+        R.launches += R.c.use_static ? 4 : 2;
+      }
     }
     if (any_count && use_ss && net) cudaStreamWaitEvent(st, ss.count_done, 0);
     if (any_pred || any_code) {
       launch_mixcode(R.p, T, st);
       R.launches++;
+    }
+    if (split_static && T + 1 < S.T_total && pred_at[T + 1]) {
+      // static forward of the next step: its contexts are decoded by now, and the mixer has read
+      // this step's static logits
+      cudaEventRecord(ss.mix_done, st);
+      cudaStreamWaitEvent(ss.aux[2], ss.mix_done, 0);
+      prof_step(T + 1, work_at(T + 1));
+      launch_forward_bf16(R.p, T + 1, ss.aux[2], kFwdStatic);
+      prof_step(T, w);
+      cudaEventRecord(ss.static_done, ss.aux[2]);
+      static_for = T + 1;
+      R.launches += 2;
     }
     if (any_pred) {
       if (bf) {
@@ -505,14 +545,13 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
     }
   }
   prof_stop_sampling();
-  if (use_ss) {
-    cudaStreamSynchronize(ss.aux[0]);
-    cudaStreamSynchronize(ss.aux[1]);
-  }
+  if (use_ss)
+    for (auto &a : ss.aux) cudaStreamSynchronize(a);
   for (auto &a : ss.aux)
     if (use_ss) cudaStreamDestroy(a);
   if (use_ss)
-    for (cudaEvent_t e : {ss.fork, ss.join[0], ss.join[1], ss.count_done}) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ss.fork, ss.join[0], ss.join[1], ss.count_done, ss.mix_done, ss.static_done})
+      cudaEventDestroy(e);
 }
 
 __global__ void gather_kernel(const unsigned long long *seg, int n_seg, const uint8_t *src0, const uint8_t *src1,

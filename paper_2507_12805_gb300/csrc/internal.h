@@ -76,18 +76,21 @@ void launch_export_grad(const Plan &p, float *d_out, cudaStream_t st);
 // Auxiliary streams of a run's step loop: independent kernels of a step are forked onto them and
 // joined back by events (fork/join events reused every step).
 struct StepStreams {
-  cudaStream_t aux[2];
-  cudaEvent_t fork, join[2], count_done;
+  cudaStream_t aux[3];  // 0: count model, dW2; 1: dX; 2: the static model's forward
+  cudaEvent_t fork, join[2], count_done, mix_done, static_done;
 };
 
 // predictor_tc.cu: the BF16 form's GEMMs on tcgen05, for shapes with E % 8 == 0, H % 16 == 0,
 // 4^k % 8 == 0 and a parameter count divisible by 8 (16-byte aligned per-group BF16 copies)
 bool tc_supported(const Plan &p);
-void launch_forward_tc(const Plan &p, int T, cudaStream_t st);
+// which: kFwdDynamic and/or kFwdStatic (the static model's forward depends on the tokens only, so a
+// step loop may run it on another stream)
+constexpr int kFwdDynamic = 1, kFwdStatic = 2, kFwdBoth = 3;
+void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which = kFwdBoth);
 // ss (optional): run dW2, dX and dW1 concurrently on st and ss->aux
 void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss);
 // predictor_bf16.cu: the BF16 form (tcgen05 engine where tc_supported, else mma.sync)
-void launch_forward_bf16(const Plan &p, int T, cudaStream_t st);
+void launch_forward_bf16(const Plan &p, int T, cudaStream_t st, int which = kFwdBoth);
 // gradient GEMMs into the gradient buffer (the optimiser is launch_update)
 void launch_backward_bf16(const Plan &p, int T, cudaStream_t st, const StepStreams *ss = nullptr);
 void launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st);

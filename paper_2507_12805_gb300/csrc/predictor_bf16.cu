@@ -536,11 +536,12 @@ void launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st) {
   to_bf16_kernel<<<(unsigned)grid, 256, 0, st>>>(src, reinterpret_cast<bf16 *>(dst), n);
 }
 
-void launch_forward_bf16(const Plan &p, int T, cudaStream_t st) {
+void launch_forward_bf16(const Plan &p, int T, cudaStream_t st, int which) {
   if (tc_supported(p)) {
-    launch_forward_tc(p, T, st);
+    launch_forward_tc(p, T, st, which);
     return;
   }
+  if (which != kFwdBoth) return;  // the mma.sync form runs both models together only
   const double R = prof_work().pred_rows;
   const int Z = p.use_static ? 2 * p.G : p.G;
   const int Hmax = p.use_static ? max(p.dm.H, p.st.H) : p.dm.H;

@@ -47,16 +47,19 @@ struct MetaLayout {
   __host__ __device__ size_t bytes() const { return tab_off() + (size_t)table; }
 };
 
+struct NoGather {
+  __device__ void gather(uint8_t *, int) const {}
+};
+
 struct TBase {
   static constexpr bool kFinish = false;
   static constexpr bool kFP8 = false;
   Plan p;
   int T;
   MetaLayout ml;
+  int zb = 0;
   __device__ void finish(uint8_t *, int) const {}
-  __device__ void epilogue(const uint8_t *, int, int, int, int, const float *) const {}
-  __device__ bool row_active(const uint8_t *, int, int, int) const { return false; }
-  __device__ void emit(const uint8_t *, int, int, int, int, float) const {}
+  __device__ NoGather gather_ctx(const uint8_t *, int, int, int) const { return {}; }
   __device__ int *err() const { return p.err; }
   __device__ int nrows(int g) const { return p.grp_lane_off[g + 1] - p.grp_lane_off[g]; }
   __device__ int row(int g, int r) const { return p.grp_lane_off[g] + r; }
@@ -71,32 +74,31 @@ struct TBase {
   __device__ const uint16_t *tk(const uint8_t *meta) const {
     return reinterpret_cast<const uint16_t *>(meta + ml.tok_off());
   }
-  __device__ const bf16 *table(const uint8_t *meta) const {
-    return reinterpret_cast<const bf16 *>(meta + ml.tab_off());
-  }
   // targets of rows r0 .. r0 + n - 1 of group g (-1 past the group or for rows that predict
   // nothing), their t context tokens and the embedding table emb (A x E) if ml.table.  The table
   // arrives by one bulk copy that overlaps the target and token loads.
-  __device__ void fill(uint8_t *meta, const MetaLayout &ml, int g, int r0, int n, const void *emb, int bytes) const {
+  __device__ void fill(uint8_t *meta, const MetaLayout &ml_, int g, int r0, int n, const void *emb, int bytes) const {
     __shared__ __align__(8) uint64_t tbar;
+    const MetaLayout l = ml_;
     long long *tpw = reinterpret_cast<long long *>(meta);
-    const bool copy = emb != nullptr && bytes > 0 && ml.table >= bytes;
+    const bool copy = emb != nullptr && bytes > 0 && l.table >= bytes;
     if (copy && threadIdx.x == 0) {
       const uint32_t bar = tc::sa(&tbar);
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
       tc::expect_tx(bar, (uint32_t)bytes);
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                       tc::sa(meta + ml.tab_off())),
+                       tc::sa(meta + l.tab_off())),
                    "l"(emb), "r"(bytes), "r"(bar)
                    : "memory");
     }
     const int L = nrows(g);
     for (int i = threadIdx.x; i < n; i += tc::kThreads) tpw[i] = r0 + i < L ? target_pos(g, r0 + i) : -1;
     __syncthreads();
-    if (ml.t > 0) {
-      uint16_t *tkw = reinterpret_cast<uint16_t *>(meta + ml.tok_off());
-      const int t = ml.t, total = n * t;
+    if (l.t > 0) {
+      uint16_t *tkw = reinterpret_cast<uint16_t *>(meta + l.tok_off());
+      const uint16_t *tokens = p.tokens;
+      const int t = l.t, total = n * t;
       for (int i0 = 0; i0 < total; i0 += 16 * tc::kThreads) {  // sixteen loads in flight per thread
         uint16_t v[16];
 #pragma unroll
@@ -106,7 +108,7 @@ struct TBase {
           if (i < total) {
             const int r = i / t;
             const long long b = tpw[r];
-            if (b >= 0) v[q] = p.tokens[b - t + (i - r * t)];
+            if (b >= 0) v[q] = tokens[b - t + (i - r * t)];
           }
         }
 #pragma unroll
@@ -120,25 +122,7 @@ struct TBase {
   }
 };
 
-// 16 bytes from the shared-memory table or, without one, an async copy from global memory
-__device__ __forceinline__ void put16(uint8_t *dst, const bf16 *tab_s, const bf16 *tab_g, size_t off) {
-  if (tab_s) {
-    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tab_s + off);
-  } else {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(tab_g + off));
-  }
-}
 __device__ __forceinline__ void zero16(uint8_t *dst) { *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0); }
-
-// z < G: dynamic model of group z; z >= G: static model on group z - G's rows
-struct TwoModels : TBase {
-  __device__ bool stat(int z) const { return z >= p.G; }
-  __device__ int grp(int z) const { return stat(z) ? z - p.G : z; }
-  __device__ const Dims &d(int z) const { return stat(z) ? p.st : p.dm; }
-  __device__ const bf16 *w(int z) const { return stat(z) ? p.static_bf : wb(grp(z)); }
-  __device__ const float *w32(int z) const { return stat(z) ? p.static_params : p.params + (size_t)grp(z) * p.P; }
-  __device__ bool active(int z) const { return group_trains(p, T, grp(z)); }
-};
 
 __device__ __forceinline__ uint4 pack8(const float *x) {
   uint32_t w[4];
@@ -156,6 +140,78 @@ __device__ __forceinline__ void store8(float *dst, const float *v) {
 }
 
 constexpr tc::TmaOperand kNoTma = {nullptr, 2, 0, 0};
+constexpr int kRowsPerThread = tc::kRows * 8 / tc::kThreads;  // K-major gathers: rows a thread fills
+constexpr int kRowStep = tc::kThreads / 8;                     // ... 32 apart, one 16-byte chunk each
+
+// Gather of a K-major operand from an embedding table: thread (chunk c = tid % 8, rows tid / 8 +
+// 32 i) fills 16-byte chunk c of its rows with the embedding codes of the context token at the
+// chunk's position (bytes per element eb: 2 for BF16, 1 for E4M3; E * eb a multiple of 16).
+struct EmbGather {
+  const uint8_t *tab_s;  // table in shared memory, else nullptr
+  const uint8_t *tab_g;  // table in global memory
+  const uint16_t *tk;    // context tokens of the tile's rows (t per row)
+  int E, t, K1, eb;
+  int c;
+  int tokrow[kRowsPerThread];  // row r * t, or -1 for rows that predict nothing
+  __device__ void gather(uint8_t *tile, int k0) const {
+    const int per = 16 / eb, k = k0 + per * c;
+    const bool kin = k < K1;
+    const int pos = kin ? k / E : 0, e = k - pos * E;
+    int off[kRowsPerThread];
+    bool ok[kRowsPerThread];
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) {
+      ok[i] = kin && tokrow[i] >= 0;
+      off[i] = ok[i] ? ((int)tk[tokrow[i] + pos] * E + e) * eb : 0;
+    }
+    const int r0 = threadIdx.x >> 3;
+    if (tab_s) {
+      uint4 v[kRowsPerThread];
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i)
+        v[i] = ok[i] ? *reinterpret_cast<const uint4 *>(tab_s + off[i]) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) *reinterpret_cast<uint4 *>(tile + tc::sw_k(r0 + kRowStep * i, c)) = v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) {
+        uint8_t *dst = tile + tc::sw_k(r0 + kRowStep * i, c);
+        if (ok[i])
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(tab_g + off[i]));
+        else
+          zero16(dst);
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ EmbGather emb_gather(const uint8_t *meta, const MetaLayout &ml, const Dims &D,
+                                                const void *tab_g, bool in_smem, int eb) {
+  EmbGather g;
+  g.tab_s = in_smem ? meta + ml.tab_off() : nullptr;
+  g.tab_g = reinterpret_cast<const uint8_t *>(tab_g);
+  g.tk = reinterpret_cast<const uint16_t *>(meta + ml.tok_off());
+  g.E = D.E, g.t = D.t, g.K1 = D.K1(), g.eb = eb;
+  g.c = threadIdx.x & 7;
+  const long long *tpv = reinterpret_cast<const long long *>(meta);
+  const int r0 = threadIdx.x >> 3;
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const int r = r0 + kRowStep * i;
+    g.tokrow[i] = tpv[r] >= 0 ? r * D.t : -1;
+  }
+  return g;
+}
+
+// z < G: dynamic model of group z; z >= G: static model on group z - G's rows
+struct TwoModels : TBase {
+  __device__ bool stat(int z) const { return z >= p.G; }
+  __device__ int grp(int z) const { return stat(z) ? z - p.G : z; }
+  __device__ Dims d(int z) const { return stat(z) ? p.st : p.dm; }
+  __device__ const bf16 *w(int z) const { return stat(z) ? p.static_bf : wb(grp(z)); }
+  __device__ const float *w32(int z) const { return stat(z) ? p.static_params : p.params + (size_t)grp(z) * p.P; }
+  __device__ bool active(int z) const { return group_trains(p, T, grp(z)); }
+};
 
 // h = relu(X W1 + b1): A = X gathered (K-major), B = W1t by TMA (K-major)
 struct HiddenT : TwoModels {
@@ -167,63 +223,40 @@ struct HiddenT : TwoModels {
   __device__ int M(int z) const { return nrows(grp(z)); }
   __device__ int N(int z) const { return d(z).H; }
   __device__ int K(int z) const { return d(z).K1(); }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+  __device__ MetaLayout lay(int z) const {
     MetaLayout l = ml;
     l.t = d(z).t;
     l.table = table[stat(z)] ? d(z).A * d(z).E * 2 : 0;
-    fill(meta, l, grp(z), m0, tc::kRows, w(z) + d(z).off_emb(), d(z).A * d(z).E * 2);
+    return l;
+  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    const Dims D = d(z);
+    fill(meta, lay(z), grp(z), m0, tc::kRows, w(z) + D.off_emb(), D.A * D.E * 2);
   }
   __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
   __device__ tc::TmaOperand tma_b(int z) const { return {&w1[stat(z)], stat(z) ? 2 : 3, grp(z), 0}; }
   __device__ int row_a(int, int) const { return 0; }
   __device__ int row_b(int, int n0) const { return n0; }
-  // thread: 16-byte chunk c = tid % 8 of rows tid / 8 + 32 i; the 4 table reads are in flight together
-  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int, int k0, int) const {
-    const Dims &D = d(z);
-    MetaLayout l = ml;
-    l.t = D.t;
-    const long long *tpv = reinterpret_cast<const long long *>(meta);
-    const uint16_t *tkv = reinterpret_cast<const uint16_t *>(meta + l.tok_off());
-    const bf16 *tab_s = table[stat(z)] ? reinterpret_cast<const bf16 *>(meta + l.tab_off()) : nullptr;
-    const bf16 *tab_g = w(z) + D.off_emb();
-    const int c = threadIdx.x & 7, k = k0 + 8 * c, r0 = threadIdx.x >> 3;
-    const bool kin = k < D.K1();
-    const int pos = kin ? k / D.E : 0, e = k - pos * D.E;
-    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
-    int off[kPer];
-    bool ok[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int r = r0 + kStep * i;
-      ok[i] = kin && tpv[r] >= 0;
-      off[i] = ok[i] ? (int)tkv[r * D.t + pos] * D.E + e : 0;
-    }
-    if (tab_s) {
-      uint4 v[kPer];
-#pragma unroll
-      for (int i = 0; i < kPer; ++i)
-        v[i] = ok[i] ? *reinterpret_cast<const uint4 *>(tab_s + off[i]) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) *reinterpret_cast<uint4 *>(tile + tc::sw_k(r0 + kStep * i, c)) = v[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        uint8_t *dst = tile + tc::sw_k(r0 + kStep * i, c);
-        if (ok[i])
-          put16(dst, nullptr, tab_g, (size_t)off[i]);
-        else
-          zero16(dst);
-      }
-    }
+  __device__ EmbGather gather_ctx(const uint8_t *meta, int z, int, int) const {
+    const Dims D = d(z);
+    return emb_gather(meta, lay(z), D, w(z) + D.off_emb(), table[stat(z)] != 0, 2);
   }
-  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (tp(meta)[rl] < 0) return;
-    const Dims &D = d(z);
-    const float *b1 = w32(z) + D.off_b1() + n;
-    float x[8];
+  struct Epi {
+    const long long *tp;
+    const float *b1;
+    bf16 *out;  // row 0 of the group
+    int H;
+    __device__ void epilogue(int m, int rl, int n, const float *v) const {
+      if (tp[rl] < 0) return;
+      float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = fmaxf(v[j] + b1[j], 0.f);
-    *reinterpret_cast<uint4 *>((stat(z) ? p.hs_b : p.hd_b) + (size_t)row(grp(z), m) * D.H + n) = pack8(x);
+      for (int j = 0; j < 8; ++j) x[j] = fmaxf(v[j] + b1[n + j], 0.f);
+      *reinterpret_cast<uint4 *>(out + (size_t)m * H + n) = pack8(x);
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    const Dims D = d(z);
+    return {tp(meta), w32(z) + D.off_b1(), (stat(z) ? p.hs_b : p.hd_b) + (size_t)row(grp(z), 0) * D.H, D.H};
   }
 };
 
@@ -241,15 +274,22 @@ struct LogitsT : TwoModels {
   __device__ tc::TmaOperand tma_b(int z) const { return {&w2[stat(z)], stat(z) ? 2 : 3, grp(z), 0}; }
   __device__ int row_a(int z, int m0) const { return row(grp(z), m0); }
   __device__ int row_b(int, int n0) const { return n0; }
-  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
-  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (tp(meta)[rl] < 0) return;
-    const Dims &D = d(z);
-    const float *b2 = w32(z) + D.off_b2() + n;
-    float x[8];
+  struct Epi {
+    const long long *tp;
+    const float *b2;
+    float *out;
+    int A;
+    __device__ void epilogue(int m, int rl, int n, const float *v) const {
+      if (tp[rl] < 0) return;
+      float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = v[j] + b2[j];
-    store8((stat(z) ? p.zu : p.zm) + (size_t)row(grp(z), m) * D.A + n, x);
+      for (int j = 0; j < 8; ++j) x[j] = v[j] + b2[n + j];
+      store8(out + (size_t)m * A + n, x);
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    const Dims D = d(z);
+    return {tp(meta), w32(z) + D.off_b2(), (stat(z) ? p.zu : p.zm) + (size_t)row(grp(z), 0) * D.A, D.A};
   }
 };
 
@@ -268,16 +308,25 @@ struct DhT : TBase {
   __device__ tc::TmaOperand tma_b(int z) const { return {&w2, 3, z, 0}; }
   __device__ int row_a(int z, int m0) const { return row(z, m0); }
   __device__ int row_b(int, int n0) const { return n0; }
-  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
-  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    const size_t i = (size_t)row(z, m) * p.dm.H + n;
-    const bool ok = tp(meta)[rl] >= 0;  // zeros where nothing is predicted
-    uint4 hw = *reinterpret_cast<const uint4 *>(p.hd_b + i);
-    const bf16 *hv = reinterpret_cast<const bf16 *>(&hw);
-    float x[8];
+  struct Epi {
+    const long long *tp;
+    const bf16 *h;
+    bf16 *dh;
+    int H;
+    __device__ void epilogue(int m, int rl, int n, const float *v) const {
+      const size_t i = (size_t)m * H + n;
+      const bool ok = tp[rl] >= 0;  // zeros where nothing is predicted
+      const uint4 hw = *reinterpret_cast<const uint4 *>(h + i);
+      const bf16 *hv = reinterpret_cast<const bf16 *>(&hw);
+      float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (ok && __bfloat162float(hv[j]) > 0.f) ? v[j] : 0.f;
-    *reinterpret_cast<uint4 *>(p.dh_b + i) = pack8(x);
+      for (int j = 0; j < 8; ++j) x[j] = (ok && __bfloat162float(hv[j]) > 0.f) ? v[j] : 0.f;
+      *reinterpret_cast<uint4 *>(dh + i) = pack8(x);
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    const size_t r0 = (size_t)row(z, 0) * p.dm.H;
+    return {tp(meta), p.hd_b + r0, p.dh_b + r0, p.dm.H};
   }
 };
 
@@ -296,28 +345,34 @@ struct DW2T : TBase {
   __device__ tc::TmaOperand tma_b(int z) const { return {&dz, 2, 0, p.grp_lane_off[z]}; }
   __device__ int row_a(int, int m0) const { return m0; }
   __device__ int row_b(int, int n0) const { return n0; }
-  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
-  __device__ void epilogue(const uint8_t *, int z, int h_, int, int n, const float *v) const {
-    store8(p.grad + (size_t)z * p.P + p.dm.off_w2() + (size_t)h_ * p.dm.A + n, v);
+  struct Epi {
+    float *g;  // the group's dW2
+    int A;
+    __device__ void epilogue(int h_, int, int n, const float *v) const { store8(g + (size_t)h_ * A + n, v); }
+  };
+  __device__ Epi epi_ctx(const uint8_t *, int z, int, int) const {
+    return {p.grad + (size_t)z * p.P + p.dm.off_w2(), p.dm.A};
   }
 };
 
 // dX = dh W1^T scattered into the embedding rows as fixed-point integers (order-free sums, so the
 // result does not depend on scheduling): A = dh by TMA (K-major), B = W1t[h][i] as N = i, K = h
 // by TMA (MN-major).  The lanes of a warp add consecutive elements of one embedding row.  Where
-// the group's fixed-point table (A x E x 8 bytes) fits in shared memory, the CTA first sums its
-// tile there and then adds each non-zero entry to global memory once, so a token that appears at
-// several (lane, position) pairs of the tile costs one global atomic per element instead of one
-// per pair.  A 64-bit shared-memory sum is kept as two 32-bit words updated by native 32-bit
-// atomics: the low word first, then the high word plus the carry out of the low word (the number
-// of wraps of the low word does not depend on the order of the adds, so the sum is exact).
+// the group's fixed-point table fits in shared memory, the CTA first sums its tile there and then
+// adds each non-zero entry to global memory once, so a token that appears at several (lane,
+// position) pairs of the tile costs one global atomic per element instead of one per pair.  In
+// shared memory a 64-bit value q is held as a 22-bit low part (q mod 2^22, unsigned) and a 32-bit
+// high part (q >> 22, signed), each summed by a fire-and-forget 32-bit atomic add: an address
+// receives at most 128 rows x 8 positions = 1024 adds per tile, so the low sum stays below 2^32,
+// and the high sum is exact (modulo 2^32) for tile sums below 2^13 in magnitude; the two
+// recombine as high * 2^22 + low.
 struct DXT : TBase {
   static constexpr bool kAMN = false, kBMN = true, kTail = false;
   static constexpr int kEpi = 1;
   static constexpr int kGather = 0;
   static constexpr bool kFinish = true;
   CUtensorMap dh, w1;
-  int sacc;    // sum the tile in shared memory (ml.table bytes: low words [A*E] then high words [A*E])
+  int sacc;    // sum the tile in shared memory (ml.table bytes: low parts [A*E] then high parts [A*E])
   int eshift;  // log2 E when E is a power of two, else -1
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
@@ -332,39 +387,54 @@ struct DXT : TBase {
     fill(meta, l, z, m0, tc::kRows, nullptr, 0);
     if (sacc) {
       uint4 *a = reinterpret_cast<uint4 *>(lo_s(meta));
-      for (int i = threadIdx.x; i < p.dm.A * p.dm.E / 2; i += tc::kThreads) a[i] = make_uint4(0, 0, 0, 0);
+      const int n4 = p.dm.A * p.dm.E / 2;
+      for (int i = threadIdx.x; i < n4; i += tc::kThreads) a[i] = make_uint4(0, 0, 0, 0);
     }
   }
   __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
   __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
   __device__ int row_a(int z, int m0) const { return row(z, m0); }
   __device__ int row_b(int, int n0) const { return n0; }
-  __device__ void gather(uint8_t *, const uint8_t *, int, int, int, int) const {}
-  __device__ bool row_active(const uint8_t *meta, int, int, int rl) const { return tp(meta)[rl] >= 0; }
-  __device__ void emit(const uint8_t *meta, int z, int, int rl, int n, float v) const {
-    const int pos = eshift >= 0 ? n >> eshift : n / p.dm.E;
-    const uint32_t i = (uint32_t)tk(meta)[rl * p.dm.t + pos] * (uint32_t)p.dm.E + (uint32_t)(n - pos * p.dm.E);
-    const long long q = fix40(v);
-    if (q == 0) return;
-    if (sacc) {
-      uint32_t *lo = lo_s(meta);
-      const uint32_t ql = (uint32_t)(unsigned long long)q, qh = (uint32_t)((unsigned long long)q >> 32);
-      const uint32_t old = atomicAdd(lo + i, ql);
-      const uint32_t up = qh + (old + ql < old ? 1u : 0u);  // high part plus the carry out of the low word
-      if (up) atomicAdd(lo + p.dm.A * p.dm.E + i, up);
-    } else {
-      atomicAdd(reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * p.dm.A * p.dm.E + i,
-                (unsigned long long)q);
+  struct Epi {
+    const long long *tp;
+    const uint16_t *tk;
+    uint32_t *lo;               // shared-memory sums (sacc), else nullptr
+    unsigned long long *glob;   // the group's global accumulators
+    int E, t, AE, eshift;
+    __device__ bool row_active(int rl) const { return tp[rl] >= 0; }
+    // fixed point v 2^40: shared sums take (low 22 bits, the rest), global ones the two 32-bit halves
+    __device__ uint2 stage(float v) const {
+      const long long q = fix40(v);
+      return lo ? make_uint2((uint32_t)(q & ((1ll << 22) - 1)), (uint32_t)(int)(q >> 22))
+                : make_uint2((uint32_t)(unsigned long long)q, (uint32_t)((unsigned long long)q >> 32));
     }
+    __device__ void emit(int, int rl, int n, uint2 s) const {
+      if ((s.x | s.y) == 0) return;
+      const int pos = eshift >= 0 ? n >> eshift : n / E;
+      const uint32_t i = (uint32_t)tk[rl * t + pos] * (uint32_t)E + (uint32_t)(n - pos * E);
+      if (lo) {
+        atomicAdd(lo + i, s.x);  // results unused: reductions, no return
+        if (s.y) atomicAdd(reinterpret_cast<int *>(lo) + AE + i, (int)s.y);
+      } else {
+        atomicAdd(glob + i, ((unsigned long long)s.y << 32) | s.x);
+      }
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    const int AE = p.dm.A * p.dm.E;
+    return {tp(meta), tk(meta), sacc ? lo_s(meta) : nullptr,
+            reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * AE, p.dm.E, p.dm.t, AE, eshift};
   }
   // every thread, after the epilogue's last barrier: the non-zero sums of the tile to global memory
   __device__ void finish(uint8_t *meta, int z) const {
     if (!sacc) return;
-    const uint32_t *lo = lo_s(meta), *hi = lo + p.dm.A * p.dm.E;
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * p.dm.A * p.dm.E;
-    for (int i = threadIdx.x; i < p.dm.A * p.dm.E; i += tc::kThreads) {
-      const unsigned long long q = ((unsigned long long)hi[i] << 32) | lo[i];
-      if (q) atomicAdd(dst + i, q);
+    const int AE = p.dm.A * p.dm.E;
+    const uint32_t *lo = lo_s(meta);
+    const int *hi = reinterpret_cast<const int *>(lo) + AE;
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * AE;
+    for (int i = threadIdx.x; i < AE; i += tc::kThreads) {
+      const long long q = (long long)hi[i] * (1ll << 22) + (long long)lo[i];
+      if (q) atomicAdd(dst + i, (unsigned long long)q);
     }
   }
 };
@@ -388,50 +458,101 @@ struct DW1T : TBase {
   __device__ tc::TmaOperand tma_b(int) const { return kNoTma; }
   __device__ int row_a(int, int m0) const { return m0; }
   __device__ int row_b(int, int) const { return 0; }
-  // chunk idx = 16 bytes at column n = 8 (idx % (R/8)) of K row idx / (R/8); consecutive threads
-  // take consecutive chunks of a row, four per thread in flight
-  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int n0, int k0, int R) const {
-    const Dims &D = p.dm;
-    const long long *tpv = tp(meta);
-    const uint16_t *tkv = tk(meta);
-    const bf16 *tab_s = table ? this->table_ptr(meta) : nullptr;
-    const bf16 *tab_g = wb(z) + D.off_emb();
-    const int K = npred(z), cpr = R / 8, total = cpr * tc::kBK;
-    for (int i0 = 0; i0 < total; i0 += 4 * tc::kThreads) {
-      int off[4], dsto[4];
-      bool ok[4];
+  // The MN-major X tile of K block k0: chunk idx = 16 bytes at column n = 8 (idx % cpr) of lane
+  // row idx / cpr (cpr = R / 8 chunks per K row).  Where cpr divides the thread count a thread
+  // keeps one column n (one context position and embedding offset) and steps over lane rows;
+  // otherwise (general) every chunk computes its own column.
+  struct Gather {
+    const bf16 *tab_s, *tab_g;
+    const uint16_t *tk;
+    const long long *tp;
+    int K, t, E, pos, e, n, kfirst, kstep, nper;
+    int general, cpr, n0;
+    __device__ void gather(uint8_t *tile, int k0) const {
+      if (general) {
+        const int total = cpr * tc::kBK;
+        for (int i0 = 0; i0 < total; i0 += 4 * tc::kThreads) {
+          int off[4], dsto[4];
+          bool ok[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int idx = i0 + j * tc::kThreads + threadIdx.x;
-        const int n = (idx % cpr) * 8, k = idx / cpr, m = k0 + k;
-        dsto[j] = idx < total ? (int)tc::sw_mn(n, k) : -1;
-        ok[j] = idx < total && m < K && tpv[m] >= 0;
-        const int i = n0 + n, pos = i / D.E;
-        off[j] = ok[j] ? (int)tkv[m * D.t + pos] * D.E + (i - pos * D.E) : 0;
+          for (int j = 0; j < 4; ++j) {
+            const int idx = i0 + j * tc::kThreads + threadIdx.x;
+            const int nn = (idx % cpr) * 8, k = idx / cpr, m = k0 + k;
+            dsto[j] = idx < total ? (int)tc::sw_mn(nn, k) : -1;
+            ok[j] = idx < total && m < K && tp[m] >= 0;
+            const int i = n0 + nn, ps = i / E;
+            off[j] = ok[j] ? (int)tk[m * t + ps] * E + (i - ps * E) : 0;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (dsto[j] < 0) continue;
+            uint8_t *dst = tile + dsto[j];
+            if (!ok[j])
+              zero16(dst);
+            else if (tab_s)
+              *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tab_s + off[j]);
+            else
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(tab_g + off[j]));
+          }
+        }
+        return;
       }
-      if (tab_s) {
-        uint4 v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          v[j] = ok[j] ? *reinterpret_cast<const uint4 *>(tab_s + off[j]) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (dsto[j] >= 0) *reinterpret_cast<uint4 *>(tile + dsto[j]) = v[j];
-      } else {
+      for (int j0 = 0; j0 < nper; j0 += 4) {
+        int off[4], kk[4];
+        bool ok[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (dsto[j] < 0) continue;
-          if (ok[j])
-            put16(tile + dsto[j], nullptr, tab_g, (size_t)off[j]);
-          else
-            zero16(tile + dsto[j]);
+          kk[j] = kfirst + (j0 + j) * kstep;
+          const int m = k0 + kk[j];
+          ok[j] = j0 + j < nper && m < K && tp[m] >= 0;
+          off[j] = ok[j] ? (int)tk[m * t + pos] * E + e : 0;
+        }
+        if (tab_s) {
+          uint4 v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            v[j] = ok[j] ? *reinterpret_cast<const uint4 *>(tab_s + off[j]) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j0 + j < nper) *reinterpret_cast<uint4 *>(tile + tc::sw_mn(n, kk[j])) = v[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (j0 + j >= nper) continue;
+            uint8_t *dst = tile + tc::sw_mn(n, kk[j]);
+            if (ok[j])
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(tab_g + off[j]));
+            else
+              zero16(dst);
+          }
         }
       }
     }
+  };
+  __device__ Gather gather_ctx(const uint8_t *meta, int z, int n0, int R) const {
+    Gather g;
+    g.tab_s = table ? reinterpret_cast<const bf16 *>(meta + ml.tab_off()) : nullptr;
+    g.tab_g = wb(z) + p.dm.off_emb();
+    g.tk = tk(meta);
+    g.tp = tp(meta);
+    g.K = npred(z), g.t = p.dm.t, g.E = p.dm.E;
+    const int cpr = R / 8;
+    g.general = tc::kThreads % cpr != 0;
+    g.cpr = cpr, g.n0 = n0;
+    g.n = (threadIdx.x % cpr) * 8;
+    g.pos = (n0 + g.n) / g.E, g.e = n0 + g.n - g.pos * g.E;
+    g.kfirst = threadIdx.x / cpr;
+    g.kstep = tc::kThreads / cpr;
+    g.nper = tc::kBK / g.kstep;
+    return g;
   }
-  __device__ const bf16 *table_ptr(const uint8_t *meta) const { return TBase::table(meta); }
-  __device__ void epilogue(const uint8_t *, int z, int h_, int, int n, const float *v) const {
-    store8(p.grad + (size_t)z * p.P + p.dm.off_w1() + (size_t)h_ * p.dm.K1() + n, v);
+  struct Epi {
+    float *g;  // the group's dW1t
+    int K1;
+    __device__ void epilogue(int h_, int, int n, const float *v) const { store8(g + (size_t)h_ * K1 + n, v); }
+  };
+  __device__ Epi epi_ctx(const uint8_t *, int z, int, int) const {
+    return {p.grad + (size_t)z * p.P + p.dm.off_w1(), p.dm.K1()};
   }
 };
 
@@ -449,52 +570,44 @@ struct HiddenF8 : TBase {
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.st.H; }
   __device__ int K(int) const { return p.st.K1(); }
-  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+  __device__ MetaLayout lay() const {
     MetaLayout l = ml;
     l.table = table ? p.st.A * p.st.E : 0;
-    fill(meta, l, z, m0, tc::kRows, p.st8, p.st.A * p.st.E);
+    return l;
+  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    fill(meta, lay(), z, m0, tc::kRows, p.st8, p.st.A * p.st.E);
   }
   __device__ tc::TmaOperand tma_a(int) const { return kNoTma; }
   __device__ tc::TmaOperand tma_b(int) const { return {&w1, 2, 0, 0}; }
   __device__ int row_a(int, int) const { return 0; }
   __device__ int row_b(int, int n0) const { return n0; }
-  // thread: 16-byte chunk c = tid % 8 (16 codes) of rows tid / 8 + 32 i
-  __device__ void gather(uint8_t *tile, const uint8_t *meta, int, int, int k0, int) const {
-    const Dims &D = p.st;
-    const long long *tpv = tp(meta);
-    const uint16_t *tkv = tk(meta);
-    const uint8_t *tab_s = table ? meta + ml.tab_off() : nullptr;
-    const int c = threadIdx.x & 7, k = k0 + 16 * c, r0 = threadIdx.x >> 3;
-    const bool kin = k < D.K1();
-    const int pos = kin ? k / D.E : 0, e = k - pos * D.E;
-    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int r = r0 + kStep * i;
-      uint8_t *dst = tile + tc::sw_k(r, c);
-      const bool ok = kin && tpv[r] >= 0;
-      const int off = ok ? (int)tkv[r * D.t + pos] * D.E + e : 0;
-      if (!ok)
-        zero16(dst);
-      else if (tab_s)
-        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tab_s + off);
-      else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::sa(dst)), "l"(p.st8 + off));
-    }
+  __device__ EmbGather gather_ctx(const uint8_t *meta, int, int, int) const {
+    return emb_gather(meta, lay(), p.st, p.st8, table != 0, 1);
   }
-  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (tp(meta)[rl] < 0) return;
-    const float *c1 = p.st8_c1 + n, *b1 = p.static_params + p.st.off_b1() + n;
-    const int rw = row(z, m);
-    float x[8], mx = 0.f;
+  struct Epi {
+    const long long *tp;
+    const float *c1, *b1;
+    float *hs;       // row 0 of the group
+    unsigned *rmax;  // row 0 of the group
+    int H;
+    __device__ void epilogue(int m, int rl, int n, const float *v) const {
+      if (tp[rl] < 0) return;
+      float x[8], mx = 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float a = fmaf(v[j], c1[j], b1[j]);
-      x[j] = a > 0.f ? a : 0.f;  // +0 below zero (its bits must order as a float)
-      mx = fmaxf(mx, x[j]);
+      for (int j = 0; j < 8; ++j) {
+        const float a = fmaf(v[j], c1[n + j], b1[n + j]);
+        x[j] = a > 0.f ? a : 0.f;  // +0 below zero (its bits must order as a float)
+        mx = fmaxf(mx, x[j]);
+      }
+      store8(hs + (size_t)m * H + n, x);
+      atomicMax(rmax + m, __float_as_uint(mx));
     }
-    store8(p.hs + (size_t)rw * p.st.H + n, x);
-    atomicMax(p.hs_rowmax + rw, __float_as_uint(mx));
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    const int r0 = row(z, 0);
+    return {tp(meta), p.st8_c1, p.static_params + p.st.off_b1(), p.hs + (size_t)r0 * p.st.H, p.hs_rowmax + r0,
+            p.st.H};
   }
 };
 
@@ -516,9 +629,10 @@ struct LogitsF8 : TBase {
   __device__ void prepare(uint8_t *meta, int z, int m0) const {
     fill(meta, ml, z, m0, tc::kRows, nullptr, 0);
     float *r = rs(meta);
+    const int L = nrows(z), r0 = row(z, m0);
+    const unsigned *rmax = p.hs_rowmax;
     for (int i = threadIdx.x; i < tc::kRows; i += tc::kThreads) {
-      const int m = m0 + i;
-      const float mx = m < nrows(z) ? __uint_as_float(p.hs_rowmax[row(z, m)]) : 0.f;
+      const float mx = m0 + i < L ? __uint_as_float(rmax[r0 + i]) : 0.f;
       r[2 * i] = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
       r[2 * i + 1] = mx > 0.f ? __fdiv_rn(448.f, mx) : 0.f;
     }
@@ -528,39 +642,61 @@ struct LogitsF8 : TBase {
   __device__ int row_a(int, int) const { return 0; }
   __device__ int row_b(int, int n0) const { return n0; }
   // thread: 16-byte chunk c = tid % 8 (16 activations) of rows tid / 8 + 32 i
-  __device__ void gather(uint8_t *tile, const uint8_t *meta, int z, int m0, int k0, int) const {
-    const int H = p.st.H;
+  struct Gather {
+    const float *src[kRowsPerThread];  // the row's FP32 activations, nullptr for rows that predict nothing
+    float inv[kRowsPerThread];
+    int H, c;
+    __device__ void gather(uint8_t *tile, int k0) const {
+      const int k = k0 + 16 * c, r0 = threadIdx.x >> 3;
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) {
+        uint4 out = make_uint4(0, 0, 0, 0);
+        if (k < H && src[i]) {  // H % 16 == 0: a chunk is all in or all out
+          const float4 *s4 = reinterpret_cast<const float4 *>(src[i] + k);
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 f = s4[q];
+            const __nv_fp8x4_e4m3 x(make_float4(f.x * inv[i], f.y * inv[i], f.z * inv[i], f.w * inv[i]));
+            w[q] = *reinterpret_cast<const uint32_t *>(&x);
+          }
+          out = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        *reinterpret_cast<uint4 *>(tile + tc::sw_k(r0 + kRowStep * i, c)) = out;
+      }
+    }
+  };
+  __device__ Gather gather_ctx(const uint8_t *meta, int z, int m0, int) const {
+    Gather g;
+    g.H = p.st.H, g.c = threadIdx.x & 7;
     const long long *tpv = tp(meta);
     const float *r = rs(meta);
-    const int c = threadIdx.x & 7, k = k0 + 16 * c, r0 = threadIdx.x >> 3;
-    constexpr int kPer = tc::kRows * 8 / tc::kThreads, kStep = tc::kThreads / 8;
+    const int r0 = threadIdx.x >> 3;
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int rl = r0 + kStep * i;
-      uint4 out = make_uint4(0, 0, 0, 0);
-      if (k < H && tpv[rl] >= 0) {  // H % 16 == 0: a chunk is all in or all out
-        const float inv = r[2 * rl + 1];
-        const float4 *src = reinterpret_cast<const float4 *>(p.hs + (size_t)row(z, m0 + rl) * H + k);
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 f = src[q];
-          const __nv_fp8x4_e4m3 x(make_float4(f.x * inv, f.y * inv, f.z * inv, f.w * inv));
-          w[q] = *reinterpret_cast<const uint32_t *>(&x);
-        }
-        out = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-      *reinterpret_cast<uint4 *>(tile + tc::sw_k(rl, c)) = out;
+    for (int i = 0; i < kRowsPerThread; ++i) {
+      const int rl = r0 + kRowStep * i;
+      g.src[i] = tpv[rl] >= 0 ? p.hs + (size_t)row(z, m0 + rl) * g.H : nullptr;
+      g.inv[i] = r[2 * rl + 1];
     }
+    return g;
   }
-  __device__ void epilogue(const uint8_t *meta, int z, int m, int rl, int n, const float *v) const {
-    if (tp(meta)[rl] < 0) return;
-    const float sr = rs(meta)[2 * rl];
-    const float *s2 = p.st8_s2 + n, *b2 = p.static_params + p.st.off_b2() + n;
-    float x[8];
+  struct Epi {
+    const long long *tp;
+    const float *rs, *s2, *b2;
+    float *zu;  // row 0 of the group
+    int A;
+    __device__ void epilogue(int m, int rl, int n, const float *v) const {
+      if (tp[rl] < 0) return;
+      const float sr = rs[2 * rl];
+      float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = fmaf(v[j], __fmul_rn(sr, s2[j]), b2[j]);
-    store8(p.zu + (size_t)row(z, m) * p.st.A + n, x);
+      for (int j = 0; j < 8; ++j) x[j] = fmaf(v[j], __fmul_rn(sr, s2[n + j]), b2[n + j]);
+      store8(zu + (size_t)m * A + n, x);
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
+    return {tp(meta), rs(meta), p.st8_s2, p.static_params + p.st.off_b2(), p.zu + (size_t)row(z, 0) * p.st.A,
+            p.st.A};
   }
 };
 
@@ -691,6 +827,14 @@ bool build(TcSetup &S, const Plan &p) {
   S.t_dh = tc::plan_tiles(p.Mmax, D.H, D.A, p.G, S.ml_dh.bytes());
   S.t_w2 = tc::plan_tiles(D.H, D.A, p.Mmax, p.G, S.ml_w2.bytes());
   S.t_dx = tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes());
+  if (S.sacc_dx && S.t_dx.nt > 8 * D.E) {  // over 8 positions per tile the 22-bit low sums could overflow
+    S.sacc_dx = 0;
+    S.ml_dx.table = 0;
+    S.t_dx = tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes());
+  }
+  // the staged epilogue needs kStagedBytes of stage buffers (checked against the limit below)
+  while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < tc::kStagedBytes) ++S.t_dx.ns;
+  if (S.t_dx.ns > tc::kStages) return false;
   S.t_w1 = tc::plan_tiles(D.H, D.K1(), p.Mmax, p.G, S.ml_w1.bytes());
   for (const auto &pr : {std::make_pair(S.t_h, S.ml_h.bytes()), std::make_pair(S.t_l, S.ml_l.bytes()),
                          std::make_pair(S.t_dh, S.ml_dh.bytes()), std::make_pair(S.t_w2, S.ml_w2.bytes()),
@@ -769,13 +913,13 @@ bool tc_supported(const Plan &p) {
   return get_setup(p, S);
 }
 
-void launch_forward_tc(const Plan &p, int T, cudaStream_t st) {
+void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which) {
   TcSetup S;
   if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
+  const bool stat = p.use_static && (which & kFwdStatic), dyn = (which & kFwdDynamic) != 0;
   const bool f8 = p.use_static && p.st8 != nullptr;  // static model on its own E4M3 launches
-  const int Z = p.use_static && !f8 ? 2 * p.G : p.G;
-  if (f8) {
+  if (stat && f8) {
     {
       ProfScope ps("fwd_hidden_static_fp8", 2.0 * R * p.st.K1() * p.st.H, 0, st);
       HiddenF8 op;
@@ -787,18 +931,25 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st) {
     op.p = p, op.T = T, op.ml = S.ml_l8, op.w2 = S.w2_8;
     tc::launch(op, p.Mmax, p.st.A, p.G, S.t_l8, S.ml_l8.bytes(), st);
   }
+  // BF16 problems: z < G dynamic models, z >= G the static model; one launch covers [zb, zb + Z)
+  const bool sbf = stat && !f8;
+  if (!dyn && !sbf) return;
+  const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (sbf ? p.G : 0);
+  const char *hname = dyn && sbf ? "fwd_hidden_bf16" : dyn ? "fwd_hidden_dyn_bf16" : "fwd_hidden_static_bf16";
+  const char *lname = dyn && sbf ? "fwd_logits_bf16" : dyn ? "fwd_logits_dyn_bf16" : "fwd_logits_static_bf16";
   {
-    double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static && !f8 ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
-    ProfScope ps("fwd_hidden_bf16", fl, 0, st);
+    double fl = (dyn ? 2.0 * R * p.dm.K1() * p.dm.H : 0.0) + (sbf ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
+    ProfScope ps(hname, fl, 0, st);
     HiddenT op;
-    op.p = p, op.T = T, op.ml = S.ml_h, op.w1[0] = S.w1k[0], op.w1[1] = S.w1k[1];
+    op.p = p, op.T = T, op.ml = S.ml_h, op.w1[0] = S.w1k[0], op.w1[1] = S.w1k[1], op.zb = zb;
     op.table[0] = S.table_h[0], op.table[1] = S.table_h[1];
     tc::launch(op, p.Mmax, p.use_static ? max(p.dm.H, p.st.H) : p.dm.H, Z, S.t_h, S.ml_h.bytes(), st);
   }
-  double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static && !f8 ? 2.0 * R * p.st.H * p.st.A : 0.0);
-  ProfScope ps("fwd_logits_bf16", fl, 0, st);
+  double fl = (dyn ? 2.0 * R * p.dm.H * p.dm.A : 0.0) + (sbf ? 2.0 * R * p.st.H * p.st.A : 0.0);
+  ProfScope ps(lname, fl, 0, st);
   LogitsT op;
   op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0], op.w2[1] = S.w2mn[1];
+  op.zb = zb;
   tc::launch(op, p.Mmax, p.dm.A, Z, S.t_l, S.ml_l.bytes(), st);
 }
 

@@ -40,6 +40,9 @@ constexpr int kRowBytes = 128;         // bytes of K per operand row and stage (
 constexpr int kThreads = 256;          // eight warps: warps w and w + 4 share tensor-memory lanes 32(w % 4)..
 constexpr int kStages = 6;             // most stage buffers of a ring (a launch may use fewer)
 constexpr long kSpinLimit = 1L << 24;  // mbarrier polls before a wait gives up
+constexpr int kStagedPitch = 66;       // uint2 per staged row of a kEpi == 1 epilogue (64 columns + pad)
+// bytes of stage buffers a kEpi == 1 epilogue stages its 64-column chunks through
+constexpr size_t kStagedBytes = (size_t)kRows * kStagedPitch * 8;
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -122,18 +125,26 @@ __device__ __forceinline__ uint32_t sw_mn(int n, int k) {
 //                                             per-tile data (row targets, context tokens, the
 //                                             embedding table of a gathered operand)
 //   TmaOperand tma_a(z), tma_b(z); int row_a(z, m0), row_b(z, n0): TMA row coordinates
-//   void gather(uint8_t *tile, const uint8_t *meta, z, mn0, k0, R)   the gathered operand
-//   static constexpr int kEpi;                0: void epilogue(const uint8_t *meta, z, m, rl, n,
-//                                             const float v[8]) per row (8 columns n.., m < M);
-//                                             1: bool row_active(meta, z, m, rl) and void emit(meta,
-//                                             z, m, rl, n, float v) per element, the 32 lanes of a
-//                                             warp on consecutive n of one row
+//   G gather_ctx(const uint8_t *meta, z, mn0, R)   once per thread after the first barrier: a
+//                                             value holding everything the thread's gathers read
+//                                             (kept in registers: per-element work never reloads
+//                                             the op's fields from the parameter space, which the
+//                                             compiler must assume the tile stores may alias)
+//   void G::gather(uint8_t *tile, int k0) const      the gathered operand of K block k0
+//   E epi_ctx(const uint8_t *meta, z, m0, n0) likewise for the epilogue, with
+//   static constexpr int kEpi;                0: void E::epilogue(m, rl, n, const float v[8]) per
+//                                             row (8 columns n.., m < M);
+//                                             1: uint2 E::stage(float v) applied by the row's thread,
+//                                             then bool E::row_active(rl) and void E::emit(m, rl, n,
+//                                             uint2 staged) per element, the 32 lanes of a warp on
+//                                             consecutive n of one row
 //   static constexpr bool kFinish; void finish(uint8_t *meta, z): every thread, after the epilogue
+//   int zb;                                   first problem of the launch (blockIdx.z + zb)
 //   int *err();                               the error word
 template <class Op>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ Op op, int nt_max, int tmem_cols,
+__global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ Op op, int nt_max, int tmem_cols,
                                                          int ns) {
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + op.zb;  // problem index (a launch may cover a subrange of the problems)
   if (!op.active(z)) return;
   const int M = op.M(z), N = op.N(z), K = op.K(z);
   const int m0 = blockIdx.x * kRows, n0 = blockIdx.y * nt_max;
@@ -167,6 +178,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
+  const auto gc = op.gather_ctx(meta, z, Op::kGather == 2 ? n0 : m0, Op::kGather == 2 ? nt : kRows);
 
   const int nk = max(1, (K + BK - 1) / BK);  // K = 0 still runs one all-zero stage
   const TmaOperand ta = op.tma_a(z), tb = op.tma_b(z);
@@ -194,8 +206,8 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
           tma_k_tile(sB + s * b_bytes, tb, k0, rb, bar);
       }
     }
-    if (Op::kGather == 1) op.gather(gbase + s * a_bytes, meta, z, m0, k0, kRows);
-    if (Op::kGather == 2) op.gather(gbase + ns * a_bytes + s * b_bytes, meta, z, n0, k0, nt);
+    if (Op::kGather == 1) gc.gather(gbase + s * a_bytes, k0);
+    if (Op::kGather == 2) gc.gather(gbase + ns * a_bytes + s * b_bytes, k0);
     if (Op::kGather) asm volatile("cp.async.commit_group;\n" ::);  // gathers copied from global memory
   };
   // zero the K rows r >= rows of a stage (MN-major operands of the last, partial K block)
@@ -302,7 +314,8 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const int quad = warp & 3, half = warp >> 2;  // tensor-memory lanes 32 quad.., column half
     const int rl = quad * 32 + lane;
-    if (Op::kEpi == 0) {
+    const auto ec = op.epi_ctx(meta, z, m0, n0);
+    if constexpr (Op::kEpi == 0) {
       // per row: thread rl hands the op 8 consecutive columns of its row at a time, the two warps
       // of a lane quarter taking one half of the columns each
       const int m = m0 + rl;
@@ -319,16 +332,17 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
           float f[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
-          op.epilogue(meta, z, m, rl, n0 + c0, f);
-          op.epilogue(meta, z, m, rl, n0 + c0 + 8, f + 8);
+          ec.epilogue(m, rl, n0 + c0, f);
+          ec.epilogue(m, rl, n0 + c0 + 8, f + 8);
         }
       }
     } else {
-      // 64-column chunks staged through the (now idle) stage buffers: thread rl moves its half of
-      // its row from tensor memory to shared memory, then warp w emits rows w, w + 8, ... with its
-      // lanes on consecutive columns, so the global accesses of a warp touch one row
-      float *stg = reinterpret_cast<float *>(gbase);
-      constexpr int kPitch = 68;  // floats per staged row: float4 writes of 8 threads hit distinct banks
+      // 64-column chunks staged through the (now idle) stage buffers: thread rl converts its half of
+      // its row (E::stage, 16 independent values per tensor-memory load) and stores it to shared
+      // memory, then warp w emits rows w, w + 8, ... with its lanes on consecutive columns, so the
+      // global accesses of a warp touch one row
+      uint2 *stg = reinterpret_cast<uint2 *>(gbase);
+      constexpr int kPitch = kStagedPitch;  // the 16-byte stores of 8 threads hit distinct banks
       for (int c0 = 0; c0 < nt; c0 += 64) {
 #pragma unroll
         for (int q = half * 32; q < half * 32 + 32; q += 16) {
@@ -340,17 +354,18 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-          float4 *dst = reinterpret_cast<float4 *>(stg + rl * kPitch + q);
+          uint2 w[16];
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+          for (int i = 0; i < 16; ++i) w[i] = ec.stage(__uint_as_float(v[i]));
+          uint4 *dst = reinterpret_cast<uint4 *>(stg + rl * kPitch + q);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) dst[i] = make_uint4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x, w[2 * i + 1].y);
         }
         __syncthreads();
-        for (int r = warp; r < kRows && m0 + r < M; r += kThreads / 32) {
-          if (!op.row_active(meta, z, m0 + r, r)) continue;
-          for (int j = lane; j < 64 && n0 + c0 + j < N; j += 32)
-            op.emit(meta, z, m0 + r, r, n0 + c0 + j, stg[r * kPitch + j]);
+#pragma unroll 4
+        for (int r = warp; r < kRows; r += kThreads / 32) {
+          if (m0 + r >= M || !ec.row_active(r)) continue;
+          for (int j = lane; j < 64 && n0 + c0 + j < N; j += 32) ec.emit(m0 + r, r, n0 + c0 + j, stg[r * kPitch + j]);
         }
         __syncthreads();
       }
