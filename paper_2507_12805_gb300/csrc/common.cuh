@@ -186,6 +186,22 @@ __device__ __forceinline__ long long fix40(float v) {
   return neg ? -(long long)q : (long long)q;
 }
 
+// The same fixed-point value q = rint(v 2^40) split as (q mod 2^22, floor(q / 2^22)), branch-free
+// in FP32 on |v|: x = |v| 2^18 is exact, f = floor(x) and x - f are exact (x - f = x below 1,
+// Sterbenz's lemma above), and rint((x - f) 2^22) = q - f 2^22 because f 2^22 is an even integer
+// (ties to even are unaffected); a negative v negates the pair (rint is odd).  Exact for
+// |v| < 2^13 (the high part then fits in 32 bits); beyond that the high part saturates.
+__device__ __forceinline__ uint2 fix40_split22(float v) {
+  const float x = __fmul_rn(fabsf(v), 262144.f);  // 2^18
+  const float f = floorf(x);
+  const float l = rintf(__fmul_rn(__fsub_rn(x, f), 4194304.f));  // in [0, 2^22]
+  const bool carry = l == 4194304.f;
+  const uint32_t lo = carry ? 0u : (uint32_t)l;
+  const int hi = __float2int_rz(f) + (carry ? 1 : 0);
+  if (!signbit(v)) return make_uint2(lo, (uint32_t)hi);
+  return make_uint2(lo ? 4194304u - lo : 0u, (uint32_t)(lo ? -hi - 1 : -hi));
+}
+
 // q * 2^-40 rounded once to the nearest float (ties to even), in integer arithmetic.
 __device__ __forceinline__ float unfix40(long long q) {
   if (q == 0) return 0.f;
@@ -203,6 +219,32 @@ __device__ __forceinline__ float unfix40(long long q) {
   return neg ? -mag : mag;
 }
 
+}  // namespace pmklc
+
+namespace pmklc {
+// Programmatic dependent launch: a kernel launched by launch_pdl may be scheduled while the previous
+// kernel of its stream is still running.  Every such kernel calls pdl_wait() first, before any early
+// exit (it returns once the previous kernel has completed and its writes are visible, so a kernel's
+// completion still implies its predecessor's), then pdl_trigger() to let its own successor be
+// scheduled early.  Launched the ordinary way, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 }  // namespace pmklc
 
 #define PMKLC_CUDA_TRY(expr)                   \

@@ -302,6 +302,8 @@ __device__ __forceinline__ int reg_symbol(const RegRow<NR> &R, int lane, uint32_
 
 template <int NR>
 __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= p.NL) return;
@@ -581,10 +583,10 @@ void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
   ProfScope ps("mix_cdf_code", 0, 12.0 * prof_work().pred_rows * p.dm.A, st);
   const unsigned grid = (unsigned)((p.NL * 32 + 255) / 256);
   switch (p.dm.A) {  // register-resident rows where a lane's chunk fits in registers
-    case 64: mixcode_kernel<2><<<grid, 256, 0, st>>>(p, T); break;
-    case 256: mixcode_kernel<8><<<grid, 256, 0, st>>>(p, T); break;
-    case 1024: mixcode_kernel<32><<<grid, 256, 0, st>>>(p, T); break;
-    default: mixcode_kernel<0><<<grid, 256, 0, st>>>(p, T); break;
+    case 64: launch_pdl(mixcode_kernel<2>, dim3(grid), dim3(256), 0, st, p, T); break;
+    case 256: launch_pdl(mixcode_kernel<8>, dim3(grid), dim3(256), 0, st, p, T); break;
+    case 1024: launch_pdl(mixcode_kernel<32>, dim3(grid), dim3(256), 0, st, p, T); break;
+    default: launch_pdl(mixcode_kernel<0>, dim3(grid), dim3(256), 0, st, p, T); break;
   }
 }
 

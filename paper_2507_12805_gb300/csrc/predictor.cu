@@ -361,8 +361,11 @@ struct DXOp : RowBase {
 // (Emb, zeroed on the way); all loads of a group are issued before its stores.  The FP32
 // master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.  Grid row
 // blockIdx.y is a group; its blocks stride over the group's float4 groups with 32-bit indices
-// (no 64-bit division, whose FP64-based code is slow on GB300).
+// (no 64-bit division, whose FP64-based code is slow on GB300).  The first warp of a group's
+// first block also updates the group's mixing weight alpha (Eq. 1) by the same rule.
 __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
+  pdl_wait();
+  pdl_trigger();
   const int g = blockIdx.y;
   if (!group_trains(p, T, g)) return;
   const uint32_t P = (uint32_t)p.P, nq = (P + 3) / 4, nemb = (uint32_t)(p.dm.A * p.dm.E);
@@ -376,6 +379,18 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
   const float *__restrict__ gr = p.grad + base;
   long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
   const bool aligned = (base & 3) == 0;
+  if (blockIdx.x == 0 && threadIdx.x < 32) {  // the mixing weight alpha of Eq. (1), same rule
+    const float ga = alpha_grad(p, T, g);
+    if (threadIdx.x == 0) {
+      p.dalpha_grp[g] = ga;
+      float t1[4] = {p.alpha[g], 0, 0, 0}, m1[4] = {p.alpha_m[g], 0, 0, 0}, v1[4] = {p.alpha_v[g], 0, 0, 0},
+            g1[4] = {ga, 0, 0, 0};
+      adam_n<1>(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
+      p.alpha[g] = t1[0];
+      p.alpha_m[g] = m1[0];
+      p.alpha_v[g] = v1[0];
+    }
+  }
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nq; w += gridDim.x * blockDim.x) {
     const uint32_t i0 = w * 4;
     float t[4], m[4], v[4], gg[4];
@@ -422,24 +437,6 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
       }
     }
   }
-}
-
-// alpha of every training group (one warp per group)
-__global__ void alpha_update_kernel(Plan p, int T) {
-  int g = blockIdx.x;
-  if (!group_trains(p, T, g)) return;
-  float ga = alpha_grad(p, T, g);
-  if (threadIdx.x != 0) return;
-  int j = T - p.grp_start[g];
-  int tau = p.grp_tau0[g] + (j - p.t_eff) + 1;
-  float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
-  p.dalpha_grp[g] = ga;
-  float t[4] = {p.alpha[g], 0, 0, 0}, m[4] = {p.alpha_m[g], 0, 0, 0}, v[4] = {p.alpha_v[g], 0, 0, 0},
-        gg[4] = {ga, 0, 0, 0};
-  adam_n<1>(t, m, v, gg, p.lr, bc1, bc2, p.optimizer == PMKLC_ADAM);
-  p.alpha[g] = t[0];
-  p.alpha_m[g] = m[0];
-  p.alpha_v[g] = v[0];
 }
 
 __global__ void smp_copy_kernel(Plan p, const int *pairs, int n_pairs) {
@@ -529,9 +526,8 @@ void launch_update(const Plan &p, int T, cudaStream_t st) {
     size_t gx = (nq + 255) / 256;
     const size_t cap = std::max<size_t>(1, (size_t)152 * 16 / std::max(1, p.G));
     if (gx > cap) gx = cap;
-    opt_stream_kernel<<<dim3((unsigned)gx, (unsigned)p.G), 256, 0, st>>>(p, T);
+    launch_pdl(opt_stream_kernel, dim3((unsigned)gx, (unsigned)p.G), dim3(256), 0, st, p, T);  // also updates alpha
   }
-  alpha_update_kernel<<<p.G, 32, 0, st>>>(p, T);
 }
 
 void launch_backward_update(const Plan &p, int T, cudaStream_t st) {

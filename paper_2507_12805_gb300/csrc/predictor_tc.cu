@@ -404,18 +404,20 @@ struct DXT : TBase {
     __device__ bool row_active(int rl) const { return tp[rl] >= 0; }
     // fixed point v 2^40: shared sums take (low 22 bits, the rest), global ones the two 32-bit halves
     __device__ uint2 stage(float v) const {
+      if (lo) return fix40_split22(v);
       const long long q = fix40(v);
-      return lo ? make_uint2((uint32_t)(q & ((1ll << 22) - 1)), (uint32_t)(int)(q >> 22))
-                : make_uint2((uint32_t)(unsigned long long)q, (uint32_t)((unsigned long long)q >> 32));
+      return make_uint2((uint32_t)(unsigned long long)q, (uint32_t)((unsigned long long)q >> 32));
     }
-    __device__ void emit(int, int rl, int n, uint2 s) const {
-      if ((s.x | s.y) == 0) return;
+    // table entry of column n of tile row rl: its context token's row, embedding offset
+    __device__ uint32_t index(int rl, int n) const {
       const int pos = eshift >= 0 ? n >> eshift : n / E;
-      const uint32_t i = (uint32_t)tk[rl * t + pos] * (uint32_t)E + (uint32_t)(n - pos * E);
+      return (uint32_t)tk[rl * t + pos] * (uint32_t)E + (uint32_t)(n - pos * E);
+    }
+    __device__ void add(uint32_t i, uint2 s) const {
       if (lo) {
-        atomicAdd(lo + i, s.x);  // results unused: reductions, no return
+        if (s.x) atomicAdd(lo + i, s.x);  // results unused: reductions, no return
         if (s.y) atomicAdd(reinterpret_cast<int *>(lo) + AE + i, (int)s.y);
-      } else {
+      } else if (s.x | s.y) {
         atomicAdd(glob + i, ((unsigned long long)s.y << 32) | s.x);
       }
     }
@@ -706,6 +708,8 @@ struct LogitsF8 : TBase {
 // so the result does not depend on scheduling.
 constexpr int kBiasChunks = 16, kBiasSlices = 16;
 __global__ void __launch_bounds__(kBiasChunks * kBiasSlices) bias_grad_kernel(Plan p, int T) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float part[kBiasSlices][kBiasChunks * 8 + 4];
   const int g = blockIdx.y;
   if (!group_trains(p, T, g)) return;
@@ -985,8 +989,8 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     DW2T op;
     op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
     tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
-    bias_grad_kernel<<<dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G), kBiasChunks * kBiasSlices, 0,
-                       s1>>>(p, T);
+    launch_pdl(bias_grad_kernel, dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G),
+               dim3(kBiasChunks * kBiasSlices), 0, s1, p, T);
   }
   {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);

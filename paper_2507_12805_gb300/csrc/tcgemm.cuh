@@ -135,15 +135,18 @@ __device__ __forceinline__ uint32_t sw_mn(int n, int k) {
 //   static constexpr int kEpi;                0: void E::epilogue(m, rl, n, const float v[8]) per
 //                                             row (8 columns n.., m < M);
 //                                             1: uint2 E::stage(float v) applied by the row's thread,
-//                                             then bool E::row_active(rl) and void E::emit(m, rl, n,
-//                                             uint2 staged) per element, the 32 lanes of a warp on
-//                                             consecutive n of one row
+//                                             then bool E::row_active(rl), uint32_t E::index(rl, n)
+//                                             and void E::add(index, uint2 staged) per element (a
+//                                             zero staged value adds nothing), the 32 lanes of a
+//                                             warp on consecutive n of one row
 //   static constexpr bool kFinish; void finish(uint8_t *meta, z): every thread, after the epilogue
 //   int zb;                                   first problem of the launch (blockIdx.z + zb)
 //   int *err();                               the error word
 template <class Op>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ Op op, int nt_max, int tmem_cols,
                                                          int ns) {
+  pdl_wait();
+  pdl_trigger();
   const int z = blockIdx.z + op.zb;  // problem index (a launch may cover a subrange of the problems)
   if (!op.active(z)) return;
   const int M = op.M(z), N = op.N(z), K = op.K(z);
@@ -362,10 +365,28 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           for (int i = 0; i < 8; ++i) dst[i] = make_uint4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x, w[2 * i + 1].y);
         }
         __syncthreads();
-#pragma unroll 4
-        for (int r = warp; r < kRows; r += kThreads / 32) {
-          if (m0 + r >= M || !ec.row_active(r)) continue;
-          for (int j = lane; j < 64 && n0 + c0 + j < N; j += 32) ec.emit(m0 + r, r, n0 + c0 + j, stg[r * kPitch + j]);
+        // rows in batches of four: every load of a batch (staged values, destinations) is issued
+        // before its first reduction, so the latencies overlap (8 warps per SM leave little else
+        // to hide them)
+        for (int r0 = warp; r0 < kRows; r0 += 4 * (kThreads / 32)) {
+          uint2 v[4][2];
+          uint32_t dst[4][2];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = r0 + b * (kThreads / 32);
+            const bool act = m0 + r < M && ec.row_active(r);
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+              const int j = lane + 32 * jj, n = n0 + c0 + j;
+              const bool in = act && n < N;
+              v[b][jj] = in ? stg[r * kPitch + j] : make_uint2(0u, 0u);
+              dst[b][jj] = in ? ec.index(r, n) : 0u;
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) ec.add(dst[b][jj], v[b][jj]);
         }
         __syncthreads();
       }
@@ -416,7 +437,7 @@ void launch(const Op &op, int Mmax, int Nmax, int Z, const TilePlan &t, size_t m
     configured = smem;
   }
   dim3 grid((Mmax + kRows - 1) / kRows, (Nmax + t.nt - 1) / t.nt, Z);
-  gemm_kernel<Op><<<grid, kThreads, smem, st>>>(op, t.nt, pow2_at_least(t.nt), t.ns);
+  launch_pdl(gemm_kernel<Op>, grid, dim3(kThreads), (size_t)smem, st, op, t.nt, pow2_at_least(t.nt), t.ns);
 }
 
 }  // namespace tc
