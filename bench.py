@@ -177,20 +177,22 @@ PROFILE_EVERY = 8  # every 8th global step's launches are bracketed with CUDA ev
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 
-def roofline(prof: dict, pk: dict, pk_kind: str):
-    """Achieved vs peak of the kernel with the largest sampled time, against the bound that its
-    algorithmic work reaches first (tensor/ALU FLOPs or HBM bytes)."""
-    if not prof:
-        return None, {}
-    tot = sum(x["ms"] for x in prof.values())
-    per = {k: {"launches": v["launches"], "ms_avg": v["ms"] / max(v["launches"], 1), "share": v["ms"] / tot,
-               "work_flops_per_launch": v["flops"] / max(v["launches"], 1),
-               "work_bytes_per_launch": v["bytes"] / max(v["launches"], 1)} for k, v in prof.items()}
-    name = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[name]
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of step kernels, from the
+# ncu --set full capture summarised in profiles/ncu_step_kernels_plain_bf16.md (the plain workload
+# cut to 2^14-base blocks: the same 64 groups x 128 lanes per launch as the full workload, so a
+# steady-state launch moves the same bytes).  Valid for the kernels as they stand in that capture.
+NCU_TRAFFIC = {}
+
+
+def _bound(name: str, d: dict, pk: dict, pk_kind: str):
+    """Achieved vs peak of one profiled kernel, against the bound its algorithmic work reaches first
+    (tensor/ALU FLOPs or HBM bytes)."""
     sec = d["ms"] / 1e3
-    tensor = name.endswith("_bf16")
-    if tensor:  # BF16 mma on the tensor cores; the kernel runs inside a long step: sustained peak
+    tensor = name.endswith("_bf16") or name.endswith("_fp8")
+    if name.endswith("_fp8"):  # E4M3 MMA: the BF16 measurement x the nominal FP8/BF16 ratio (4.5 / 2.25)
+        fpeak = 2.0 * pk.get("bf16_tflops_sustained", 1700.0)
+        fsrc = f"{pk_kind} bf16_tflops_sustained x 2 (nominal fp8/bf16 ratio)"
+    elif tensor:  # BF16 mma on the tensor cores; the kernel runs inside a long step: sustained peak
         fpeak, fsrc = pk.get("bf16_tflops_sustained", 1700.0), f"{pk_kind} bf16_tflops_sustained"
     else:  # FP32 FMA on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x max SM clock
         fpeak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -199,15 +201,31 @@ def roofline(prof: dict, pk: dict, pk_kind: str):
     t_byte = d["bytes"] / (pk["hbm_gbs"] * 1e9) if d["bytes"] else 0.0
     if t_flop >= t_byte and d["flops"]:
         ach = d["flops"] / sec / 1e12
-        r = {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": ach, "peak": fpeak,
-             "unit": "TFLOP/s", "frac": ach / fpeak, "peak_source": fsrc, "traffic": None,
-             "work_per_launch": d["flops"] / d["launches"], "work_unit": "FLOP"}
-    else:
-        ach = d["bytes"] / sec / 1e9
-        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-             "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs", "traffic": None,
-             "work_per_launch": d["bytes"] / max(d["launches"], 1), "work_unit": "byte"}
-    return r, per
+        return {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": ach, "peak": fpeak,
+                "unit": "TFLOP/s", "frac": ach / fpeak, "peak_source": fsrc,
+                "traffic": NCU_TRAFFIC.get(name), "work_per_launch": d["flops"] / max(d["launches"], 1),
+                "work_unit": "FLOP"}
+    ach = d["bytes"] / sec / 1e9 if d["bytes"] else 0.0
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs", "traffic": NCU_TRAFFIC.get(name),
+            "work_per_launch": d["bytes"] / max(d["launches"], 1), "work_unit": "byte"}
+
+
+def roofline(prof: dict, pk: dict, pk_kind: str):
+    """The roofline object of the kernel with the largest sampled time, and every profiled kernel's
+    share, mean time, work per launch and fraction of its bound."""
+    if not prof:
+        return None, {}
+    tot = sum(x["ms"] for x in prof.values())
+    per = {}
+    for k, v in prof.items():
+        b = _bound(k, v, pk, pk_kind)
+        per[k] = {"launches": v["launches"], "ms_avg": v["ms"] / max(v["launches"], 1), "share": v["ms"] / tot,
+                  "work_flops_per_launch": v["flops"] / max(v["launches"], 1),
+                  "work_bytes_per_launch": v["bytes"] / max(v["launches"], 1), "bound": b["bound"],
+                  "frac": b["frac"]}
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    return _bound(name, prof[name], pk, pk_kind), per
 
 
 FORMS = {"bf16": 1, "fp32": 0}

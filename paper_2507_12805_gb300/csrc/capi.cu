@@ -422,6 +422,18 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   if (ar.failed) return PMKLC_ENOMEM;
   // the FP8 static model runs on the tcgen05 engine only (no mma.sync form of it)
   if (p.st8 && !tc_supported(p)) return PMKLC_EINVAL;
+  // BF16 forms with small embedding tables: per-tile FP32 partials of the embedding gradient
+  p.demb_part = nullptr;
+  p.dx_np = p.dx_ct = 0;
+  if (bf_form(c.precision)) {
+    int ct = 0;
+    const int np = dx_partials(p, &ct);
+    if (np > 0) {
+      p.demb_part = ar.alloc<float>(G * (size_t)np * A * c.dm.E);
+      if (ar.failed) return PMKLC_ENOMEM;
+      p.dx_np = np, p.dx_ct = ct;
+    }
+  }
   cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
   cudaMemsetAsync(p.err, 0, sizeof(int), ar.st);
   std::vector<float> init;

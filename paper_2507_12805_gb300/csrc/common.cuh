@@ -78,6 +78,11 @@ struct Plan {
   __nv_bfloat16 *hd_b, *hs_b, *dz_b, *dh_b;  // BF16 activations of the BF16 form (else nullptr)
   float *hpart;                // split-K partial sums of the hidden layer (BF16 form, mma.sync engine)
   long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
+  // BF16 form with small tables: per group, dx_np partial FP32 tables (A x E) of the dX tiles
+  // (row tile bx, column tile by at partial bx * dx_ct + by), summed by the optimiser in that
+  // order; nullptr: the fixed-point accumulators above
+  float *demb_part;
+  int dx_np, dx_ct;
   // coders
   EncState *enc;
   DecState *dec;

@@ -87,6 +87,9 @@ bool tc_supported(const Plan &p);
 // step loop may run it on another stream)
 constexpr int kFwdDynamic = 1, kFwdStatic = 2, kFwdBoth = 3;
 void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which = kFwdBoth);
+// partial embedding-gradient tables per group of the dX GEMM when it sums its tiles in FP32 by
+// owner warps (small tables), else 0; *ct = its column tiles
+int dx_partials(const Plan &p, int *ct);
 // ss (optional): run dW2, dX and dW1 concurrently on st and ss->aux
 void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss);
 // predictor_bf16.cu: the BF16 form (tcgen05 engine where tc_supported, else mma.sync)

@@ -378,6 +378,9 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
   float *__restrict__ vv = p.v + base;
   const float *__restrict__ gr = p.grad + base;
   long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
+  // the group's partials of the embedding gradient: its row tiles x the column tiles
+  const float *__restrict__ part = p.demb_part ? p.demb_part + (size_t)g * p.dx_np * nemb : nullptr;
+  const int npart = p.demb_part ? ((p.grp_lane_off[g + 1] - p.grp_lane_off[g] + 127) / 128) * p.dx_ct : 0;
   const bool aligned = (base & 3) == 0;
   if (blockIdx.x == 0 && threadIdx.x < 32) {  // the mixing weight alpha of Eq. (1), same rule
     const float ga = alpha_grad(p, T, g);
@@ -400,7 +403,14 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
       t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
       m[0] = b.x, m[1] = b.y, m[2] = b.z, m[3] = b.w;
       v[0] = c.x, v[1] = c.y, v[2] = c.z, v[3] = c.w;
-      if (i0 < nemb) {  // A*E is a multiple of 4: a group never straddles the embedding boundary
+      if (i0 < nemb && part) {  // the dX tiles' FP32 partials, summed in partial order
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < npart; ++k) {
+          const float4 q = *reinterpret_cast<const float4 *>(part + (size_t)k * nemb + i0);
+          a4.x += q.x, a4.y += q.y, a4.z += q.z, a4.w += q.w;
+        }
+        gg[0] = a4.x, gg[1] = a4.y, gg[2] = a4.z, gg[3] = a4.w;
+      } else if (i0 < nemb) {  // A*E is a multiple of 4: a group never straddles the embedding boundary
         longlong2 q0 = *reinterpret_cast<const longlong2 *>(acc + i0),
                   q1 = *reinterpret_cast<const longlong2 *>(acc + i0 + 2);
         gg[0] = unfix40(q0.x), gg[1] = unfix40(q0.y), gg[2] = unfix40(q1.x), gg[3] = unfix40(q1.y);
@@ -424,7 +434,9 @@ __global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
     } else {
       for (uint32_t i = i0; i < i0 + 4 && i < P; ++i) {
         float t1[4] = {th[i], 0, 0, 0}, m1[4] = {mm[i], 0, 0, 0}, v1[4] = {vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
-        if (i < nemb) {
+        if (i < nemb && part) {
+          for (int k = 0; k < npart; ++k) g1[0] += part[(size_t)k * nemb + i];
+        } else if (i < nemb) {
           g1[0] = unfix40(acc[i]);
           acc[i] = 0;
         } else {
@@ -516,11 +528,13 @@ void launch_backward(const Plan &p, int T, cudaStream_t st) {
 
 void launch_update(const Plan &p, int T, cudaStream_t st) {
   // Adam: read w, m, v, grad (16 B) and write w, m, v (12 B) per parameter of every training
-  // group (+2 B for the BF16 copy); the embedding part reads/clears 8-byte accumulators instead
+  // group (+2 B for the BF16 copy); the embedding part reads/clears 8-byte accumulators instead of
+  // the 4-byte gradient, or reads the dX partials (dx_np of 4 bytes)
   const double nemb = (double)p.dm.A * p.dm.E;
   const double per = p.wbf ? 30.0 : 28.0;
+  const double emb_extra = p.demb_part ? nemb * 4.0 * (p.dx_np - 1) : nemb * 12.0;
   {
-    ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * per + nemb * 12.0), st);
+    ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * per + emb_extra), st);
     // about 16 blocks of 256 threads per SM over all groups; each grid row is one group
     const size_t nq = (p.P + 3) / 4;
     size_t gx = (nq + 255) / 256;
@@ -539,9 +553,19 @@ namespace {
 __global__ void export_grad_kernel(Plan p, float *out) {
   int g = blockIdx.y;
   size_t nemb = (size_t)p.dm.A * p.dm.E;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < p.P; i += (size_t)gridDim.x * blockDim.x)
-    out[(size_t)g * p.P + i] = i < nemb ? unfix40(p.demb_acc[(size_t)g * nemb + i])
-                                        : p.grad[(size_t)g * p.P + i];
+  const int npart = p.demb_part ? ((p.grp_lane_off[g + 1] - p.grp_lane_off[g] + 127) / 128) * p.dx_ct : 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < p.P; i += (size_t)gridDim.x * blockDim.x) {
+    float v;
+    if (i >= nemb) {
+      v = p.grad[(size_t)g * p.P + i];
+    } else if (p.demb_part) {  // the same partial order as the optimiser
+      v = 0.f;
+      for (int k = 0; k < npart; ++k) v += p.demb_part[((size_t)g * p.dx_np + k) * nemb + i];
+    } else {
+      v = unfix40(p.demb_acc[(size_t)g * nemb + i]);
+    }
+    out[(size_t)g * p.P + i] = v;
+  }
 }
 }  // namespace
 

@@ -441,6 +441,107 @@ struct DXT : TBase {
   }
 };
 
+// dX = dh W1^T summed into the embedding rows without atomics (groups whose table A x E fits in
+// 32 KB of FP32 and E divides 64): the tile is staged out of tensor memory 64 columns at a time
+// and warp w owns the table rows of the tokens a with a % 8 == w; each warp walks the chunk's
+// (row, position) pairs in order and adds the E values of every pair of one of its tokens to
+// that token's row, lane e on element e, so every table element is summed by one lane in a
+// fixed order.  The CTA's table goes to its own partial (row tile bx, column tile by) and the
+// optimiser sums a group's partials in order: the result does not depend on scheduling.
+struct DXOwnT : TBase {
+  static constexpr bool kAMN = false, kBMN = true, kTail = false;
+  static constexpr int kEpi = 2;
+  static constexpr int kGather = 0;
+  static constexpr bool kFinish = true;
+  CUtensorMap dh, w1;
+  int qshift;  // log2 of the positions per 64-column chunk (64 / E)
+  __device__ bool active(int z) const { return group_trains(p, T, z); }
+  __device__ int M(int z) const { return nrows(z); }
+  __device__ int N(int) const { return p.dm.K1(); }
+  __device__ int K(int) const { return p.dm.H; }
+  __device__ float *tab(const uint8_t *meta) const {
+    return reinterpret_cast<float *>(const_cast<uint8_t *>(meta) + ml.tab_off());
+  }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const {
+    MetaLayout l = ml;
+    l.table = 0;  // the table region is not an embedding copy
+    fill(meta, l, z, m0, tc::kRows, nullptr, 0);
+    float4 *t4 = reinterpret_cast<float4 *>(tab(meta));
+    const int n4 = p.dm.A * p.dm.E / 4;
+    for (int i = threadIdx.x; i < n4; i += tc::kThreads) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
+  __device__ int row_a(int z, int m0) const { return row(z, m0); }
+  __device__ int row_b(int, int n0) const { return n0; }
+  struct Epi {
+    const long long *tp;
+    const uint16_t *tk;
+    float *tab;
+    int E, t, n0, qshift;
+    __device__ void chunk(const float *stg, int c0) const {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int p0 = (n0 + c0) / E, q = 1 << qshift, npairs = tc::kRows << qshift;
+      for (int i0 = 0; i0 < npairs; i0 += 32) {
+        const int i = i0 + lane, r = i >> qshift, ps = p0 + (i & (q - 1));
+        int tok = -1;
+        if (i < npairs && ps < t && tp[r] >= 0) tok = tk[r * t + ps];
+        unsigned mine = __ballot_sync(0xffffffffu, tok >= 0 && (tok & 7) == warp);
+        // matches four at a time, in pair order: every load of the batch first, a token met twice
+        // in the batch chained in registers (same order as one at a time), one store per token
+        while (mine) {
+          int tb[4];
+          const float *src[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            tb[k] = -1;
+            src[k] = stg;
+            if (mine) {
+              const int b = __ffs(mine) - 1;
+              mine &= mine - 1;
+              tb[k] = __shfl_sync(0xffffffffu, tok, b);
+              const int ib = i0 + b;
+              src[k] = stg + (ib >> qshift) * tc::kFloatPitch + (ib & (q - 1)) * E;
+            }
+          }
+          for (int e = lane; e < E; e += 32) {
+            float v[4], d[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              v[k] = tb[k] >= 0 ? src[k][e] : 0.f;
+              d[k] = tb[k] >= 0 ? tab[tb[k] * E + e] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (tb[k] < 0) continue;
+              bool first = true;  // the batch's first match of this token carries the running sum
+#pragma unroll
+              for (int j = 0; j < k; ++j)
+                if (tb[j] == tb[k]) first = false;
+              if (!first) continue;
+              float acc = d[k] + v[k];
+#pragma unroll
+              for (int j = k + 1; j < 4; ++j)
+                if (tb[j] == tb[k]) acc += v[j];
+              tab[tb[k] * E + e] = acc;
+            }
+          }
+        }
+      }
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int, int, int n0) const {
+    return {tp(meta), tk(meta), tab(meta), p.dm.E, p.dm.t, n0, qshift};
+  }
+  // every thread, after the last chunk's barrier: the CTA's table to its partial
+  __device__ void finish(uint8_t *meta, int z) const {
+    const int AE = p.dm.A * p.dm.E;
+    const float4 *src = reinterpret_cast<const float4 *>(tab(meta));
+    float4 *dst = reinterpret_cast<float4 *>(p.demb_part + ((size_t)z * p.dx_np + blockIdx.x * p.dx_ct + blockIdx.y) * AE);
+    for (int i = threadIdx.x; i < AE / 4; i += tc::kThreads) dst[i] = src[i];
+  }
+};
+
 // dW1 (stored transposed: dW1t[h][i] = sum over predicted lanes of dh[m][h] X[m][i]): M = H,
 // N = t*E, K = lanes; A = dh by TMA (MN-major), B = X gathered (MN-major)
 struct DW1T : TBase {
@@ -785,7 +886,7 @@ struct TcSetup {
   bool ok;
   tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8;
   MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
-  int table_h[2], table_w1, sacc_dx, table_h8;
+  int table_h[2], table_w1, sacc_dx, table_h8, dx_owner;
   CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
 };
 
@@ -796,6 +897,13 @@ bool same_key(const TcSetup &a, const Plan &p) {
          a.use_static == p.use_static &&
          dims_eq(a.dm, p.dm) && (!p.use_static || dims_eq(a.st, p.st)) && a.P == p.P;
 }
+
+// dX by owner warps: the group's FP32 table fits in 32 KB and E divides the 64-column chunks
+bool dx_owner_rule(const Plan &p) {
+  const Dims &D = p.dm;
+  return D.E >= 8 && 64 % D.E == 0 && (size_t)D.A * D.E * 4 <= 32 * 1024;
+}
+int dx_owner_nt(const Plan &p) { return p.dm.K1() >= 128 ? 128 : 64; }
 
 bool shapes_ok(const Plan &p) {
   auto ok = [](const Dims &d) { return d.E % 8 == 0 && d.H % 64 == 0 && d.A % 64 == 0 && d.K1() % 64 == 0; };
@@ -839,6 +947,13 @@ bool build(TcSetup &S, const Plan &p) {
   // the staged epilogue needs kStagedBytes of stage buffers (checked against the limit below)
   while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < tc::kStagedBytes) ++S.t_dx.ns;
   if (S.t_dx.ns > tc::kStages) return false;
+  S.dx_owner = dx_owner_rule(p);
+  if (S.dx_owner) {  // 128-column tiles, two stage buffers: two CTAs per SM
+    S.ml_dx = {tc::kRows, D.t, D.A * D.E * 4};
+    S.t_dx = {dx_owner_nt(p), 2};
+    if ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < (size_t)tc::kRows * tc::kFloatPitch * 4)
+      return false;
+  }
   S.t_w1 = tc::plan_tiles(D.H, D.K1(), p.Mmax, p.G, S.ml_w1.bytes());
   for (const auto &pr : {std::make_pair(S.t_h, S.ml_h.bytes()), std::make_pair(S.t_l, S.ml_l.bytes()),
                          std::make_pair(S.t_dh, S.ml_dh.bytes()), std::make_pair(S.t_w2, S.ml_w2.bytes()),
@@ -911,6 +1026,13 @@ bool get_setup(const Plan &p, TcSetup &out) {
 
 }  // namespace
 
+int dx_partials(const Plan &p, int *ct) {
+  *ct = 0;
+  if (!dx_owner_rule(p) || !tc_supported(p)) return 0;
+  *ct = (p.dm.K1() + dx_owner_nt(p) - 1) / dx_owner_nt(p);
+  return ((p.Mmax + tc::kRows - 1) / tc::kRows) * *ct;
+}
+
 bool tc_supported(const Plan &p) {
   if (!shapes_ok(p)) return false;
   TcSetup S;
@@ -977,7 +1099,13 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     cudaStreamWaitEvent(ss->aux[1], ss->fork, 0);
     s1 = ss->aux[0], s2 = ss->aux[1];
   }
-  {
+  if (S.dx_owner) {
+    ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
+    DXOwnT op;
+    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
+    op.qshift = __builtin_ctz((unsigned)(64 / D.E));
+    tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
+  } else {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXT op;
     op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn, op.sacc = S.sacc_dx;

@@ -43,6 +43,7 @@ constexpr long kSpinLimit = 1L << 24;  // mbarrier polls before a wait gives up
 constexpr int kStagedPitch = 66;       // uint2 per staged row of a kEpi == 1 epilogue (64 columns + pad)
 // bytes of stage buffers a kEpi == 1 epilogue stages its 64-column chunks through
 constexpr size_t kStagedBytes = (size_t)kRows * kStagedPitch * 8;
+constexpr int kFloatPitch = 68;        // floats per staged row of a kEpi == 2 epilogue
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -138,7 +139,10 @@ __device__ __forceinline__ uint32_t sw_mn(int n, int k) {
 //                                             then bool E::row_active(rl), uint32_t E::index(rl, n)
 //                                             and void E::add(index, uint2 staged) per element (a
 //                                             zero staged value adds nothing), the 32 lanes of a
-//                                             warp on consecutive n of one row
+//                                             warp on consecutive n of one row;
+//                                             2: void E::chunk(const float *stg, c0), every thread,
+//                                             after the 64 columns c0.. of all rows are staged as
+//                                             FP32 (row r at stg + r * kFloatPitch)
 //   static constexpr bool kFinish; void finish(uint8_t *meta, z): every thread, after the epilogue
 //   int zb;                                   first problem of the launch (blockIdx.z + zb)
 //   int *err();                               the error word
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           ec.epilogue(m, rl, n0 + c0 + 8, f + 8);
         }
       }
-    } else {
+    } else if constexpr (Op::kEpi == 1) {
       // 64-column chunks staged through the (now idle) stage buffers: thread rl converts its half of
       // its row (E::stage, 16 independent values per tensor-memory load) and stores it to shared
       // memory, then warp w emits rows w, w + 8, ... with its lanes on consecutive columns, so the
@@ -391,6 +395,32 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         __syncthreads();
       }
     }
+    if constexpr (Op::kEpi == 2) {
+      // 64-column chunks staged as FP32 through the stage buffers, each followed by a pass of the
+      // whole CTA over the staged chunk (E::chunk), between barriers
+      float *stg = reinterpret_cast<float *>(gbase);
+      for (int c0 = 0; c0 < nt; c0 += 64) {
+#pragma unroll
+        for (int q = half * 32; q < half * 32 + 32; q += 16) {
+          uint32_t v[16];
+          const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c0 + q);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+          float4 *dst = reinterpret_cast<float4 *>(stg + rl * kFloatPitch + q);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        }
+        __syncthreads();
+        ec.chunk(stg, c0);
+        __syncthreads();
+      }
+    }
     if (Op::kFinish) op.finish(meta, z);  // the op's CTA-wide step after the epilogue
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -416,9 +446,9 @@ inline size_t smem_bytes(const TilePlan &t, size_t meta_bytes) {
   return 1024 + (size_t)t.ns * (kRows + t.nt) * kRowBytes + ((meta_bytes + 15) & ~(size_t)15);
 }
 inline TilePlan plan_tiles(int Mmax, int Nmax, int Kmax, int Z, size_t meta_bytes, bool split = true, int bk = kBK) {
-  const int mt = (Mmax + kRows - 1) / kRows;
+  const int mt = (Mmax + kRows - 1) / kRows, nk = (Kmax + bk - 1) / bk;
   // K blocks + 2 buffers let every block be staged before the MMAs need it (prefetch ns - 2)
-  TilePlan t{min(256, Nmax), max(2, min(kStages, (Kmax + bk - 1) / bk + 2))};
+  TilePlan t{min(256, Nmax), max(2, min(kStages, nk + 2))};
   // (an op that gathers its A operand pays the gather once per column tile: split = false)
   while (split && t.nt > 64 && (t.nt / 2) % 64 == 0 && (long)mt * ((Nmax + t.nt - 1) / t.nt) * Z < 152L) t.nt /= 2;
   while (t.ns > 2 && smem_bytes(t, meta_bytes) > 220 * 1024) --t.ns;  // fewer buffers before narrower tiles
