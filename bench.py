@@ -107,6 +107,10 @@ def load_workload(name: str, block_bases: int = 0):
     return w, kw
 
 
+def workload_name(name, w, kw) -> str:
+    return f"{name}: {w.recipe}, {int(w.seq.size)} bases, {len(w.block_lens)} blocks, (s,k)=({kw['s']},{kw['k']})"
+
+
 def static_weights(P, kw):
     if not kw.get("use_static"):
         return None
@@ -168,7 +172,7 @@ def run_reference(args, w, kw, sw):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "MB/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload}, "cpu_baseline": cb,
+            "config": {"workload": workload_name(args.workload, w, kw), "model": kw}, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -181,7 +185,12 @@ SM_COUNT, FP32_LANES_PER_SM = 152, 128
 # ncu --set full capture summarised in profiles/ncu_step_kernels_plain_bf16.md (the plain workload
 # cut to 2^14-base blocks: the same 64 groups x 128 lanes per launch as the full workload, so a
 # steady-state launch moves the same bytes).  Valid for the kernels as they stand in that capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "bwd_dx_bf16": 10051584 + 0,            # gemm_kernel<DXOwnT>
+    "fwd_hidden_dyn_bf16": 9544448 + 0,     # gemm_kernel<HiddenT>, the 64 dynamic models
+    "fwd_hidden_static_bf16": 897792 + 0,   # gemm_kernel<HiddenT>, the shared static model
+    "update_adam": 95683840 + 19200768,     # opt_stream_kernel
+}
 
 
 def _bound(name: str, d: dict, pk: dict, pk_kind: str):
@@ -362,8 +371,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if form == "bf16" else "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {w.recipe}, {n} bases, {len(w.block_lens)} blocks, "
-                               f"(s,k)=({kw['s']},{kw['k']})", "model": kw,
+        "config": {"workload": workload_name(args.workload, w, kw), "model": kw,
                    "form": {"bf16": "BF16 batched", "fp32": "FP32 plain"}[form],
                    "bits_per_base": 8 * head["clen"] / n, "compressed_bytes": head["clen"],
                    "net_blocks": st1["net_blocks"], "count_blocks": st1["count_blocks"],
