@@ -534,9 +534,11 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       launch_mixcode(R.p, T, st);
       R.launches++;
     }
-    if (split_static && T + 1 < S.T_total && pred_at[T + 1]) {
-      // static forward of the next step: its contexts are decoded by now, and the mixer has read
-      // this step's static logits
+    // static forward of the next step (BF16 forms): its contexts are decoded by now and the mixer
+    // has read this step's static logits; queued once this step's gradient GEMMs are done, so it
+    // shares the SMs with the HBM-bound optimiser rather than with the latency-bound GEMMs
+    auto queue_static_next = [&]() {
+      if (!(split_static && T + 1 < S.T_total && pred_at[T + 1])) return;
       cudaEventRecord(ss.mix_done, st);
       cudaStreamWaitEvent(ss.aux[2], ss.mix_done, 0);
       prof_step(T + 1, work_at(T + 1));
@@ -545,15 +547,18 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       cudaEventRecord(ss.static_done, ss.aux[2]);
       static_for = T + 1;
       R.launches += 2;
-    }
+    };
     if (any_pred) {
       if (bf) {
         launch_backward_bf16(R.p, T, st, use_ss ? &ss : nullptr);
+        queue_static_next();
         launch_update(R.p, T, st);
       } else {
         launch_backward_update(R.p, T, st);
       }
       R.launches += 5;
+    } else {
+      queue_static_next();
     }
   }
   prof_stop_sampling();
