@@ -1084,21 +1084,33 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
   if (!get_setup(p, S)) return;
   const double R = prof_work().pred_rows;
   const Dims &D = p.dm;
+  // dW2 reads only h and dz: with auxiliary streams it starts beside dh; dX and dW1 follow dh side
+  // by side, and the bias sums (db1 needs dh) follow both dW2 and dh
+  cudaStream_t s1 = st, s2 = st;
+  if (ss) {
+    cudaEventRecord(ss->fork, st);
+    cudaStreamWaitEvent(ss->aux[0], ss->fork, 0);
+    s1 = ss->aux[0], s2 = ss->aux[1];
+  }
+  {
+    ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, s1);
+    DW2T op;
+    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
+    tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
+  }
   {
     ProfScope ps("bwd_dh_bf16", 2.0 * R * D.A * D.H, 0, st);
     DhT op;
     op.p = p, op.T = T, op.ml = S.ml_dh, op.dz = S.dzk, op.w2 = S.w2k;
     tc::launch(op, p.Mmax, D.H, p.G, S.t_dh, S.ml_dh.bytes(), st);
   }
-  // dW2 (+ bias sums), dX and dW1 only read dh, dz, h and the weights
-  // and write disjoint buffers: with auxiliary streams they run side by side
-  cudaStream_t s1 = st, s2 = st;
   if (ss) {
-    cudaEventRecord(ss->fork, st);
-    cudaStreamWaitEvent(ss->aux[0], ss->fork, 0);
+    cudaEventRecord(ss->fork, st);  // dh done
     cudaStreamWaitEvent(ss->aux[1], ss->fork, 0);
-    s1 = ss->aux[0], s2 = ss->aux[1];
+    cudaStreamWaitEvent(ss->aux[0], ss->fork, 0);
   }
+  launch_pdl(bias_grad_kernel, dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G),
+             dim3(kBiasChunks * kBiasSlices), 0, s1, p, T);
   if (S.dx_owner) {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXOwnT op;
@@ -1111,14 +1123,6 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn, op.sacc = S.sacc_dx;
     op.eshift = (D.E & (D.E - 1)) == 0 ? __builtin_ctz((unsigned)D.E) : -1;
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
-  }
-  {
-    ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, s1);
-    DW2T op;
-    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
-    tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
-    launch_pdl(bias_grad_kernel, dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G),
-               dim3(kBiasChunks * kBiasSlices), 0, s1, p, T);
   }
   {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);
