@@ -1,0 +1,65 @@
+"""Host logic of bench.py (no GPU): the roofline object of the dominant kernel, every kernel's
+fraction of its own bound, the measured-traffic lookup, and the profiling case that cuts the
+workload's blocks while keeping their number."""
+import numpy as np
+import pytest
+
+import bench
+
+PEAKS = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1600.0, "sm_max_mhz": 2000.0}
+
+
+def _prof():
+    # ms totals over 10 launches; work totals over the same launches
+    return {
+        "bwd_dx_bf16": {"launches": 10, "ms": 0.5, "flops": 10 * 1.6e9, "bytes": 0.0},
+        "update_adam": {"launches": 10, "ms": 0.4, "flops": 0.0, "bytes": 10 * 3.0e8},
+        "fwd_hidden_static_fp8": {"launches": 10, "ms": 0.2, "flops": 10 * 2.0e9, "bytes": 0.0},
+        "fwd_hidden_dm": {"launches": 10, "ms": 0.1, "flops": 10 * 1.0e9, "bytes": 0.0},
+        "count_step": {"launches": 10, "ms": 0.1, "flops": 0.0, "bytes": 0.0},
+    }
+
+
+def test_dominant_kernel_and_its_bound():
+    r, per = bench.roofline(_prof(), PEAKS, "measured")
+    assert r["kernel"] == "bwd_dx_bf16" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    # 1.6 GFLOP per launch in 0.05 ms = 32 TFLOP/s against the sustained BF16 peak
+    assert r["achieved"] == pytest.approx(32.0)
+    assert r["frac"] == pytest.approx(32.0 / 1600.0)
+    assert r["work_per_launch"] == pytest.approx(1.6e9)
+    assert r["traffic"] == bench.NCU_TRAFFIC["bwd_dx_bf16"]
+    assert sum(v["share"] for v in per.values()) == pytest.approx(1.0)
+
+
+def test_every_kernel_against_its_own_bound():
+    _, per = bench.roofline(_prof(), PEAKS, "measured")
+    # HBM-bound optimiser: 300 MB per launch in 0.04 ms = 7500 GB/s against 6000
+    assert per["update_adam"]["bound"] == "hbm"
+    assert per["update_adam"]["frac"] == pytest.approx(7500.0 / 6000.0)
+    # E4M3 kernels against twice the BF16 figure
+    assert per["fwd_hidden_static_fp8"]["bound"] == "tensor"
+    assert per["fwd_hidden_static_fp8"]["frac"] == pytest.approx(100.0 / 3200.0)
+    # FP32 form: ALU peak = 152 SMs x 128 lanes x 2 x 2.0 GHz
+    alu = 152 * 128 * 2 * 2000e6 / 1e12
+    assert per["fwd_hidden_dm"]["bound"] == "alu"
+    assert per["fwd_hidden_dm"]["frac"] == pytest.approx(100.0 / alu)
+    assert per["count_step"]["frac"] == 0.0
+
+
+def test_no_profile_gives_no_roofline():
+    assert bench.roofline({}, PEAKS, "measured") == (None, {})
+
+
+def test_profiling_case_keeps_blocks_and_cuts_them():
+    w, kw = bench.load_workload("plain", 1 << 12)
+    assert len(w.block_lens) == 64 and np.all(w.block_lens == (1 << 12))
+    assert w.seq.size == 64 << 12
+    full, _ = bench.load_workload("plain")
+    assert np.array_equal(w.seq, full.seq[: 64 << 12])  # the blocks' leading bases
+    assert kw["k"] == 4 and kw["lanes_per_block"] == 64
+    name = bench.workload_name("plain", w, kw)
+    assert "262144 bases" in name and "64 blocks" in name and "(s,k)=(2,4)" in name
+
+
+def test_job_throughput_is_whole_job():
+    assert bench.job_throughput(4, 1 << 24, 1000.0) == pytest.approx(4 * (1 << 24) / 1e6)
