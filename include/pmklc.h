@@ -90,7 +90,7 @@ size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid);
 
 /*
  * Seeded initial parameters of an MLP predictor (the paper's "randomly
- * initialized parameters", §4.3; reading R8: counter-based splitmix64 draws
+ * initialized parameters", §4.3; the paper names no generator: counter-based splitmix64 draws
  * scaled by 1 for the embedding and 1/sqrt(fan_in) for W1, W2; biases 0).
  * out: host array of pmklc_model_count(k, emb, ctx, hid) floats.
  */
@@ -179,7 +179,7 @@ int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint1
 
 /*
  * Quantisation of probabilities into an integer frequency table (paper §2
- * step 3; reading R10): for each of `rows` rows of A probabilities,
+ * step 3; the paper does not say how P becomes integers): for each of `rows` rows of A probabilities,
  * freq_j = 1 + floor(P_j*(2^24 - A)) (FP32 product), the remainder added to
  * the first maximal entry.  d_P: rows x A FP32; d_freq: rows x A uint32.
  */
@@ -194,7 +194,8 @@ int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32
                        uint32_t use_static, float *d_P, uint32_t *d_freq, void *stream);
 
 /*
- * Range coding of independent streams (paper §2 step 3, reading R11).
+ * Range coding of independent streams (paper §2 step 3; the paper leaves its entropy encoder unspecified:
+ * a byte-oriented range coder with a 56-bit window, carries through a cache byte).
  * Stream i codes L symbols d_sym[i*L + j] with frequency tables
  * d_freq[(i*L + j)*A .. +A) (each summing to 2^24).  Output bytes of stream i
  * go to d_out[i*cap ...], their count to d_len[i]; cap >= 3*L + 8 always

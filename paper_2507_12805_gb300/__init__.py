@@ -341,7 +341,7 @@ def pmklc_train_model(seq, cfg: ModelConfig, epochs: int = 1, stream=None) -> np
 
 
 def pmklc_init_model(k: int, E: int, t: int, H: int, seed: int) -> np.ndarray:
-    """Seeded initial parameters of an MLP predictor in the library's layout (reading R8)."""
+    """Seeded initial parameters of an MLP predictor in the library's layout (counter-based splitmix64 draws)."""
     n = model_count(k, E, t, H)
     out = np.zeros(n, dtype=np.float32)
     _check(lib.pmklc_init_model(k, E, t, H, seed, out.ctypes.data_as(_vp)), "pmklc_init_model")

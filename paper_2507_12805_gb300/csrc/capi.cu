@@ -63,7 +63,7 @@ uint64_t sm64_draw(uint64_t seed, uint64_t i) {  // splitmix64 output i of the s
   return z ^ (z >> 31);
 }
 
-// Seeded initial parameters (reading R8): w = (2u - 2^24) 2^-24, value = w * bound (float32 RN).
+// Seeded initial parameters (counter-based splitmix64): w = (2u - 2^24) 2^-24, value = w * bound (float32 RN).
 void init_params(const Dims &d, uint64_t seed, std::vector<float> &out) {
   out.assign(d.count(), 0.f);
   auto fill = [&](size_t lo, size_t hi, float bound) {

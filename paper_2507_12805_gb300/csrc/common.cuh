@@ -8,7 +8,7 @@
 
 namespace pmklc {
 
-constexpr int kTotalBits = 24;             // frequency tables sum to 2^24 (reading R10)
+constexpr int kTotalBits = 24;             // frequency tables sum to 2^24 (the quantiser's total)
 constexpr uint32_t kTotal = 1u << kTotalBits;
 
 // K-slices of the BF16 hidden-layer GEMM (split-K; the slices are summed in a fixed order)
@@ -31,7 +31,7 @@ struct Dims {
   __host__ __device__ size_t count() const { return off_b2() + A; }
 };
 
-// Per-lane range-coder states (reading R11).
+// Per-lane range-coder states (byte-oriented range coder, 56-bit window).
 struct EncState {
   unsigned long long low, range;
   uint32_t cache, pending, pos, has_cache;

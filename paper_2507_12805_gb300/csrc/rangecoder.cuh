@@ -1,5 +1,5 @@
 // Byte-oriented range coder (the paper's unspecified entropy encoder, §2 step 3;
-// reading R11: G. N. N. Martin's range encoding with a 56-bit window, carry
+// the reading used: G. N. N. Martin's range encoding with a 56-bit window, carry
 // propagation through a cache byte and a count of pending 0xFF bytes).
 // One coder state per lane; each call is made by one thread.
 #pragma once
