@@ -253,6 +253,17 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
 int pmklc_quantize_static_fp8(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H,
                               uint8_t *d_codes, float *d_scales, void *stream);
 
+/*
+ * Failure-detection self-test (the paper has no counterpart: a library service).
+ * Every wait of the library's kernels is bounded: on expiry the kernel sets an
+ * error bit, lets its copies land, frees its tensor memory and returns, and the
+ * call returns PMKLC_ETIMEOUT with the CUDA context intact.  This runs that path
+ * on its own: one thread polls, at most `polls` times, an mbarrier that expects
+ * an arrival which never comes.  Returns PMKLC_ETIMEOUT (the expected outcome),
+ * EINVAL for polls = 0 or above 2^30, ECUDA on a CUDA error.
+ */
+int pmklc_wait_selftest(uint64_t polls, void *stream);
+
 /* CRC-32 (IEEE 802.3, reflected, as zlib) of n device bytes. */
 int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
 

@@ -79,6 +79,7 @@ _sigs = {
     "pmklc_train_step": ([_cfgp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
                           _vp], _i),
     "pmklc_quantize_static_fp8": ([_vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp], _i),
+    "pmklc_wait_selftest": ([_u64, _vp], _i),
     "pmklc_crc32": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_crc32_noalloc": ([_vp, _sz, ctypes.POINTER(_u32), _vp], _i),
     "pmklc_last_stats": ([ctypes.POINTER(CStats)], _i),
@@ -273,6 +274,11 @@ def pmklc_quantize_static_fp8(d_params, k: int, E: int, t: int, H: int, d_codes,
     """FP8 (E4M3) codes [Emb | W1t | W2 transposed] and scales [s_emb | s_w1 | s_w2] of a frozen model."""
     _check(lib.pmklc_quantize_static_fp8(_ptr(d_params), k, E, t, H, _ptr(d_codes), _ptr(d_scales),
                                          _stream(stream)), "pmklc_quantize_static_fp8")
+
+
+def pmklc_wait_selftest(polls: int, stream=None) -> int:
+    """Return code of the bounded-wait self-test (PMKLC_ETIMEOUT when the wait gave up)."""
+    return lib.pmklc_wait_selftest(polls, _stream(stream))
 
 
 def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:

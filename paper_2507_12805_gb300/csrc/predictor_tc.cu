@@ -1039,6 +1039,21 @@ bool tc_supported(const Plan &p) {
   return get_setup(p, S);
 }
 
+namespace {
+// The bounded-wait path of every kernel here, on its own: one thread waits, at most `polls` polls,
+// on an mbarrier that expects one arrival which never comes, gives up and reports kErrTimeout in
+// the error word, exactly as a GEMM whose copies never land would.
+__global__ void wait_selftest_kernel(long polls, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::sa(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(tc::sa(&bar), 0, polls)) atomicOr(err, kErrTimeout);
+}
+}  // namespace
+
 void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which) {
   TcSetup S;
   if (!get_setup(p, S)) return;
@@ -1139,3 +1154,19 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
 }
 
 }  // namespace pmklc
+
+extern "C" int pmklc_wait_selftest(uint64_t polls, void *stream) {
+  using namespace pmklc;
+  if (polls == 0 || polls > (1ull << 30)) return PMKLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d_err = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_err, sizeof(int), st));
+  cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  wait_selftest_kernel<<<1, 32, 0, st>>>((long)polls, d_err);
+  int h = 0;
+  cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_err, st);
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  return (h & kErrTimeout) ? PMKLC_ETIMEOUT : PMKLC_OK;
+}

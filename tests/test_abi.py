@@ -64,3 +64,10 @@ def test_bad_config_rejected_before_any_device_work(P):
     with pytest.raises(P.PmklcError) as e:
         P.pmklc_decompress(b"XMKL" + bytes(100))
     assert e.value.rc == P.PMKLC_ECORRUPT
+
+
+def test_wait_selftest_rejects_bad_poll_counts():
+    """Argument checks come before any CUDA call (no GPU needed)."""
+    import paper_2507_12805_gb300 as P
+    assert P.pmklc_wait_selftest(0) == P.PMKLC_EINVAL
+    assert P.pmklc_wait_selftest((1 << 30) + 1) == P.PMKLC_EINVAL
