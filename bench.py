@@ -10,7 +10,12 @@ region starts; `e2e` is the same metric through the host-buffer C-ABI calls
 
 Default workload ("plain"): 2^24 bases from a seeded order-5 Markov source
 (GC 0.40), 64 blocks of 2^18, (s,k) = (2,4), static + dynamic MLP predictors
-(E 32, t 32, H 128), FP32, tree step-wise model passing.
+(E 32, t 32, H 128), tree step-wise model passing, count-model judge.  Both
+forms run: the FP32 plain form (64 lanes per block) and the BF16 batched form
+(lanes per block autotuned on 8 blocks), which is the headline `value`; the
+FP32 figures are reported under `fp32_plain`.  Every step is preceded by a
+256 MB write that flushes the 129 MB L2.  `--block-bases` cuts every block
+(the same per-step shapes, fewer steps) for profiling runs.
 """
 from __future__ import annotations
 
