@@ -342,9 +342,13 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        import paper_2507_12805_gb300 as P
+        # the oracle alone: its own initialiser draws the frozen static weights (the same splitmix64
+        # values the library's pmklc_init_model returns), so no library code runs on this arm
+        from oracle.model import Shape, init_params
         w, kw = load_workload(args.workload, args.block_bases)
-        sw = static_weights(P, kw)
+        sw = None
+        if kw.get("use_static"):
+            sw = init_params(Shape(4 ** kw["k"], kw["emb_s"], kw["ctx_s"], kw["hid_s"]), STATIC_SEED)
         print(json.dumps(run_reference(args, w, kw, sw)))
         return
 

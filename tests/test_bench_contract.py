@@ -63,3 +63,21 @@ def test_profiling_case_keeps_blocks_and_cuts_them():
 
 def test_job_throughput_is_whole_job():
     assert bench.job_throughput(4, 1 << 24, 1000.0) == pytest.approx(4 * (1 << 24) / 1e6)
+
+
+def test_reference_arm_runs_the_oracle_alone(monkeypatch, capsys):
+    """--impl reference times the oracle on the host cores and loads nothing of the library."""
+    import json
+    import sys
+    monkeypatch.delitem(sys.modules, "paper_2507_12805_gb300", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                                      "--block-bases", "2048"])
+    bench.main()
+    assert "paper_2507_12805_gb300" not in sys.modules
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "MB/s"
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "MB/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "1024 bases" in line["cpu_baseline"]["sample"]
