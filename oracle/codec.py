@@ -185,14 +185,19 @@ def unpack_tail(buf: bytes, n: int):
     return np.array([(buf[i >> 2] >> (2 * (i & 3))) & 3 for i in range(n)], dtype=np.uint8)
 
 
+def fnv1a64(data: bytes) -> int:
+    """FNV-1a, 64-bit (Fowler, Noll, Vo): offset basis, then per byte xor and multiply by the prime."""
+    h = 0xCBF29CE484222325
+    for b in data:
+        h = ((h ^ b) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
 def static_hash(weights) -> int:
     """FNV-1a 64 over the little-endian float32 bytes (0 when there is no static model)."""
     if weights is None:
         return 0
-    h = 0xCBF29CE484222325
-    for b in np.asarray(weights, dtype="<f4").tobytes():
-        h = ((h ^ b) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
-    return h
+    return fnv1a64(np.asarray(weights, dtype="<f4").tobytes())
 
 
 def tail_len(n: int, s: int, k: int) -> int:
