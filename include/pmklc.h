@@ -147,7 +147,12 @@ int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_l
                          size_t sample_blocks, pmklc_model_cfg *cfg, const uint32_t *candidates,
                          size_t n_candidates, float max_rel_size, void *stream, uint64_t *sizes, float *ms);
 
-/* Upper bound of the container size of pmklc_compress_dev for this input. */
+/*
+ * Upper bound of the container size of pmklc_compress_dev for this input (0 for an invalid
+ * configuration).  Per lane: at most 3 bytes per token + 8 for the network's stream (24-bit
+ * totals); with fallback 2 (count model only) at most 2 bytes per base + 8 (count totals stay
+ * below 2^13).  No input, however adversarial, makes a valid compression exceed it.
+ */
 size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg);
 
 /*

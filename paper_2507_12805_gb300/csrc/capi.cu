@@ -599,7 +599,13 @@ size_t bound_of(const std::vector<unsigned long long> &lens, const Cfg &c) {
   for (unsigned long long n : lens) {
     long long l = n_tokens_of((long long)n, c.s, c.k);
     long long Mb = lanes_of(l, c.lanes, c.lane_tokens);
-    b += 10 + 1 + 2 + (size_t)Mb * 10 + (size_t)l * 3 + (size_t)Mb * 8;
+    // a lane's stream: the network's at most 3 bytes per token + 8 (24-bit totals); the count
+    // model's at most 2 bytes per base + 8 (totals below 2^13), which only the count-only form
+    // (fallback 2) stores unconditionally; the judge keeps it only when it is the smaller
+    size_t stream = (size_t)l * 3 + (size_t)Mb * 8;
+    if (c.fallback == 2)
+      stream = 2 * ((size_t)c.k * Mb + (size_t)c.s * (size_t)(l - Mb)) + (size_t)Mb * 8;
+    b += 10 + 1 + 2 + (size_t)Mb * 10 + stream;
   }
   return b;
 }

@@ -1,8 +1,11 @@
 """Host-side checks of the C ABI that run before any CUDA call (no GPU): malformed container
-headers are rejected with PMKLC_ECORRUPT, invalid configurations with PMKLC_EINVAL.  The
-containers are written by the oracle (the same format), then damaged field by field."""
+headers are rejected with PMKLC_ECORRUPT, invalid configurations with PMKLC_EINVAL, and the
+container size bound (pmklc_compress_bound, the capacity every compression allocates) covers the
+costliest inputs.  The containers are written by the oracle (the same format), then damaged field
+by field."""
 import struct
 
+import numpy as np
 import pytest
 
 from oracle import codec as ocodec
@@ -70,3 +73,58 @@ def test_invalid_configurations_are_rejected(P, change):
     seq = b"ACGT" * 64
     assert _rc(P, lambda: P.pmklc_compress(seq, [len(seq)], cfg)) == P.PMKLC_EINVAL
 
+
+
+def _de_bruijn(n: int) -> np.ndarray:
+    """A de Bruijn sequence of order n over the four bases (the Fredricksen-Kessler-Maiorana
+    construction: the Lyndon words whose length divides n, in lexicographic order)."""
+    a = [0] * (n + 1)
+    out = []
+
+    def gen(t, p):
+        if t > n:
+            if n % p == 0:
+                out.extend(a[1:p + 1])
+        else:
+            a[t] = a[t - p]
+            gen(t + 1, p)
+            for j in range(a[t - p] + 1, 4):
+                a[t] = j
+                gen(t + 1, t)
+
+    gen(1, 1)
+    return np.array(out, np.uint8)
+
+
+def test_de_bruijn_helper_visits_every_window_once():
+    for n in (1, 2, 3, 5):
+        d = _de_bruijn(n)
+        assert d.size == 4 ** n
+        wins = {tuple(np.roll(d, -i)[:n]) for i in range(d.size)}
+        assert len(wins) == 4 ** n
+
+
+@pytest.mark.parametrize("s,k,M,m,fallback", [
+    (8, 8, 4, 5, 2), (4, 4, 64, 4, 2), (2, 2, 32, 3, 2), (1, 1, 64, 2, 2),
+    (4, 4, 8, 4, 1), (4, 4, 8, 4, 0),
+])
+def test_compress_bound_holds_for_adversarial_lanes(P, s, k, M, m, fallback):
+    """M identical lanes, each an order-(m+1) de Bruijn sequence, against the order-m count
+    model: every context is met four times, each time with a base it has not seen, while all
+    lanes read one table -- the count model's costliest input.  The container the oracle writes
+    (integer coding, the same bytes as the library's) fits the library's size bound."""
+    lane = _de_bruijn(m + 1)
+    seq = bytes(b"ACGT"[x] for x in lane) * M
+    kw = dict(s=s, k=k, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=M, count_order=m, fallback=fallback)
+    out = ocodec.compress(seq, [len(seq)], ocodec.Config(**kw))
+    assert len(out) <= P.pmklc_compress_bound(len(seq), [len(seq)], P.ModelConfig(**kw))
+
+
+@pytest.mark.parametrize("fallback", [0, 1, 2])
+def test_compress_bound_holds_for_random_ragged_blocks(P, fallback):
+    rng = np.random.default_rng(11 + fallback)
+    lens = [0, 3, 5, 1000, 2047]
+    seq = bytes(b"ACGT"[x] for x in rng.integers(0, 4, sum(lens)))
+    kw = dict(s=2, k=4, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=3, count_order=4, fallback=fallback)
+    out = ocodec.compress(seq, lens, ocodec.Config(**kw))
+    assert len(out) <= P.pmklc_compress_bound(len(seq), lens, P.ModelConfig(**kw))

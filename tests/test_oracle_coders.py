@@ -145,3 +145,25 @@ def test_count_model_halving():
         t.finish_substep([0, 1, 2], [0, 0, 0])
         t.ctx = [0, 0, 0]
     assert t.c[0].max() < countmodel.LIMIT and t.c[0, 0] > 0
+
+
+def test_count_model_totals_stay_below_2_13_with_1024_lanes():
+    """With up to 1024 lanes adding to one context in a sub-step, every count read is below the
+    halving limit (1024), so a total is at most 2 * 4 * 1023 + 4 = 8188 < 2^13 and no base costs
+    more than 13 bits: the 2-bytes-per-base capacity of a count-model stream."""
+    rng = np.random.default_rng(3)
+    M = 1024
+    t = countmodel.Table(1, M)
+    lanes = list(range(M))
+    worst = 0
+    for step in range(300):
+        # all lanes in one of two contexts; skewed bases so one count races ahead of the others
+        t.ctx = [int(step % 2)] * M
+        bases = np.where(rng.random(M) < 0.9, step % 4, rng.integers(0, 4, M))
+        for r in lanes:
+            f, tot = t.freqs(r)
+            assert t.c[t.ctx[r]].max() < countmodel.LIMIT
+            worst = max(worst, tot)
+            assert -math.log2(f.min() / tot) < 13
+        t.finish_substep(lanes, bases.tolist())
+    assert 2 * 4 * (countmodel.LIMIT - 1) + 4 >= worst > 4 * countmodel.LIMIT  # reached the high range
