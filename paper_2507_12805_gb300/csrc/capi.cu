@@ -815,10 +815,13 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   int A = 1 << (2 * c.k);
   c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
   c.st = Dims{A, get_le<uint16_t>(h + 18), get_le<uint16_t>(h + 20), get_le<uint16_t>(h + 22)};
-  if (c.dm.E < 1 || c.dm.t < 1 || c.dm.H < 1) return PMKLC_ECORRUPT;
-  if (c.use_static && (c.st.E < 1 || c.st.t < 1 || c.st.H < 1)) return PMKLC_ECORRUPT;
+  // the limits compression accepts (check_cfg): a header beyond them was not written by it, and
+  // widths above 4096 would overflow the 32-bit row width t x E
+  if (c.dm.E < 1 || c.dm.t < 1 || c.dm.H < 1 || c.dm.E > 4096 || c.dm.t > 4096) return PMKLC_ECORRUPT;
+  if (c.use_static && (c.st.E < 1 || c.st.t < 1 || c.st.H < 1 || c.st.E > 4096 || c.st.t > 4096))
+    return PMKLC_ECORRUPT;
   c.lanes = (int)get_le<uint32_t>(h + 24);
-  if (c.lanes < 1) return PMKLC_ECORRUPT;
+  if (c.lanes < 1 || c.lanes > (1 << 20)) return PMKLC_ECORRUPT;
   c.lr = get_le<float>(h + 28);
   c.alpha0 = get_le<float>(h + 32);
   c.smp_f = get_le<float>(h + 36);
@@ -829,13 +832,18 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   P.crc = get_le<uint32_t>(h + 68);
   c.lane_tokens = (int)get_le<uint32_t>(h + 76);
   if (c.lane_tokens < 0) return PMKLC_ECORRUPT;
-  if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !isfinite(c.lr)) return PMKLC_ECORRUPT;
+  if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !(c.lr > 0.f) || !isfinite(c.lr) || !isfinite(c.alpha0))
+    return PMKLC_ECORRUPT;
+  if (P.n > (1ull << 56)) return PMKLC_ECORRUPT;  // keeps every length sum below 2^63
   return PMKLC_OK;
 }
 
 int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
   const Cfg &c = P.c;
   size_t pos = kHeader;
+  // a block record takes at least two bytes (its length and its mode): a count the input cannot
+  // hold is corrupt, and is refused before any per-block allocation
+  if (in_len < kHeader || P.n_blocks > (in_len - kHeader) / 2) return PMKLC_ECORRUPT;
   P.lens.resize(P.n_blocks);
   P.mode.resize(P.n_blocks);
   P.tails.assign((size_t)P.n_blocks * 8, 0);
@@ -843,7 +851,7 @@ int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
   unsigned long long sum = 0, pay = 0;
   for (uint32_t b = 0; b < P.n_blocks; ++b) {
     uint64_t nb;
-    if (!get_varint(h, len, pos, nb)) return PMKLC_ECORRUPT;
+    if (!get_varint(h, len, pos, nb) || nb > P.n - sum) return PMKLC_ECORRUPT;
     P.lens[b] = nb;
     sum += nb;
     if (pos >= len) return PMKLC_ECORRUPT;
@@ -882,8 +890,10 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
   int rc = parse_fixed(h.data(), kHeader, P);
   if (rc) return rc;
-  size_t rec_bound = kHeader + (size_t)P.n_blocks * 23 + (size_t)P.n_blocks * (size_t)P.c.lanes * 10;
-  size_t hl = std::min(rec_bound, in_len);
+  // the block records end within n_blocks x (23 + 10 x lanes) bytes of the fixed header
+  const size_t per_block = 23 + 10 * (size_t)P.c.lanes;
+  size_t hl = in_len;
+  if (P.n_blocks <= (in_len - kHeader) / per_block) hl = std::min(in_len, kHeader + P.n_blocks * per_block);
   h.resize(hl);
   PMKLC_CUDA_TRY(cudaMemcpyAsync(h.data(), d_in, hl, cudaMemcpyDeviceToHost, st));
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1141,6 +1151,7 @@ int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weigh
   cudaStream_t st = (cudaStream_t)stream;
   Parsed P;
   int rc = parse_fixed(in, in_len, P);
+  if (!rc) rc = parse_records(in, in_len, in_len, P);  // the whole container is on the host
   if (rc) return rc;
   uint8_t *d_in = nullptr, *d_seq = nullptr;
   PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_in, in_len, st));

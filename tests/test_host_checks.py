@@ -50,12 +50,45 @@ def _patched(data: bytes, offset: int, fmt: str, value) -> bytes:
     (24, "<I", 0),         # lanes per block
     (36, "<f", 1.5),       # SMP fraction above 1
     (28, "<f", float("inf")),  # learning rate
+    (28, "<f", -1e-3),     # learning rate not positive
+    (32, "<f", float("nan")),  # alpha_0
+    (12, "<H", 4097),      # embedding width above the configuration limit
+    (14, "<H", 65535),     # context width: t x E would overflow 32 bits
+    (24, "<I", (1 << 20) + 1),  # lanes per block above the limit
+    (56, "<Q", 1 << 57),   # n beyond any real input
+    (56, "<Q", 299),       # n differs from the block lengths' sum
+    (64, "<I", 0xFFFFFFFF),  # block count the input cannot hold
+    (64, "<I", 2),         # block count: the records run out
+    (80, "<H", 0x7FFF),    # first block length 16383 (varint FF 7F), above n
 ])
 def test_damaged_header_fields_are_corrupt(P, container, offset, fmt, value):
     bad = _patched(container, offset, fmt, value)
     if offset == 6:
         bad = _patched(bad, 5, "<B", 1)
     assert _rc(P, lambda: P.pmklc_decompress(bad)) == P.PMKLC_ECORRUPT
+
+
+def test_damaged_containers_never_crash_the_host_parser(P, container):
+    """Random damage to the header and block records: the host parser answers ECORRUPT or lets
+    the container through to the device stage (ECUDA without a GPU), and never aborts."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-parser fuzzing only: with a GPU, damaged payloads would be decoded")
+    rng = np.random.default_rng(5)
+    seen = set()
+    for it in range(3000):
+        c = bytearray(container)
+        for _ in range(int(rng.integers(1, 4))):
+            c[int(rng.integers(0, min(100, len(c))))] ^= int(rng.integers(1, 256))
+        if it % 3 == 0:
+            c = c[: int(rng.integers(0, len(c) + 1))]
+        try:
+            P.pmklc_decompress(bytes(c))
+            rc = 0
+        except P.PmklcError as e:
+            rc = e.rc
+        seen.add(rc)
+    assert seen <= {P.PMKLC_ECORRUPT, P.PMKLC_ECUDA} and P.PMKLC_ECORRUPT in seen
 
 
 @pytest.mark.parametrize("cut", [0, 1, 40, 79])
