@@ -119,7 +119,9 @@ void pmklc_default_cfg(pmklc_model_cfg *cfg, uint32_t s, uint32_t k, uint32_t em
  * (format: an 80-byte header, per-block records, then the lane payloads).  The static weights are not stored, only their
  * hash (§4.2.2: the public static model is part of the compressor).
  * Output: *out (library-allocated, pmklc_free) of *out_len bytes.
- * Errors: EINVAL (bad cfg, non-ACGT byte, block lengths), ENOMEM, ECUDA.
+ * At most 32,767 blocks per call (each block is a model group, and both models' groups share
+ * one grid dimension of the GEMM launches).
+ * Errors: EINVAL (bad cfg, non-ACGT byte, block lengths, more than 32,767 blocks), ENOMEM, ECUDA.
  */
 int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
                    const pmklc_model_cfg *cfg, void *stream, uint8_t **out, size_t *out_len);
@@ -149,7 +151,7 @@ int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_l
 
 /*
  * Upper bound of the container size of pmklc_compress_dev for this input (0 for an invalid
- * configuration).  Per lane: at most 3 bytes per token + 8 for the network's stream (24-bit
+ * configuration or more than 32,767 blocks).  Per lane: at most 3 bytes per token + 8 for the network's stream (24-bit
  * totals); with fallback 2 (count model only) at most 2 bytes per base + 8 (count totals stay
  * below 2^13).  No input, however adversarial, makes a valid compression exceed it.
  */
@@ -234,6 +236,7 @@ int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uin
  *   d_target: G*M tokens.  d_static: the static parameters (if use_static).
  *   d_P (optional, G*M x A) receives the mixed probabilities before the
  *   update; d_grad (optional, G x P) the gradient; d_dalpha (optional, G).
+ * 1 <= G <= 32,767 (the limit of pmklc_compress's blocks), else EINVAL.
  */
 int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *d_params, float *d_m,
                      float *d_v, float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static,

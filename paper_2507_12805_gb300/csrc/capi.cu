@@ -135,6 +135,9 @@ T get_le(const uint8_t *p) {
 
 constexpr size_t kHeader = 80;
 constexpr uint8_t kVersion = 1;
+// Each block is one model group; the GEMMs run the groups of both models (static and dynamic)
+// along the grid's z dimension and the per-group kernels along y, both limited to 65,535.
+constexpr uint32_t kMaxGroups = 32767;
 
 // ---------------------------------------------------------------- configuration
 
@@ -620,7 +623,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   if (rc) return rc;
   const Cfg &c = R.c;
   if ((n && !d_seq) || (n_blocks && !block_lens) || !out_len || !d_out) return PMKLC_EINVAL;
-  if (n_blocks > (1u << 24)) return PMKLC_EINVAL;
+  if (n_blocks > kMaxGroups) return PMKLC_EINVAL;
   std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
   unsigned long long sum = 0;
   for (auto x : lens) sum += x;
@@ -829,6 +832,7 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   P.shash = get_le<uint64_t>(h + 48);
   P.n = get_le<uint64_t>(h + 56);
   P.n_blocks = get_le<uint32_t>(h + 64);
+  if (P.n_blocks > kMaxGroups) return PMKLC_ECORRUPT;
   P.crc = get_le<uint32_t>(h + 68);
   c.lane_tokens = (int)get_le<uint32_t>(h + 76);
   if (c.lane_tokens < 0) return PMKLC_ECORRUPT;
@@ -1035,7 +1039,7 @@ void pmklc_default_cfg(pmklc_model_cfg *c, uint32_t s, uint32_t k, uint32_t emb,
 
 size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg) {
   Cfg c;
-  if (check_cfg(cfg, c) || (n_blocks && !block_lens)) return 0;
+  if (check_cfg(cfg, c) || (n_blocks && !block_lens) || n_blocks > kMaxGroups) return 0;
   std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
   (void)n;
   return bound_of(lens, c);
@@ -1444,7 +1448,7 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
   if (tmp.use_static && !tmp.static_weights) tmp.static_weights = (const float *)d_static;  // only checked non-null
   int rc = check_cfg(&tmp, c);
   if (rc) return rc;
-  if (!G || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||
+  if (!G || G > kMaxGroups || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||
       !d_target || (c.use_static && !d_static))
     return PMKLC_EINVAL;
   return one_step(c, G, M, d_params, d_m, d_v, d_alpha, d_alpha_m, d_alpha_v, d_static, d_ctx, d_target, tau, d_P,

@@ -59,6 +59,7 @@ def _patched(data: bytes, offset: int, fmt: str, value) -> bytes:
     (56, "<Q", 299),       # n differs from the block lengths' sum
     (64, "<I", 0xFFFFFFFF),  # block count the input cannot hold
     (64, "<I", 2),         # block count: the records run out
+    (64, "<I", 32768),     # more blocks (model groups) than one launch grid dimension holds
     (80, "<H", 0x7FFF),    # first block length 16383 (varint FF 7F), above n
 ])
 def test_damaged_header_fields_are_corrupt(P, container, offset, fmt, value):
@@ -161,3 +162,12 @@ def test_compress_bound_holds_for_random_ragged_blocks(P, fallback):
     kw = dict(s=2, k=4, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=3, count_order=4, fallback=fallback)
     out = ocodec.compress(seq, lens, ocodec.Config(**kw))
     assert len(out) <= P.pmklc_compress_bound(len(seq), lens, P.ModelConfig(**kw))
+
+
+def test_block_count_limit(P):
+    """Each block is a model group and both models' groups share one grid dimension of the GEMM
+    launches (at most 65,535): more than 32,767 blocks are refused before any device work."""
+    cfg = P.ModelConfig(s=2, k=4, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=2)
+    assert P.pmklc_compress_bound(0, [0] * 32768, cfg) == 0
+    assert P.pmklc_compress_bound(0, [0] * 32767, cfg) > 0
+    assert _rc(P, lambda: P.pmklc_compress(b"", [0] * 32768, cfg)) == P.PMKLC_EINVAL
