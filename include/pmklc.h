@@ -85,7 +85,8 @@ int pmklc_abi_version(void);
 const char *pmklc_strerror(int rc);
 void pmklc_free(void *p);
 
-/* Number of FP32 parameters of an MLP predictor with alphabet 4^k. */
+/* Number of FP32 parameters of an MLP predictor with alphabet 4^k (0 outside the accepted
+ * widths: 1 <= k <= 8, 1 <= emb, ctx <= 4096, 1 <= hid <= 65535). */
 size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid);
 
 /*

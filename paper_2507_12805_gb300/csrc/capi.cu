@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <new>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -204,6 +206,38 @@ long long lanes_of(long long l, int M, int lane_tokens) {
   long long m = std::min<long long>(M, l);
   if (lane_tokens > 0) m = std::min(m, std::max(1LL, (l + lane_tokens - 1) / lane_tokens));
   return m;
+}
+
+// Limits of one call's layout, checked on the host before anything is allocated: at most 2^24
+// lanes in all (grids count lanes x 32 threads in 32 bits), lanes x hidden width below 2^31 (the
+// BF16 hidden reduction walks rows x H with a 32-bit index), at most 2^27 tokens per lane (a lane's
+// byte capacities are 32-bit: 3 per token for the network, 2 per base for the count model) and at
+// most 2^30 steps in the schedule (placed as make_schedule places the groups).
+constexpr long long kMaxLanes = 1LL << 24, kMaxLaneTokens = 1LL << 27, kMaxSteps = 1LL << 30;
+
+bool layout_fits(const std::vector<unsigned long long> &lens, const Cfg &c, int smp_mode, float f32) {
+  if (lens.size() > kMaxGroups) return false;
+  const double f = (double)f32;
+  long long lanes = 0, mx = 0;
+  std::vector<long long> steps(lens.size(), 0);
+  for (size_t g = 0; g < lens.size(); ++g) {
+    if (lens[g] > (1ull << 56)) return false;
+    const long long l = n_tokens_of((long long)lens[g], c.s, c.k), Mb = lanes_of(l, c.lanes, c.lane_tokens);
+    if (Mb > 0) steps[g] = (l + Mb - 1) / Mb;
+    if (steps[g] > kMaxLaneTokens) return false;
+    lanes += Mb;
+    mx = std::max(mx, steps[g]);
+  }
+  const long long hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
+  if (lanes > kMaxLanes || lanes * hmax >= (1LL << 31)) return false;
+  long long T = 0, start = 0;
+  const long long D = (long long)ceil(f * (double)mx);
+  for (size_t g = 0; g < lens.size(); ++g) {
+    if (smp_mode == PMKLC_SMP_CHAIN && g > 0) start += (long long)ceil(f * (double)steps[g - 1]);
+    if (smp_mode == PMKLC_SMP_TREE) start = g ? (long long)(64 - __builtin_clzll((unsigned long long)g)) * D : 0;
+    T = std::max(T, start + steps[g]);
+  }
+  return T <= kMaxSteps;
 }
 
 void make_layout(const std::vector<unsigned long long> &lens, int s, int k, int M, int lane_tokens, Layout &L) {
@@ -627,7 +661,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
   unsigned long long sum = 0;
   for (auto x : lens) sum += x;
-  if (sum != n) return PMKLC_EINVAL;
+  if (sum != n || !layout_fits(lens, c, c.smp_mode, c.smp_f)) return PMKLC_EINVAL;
   if (out_cap < bound_of(lens, c)) return PMKLC_ENOSPC;
   make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
   make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
@@ -876,7 +910,7 @@ int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
       pay += x;
     }
   }
-  if (sum != P.n) return PMKLC_ECORRUPT;
+  if (sum != P.n || !layout_fits(P.lens, c, c.smp_mode, c.smp_f)) return PMKLC_ECORRUPT;
   P.header_len = pos;
   P.payload = pay;
   if (pos + pay != in_len) return PMKLC_ECORRUPT;
@@ -990,6 +1024,20 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
 
 using namespace pmklc;
 
+// Every C++ exception stops at the C boundary: a host allocation that fails (std::bad_alloc)
+// becomes ENOMEM, anything else EINVAL (size_t results: 0).  Work already queued on the stream
+// completes and the arena's stream-ordered frees follow it.
+template <class R, class F>
+R guarded(F &&f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc &) {
+    return std::is_same<R, size_t>::value ? (R)0 : (R)PMKLC_ENOMEM;
+  } catch (...) {
+    return std::is_same<R, size_t>::value ? (R)0 : (R)PMKLC_EINVAL;
+  }
+}
+
 extern "C" {
 
 int pmklc_abi_version(void) { return PMKLC_ABI_VERSION; }
@@ -1010,8 +1058,13 @@ const char *pmklc_strerror(int rc) {
 
 void pmklc_free(void *p) { free(p); }
 
+// the widths a configuration accepts (check_cfg)
+static bool widths_ok(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid) {
+  return k >= 1 && k <= 8 && emb >= 1 && emb <= 4096 && ctx >= 1 && ctx <= 4096 && hid >= 1 && hid <= 65535;
+}
+
 size_t pmklc_model_count(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid) {
-  if (k < 1 || k > 8) return 0;
+  if (!widths_ok(k, emb, ctx, hid)) return 0;
   Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
   return d.count();
 }
@@ -1038,222 +1091,240 @@ void pmklc_default_cfg(pmklc_model_cfg *c, uint32_t s, uint32_t k, uint32_t emb,
 }
 
 size_t pmklc_compress_bound(size_t n, const uint64_t *block_lens, size_t n_blocks, const pmklc_model_cfg *cfg) {
-  Cfg c;
-  if (check_cfg(cfg, c) || (n_blocks && !block_lens) || n_blocks > kMaxGroups) return 0;
-  std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
-  (void)n;
-  return bound_of(lens, c);
+  return guarded<size_t>([&]() -> size_t {
+    Cfg c;
+    if (check_cfg(cfg, c) || (n_blocks && !block_lens) || n_blocks > kMaxGroups) return 0;
+    std::vector<unsigned long long> lens(block_lens, block_lens + n_blocks);
+    (void)n;
+    if (!layout_fits(lens, c, c.smp_mode, c.smp_f)) return 0;
+    return bound_of(lens, c);
+  });
 }
 
 int pmklc_compress_dev(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
                        const pmklc_model_cfg *cfg, void *stream, uint8_t *d_out, size_t out_cap, size_t *out_len) {
-  return compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, (cudaStream_t)stream, d_out, out_cap, out_len);
+  return guarded<int>([&]() -> int {
+    return compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, (cudaStream_t)stream, d_out, out_cap, out_len);
+  });
 }
 
 int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
                          size_t sample_blocks, pmklc_model_cfg *cfg, const uint32_t *candidates, size_t n_candidates,
                          float max_rel_size, void *stream, uint64_t *sizes, float *ms) {
-  if (!cfg || !candidates || n_candidates == 0 || (n_blocks && !block_lens) || !(max_rel_size >= 0.f))
-    return PMKLC_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  size_t nb = std::min(n_blocks, std::max<size_t>(sample_blocks, 1));
-  size_t ns = 0;
-  for (size_t b = 0; b < nb; ++b) ns += block_lens[b];
-  if (ns > n) return PMKLC_EINVAL;
-  pmklc_model_cfg trial = *cfg;
-  size_t cap = 0;
-  for (size_t i = 0; i < n_candidates; ++i) {
-    trial.lanes_per_block = candidates[i];
-    cap = std::max(cap, pmklc_compress_bound(ns, block_lens, nb, &trial));
-  }
-  if (cap == 0) return PMKLC_EINVAL;
-  uint8_t *d_out = nullptr;
-  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_out, cap, st));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  int rc = PMKLC_OK, best = -1;
-  std::vector<uint64_t> sz(n_candidates, 0);
-  std::vector<float> tm(n_candidates, 0.f);
-  for (size_t i = 0; i < n_candidates && rc == PMKLC_OK; ++i) {
-    trial.lanes_per_block = candidates[i];
-    size_t len = 0;
-    rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);  // warm-up
-    if (rc) break;
-    cudaEventRecord(e0, st);
-    rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&tm[i], e0, e1);
-    sz[i] = len;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFreeAsync(d_out, st);
-  cudaStreamSynchronize(st);
-  if (rc) return rc;
-  for (size_t i = 0; i < n_candidates; ++i) {
-    bool ok = (double)sz[i] <= (double)sz[0] * (1.0 + (double)max_rel_size);
-    if (ok && (best < 0 || tm[i] < tm[best])) best = (int)i;
-  }
-  cfg->lanes_per_block = candidates[best < 0 ? 0 : best];
-  for (size_t i = 0; i < n_candidates; ++i) {
-    if (sizes) sizes[i] = sz[i];
-    if (ms) ms[i] = tm[i];
-  }
-  return PMKLC_OK;
+  return guarded<int>([&]() -> int {
+    if (!cfg || !candidates || n_candidates == 0 || (n_blocks && !block_lens) || !(max_rel_size >= 0.f))
+      return PMKLC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t nb = std::min(n_blocks, std::max<size_t>(sample_blocks, 1));
+    size_t ns = 0;
+    for (size_t b = 0; b < nb; ++b) ns += block_lens[b];
+    if (ns > n) return PMKLC_EINVAL;
+    pmklc_model_cfg trial = *cfg;
+    size_t cap = 0;
+    for (size_t i = 0; i < n_candidates; ++i) {
+      trial.lanes_per_block = candidates[i];
+      cap = std::max(cap, pmklc_compress_bound(ns, block_lens, nb, &trial));
+    }
+    if (cap == 0) return PMKLC_EINVAL;
+    uint8_t *d_out = nullptr;
+    PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_out, cap, st));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = PMKLC_OK, best = -1;
+    std::vector<uint64_t> sz(n_candidates, 0);
+    std::vector<float> tm(n_candidates, 0.f);
+    for (size_t i = 0; i < n_candidates && rc == PMKLC_OK; ++i) {
+      trial.lanes_per_block = candidates[i];
+      size_t len = 0;
+      rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      rc = compress_dev_impl(d_seq, ns, block_lens, nb, &trial, st, d_out, cap, &len);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&tm[i], e0, e1);
+      sz[i] = len;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(d_out, st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    for (size_t i = 0; i < n_candidates; ++i) {
+      bool ok = (double)sz[i] <= (double)sz[0] * (1.0 + (double)max_rel_size);
+      if (ok && (best < 0 || tm[i] < tm[best])) best = (int)i;
+    }
+    cfg->lanes_per_block = candidates[best < 0 ? 0 : best];
+    for (size_t i = 0; i < n_candidates; ++i) {
+      if (sizes) sizes[i] = sz[i];
+      if (ms) ms[i] = tm[i];
+    }
+    return PMKLC_OK;
+  });
 }
 
 int pmklc_decompress_dev(const uint8_t *d_in, size_t in_len, const float *static_weights, size_t static_count,
                          void *stream, uint8_t *d_seq, size_t seq_cap, size_t *n) {
-  return decompress_dev_impl(d_in, in_len, static_weights, static_count, (cudaStream_t)stream, d_seq, seq_cap, n,
-                             nullptr);
+  return guarded<int>([&]() -> int {
+    return decompress_dev_impl(d_in, in_len, static_weights, static_count, (cudaStream_t)stream, d_seq, seq_cap, n,
+                               nullptr);
+  });
 }
 
 int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
                    const pmklc_model_cfg *cfg, void *stream, uint8_t **out, size_t *out_len) {
-  if (!out || !out_len || (n && !seq)) return PMKLC_EINVAL;
-  *out = nullptr;
-  *out_len = 0;
-  size_t cap = pmklc_compress_bound(n, block_lens, n_blocks, cfg);
-  if (cap == 0) return PMKLC_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  uint8_t *d_seq = nullptr, *d_out = nullptr;
-  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_seq, n ? n : 1, st));
-  if (cudaMallocAsync((void **)&d_out, cap, st) != cudaSuccess) {
+  return guarded<int>([&]() -> int {
+    if (!out || !out_len || (n && !seq)) return PMKLC_EINVAL;
+    *out = nullptr;
+    *out_len = 0;
+    size_t cap = pmklc_compress_bound(n, block_lens, n_blocks, cfg);
+    if (cap == 0) return PMKLC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *d_seq = nullptr, *d_out = nullptr;
+    PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_seq, n ? n : 1, st));
+    if (cudaMallocAsync((void **)&d_out, cap, st) != cudaSuccess) {
+      cudaFreeAsync(d_seq, st);
+      return PMKLC_ENOMEM;
+    }
+    if (n) cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
+    size_t len = 0;
+    int rc = compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, st, d_out, cap, &len);
+    uint8_t *h = nullptr;
+    if (rc == PMKLC_OK) {
+      h = (uint8_t *)malloc(len ? len : 1);
+      if (!h) rc = PMKLC_ENOMEM;
+      else if (cudaMemcpyAsync(h, d_out, len, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess)
+        rc = PMKLC_ECUDA;
+    }
     cudaFreeAsync(d_seq, st);
-    return PMKLC_ENOMEM;
-  }
-  if (n) cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
-  size_t len = 0;
-  int rc = compress_dev_impl(d_seq, n, block_lens, n_blocks, cfg, st, d_out, cap, &len);
-  uint8_t *h = nullptr;
-  if (rc == PMKLC_OK) {
-    h = (uint8_t *)malloc(len ? len : 1);
-    if (!h) rc = PMKLC_ENOMEM;
-    else if (cudaMemcpyAsync(h, d_out, len, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-             cudaStreamSynchronize(st) != cudaSuccess)
-      rc = PMKLC_ECUDA;
-  }
-  cudaFreeAsync(d_seq, st);
-  cudaFreeAsync(d_out, st);
-  if (rc) {
-    free(h);
-    return rc;
-  }
-  *out = h;
-  *out_len = len;
-  return PMKLC_OK;
+    cudaFreeAsync(d_out, st);
+    if (rc) {
+      free(h);
+      return rc;
+    }
+    *out = h;
+    *out_len = len;
+    return PMKLC_OK;
+  });
 }
 
 int pmklc_decompress(const uint8_t *in, size_t in_len, const float *static_weights, size_t static_count,
                      void *stream, uint8_t **seq, size_t *n, uint64_t **block_lens, size_t *n_blocks) {
-  if (!in || !seq || !n) return PMKLC_EINVAL;
-  *seq = nullptr;
-  *n = 0;
-  if (in_len < kHeader) return PMKLC_ECORRUPT;
-  cudaStream_t st = (cudaStream_t)stream;
-  Parsed P;
-  int rc = parse_fixed(in, in_len, P);
-  if (!rc) rc = parse_records(in, in_len, in_len, P);  // the whole container is on the host
-  if (rc) return rc;
-  uint8_t *d_in = nullptr, *d_seq = nullptr;
-  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_in, in_len, st));
-  if (cudaMallocAsync((void **)&d_seq, P.n ? P.n : 1, st) != cudaSuccess) {
-    cudaFreeAsync(d_in, st);
-    return PMKLC_ENOMEM;
-  }
-  cudaMemcpyAsync(d_in, in, in_len, cudaMemcpyHostToDevice, st);
-  size_t nn = 0;
-  std::vector<unsigned long long> lens;
-  rc = decompress_dev_impl(d_in, in_len, static_weights, static_count, st, d_seq, P.n, &nn, &lens);
-  uint8_t *h = nullptr;
-  if (rc == PMKLC_OK) {
-    h = (uint8_t *)malloc(nn ? nn : 1);
-    if (!h) rc = PMKLC_ENOMEM;
-    else if (cudaMemcpyAsync(h, d_seq, nn, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-             cudaStreamSynchronize(st) != cudaSuccess)
-      rc = PMKLC_ECUDA;
-  }
-  cudaFreeAsync(d_in, st);
-  cudaFreeAsync(d_seq, st);
-  if (rc) {
-    free(h);
-    return rc;
-  }
-  if (block_lens && n_blocks) {
-    uint64_t *bl = (uint64_t *)malloc(sizeof(uint64_t) * (lens.size() ? lens.size() : 1));
-    if (!bl) {
-      free(h);
+  return guarded<int>([&]() -> int {
+    if (!in || !seq || !n) return PMKLC_EINVAL;
+    *seq = nullptr;
+    *n = 0;
+    if (in_len < kHeader) return PMKLC_ECORRUPT;
+    cudaStream_t st = (cudaStream_t)stream;
+    Parsed P;
+    int rc = parse_fixed(in, in_len, P);
+    if (!rc) rc = parse_records(in, in_len, in_len, P);  // the whole container is on the host
+    if (rc) return rc;
+    uint8_t *d_in = nullptr, *d_seq = nullptr;
+    PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_in, in_len, st));
+    if (cudaMallocAsync((void **)&d_seq, P.n ? P.n : 1, st) != cudaSuccess) {
+      cudaFreeAsync(d_in, st);
       return PMKLC_ENOMEM;
     }
-    for (size_t i = 0; i < lens.size(); ++i) bl[i] = lens[i];
-    *block_lens = bl;
-    *n_blocks = lens.size();
-  }
-  *seq = h;
-  *n = nn;
-  return PMKLC_OK;
+    cudaMemcpyAsync(d_in, in, in_len, cudaMemcpyHostToDevice, st);
+    size_t nn = 0;
+    std::vector<unsigned long long> lens;
+    rc = decompress_dev_impl(d_in, in_len, static_weights, static_count, st, d_seq, P.n, &nn, &lens);
+    uint8_t *h = nullptr;
+    if (rc == PMKLC_OK) {
+      h = (uint8_t *)malloc(nn ? nn : 1);
+      if (!h) rc = PMKLC_ENOMEM;
+      else if (cudaMemcpyAsync(h, d_seq, nn, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess)
+        rc = PMKLC_ECUDA;
+    }
+    cudaFreeAsync(d_in, st);
+    cudaFreeAsync(d_seq, st);
+    if (rc) {
+      free(h);
+      return rc;
+    }
+    if (block_lens && n_blocks) {
+      uint64_t *bl = (uint64_t *)malloc(sizeof(uint64_t) * (lens.size() ? lens.size() : 1));
+      if (!bl) {
+        free(h);
+        return PMKLC_ENOMEM;
+      }
+      for (size_t i = 0; i < lens.size(); ++i) bl[i] = lens[i];
+      *block_lens = bl;
+      *n_blocks = lens.size();
+    }
+    *seq = h;
+    *n = nn;
+    return PMKLC_OK;
+  });
 }
 
 int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, uint32_t epochs, void *stream,
                       float *out) {
-  Cfg c;
-  int rc = check_cfg(cfg, c);
-  if (rc) return rc;
-  if (c.use_static || !out || (n && !seq) || epochs < 1) return PMKLC_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  Run R;
-  R.c = c;
-  // one group holding all training tokens; epochs are consecutive groups chained with f = 1
-  std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
-  make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
-  make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
-  Arena ar(st);
-  uint8_t *d_seq = ar.alloc<uint8_t>(n);
-  long long *d_base_off = ar.upload(R.L.base_off);
-  long long *d_tok_off = ar.upload(R.L.tok_off);
-  uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
-  if (ar.failed) return PMKLC_ENOMEM;
-  // every epoch reads the same bases: the blocks all start at offset 0
-  std::vector<long long> zero_off(R.L.G + 1, 0);
-  for (int g = 0; g <= R.L.G; ++g) zero_off[g] = (long long)n * std::min(g, 1);
-  long long *d_epoch_off = ar.upload(zero_off);
-  std::vector<long long> tok_one = {0, R.L.tok_off[1]};
-  long long *d_tok_one = ar.upload(tok_one);
-  std::vector<int> grp_mode(R.L.G, kReplay);
-  R.p.tokens = d_tokens;
-  R.p.lane_buf = nullptr;
-  std::vector<unsigned long long> zoff(std::max(R.L.NL, 1), 0);
-  std::vector<uint32_t> zcap(std::max(R.L.NL, 1), 0);
-  R.p.lane_buf_off = ar.upload(zoff);
-  R.p.lane_buf_cap = ar.upload(zcap);
-  if (ar.failed) return PMKLC_ENOMEM;
-  rc = setup_run(ar, R, grp_mode, nullptr);
-  if (rc) return rc;
-  cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
-  launch_validate(d_seq, n, R.p.err, st);
-  for (int g = 0; g < R.L.G; ++g)  // identical tokens for every epoch
-    launch_tokenize(d_seq, d_epoch_off, d_tok_one, 1, R.L.tok_off[1], c.s, c.k, d_tokens + R.L.tok_off[g], st);
-  (void)d_base_off;
-  (void)d_tok_off;
-  run_steps(R, grp_mode, st);
-  int h_err = 0;
-  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  int last = R.L.G - 1;
-  cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
-  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
-  PMKLC_CUDA_TRY(cudaGetLastError());
-  return h_err ? err_to_rc(h_err) : PMKLC_OK;
+  return guarded<int>([&]() -> int {
+    Cfg c;
+    int rc = check_cfg(cfg, c);
+    if (rc) return rc;
+    if (c.use_static || !out || (n && !seq) || epochs < 1 || epochs > kMaxGroups) return PMKLC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Run R;
+    R.c = c;
+    // one group holding all training tokens; epochs are consecutive groups chained with f = 1
+    std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
+    if (!layout_fits(lens, c, PMKLC_SMP_CHAIN, 1.0f)) return PMKLC_EINVAL;
+    make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
+    make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
+    Arena ar(st);
+    uint8_t *d_seq = ar.alloc<uint8_t>(n);
+    long long *d_base_off = ar.upload(R.L.base_off);
+    long long *d_tok_off = ar.upload(R.L.tok_off);
+    uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
+    if (ar.failed) return PMKLC_ENOMEM;
+    // every epoch reads the same bases: the blocks all start at offset 0
+    std::vector<long long> zero_off(R.L.G + 1, 0);
+    for (int g = 0; g <= R.L.G; ++g) zero_off[g] = (long long)n * std::min(g, 1);
+    long long *d_epoch_off = ar.upload(zero_off);
+    std::vector<long long> tok_one = {0, R.L.tok_off[1]};
+    long long *d_tok_one = ar.upload(tok_one);
+    std::vector<int> grp_mode(R.L.G, kReplay);
+    R.p.tokens = d_tokens;
+    R.p.lane_buf = nullptr;
+    std::vector<unsigned long long> zoff(std::max(R.L.NL, 1), 0);
+    std::vector<uint32_t> zcap(std::max(R.L.NL, 1), 0);
+    R.p.lane_buf_off = ar.upload(zoff);
+    R.p.lane_buf_cap = ar.upload(zcap);
+    if (ar.failed) return PMKLC_ENOMEM;
+    rc = setup_run(ar, R, grp_mode, nullptr);
+    if (rc) return rc;
+    cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
+    launch_validate(d_seq, n, R.p.err, st);
+    for (int g = 0; g < R.L.G; ++g)  // identical tokens for every epoch
+      launch_tokenize(d_seq, d_epoch_off, d_tok_one, 1, R.L.tok_off[1], c.s, c.k, d_tokens + R.L.tok_off[g], st);
+    (void)d_base_off;
+    (void)d_tok_off;
+    run_steps(R, grp_mode, st);
+    int h_err = 0;
+    cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int last = R.L.G - 1;
+    cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
+    PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+    PMKLC_CUDA_TRY(cudaGetLastError());
+    return h_err ? err_to_rc(h_err) : PMKLC_OK;
+  });
 }
 
 int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint64_t seed, float *out) {
-  if (k < 1 || k > 8 || !emb || !ctx || !hid || !out) return PMKLC_EINVAL;
-  Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
-  std::vector<float> v;
-  init_params(d, seed, v);
-  memcpy(out, v.data(), v.size() * sizeof(float));
-  return PMKLC_OK;
+  return guarded<int>([&]() -> int {
+    if (!widths_ok(k, emb, ctx, hid) || !out) return PMKLC_EINVAL;
+    Dims d{1 << (2 * (int)k), (int)emb, (int)ctx, (int)hid};
+    std::vector<float> v;
+    init_params(d, seed, v);
+    memcpy(out, v.data(), v.size() * sizeof(float));
+    return PMKLC_OK;
+  });
 }
 
 int pmklc_last_stats(pmklc_stats *st) {
@@ -1269,28 +1340,30 @@ int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream) {
 
 int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint16_t *d_tokens, uint8_t *d_tail,
                    size_t *n_tokens, void *stream) {
-  if (s < 1 || s > k || k > 8 || !n_tokens || (n && !d_seq)) return PMKLC_EINVAL;
-  long long l = n_tokens_of((long long)n, (int)s, (int)k);
-  if ((l && !d_tokens) || (!d_tail && tail_len_of((long long)n, (int)s, (int)k))) return PMKLC_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  Arena ar(st);
-  std::vector<long long> boff = {0, (long long)n}, toff = {0, l};
-  long long *d_boff = ar.upload(boff), *d_toff = ar.upload(toff);
-  int *d_err = ar.alloc<int>(1);
-  uint8_t *d_t8 = ar.alloc<uint8_t>(8);
-  if (ar.failed) return PMKLC_ENOMEM;
-  cudaMemsetAsync(d_err, 0, sizeof(int), st);
-  launch_validate(d_seq, n, d_err, st);
-  launch_tokenize(d_seq, d_boff, d_toff, 1, l, (int)s, (int)k, d_tokens, st);
-  launch_tails(d_seq, d_boff, d_toff, 1, (int)s, (int)k, d_t8, st);
-  long long tl = tail_len_of((long long)n, (int)s, (int)k);
-  if (tl) cudaMemcpyAsync(d_tail, d_t8, (size_t)tl, cudaMemcpyDeviceToDevice, st);
-  int h_err = 0;
-  cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
-  PMKLC_CUDA_TRY(cudaGetLastError());
-  *n_tokens = (size_t)l;
-  return h_err ? PMKLC_EINVAL : PMKLC_OK;
+  return guarded<int>([&]() -> int {
+    if (s < 1 || s > k || k > 8 || !n_tokens || (n && !d_seq)) return PMKLC_EINVAL;
+    long long l = n_tokens_of((long long)n, (int)s, (int)k);
+    if ((l && !d_tokens) || (!d_tail && tail_len_of((long long)n, (int)s, (int)k))) return PMKLC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena ar(st);
+    std::vector<long long> boff = {0, (long long)n}, toff = {0, l};
+    long long *d_boff = ar.upload(boff), *d_toff = ar.upload(toff);
+    int *d_err = ar.alloc<int>(1);
+    uint8_t *d_t8 = ar.alloc<uint8_t>(8);
+    if (ar.failed) return PMKLC_ENOMEM;
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    launch_validate(d_seq, n, d_err, st);
+    launch_tokenize(d_seq, d_boff, d_toff, 1, l, (int)s, (int)k, d_tokens, st);
+    launch_tails(d_seq, d_boff, d_toff, 1, (int)s, (int)k, d_t8, st);
+    long long tl = tail_len_of((long long)n, (int)s, (int)k);
+    if (tl) cudaMemcpyAsync(d_tail, d_t8, (size_t)tl, cudaMemcpyDeviceToDevice, st);
+    int h_err = 0;
+    cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+    PMKLC_CUDA_TRY(cudaGetLastError());
+    *n_tokens = (size_t)l;
+    return h_err ? PMKLC_EINVAL : PMKLC_OK;
+  });
 }
 
 // Single-step form of the hot loop: G groups of M lanes whose token sequences are
@@ -1414,45 +1487,51 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
 
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,
                   size_t rows, uint32_t precision, float *d_logits, void *stream) {
-  if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_FP8STATIC ||
-      (rows && (!d_params || !d_ctx || !d_logits)))
-    return PMKLC_EINVAL;
-  if (rows == 0) return PMKLC_OK;
-  pmklc_model_cfg mc;
-  pmklc_default_cfg(&mc, 1, k, E, t, H);
-  mc.precision = precision;
-  if (precision == PMKLC_BF16_FP8STATIC) {  // the model runs as the frozen static predictor in FP8
-    mc.use_static = 1;
-    mc.emb_s = E, mc.ctx_s = t, mc.hid_s = H;
-    mc.static_weights = d_params;  // only checked non-null
-  }
-  Cfg c;
-  int rc = check_cfg(&mc, c);
-  if (rc) return rc;
-  if (precision == PMKLC_BF16_FP8STATIC)
+  return guarded<int>([&]() -> int {
+    if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_FP8STATIC ||
+        (rows && (!d_params || !d_ctx || !d_logits)))
+      return PMKLC_EINVAL;
+    if (rows == 0) return PMKLC_OK;
+    pmklc_model_cfg mc;
+    pmklc_default_cfg(&mc, 1, k, E, t, H);
+    mc.precision = precision;
+    if (precision == PMKLC_BF16_FP8STATIC) {  // the model runs as the frozen static predictor in FP8
+      mc.use_static = 1;
+      mc.emb_s = E, mc.ctx_s = t, mc.hid_s = H;
+      mc.static_weights = d_params;  // only checked non-null
+    }
+    Cfg c;
+    int rc = check_cfg(&mc, c);
+    if (rc) return rc;
+    if (precision == PMKLC_BF16_FP8STATIC)
+      return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
+                      d_params, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
+    // a throw-away copy of the parameters: the forward never writes them, but the plan wants a mutable pointer
     return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
-                    d_params, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
-  // a throw-away copy of the parameters: the forward never writes them, but the plan wants a mutable pointer
-  return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
-                  nullptr, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
+                    nullptr, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
+  });
 }
 
 int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *d_params, float *d_m, float *d_v,
                      float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static, const uint16_t *d_ctx,
                      const uint16_t *d_target, uint32_t tau, float *d_P, float *d_grad, float *d_dalpha,
                      void *stream) {
-  Cfg c;
-  pmklc_model_cfg tmp;
-  if (!cfg) return PMKLC_EINVAL;
-  tmp = *cfg;
-  if (tmp.use_static && !tmp.static_weights) tmp.static_weights = (const float *)d_static;  // only checked non-null
-  int rc = check_cfg(&tmp, c);
-  if (rc) return rc;
-  if (!G || G > kMaxGroups || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||
-      !d_target || (c.use_static && !d_static))
-    return PMKLC_EINVAL;
-  return one_step(c, G, M, d_params, d_m, d_v, d_alpha, d_alpha_m, d_alpha_v, d_static, d_ctx, d_target, tau, d_P,
-                  d_grad, d_dalpha, nullptr, (cudaStream_t)stream);
+  return guarded<int>([&]() -> int {
+    Cfg c;
+    pmklc_model_cfg tmp;
+    if (!cfg) return PMKLC_EINVAL;
+    tmp = *cfg;
+    if (tmp.use_static && !tmp.static_weights) tmp.static_weights = (const float *)d_static;  // only checked non-null
+    int rc = check_cfg(&tmp, c);
+    if (rc) return rc;
+    const long long hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
+    if ((long long)G * M > kMaxLanes || (long long)G * M * hmax >= (1LL << 31)) return PMKLC_EINVAL;
+    if (!G || G > kMaxGroups || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||
+        !d_target || (c.use_static && !d_static))
+      return PMKLC_EINVAL;
+    return one_step(c, G, M, d_params, d_m, d_v, d_alpha, d_alpha_m, d_alpha_v, d_static, d_ctx, d_target, tau, d_P,
+                    d_grad, d_dalpha, nullptr, (cudaStream_t)stream);
+  });
 }
 
 }  // extern "C"

@@ -171,3 +171,35 @@ def test_block_count_limit(P):
     assert P.pmklc_compress_bound(0, [0] * 32768, cfg) == 0
     assert P.pmklc_compress_bound(0, [0] * 32767, cfg) > 0
     assert _rc(P, lambda: P.pmklc_compress(b"", [0] * 32768, cfg)) == P.PMKLC_EINVAL
+
+
+def test_layout_limits(P):
+    """A call's layout is checked on the host before any allocation: at most 2^24 lanes, lanes x
+    hidden width below 2^31, at most 2^27 tokens per lane and 2^30 schedule steps.  The size bound
+    answers 0 (the library's refusal) past any of them; the benchmarked layout fits."""
+    def bound(lens, **kw):
+        base = dict(s=1, k=1, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=1)
+        base.update(kw)
+        return P.pmklc_compress_bound(sum(lens), lens, P.ModelConfig(**base))
+
+    assert bound([1 << 27]) > 0                           # one lane of 2^27 tokens ((s,k) = (1,1))
+    assert bound([(1 << 27) + 1]) == 0                    # one token more
+    assert bound([4096] * 16384, lanes_per_block=1024) > 0          # 2^24 lanes
+    assert bound([4096] * 16385, lanes_per_block=1024) == 0
+    assert bound([4096] * 32, lanes_per_block=1024, hid_d=65535) > 0  # 32768 lanes x 65535 < 2^31
+    assert bound([4096] * 33, lanes_per_block=1024, hid_d=65535) == 0
+    # chained model passing at f = 1 runs the blocks one after another: 2^30 steps at most
+    assert bound([1 << 16] * 16384, smp_mode=P.PMKLC_SMP_CHAIN, smp_fraction=1.0) > 0
+    assert bound([1 << 16] * 16385, smp_mode=P.PMKLC_SMP_CHAIN, smp_fraction=1.0) == 0
+    assert bound([1 << 16] * 16385, smp_mode=P.PMKLC_SMP_TREE, smp_fraction=1.0) > 0
+    assert bound([1 << 18] * 64, s=2, k=4, emb_d=32, ctx_d=32, hid_d=128, lanes_per_block=64) > 0
+
+
+def test_model_widths_are_bounded(P):
+    assert P.model_count(4, 32, 32, 128) == 172416
+    for bad in [(0, 8, 8, 8), (9, 8, 8, 8), (4, 4097, 8, 8), (4, 8, 4097, 8), (4, 8, 8, 65536), (4, 0, 8, 8),
+                (4, 1 << 31, 8, 8)]:
+        assert P.model_count(*bad) == 0
+    with pytest.raises(P.PmklcError) as e:
+        P.pmklc_init_model(4, 4097, 8, 8, 1)
+    assert e.value.rc == P.PMKLC_EINVAL
