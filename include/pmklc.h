@@ -190,6 +190,7 @@ int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint1
  * step 3; the paper does not say how P becomes integers): for each of `rows` rows of A probabilities,
  * freq_j = 1 + floor(P_j*(2^24 - A)) (FP32 product), the remainder added to
  * the first maximal entry.  d_P: rows x A FP32; d_freq: rows x A uint32.
+ * rows <= 2^26 (one warp per row), else EINVAL.
  */
 int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_t *d_freq, void *stream);
 
@@ -197,6 +198,7 @@ int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_t *d_freq, 
  * Probability Mixer, Eq. (1), + softmax + quantisation, per row:
  * P = softmax(alpha*Lu + (1-alpha)*Lm) (Lu ignored when use_static = 0).
  * d_Lu, d_Lm: rows x A FP32 logits; d_P: rows x A FP32; d_freq: rows x A.
+ * rows <= 2^26, else EINVAL.
  */
 int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32_t A, float alpha,
                        uint32_t use_static, float *d_P, uint32_t *d_freq, void *stream);
@@ -207,11 +209,16 @@ int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32
  * Stream i codes L symbols d_sym[i*L + j] with frequency tables
  * d_freq[(i*L + j)*A .. +A) (each summing to 2^24).  Output bytes of stream i
  * go to d_out[i*cap ...], their count to d_len[i]; cap >= 3*L + 8 always
- * suffices.  ENOSPC if a stream overflows cap.
+ * suffices.  ENOSPC if a stream overflows cap.  EINVAL if a symbol is >= A, or
+ * the table entry it codes is 0 or its interval ends past 2^24 (that stream
+ * stops there), or n_streams or L exceeds 2^31 - 1.
  */
 int pmklc_range_encode(const uint32_t *d_freq, const uint16_t *d_sym, uint32_t n_streams, uint32_t L,
                        uint32_t A, uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream);
-/* Decoding of the streams written by pmklc_range_encode (same layout). */
+/* Decoding of the streams written by pmklc_range_encode (same layout): stream i
+ * reads at most min(d_len[i], cap) bytes (bytes past them read as 0).  EINVAL if
+ * a table's entries end below the decoded target or run past 2^24 (that stream
+ * stops there). */
 int pmklc_range_decode(const uint32_t *d_freq, const uint8_t *d_in, const uint32_t *d_len, uint32_t n_streams,
                        uint32_t L, uint32_t A, uint32_t cap, uint16_t *d_sym, void *stream);
 

@@ -542,27 +542,38 @@ __global__ void range_encode_kernel(const uint32_t *freq, const uint16_t *sym, i
   uint8_t *o = out + (size_t)i * cap;
   for (int j = 0; j < L; ++j) {
     const uint32_t *f = freq + ((size_t)i * L + j) * A;
-    int e = sym[(size_t)i * L + j];
-    uint32_t cum = 0;
+    const int e = sym[(size_t)i * L + j];
+    // a caller's symbol or table the coder cannot take (symbol outside the alphabet, frequency 0,
+    // interval past the 2^24 total) ends the stream with an error instead of looping or reading on
+    if (e >= A) {
+      atomicOr(err, kErrCorrupt);
+      break;
+    }
+    unsigned long long cum = 0;
     for (int a = 0; a < e; ++a) cum += f[a];
-    enc_code24(s, cum, f[e], o, cap, err);
+    if (f[e] == 0 || cum + f[e] > kTotal) {
+      atomicOr(err, kErrCorrupt);
+      break;
+    }
+    enc_code24(s, (uint32_t)cum, f[e], o, cap, err);
   }
   len[i] = enc_finish(s, o, cap, err);
 }
 
 __global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, const uint32_t *len, int n_streams,
-                                    int L, int A, uint32_t cap, uint16_t *sym) {
+                                    int L, int A, uint32_t cap, uint16_t *sym, int *err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_streams) return;
   DecState s;
   const uint8_t *b = in + (size_t)i * cap;
-  dec_init(s, b, len[i]);
+  const uint32_t n_in = len[i] < cap ? len[i] : cap;  // never past the stream's own cap bytes
+  dec_init(s, b, n_in);
   for (int j = 0; j < L; ++j) {
     const uint32_t *f = freq + ((size_t)i * L + j) * A;
     unsigned long long rr;
     uint32_t x = dec_target24(s, rr);
-    uint32_t cum = 0;
-    int e = A - 1;
+    unsigned long long cum = 0;
+    int e = -1;
     for (int a = 0; a < A; ++a) {
       if (x < cum + f[a]) {
         e = a;
@@ -570,7 +581,12 @@ __global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, con
       }
       cum += f[a];
     }
-    dec_consume(s, rr, cum, f[e], b, len[i]);
+    // a table whose entries end below the target or run past the 2^24 total cannot be decoded
+    if (e < 0 || cum + f[e] > kTotal) {
+      atomicOr(err, kErrCorrupt);
+      break;
+    }
+    dec_consume(s, rr, (uint32_t)cum, f[e], b, n_in);
     sym[(size_t)i * L + j] = (uint16_t)e;
   }
 }
@@ -606,8 +622,11 @@ using namespace pmklc;
 
 static bool pow4(uint32_t A) { return A >= 4 && A <= 65536 && (A & (A - 1)) == 0 && (__builtin_ctz(A) % 2 == 0); }
 
+// rows of the per-row entry points: one warp per row, warp indices in 32 bits
+constexpr size_t kMaxRows = size_t(1) << 26;
+
 extern "C" int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_t *d_freq, void *stream) {
-  if (!pow4(A) || (rows && (!d_P || !d_freq))) return PMKLC_EINVAL;
+  if (!pow4(A) || rows > kMaxRows || (rows && (!d_P || !d_freq))) return PMKLC_EINVAL;
   if (rows == 0) return PMKLC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   quantize_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(d_P, (int)rows, (int)A, d_freq);
@@ -618,7 +637,8 @@ extern "C" int pmklc_quantize(const float *d_P, size_t rows, uint32_t A, uint32_
 
 extern "C" int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t rows, uint32_t A, float alpha,
                                   uint32_t use_static, float *d_P, uint32_t *d_freq, void *stream) {
-  if (!pow4(A) || (rows && (!d_Lm || !d_P || !d_freq || (use_static && !d_Lu)))) return PMKLC_EINVAL;
+  if (!pow4(A) || rows > kMaxRows || (rows && (!d_Lm || !d_P || !d_freq || (use_static && !d_Lu))))
+    return PMKLC_EINVAL;
   if (rows == 0) return PMKLC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   mix_quantize_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(d_Lu, d_Lm, (int)rows, (int)A, alpha,
@@ -630,7 +650,8 @@ extern "C" int pmklc_mix_quantize(const float *d_Lu, const float *d_Lm, size_t r
 
 extern "C" int pmklc_range_encode(const uint32_t *d_freq, const uint16_t *d_sym, uint32_t n_streams, uint32_t L,
                                   uint32_t A, uint8_t *d_out, uint32_t cap, uint32_t *d_len, void *stream) {
-  if (!pow4(A) || !d_len || (n_streams && (!d_out || (L && (!d_freq || !d_sym))))) return PMKLC_EINVAL;
+  if (!pow4(A) || !d_len || n_streams > INT32_MAX || L > INT32_MAX || (n_streams && (!d_out || (L && (!d_freq || !d_sym)))))
+    return PMKLC_EINVAL;
   if (n_streams == 0) return PMKLC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   int *d_err = nullptr;
@@ -643,18 +664,26 @@ extern "C" int pmklc_range_encode(const uint32_t *d_freq, const uint16_t *d_sym,
   cudaFreeAsync(d_err, st);
   PMKLC_CUDA_TRY(cudaGetLastError());
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
-  return h ? PMKLC_ENOSPC : PMKLC_OK;
+  return (h & kErrCorrupt) ? PMKLC_EINVAL : h ? PMKLC_ENOSPC : PMKLC_OK;
 }
 
 extern "C" int pmklc_range_decode(const uint32_t *d_freq, const uint8_t *d_in, const uint32_t *d_len,
                                   uint32_t n_streams, uint32_t L, uint32_t A, uint32_t cap, uint16_t *d_sym,
                                   void *stream) {
-  if (!pow4(A) || (n_streams && (!d_in || !d_len || (L && (!d_freq || !d_sym))))) return PMKLC_EINVAL;
+  if (!pow4(A) || n_streams > INT32_MAX || L > INT32_MAX ||
+      (n_streams && (!d_in || !d_len || (L && (!d_freq || !d_sym)))))
+    return PMKLC_EINVAL;
   if (n_streams == 0) return PMKLC_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  int *d_err = nullptr;
+  PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_err, sizeof(int), st));
+  cudaMemsetAsync(d_err, 0, sizeof(int), st);
   range_decode_kernel<<<(n_streams + 63) / 64, 64, 0, st>>>(d_freq, d_in, d_len, (int)n_streams, (int)L, (int)A, cap,
-                                                            d_sym);
+                                                            d_sym, d_err);
+  int h = 0;
+  cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_err, st);
   PMKLC_CUDA_TRY(cudaGetLastError());
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
-  return PMKLC_OK;
+  return h ? PMKLC_EINVAL : PMKLC_OK;
 }

@@ -71,3 +71,19 @@ def test_wait_selftest_rejects_bad_poll_counts():
     import paper_2507_12805_gb300 as P
     assert P.pmklc_wait_selftest(0) == P.PMKLC_EINVAL
     assert P.pmklc_wait_selftest((1 << 30) + 1) == P.PMKLC_EINVAL
+
+
+def test_step_entry_points_check_sizes_before_any_cuda_call():
+    """Row and stream counts past what the per-row and per-stream kernels index are refused
+    before any device work (no GPU needed; the pointers are never dereferenced)."""
+    import ctypes
+    import paper_2507_12805_gb300 as P
+    lib, fake = P.lib, ctypes.c_void_p(16)
+    assert lib.pmklc_quantize(fake, (1 << 26) + 1, 4, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_quantize(fake, 8, 5, fake, None) == P.PMKLC_EINVAL          # A not a power of 4
+    assert lib.pmklc_mix_quantize(fake, fake, (1 << 26) + 1, 4, ctypes.c_float(0.5), 1, fake, fake,
+                                  None) == P.PMKLC_EINVAL
+    assert lib.pmklc_range_encode(fake, fake, 1 << 31, 1, 4, fake, 8, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_range_encode(fake, fake, 1, 1 << 31, 4, fake, 8, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_range_decode(fake, fake, fake, 1 << 31, 1, 4, 8, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_range_decode(fake, fake, fake, 1, 1 << 31, 4, 8, fake, None) == P.PMKLC_EINVAL
