@@ -180,7 +180,8 @@ int pmklc_decompress_dev(const uint8_t *d_in, size_t in_len, const float *static
  * (s,k)-mer encoding, GskE (paper §4.1, Fig. 3): d_tokens[j] =
  * sum_m 4^(k-1-m) code(d_seq[j*s+m]) for j < l = floor((n-k)/s)+1 (0 if n < k);
  * the n - covered trailing bases go to d_tail as codes 0..3 (at most 7).
- * d_tokens holds l entries.  *n_tokens receives l.  EINVAL on a non-ACGT byte.
+ * d_tokens holds l entries.  *n_tokens receives l.  EINVAL on a non-ACGT byte
+ * or n > 2^56.
  */
 int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint16_t *d_tokens,
                    uint8_t *d_tail, size_t *n_tokens, void *stream);
@@ -227,6 +228,7 @@ int pmklc_range_decode(const uint32_t *d_freq, const uint8_t *d_in, const uint32
  * logits[r] = relu(X_r W1 + b1) W2 + b2 with X_r the embeddings of the t
  * context tokens d_ctx[r*t .. r*t+t) (oldest first).  d_params in the model
  * layout for (A=4^k, E, t, H); d_logits rows x A.  precision as in the cfg.
+ * Widths as in the cfg; rows <= 2^24 and rows x H < 2^31, else EINVAL.
  */
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H,
                   const uint16_t *d_ctx, size_t rows, uint32_t precision, float *d_logits, void *stream);

@@ -1341,7 +1341,7 @@ int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream) {
 int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint16_t *d_tokens, uint8_t *d_tail,
                    size_t *n_tokens, void *stream) {
   return guarded<int>([&]() -> int {
-    if (s < 1 || s > k || k > 8 || !n_tokens || (n && !d_seq)) return PMKLC_EINVAL;
+    if (s < 1 || s > k || k > 8 || !n_tokens || (n && !d_seq) || n > (size_t(1) << 56)) return PMKLC_EINVAL;
     long long l = n_tokens_of((long long)n, (int)s, (int)k);
     if ((l && !d_tokens) || (!d_tail && tail_len_of((long long)n, (int)s, (int)k))) return PMKLC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1492,6 +1492,8 @@ int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uin
         (rows && (!d_params || !d_ctx || !d_logits)))
       return PMKLC_EINVAL;
     if (rows == 0) return PMKLC_OK;
+    // the rows are the lanes of one group: the same limits as a compression's layout
+    if (rows > (size_t)kMaxLanes || (long long)rows * (long long)H >= (1LL << 31)) return PMKLC_EINVAL;
     pmklc_model_cfg mc;
     pmklc_default_cfg(&mc, 1, k, E, t, H);
     mc.precision = precision;

@@ -87,3 +87,15 @@ def test_step_entry_points_check_sizes_before_any_cuda_call():
     assert lib.pmklc_range_encode(fake, fake, 1, 1 << 31, 4, fake, 8, fake, None) == P.PMKLC_EINVAL
     assert lib.pmklc_range_decode(fake, fake, fake, 1 << 31, 1, 4, 8, fake, None) == P.PMKLC_EINVAL
     assert lib.pmklc_range_decode(fake, fake, fake, 1, 1 << 31, 4, 8, fake, None) == P.PMKLC_EINVAL
+
+
+def test_tokenize_and_predict_check_sizes_before_any_cuda_call():
+    import ctypes
+    import paper_2507_12805_gb300 as P
+    lib, fake = P.lib, ctypes.c_void_p(16)
+    n_tok = ctypes.c_size_t(0)
+    assert lib.pmklc_tokenize(fake, (1 << 56) + 1, 2, 4, fake, fake, ctypes.byref(n_tok), None) == P.PMKLC_EINVAL
+    assert lib.pmklc_tokenize(fake, 100, 5, 4, fake, fake, ctypes.byref(n_tok), None) == P.PMKLC_EINVAL  # s > k
+    assert lib.pmklc_predict(fake, 4, 32, 32, 128, fake, (1 << 24) + 1, 0, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_predict(fake, 4, 32, 32, 65535, fake, (1 << 15) + 1, 0, fake, None) == P.PMKLC_EINVAL
+    assert lib.pmklc_predict(fake, 9, 32, 32, 128, fake, 8, 0, fake, None) == P.PMKLC_EINVAL
