@@ -13,6 +13,12 @@
  *     is ordered on it; calls that return host results synchronise it.
  *   - Sizes are element counts unless the name says bytes.
  *   - Token arrays are uint16 (k <= 8, so 4^k <= 65536 symbols).
+ *   - One process drives one CUDA device: the GEMM kernels' shared-memory
+ *     opt-in is made once per process.  Calls from several host threads on
+ *     their own streams share only mutex-guarded caches, the per-thread
+ *     statistics and the process-wide profiler (enable it around one call at a
+ *     time); concurrent calls are not tested, and pmklc_crc32_noalloc's scratch
+ *     must be serialised by the caller.
  *   - A model's parameters are one FP32 array in the layout
  *         Emb[A][E] | W1t[H][t*E] | b1[H] | W2[H][A] | b2[A]     (A = 4^k)
  *     (row-major; W1 is stored transposed, row j holding the weights into
