@@ -203,3 +203,28 @@ def test_model_widths_are_bounded(P):
     with pytest.raises(P.PmklcError) as e:
         P.pmklc_init_model(4, 4097, 8, 8, 1)
     assert e.value.rc == P.PMKLC_EINVAL
+
+
+def test_lane_partition_matches_oracle_through_the_size_bound(P):
+    """The size bound is a closed form of each block's token count l and lane count M_b (section
+    "Size bound" of the container format), so equality with the formula evaluated on the
+    oracle's tokenizer and lane partition pins the library's token and lane counts, including the
+    lane-length target, on random ragged layouts."""
+    from oracle.tokenizer import n_tokens
+    rng = np.random.default_rng(17)
+    for it in range(300):
+        k = int(rng.integers(1, 9))
+        s = int(rng.integers(1, k + 1))
+        M = int(rng.integers(1, 400))
+        L = int(rng.choice([0, int(rng.integers(1, 3000))]))
+        fallback = int(rng.integers(0, 3))
+        lens = [int(x) for x in rng.choice([0, 1, k - 1, k, k + 1, int(rng.integers(0, 1 << 20))],
+                                            int(rng.integers(1, 12)))]
+        kw = dict(s=s, k=k, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=M, lane_tokens=L, fallback=fallback)
+        want = 80
+        for n in lens:
+            l = n_tokens(n, s, k)
+            Mb = len(ocodec.lanes(l, M, L)[1])
+            stream = 3 * l + 8 * Mb if fallback != 2 else 2 * (k * Mb + s * (l - Mb)) + 8 * Mb
+            want += 13 + 10 * Mb + stream
+        assert P.pmklc_compress_bound(sum(lens), lens, P.ModelConfig(**kw)) == want, (kw, lens)
