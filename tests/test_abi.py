@@ -99,3 +99,23 @@ def test_tokenize_and_predict_check_sizes_before_any_cuda_call():
     assert lib.pmklc_predict(fake, 4, 32, 32, 128, fake, (1 << 24) + 1, 0, fake, None) == P.PMKLC_EINVAL
     assert lib.pmklc_predict(fake, 4, 32, 32, 65535, fake, (1 << 15) + 1, 0, fake, None) == P.PMKLC_EINVAL
     assert lib.pmklc_predict(fake, 9, 32, 32, 128, fake, 8, 0, fake, None) == P.PMKLC_EINVAL
+
+
+def test_header_constants_equal_the_binding_and_the_library():
+    """Every value #define of include/pmklc.h has the same value in the Python binding; the ABI
+    version is also what the library reports, and every error code has its own message."""
+    import os
+    import re
+    import paper_2507_12805_gb300 as P
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "pmklc.h")) as f:
+        defs = dict(re.findall(r"^#define (PMKLC_[A-Z0-9_]+) \(?(-?\d+)\)?", f.read(), re.M))
+    assert len(defs) >= 17
+    for name, value in defs.items():
+        if name == "PMKLC_ABI_VERSION":
+            assert P.lib.pmklc_abi_version() == int(value)
+            continue
+        assert getattr(P, name) == int(value), name
+    codes = [int(v) for n, v in defs.items() if n.startswith("PMKLC_E") or n == "PMKLC_OK"]
+    msgs = {P.lib.pmklc_strerror(c) for c in codes}
+    assert len(msgs) == len(codes)
