@@ -81,3 +81,11 @@ def test_reference_arm_runs_the_oracle_alone(monkeypatch, capsys):
     assert line["e2e"] == {"value": line["value"], "unit": "MB/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "1024 bases" in line["cpu_baseline"]["sample"]
+
+
+def test_throttle_detection():
+    assert not bench.throttled({"reasons": []})
+    assert not bench.throttled({"reasons": ["sw_power_cap"]})
+    assert not bench.throttled({"reasons": ["unsampled"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.throttled({"reasons": ["sw_power_cap", r]})
