@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define PMKLC_ABI_VERSION 1
+#define PMKLC_ABI_VERSION 2
 
 /* error codes */
 #define PMKLC_OK 0
@@ -85,6 +85,11 @@ typedef struct {
   uint32_t lane_tokens;        /* 0: a block of l tokens gets min(lanes_per_block, l) lanes; else
                                   min(lanes_per_block, l, ceil(l / lane_tokens)), so lanes of uneven
                                   blocks take about the same number of steps */
+  uint32_t overlap_mask;       /* 1 (s < k; not in the paper): token j >= 1 of a lane is coded over
+                                  the 4^s tokens that share their first k - s digits with the last
+                                  k - s digits of token j - 1 (the only ones that can follow):
+                                  uniform over them in the first t symbols, else the softmax of
+                                  their mixed logits, trained on that slice's cross entropy */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);

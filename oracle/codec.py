@@ -26,6 +26,15 @@ Readings where the paper is silent:
   FP8      precision 2: the frozen static predictor runs in its FP8 form
            (fp8.py: E4M3 weights with per-channel scales, E4M3 activations with
            a per-row scale); the dynamic predictor is unchanged.
+  mask     overlap_mask = 1 (not in the paper): with s < k, token j >= 1 of a
+           lane shares its first k - s digits with token j - 1, so only the
+           4^s tokens of the slice [p 4^s, (p+1) 4^s), p = e_{j-1} mod
+           4^(k-s), can follow.  The distribution is restricted to that slice:
+           uniform over it in the first t symbols, else the softmax of the
+           slice's mixed logits (Eq. 1), quantised over the slice (T = 2^24)
+           and coded as the index within it; the loss is the slice's cross
+           entropy (zero gradient outside it).  Token 0 of a lane keeps the
+           full alphabet.  Recorded in the header's variant field (bit 0).
   judge    fallback 1: the count model (countmodel.py) codes every block in the
            same lanes alongside the network, and a block is stored with it when
            that costs fewer bytes (flag in the container); fallback 2: the count
@@ -90,6 +99,7 @@ class Config:
     seed: int = 42
     variant: int = 0
     lane_tokens: int = 0
+    overlap_mask: int = 0
 
     def f32(self, name: str) -> float:
         return float(np.float32(getattr(self, name)))
@@ -243,6 +253,16 @@ def _ctx(tokens, start, j, t):
     return tokens[start + j - t: start + j]
 
 
+def _slice(cfg: Config, b, r: int, j: int):
+    """(first token, width) of the symbols lane r's token j is coded over: the whole alphabet, or
+    with the overlap mask the 4^s tokens that agree with token j - 1 on the k - s shared digits."""
+    if not cfg.overlap_mask or j == 0 or cfg.s == cfg.k:
+        return 0, cfg.A
+    W = 4 ** cfg.s
+    prev = int(b.tokens[b.starts[r] + j - 1])
+    return (prev % (4 ** (cfg.k - cfg.s))) * W, W
+
+
 def _count_step(cfg: Config, b: _Block, j: int):
     """The count model's sub-steps of local step j for every live lane of block b (countmodel.py)."""
     live = [r for r in range(len(b.lens)) if j < b.lens[r]]
@@ -310,13 +330,15 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
             live = [r for r in range(len(b.lens)) if j < b.lens[r]]
             pred = [r for r in live if j >= t_eff]
             for r in live:
-                if j < t_eff:  # uniform distribution for the first t symbols (§2)
+                if j < t_eff:  # uniform distribution for the first t symbols (§2), over the slice
+                    base, W = _slice(cfg, b, r, j)
+                    u = TOTAL // W
                     if b.decode:
-                        cum = np.arange(A + 1, dtype=np.int64) * uni
-                        b.tokens[b.starts[r] + j] = b.dec[r].decode(cum, TOTAL)
+                        cum = np.arange(W + 1, dtype=np.int64) * u
+                        b.tokens[b.starts[r] + j] = base + b.dec[r].decode(cum, TOTAL)
                     elif not b.replay:
-                        e = int(b.tokens[b.starts[r] + j])
-                        b.enc[r].encode(e * uni, uni, TOTAL)
+                        e = int(b.tokens[b.starts[r] + j]) - base
+                        b.enc[r].encode(e * u, u, TOTAL)
             if not pred:
                 continue
             cd = np.stack([_ctx(b.tokens, b.starts[r], j, cfg.ctx_d) for r in pred])
@@ -325,19 +347,24 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
             if cfg.use_static:
                 cs = np.stack([_ctx(b.tokens, b.starts[r], j, cfg.ctx_s) for r in pred])
                 Lu = fp8.forward(fq, cs) if fq is not None else forward(static_w, sshape, cs)[3]
-            P = softmax(mix(Lu, Lm, st.alpha, S))
+            z = mix(Lu, Lm, st.alpha, S)
+            sl = [_slice(cfg, b, r, j) for r in pred]
+            P = np.zeros_like(z)  # the distribution coded: softmax over each row's slice
+            for i, (base, W) in enumerate(sl):
+                P[i, base:base + W] = softmax(z[i, base:base + W])
             if on_probs is not None:
                 on_probs(g, j, P)
-            freq = quantize(P)
-            cum = cumulative(freq)
             targets = np.zeros(len(pred), dtype=np.int64)
             for i, r in enumerate(pred):
+                base, W = sl[i]
+                freq = quantize(P[i, base:base + W])
+                cum = cumulative(freq)
                 pos = b.starts[r] + j
                 if b.decode:
-                    b.tokens[pos] = b.dec[r].decode(cum[i], TOTAL)
+                    b.tokens[pos] = base + b.dec[r].decode(cum, TOTAL)
                 elif not b.replay:
-                    e = int(b.tokens[pos])
-                    b.enc[r].encode(int(cum[i][e]), int(freq[i][e]), TOTAL)
+                    e = int(b.tokens[pos]) - base
+                    b.enc[r].encode(int(cum[e]), int(freq[e]), TOTAL)
                 targets[i] = b.tokens[pos]
             # Backward Controller: mean cross entropy (Eq. 2) over the predicted lanes
             dLm, dalpha = loss_grads(P, targets, Lu, Lm, st.alpha, S)
@@ -411,7 +438,7 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> byte
                        cfg.lanes_per_block, cfg.lr, cfg.alpha_init, cfg.smp_fraction, cfg.seed,
                        static_hash(static_w if cfg.use_static else None), codes.size, len(block_lens),
                        zlib.crc32(bytes(np.asarray(seq, dtype=np.uint8) if isinstance(seq, np.ndarray) else seq)),
-                       cfg.variant, cfg.lane_tokens)
+                       (cfg.variant & ~1) | (1 if cfg.overlap_mask else 0), cfg.lane_tokens)
     return bytes(head) + bytes(out_hdr) + bytes(payload)
 
 
@@ -424,7 +451,8 @@ def parse_header(data: bytes):
     cfg = Config(s=f[2], k=f[3], use_static=bool(f[4] & 1), fallback=(f[4] >> 1) & 3, precision=f[5],
                  optimizer=f[6], smp_mode=f[7], count_order=f[8], emb_d=f[9], ctx_d=f[10], hid_d=f[11],
                  emb_s=f[12], ctx_s=f[13], hid_s=f[14], lanes_per_block=f[15], lr=f[16], alpha_init=f[17],
-                 smp_fraction=f[18], seed=f[19], variant=f[24], lane_tokens=f[25])
+                 smp_fraction=f[18], seed=f[19], variant=f[24] & ~1, lane_tokens=f[25],
+                 overlap_mask=f[24] & 1)
     return cfg, {"static_hash": f[20], "n": f[21], "n_blocks": f[22], "crc": f[23]}
 
 

@@ -42,7 +42,8 @@ class CModelCfg(ctypes.Structure):
                 ("optimizer", ctypes.c_uint32), ("lr", ctypes.c_float), ("alpha_init", ctypes.c_float),
                 ("smp_mode", ctypes.c_uint32), ("smp_fraction", ctypes.c_float), ("count_order", ctypes.c_uint32),
                 ("fallback", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32)]
+                ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32),
+                ("overlap_mask", ctypes.c_uint32)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -125,6 +126,7 @@ class ModelConfig:
     seed: int = 42
     static_weights: np.ndarray | None = field(default=None, repr=False)
     lane_tokens: int = 0
+    overlap_mask: int = 0    # 1: code token j >= 1 over the 4^s tokens consistent with token j - 1
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()

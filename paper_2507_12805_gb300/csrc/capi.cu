@@ -150,6 +150,7 @@ struct Cfg {
   int lane_tokens;  // 0: every block gets min(lanes, l) lanes; else min(lanes, l, ceil(l / lane_tokens))
   float lr, alpha0, smp_f;
   uint64_t seed;
+  int mask = 0;                        // overlap-masked coding (s < k)
   int A() const { return 1 << (2 * k); }
   int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
 };
@@ -170,6 +171,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
   if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
+  if (c->overlap_mask > 1) return PMKLC_EINVAL;
   o.s = (int)c->s;
   o.k = (int)c->k;
   o.use_static = c->use_static ? 1 : 0;
@@ -181,6 +183,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   int A = 1 << (2 * c->k);
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
   o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
+  o.mask = (int)c->overlap_mask;
   o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
   o.lane_tokens = (int)c->lane_tokens;
   o.lr = c->lr;
@@ -365,6 +368,8 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.NL = L.NL;
   p.Mmax = L.Mmax;
   p.t_eff = c.t_eff();
+  p.ov_w = c.mask && c.s < c.k ? 1 << (2 * c.s) : 0;
+  p.ov_mod = c.mask && c.s < c.k ? 1 << (2 * (c.k - c.s)) : 0;
   p.use_static = c.use_static;
   p.optimizer = c.optimizer;
   p.lr = c.lr;
@@ -773,7 +778,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   put_le<uint64_t>(H, (uint64_t)n);
   put_le<uint32_t>(H, (uint32_t)n_blocks);
   put_le<uint32_t>(H, crc);
-  put_le<uint32_t>(H, 0u);  // kernel variant
+  put_le<uint32_t>(H, c.mask ? 1u : 0u);  // variant: bit 0 = overlap-masked coding
   put_le<uint32_t>(H, (uint32_t)c.lane_tokens);
   std::vector<unsigned long long> seg;  // (src, dst-relative, len, which)
   unsigned long long pay = 0;
@@ -868,6 +873,7 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   P.n_blocks = get_le<uint32_t>(h + 64);
   if (P.n_blocks > kMaxGroups) return PMKLC_ECORRUPT;
   P.crc = get_le<uint32_t>(h + 68);
+  c.mask = (int)(get_le<uint32_t>(h + 72) & 1u);
   c.lane_tokens = (int)get_le<uint32_t>(h + 76);
   if (c.lane_tokens < 0) return PMKLC_ECORRUPT;
   if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !(c.lr > 0.f) || !isfinite(c.lr) || !isfinite(c.alpha0))

@@ -47,6 +47,7 @@ struct Plan {
   int NL;            // lanes (= rows of every per-step GEMM)
   int Mmax;          // largest number of lanes in a group
   int t_eff;         // uniform-coded prefix length per lane
+  int ov_w, ov_mod;  // overlap-masked coding (s < k): slice width 4^s and 4^(k-s); 0 = whole alphabet
   int use_static;
   int optimizer;     // PMKLC_ADAM / PMKLC_SGD
   float lr;

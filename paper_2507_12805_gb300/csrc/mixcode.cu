@@ -316,12 +316,19 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
   const long long tpos = p.lane_tok[r] + j;
   uint8_t *buf = p.lane_buf + p.lane_buf_off[r];
   const uint32_t cap = p.lane_buf_cap[r];
+  // the symbols coded over: the whole alphabet, or with overlap masking (j >= 1) the W = 4^s
+  // tokens [base, base + W) that agree with token j - 1 on their k - s shared digits
+  int base = 0, W = A;
+  if (p.ov_w > 0 && j > 0) {
+    W = p.ov_w;
+    base = ((int)p.tokens[tpos - 1] % p.ov_mod) * W;
+  }
   if (j < p.t_eff) {  // uniform distribution for the first t symbols (§2)
     if (lane == 0 && mode != kReplay) {
-      const uint32_t u = kTotal / (uint32_t)A;
+      const uint32_t u = kTotal / (uint32_t)W;
       if (mode == kEncode) {
         EncState s = p.enc[r];
-        uint32_t e = p.tokens[tpos];
+        uint32_t e = (uint32_t)((int)p.tokens[tpos] - base);
         enc_code24(s, e * u, u, buf, cap, p.err);
         p.enc[r] = s;
       } else {
@@ -331,17 +338,28 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
         uint32_t e = x / u;
         dec_consume(s, rr, e * u, u, buf, cap);
         p.dec[r] = s;
-        p.tokens[tpos] = (uint16_t)e;
+        p.tokens[tpos] = (uint16_t)(base + (int)e);
       }
     }
     return;
   }
   const float alpha = p.alpha[g];
-  RowView v{p.zu + (size_t)r * A, p.zm + (size_t)r * A, alpha, __fsub_rn(1.f, alpha), p.use_static};
+  const size_t ro = (size_t)r * A + base;  // the slice's first element in the row-major [NL][A] buffers
+  RowView v{p.zu + ro, p.zm + ro, alpha, __fsub_rn(1.f, alpha), p.use_static};
   const int n_pred = live_lanes(p, g, j);
   const float inv_n = 1.f / (float)n_pred;
-  float *outP = p.out_P ? p.out_P + (size_t)r * A : nullptr;
+  float *outP = p.out_P ? p.out_P + ro : nullptr;
   float da = 0.f;
+  if (W < A) {  // outside the slice: zero gradient (and probability)
+    for (int a = lane; a < A; a += 32) {
+      if (a >= base && a < base + W) continue;
+      if (p.dz_b)
+        p.dz_b[(size_t)r * A + a] = __float2bfloat16_rn(0.f);
+      else
+        p.dz[(size_t)r * A + a] = 0.f;
+      if (p.out_P) p.out_P[(size_t)r * A + a] = 0.f;
+    }
+  }
   if constexpr (NR > 0) {
     RegRow<NR> R;
     reg_table<NR>(v, lane, R);
@@ -360,10 +378,10 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
       if (lane == 0) {
         dec_consume(s, rr, cum, freq, buf, cap);
         p.dec[r] = s;
-        p.tokens[tpos] = (uint16_t)e;
+        p.tokens[tpos] = (uint16_t)(base + e);
       }
     } else {
-      e = p.tokens[tpos];
+      e = (int)p.tokens[tpos] - base;
       if (mode == kEncode) {
         uint32_t cum, freq;
         reg_interval<NR>(R, e, cum, freq);
@@ -397,16 +415,16 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
 #pragma unroll
       for (int q = 0; q < NR / 2; ++q) {
         __nv_bfloat162 h = __floats2bfloat162_rn(dv[2 * q], dv[2 * q + 1]);
-        reinterpret_cast<__nv_bfloat162 *>(p.dz_b + (size_t)r * A + a0)[q] = h;
+        reinterpret_cast<__nv_bfloat162 *>(p.dz_b + ro + a0)[q] = h;
       }
     } else {
 #pragma unroll
       for (int q = 0; q < NR / 2; ++q)
-        reinterpret_cast<float2 *>(p.dz + (size_t)r * A + a0)[q] = make_float2(dv[2 * q], dv[2 * q + 1]);
+        reinterpret_cast<float2 *>(p.dz + ro + a0)[q] = make_float2(dv[2 * q], dv[2 * q + 1]);
     }
   } else {
     RowTable t;
-    row_table(v, A, t);
+    row_table(v, W, t);
     int e;
     if (mode == kDecode) {
       DecState s;
@@ -418,17 +436,17 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
       }
       x = __shfl_sync(kFull, x, 0);
       uint32_t cum, freq;
-      e = symbol_of(v, A, t, x, cum, freq);
+      e = symbol_of(v, W, t, x, cum, freq);
       if (lane == 0) {
         dec_consume(s, rr, cum, freq, buf, cap);
         p.dec[r] = s;
-        p.tokens[tpos] = (uint16_t)e;
+        p.tokens[tpos] = (uint16_t)(base + e);
       }
     } else {
-      e = p.tokens[tpos];
+      e = (int)p.tokens[tpos] - base;
       if (mode == kEncode) {
         uint32_t cum, freq;
-        symbol_interval(v, A, t, e, cum, freq);
+        symbol_interval(v, W, t, e, cum, freq);
         if (lane == 0) {
           EncState s = p.enc[r];
           enc_code24(s, cum, freq, buf, cap, p.err);
@@ -438,9 +456,9 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
     }
     // Backward Controller inputs: mean cross entropy over the group's predicted lanes
     int a0, n;
-    lane_chunk(A, lane, a0, n);
-    float *dz = p.dz + (size_t)r * A;
-    __nv_bfloat16 *dzb = p.dz_b ? p.dz_b + (size_t)r * A : nullptr;
+    lane_chunk(W, lane, a0, n);
+    float *dz = p.dz + ro;
+    __nv_bfloat16 *dzb = p.dz_b ? p.dz_b + ro : nullptr;
     for (int a = a0; a < a0 + n; ++a) {
       float P = t.prob(v, a);
       if (outP) outP[a] = P;
@@ -595,10 +613,12 @@ __global__ void range_decode_kernel(const uint32_t *freq, const uint8_t *in, con
 
 void launch_mixcode(const Plan &p, int T, cudaStream_t st) {
   if (p.NL <= 0) return;
-  // reads L^u and L^m, writes dL^m: 12 bytes per predicted row and symbol
-  ProfScope ps("mix_cdf_code", 0, 12.0 * prof_work().pred_rows * p.dm.A, st);
+  // reads L^u and L^m over the coded symbols (8 bytes each) and writes the whole row of dL^m
+  const double wc = p.ov_w > 0 ? p.ov_w : p.dm.A;
+  ProfScope ps("mix_cdf_code", 0, prof_work().pred_rows * (8.0 * wc + 4.0 * p.dm.A), st);
   const unsigned grid = (unsigned)((p.NL * 32 + 255) / 256);
-  switch (p.dm.A) {  // register-resident rows where a lane's chunk fits in registers
+  // every predicted row is coded over W symbols (the slice with overlap masking)
+  switch (p.ov_w > 0 ? p.ov_w : p.dm.A) {  // register-resident rows where a lane's chunk fits in registers
     case 64: launch_pdl(mixcode_kernel<2>, dim3(grid), dim3(256), 0, st, p, T); break;
     case 256: launch_pdl(mixcode_kernel<8>, dim3(grid), dim3(256), 0, st, p, T); break;
     case 1024: launch_pdl(mixcode_kernel<32>, dim3(grid), dim3(256), 0, st, p, T); break;
