@@ -52,6 +52,10 @@ extern "C" {
 /* BF16 batched, with the frozen static predictor in FP8 (E4M3 weights with one scale per
    channel, E4M3 activations): see pmklc_quantize_static_fp8 */
 #define PMKLC_BF16_FP8STATIC 2
+/* BF16 batched, with the frozen static predictor's embedding and hidden layer in FP8 (E4M3
+   embedding, E4M3 W1 with one scale per hidden unit; h written in BF16) and its logits layer in
+   BF16: the logits layer's E4M3 weights carry almost all of PMKLC_BF16_FP8STATIC's loss */
+#define PMKLC_BF16_FP8HIDDEN 3
 /* optimisers */
 #define PMKLC_ADAM 0
 #define PMKLC_SGD 1
@@ -71,7 +75,7 @@ typedef struct {
   uint32_t emb_s, ctx_s, hid_s;/* static predictor: embedding E, context t, hidden H */
   uint32_t emb_d, ctx_d, hid_d;/* dynamic predictor (trained online, §4.2.4) */
   uint32_t lanes_per_block;    /* M: parallel sub-streams per block (bs, §5.8); 0 = default */
-  uint32_t precision;          /* PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED or PMKLC_BF16_FP8STATIC */
+  uint32_t precision;          /* PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED, PMKLC_BF16_FP8STATIC or PMKLC_BF16_FP8HIDDEN */
   uint32_t optimizer;          /* PMKLC_ADAM or PMKLC_SGD */
   float lr;                    /* learning rate of the Backward Controller (§4.2.6) */
   float alpha_init;            /* initial mixing weight alpha of Eq. (1) */
@@ -271,7 +275,8 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
  * rounded to nearest even and saturated at 448, both divisions in FP32.
  * Channels: the whole embedding table; each hidden unit (a row of W1t); each
  * logit (a column of W2).  The compressor applies this to the static weights
- * when cfg->precision is PMKLC_BF16_FP8STATIC; the entry point exposes it.
+ * when cfg->precision is PMKLC_BF16_FP8STATIC (PMKLC_BF16_FP8HIDDEN uses the
+ * embedding and W1 codes only); the entry point exposes it.
  *   d_params: device FP32 parameters (layout above) of shape (k, E, t, H);
  *     E must be a multiple of 16 for the FP8 forward (not checked here).
  *   d_codes: device, 4^k*E + H*t*E + 4^k*H bytes: Emb codes [A][E], W1t codes

@@ -25,7 +25,9 @@ Readings where the paper is silent:
            g - 2^floor(log2 g), start[g] = (floor(log2 g)+1)*ceil(f*max L).
   FP8      precision 2: the frozen static predictor runs in its FP8 form
            (fp8.py: E4M3 weights with per-channel scales, E4M3 activations with
-           a per-row scale); the dynamic predictor is unchanged.
+           a per-row scale); precision 3: its embedding and hidden layer in that
+           form, its logits layer with the stored weights; the dynamic predictor
+           is unchanged.
   mask     overlap_mask = 1 (not in the paper): with s < k, token j >= 1 of a
            lane shares its first k - s digits with token j - 1, so only the
            4^s tokens of the slice [p 4^s, (p+1) 4^s), p = e_{j-1} mod
@@ -298,8 +300,8 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
     """Run the lockstep loop over all blocks (groups) in compress or decompress mode."""
     dshape, sshape = cfg.dm_shape, cfg.static_shape
     S = (1 if cfg.use_static else 0, 0, 1)
-    # precision 2: the frozen static model in its FP8 form (fp8.py), else as stored
-    fq = fp8.quantize_model(static_w, sshape) if cfg.use_static and cfg.precision == 2 else None
+    # precision 2 / 3: the frozen static model in its FP8 / FP8-hidden form (fp8.py), else as stored
+    fq = fp8.quantize_model(static_w, sshape) if cfg.use_static and cfg.precision in (2, 3) else None
     t_eff, A = cfg.t_eff, cfg.A
     lr = cfg.f32("lr")
     uni = TOTAL // A
@@ -346,7 +348,12 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
             Lu = None
             if cfg.use_static:
                 cs = np.stack([_ctx(b.tokens, b.starts[r], j, cfg.ctx_s) for r in pred])
-                Lu = fp8.forward(fq, cs) if fq is not None else forward(static_w, sshape, cs)[3]
+                if fq is None:
+                    Lu = forward(static_w, sshape, cs)[3]
+                elif cfg.precision == 3:
+                    Lu = fp8.forward_hidden(fq, static_w, cs)
+                else:
+                    Lu = fp8.forward(fq, cs)
             z = mix(Lu, Lm, st.alpha, S)
             sl = [_slice(cfg, b, r, j) for r in pred]
             P = np.zeros_like(z)  # the distribution coded: softmax over each row's slice

@@ -23,6 +23,9 @@ FP8 forward of the static predictor (the kernels' quantisation points):
     h  = relu(a)
     s_r = max_h h / 448  (1 if the row is all zero),  h_q = encode(h / s_r)
     L  = (h_q . W2_q) * (s_r * s_2[a]) + b2
+FP8-hidden form (precision 3): the embedding and W1 as above, h unrounded, the logits layer
+with the stored (FP32) W2 and b2:
+    a  = (X_q . W1_q^T) * (s_emb * s_1[h]) + b1,   h = relu(a),   L = h . W2 + b2
 Pins (tests): every finite code decodes and re-encodes to itself; the format's
 landmarks (1.0, 448, the smallest normal and subnormal, NaN); ties to even;
 saturation; brute-force nearest-code search; each channel's largest magnitude
@@ -121,3 +124,14 @@ def forward(fq: dict, ctx: np.ndarray) -> np.ndarray:
     s_r = np.where(amax > 0, amax / MAX, 1.0)
     hq = decode(encode(h / s_r[:, None]))
     return (hq @ decode(fq["w2t"]).T) * (s_r[:, None] * fq["s_w2"].astype(np.float64)[None, :]) + fq["b2"]
+
+
+def forward_hidden(fq: dict, flat: np.ndarray, ctx: np.ndarray) -> np.ndarray:
+    """Static logits [R, A] of the FP8-hidden form: E4M3 embedding and W1, stored W2 (float64)."""
+    shape = fq["shape"]
+    ctx = np.asarray(ctx, dtype=np.int64).reshape(-1, shape.t)
+    xq = decode(fq["emb"])[ctx].reshape(ctx.shape[0], shape.t * shape.E)
+    a = (xq @ decode(fq["w1t"]).T) * (np.float64(fq["s_emb"]) * fq["s_w1"].astype(np.float64)) + fq["b1"]
+    h = np.maximum(a, 0.0)
+    _, _, _, w2, b2 = views(np.asarray(flat, dtype=np.float32).astype(np.float64), shape)
+    return h @ w2 + b2

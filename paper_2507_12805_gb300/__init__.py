@@ -23,7 +23,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 PMKLC_OK, PMKLC_EINVAL, PMKLC_ENOMEM, PMKLC_ECUDA = 0, -1, -2, -3
 PMKLC_ECORRUPT, PMKLC_EMODEL, PMKLC_ETIMEOUT, PMKLC_ENOSPC = -4, -5, -6, -7
-PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED, PMKLC_BF16_FP8STATIC = 0, 1, 2
+PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED, PMKLC_BF16_FP8STATIC, PMKLC_BF16_FP8HIDDEN = 0, 1, 2, 3
 PMKLC_ADAM, PMKLC_SGD = 0, 1
 PMKLC_SMP_NONE, PMKLC_SMP_CHAIN, PMKLC_SMP_TREE = 0, 1, 2
 

@@ -156,7 +156,11 @@ struct Cfg {
 };
 
 // the BF16 batched forms (the static model in BF16 or in FP8)
-bool bf_form(int precision) { return precision == PMKLC_BF16_BATCHED || precision == PMKLC_BF16_FP8STATIC; }
+bool bf_form(int precision) {
+  return precision == PMKLC_BF16_BATCHED || precision == PMKLC_BF16_FP8STATIC || precision == PMKLC_BF16_FP8HIDDEN;
+}
+// the forms whose static model runs (at least partly) in E4M3 on the tcgen05 engine
+bool f8_form(int precision) { return precision == PMKLC_BF16_FP8STATIC || precision == PMKLC_BF16_FP8HIDDEN; }
 
 int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!c || c->struct_size != sizeof(pmklc_model_cfg)) return PMKLC_EINVAL;
@@ -166,7 +170,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (c->use_static && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
                         c->hid_s > 65535 || !c->static_weights))
     return PMKLC_EINVAL;
-  if (c->precision > PMKLC_BF16_FP8STATIC) return PMKLC_EINVAL;
+  if (c->precision > PMKLC_BF16_FP8HIDDEN) return PMKLC_EINVAL;
   if (c->optimizer > PMKLC_SGD || c->smp_mode > PMKLC_SMP_TREE || c->count_order > 7) return PMKLC_EINVAL;
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
@@ -404,20 +408,25 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.hs_rowmax = nullptr;
   if (bf_form(c.precision)) {
     p.wbf = ar.alloc<__nv_bfloat16>(G * p.P);
-    if (c.use_static && d_static && c.precision == PMKLC_BF16_FP8STATIC) {
-      // the frozen static model in E4M3 with per-channel scales (fp8static.cu)
+    if (c.use_static && d_static && f8_form(c.precision)) {
+      // the frozen static model in E4M3 with per-channel scales (fp8static.cu); the FP8-hidden
+      // form keeps a BF16 copy for its logits layer instead of the FP8 activations' row maxima
+      const bool hidden_only = c.precision == PMKLC_BF16_FP8HIDDEN;
       uint8_t *codes = ar.alloc<uint8_t>(fp8_code_bytes(c.st));
       float *scales = ar.alloc<float>(fp8_scale_count(c.st));
       float *c1 = ar.alloc<float>(c.st.H);
-      unsigned *rmax = ar.alloc<unsigned>(NL);
+      unsigned *rmax = hidden_only ? nullptr : ar.alloc<unsigned>(NL);
+      __nv_bfloat16 *sb = hidden_only ? ar.alloc<__nv_bfloat16>(c.st.count()) : nullptr;
       if (ar.failed) return PMKLC_ENOMEM;
       launch_quantize_fp8(d_static, c.st, codes, scales, ar.st);
       launch_fp8_hidden_scale(scales, c.st, c1, ar.st);
-      cudaMemsetAsync(rmax, 0, sizeof(unsigned) * NL, ar.st);
+      if (rmax) cudaMemsetAsync(rmax, 0, sizeof(unsigned) * NL, ar.st);
+      if (sb) launch_to_bf16(d_static, sb, c.st.count(), ar.st);
       p.st8 = codes;
       p.st8_c1 = c1;
       p.st8_s2 = scales + 1 + c.st.H;
       p.hs_rowmax = rmax;
+      p.static_bf = sb;
     } else if (c.use_static && d_static) {
       __nv_bfloat16 *sb = ar.alloc<__nv_bfloat16>(c.st.count());
       if (sb) launch_to_bf16(d_static, sb, c.st.count(), ar.st);
@@ -852,7 +861,7 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.count_order = h[11];
   c.fallback = (h[7] >> 1) & 3;
   if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 ||
-      c.fallback > 2 || c.precision > PMKLC_BF16_FP8STATIC)
+      c.fallback > 2 || c.precision > PMKLC_BF16_FP8HIDDEN)
     return PMKLC_ECORRUPT;
   int A = 1 << (2 * c.k);
   c.dm = Dims{A, get_le<uint16_t>(h + 12), get_le<uint16_t>(h + 14), get_le<uint16_t>(h + 16)};
@@ -1451,7 +1460,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
     else
       launch_forward(R.p, T, st);
     // the FP8 form returns the static model's logits (pmklc_predict runs the model as the static one)
-    const float *src = c.precision == PMKLC_BF16_FP8STATIC ? R.p.zu : R.p.zm;
+    const float *src = f8_form(c.precision) ? R.p.zu : R.p.zm;
     cudaMemcpyAsync(d_logits_only, src, sizeof(float) * rows * c.A(), cudaMemcpyDeviceToDevice, st);
   } else if (bf) {
     std::vector<unsigned long long> off(rows, 0);
@@ -1494,7 +1503,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
 int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t H, const uint16_t *d_ctx,
                   size_t rows, uint32_t precision, float *d_logits, void *stream) {
   return guarded<int>([&]() -> int {
-    if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_FP8STATIC ||
+    if (k < 1 || k > 8 || !E || !t || !H || precision > PMKLC_BF16_FP8HIDDEN ||
         (rows && (!d_params || !d_ctx || !d_logits)))
       return PMKLC_EINVAL;
     if (rows == 0) return PMKLC_OK;
@@ -1503,7 +1512,7 @@ int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uin
     pmklc_model_cfg mc;
     pmklc_default_cfg(&mc, 1, k, E, t, H);
     mc.precision = precision;
-    if (precision == PMKLC_BF16_FP8STATIC) {  // the model runs as the frozen static predictor in FP8
+    if (f8_form((int)precision)) {  // the model runs as the frozen static predictor in its FP8 form
       mc.use_static = 1;
       mc.emb_s = E, mc.ctx_s = t, mc.hid_s = H;
       mc.static_weights = d_params;  // only checked non-null
@@ -1511,7 +1520,7 @@ int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uin
     Cfg c;
     int rc = check_cfg(&mc, c);
     if (rc) return rc;
-    if (precision == PMKLC_BF16_FP8STATIC)
+    if (f8_form((int)precision))
       return one_step(c, 1, (uint32_t)rows, const_cast<float *>(d_params), nullptr, nullptr, nullptr, nullptr, nullptr,
                       d_params, d_ctx, nullptr, 1, nullptr, nullptr, nullptr, d_logits, (cudaStream_t)stream);
     // a throw-away copy of the parameters: the forward never writes them, but the plan wants a mutable pointer

@@ -691,8 +691,9 @@ struct HiddenF8 : TBase {
   struct Epi {
     const long long *tp;
     const float *c1, *b1;
-    float *hs;       // row 0 of the group
+    float *hs;       // row 0 of the group (FP32 h for the E4M3 logits layer)
     unsigned *rmax;  // row 0 of the group
+    bf16 *hb;        // row 0 of the group (BF16 h for the BF16 logits layer), else nullptr
     int H;
     __device__ void epilogue(int m, int rl, int n, const float *v) const {
       if (tp[rl] < 0) return;
@@ -703,14 +704,21 @@ struct HiddenF8 : TBase {
         x[j] = a > 0.f ? a : 0.f;  // +0 below zero (its bits must order as a float)
         mx = fmaxf(mx, x[j]);
       }
+      if (hb) {
+        *reinterpret_cast<uint4 *>(hb + (size_t)m * H + n) = pack8(x);
+        return;
+      }
       store8(hs + (size_t)m * H + n, x);
       atomicMax(rmax + m, __float_as_uint(mx));
     }
   };
   __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
     const int r0 = row(z, 0);
+    if (p.precision == PMKLC_BF16_FP8HIDDEN)
+      return {tp(meta), p.st8_c1, p.static_params + p.st.off_b1(), nullptr, nullptr,
+              p.hs_b + (size_t)r0 * p.st.H, p.st.H};
     return {tp(meta), p.st8_c1, p.static_params + p.st.off_b1(), p.hs + (size_t)r0 * p.st.H, p.hs_rowmax + r0,
-            p.st.H};
+            nullptr, p.st.H};
   }
 };
 
@@ -997,7 +1005,8 @@ bool build(TcSetup &S, const Plan &p) {
     const uint64_t d2[2] = {(uint64_t)Sd.H, (uint64_t)Sd.A}, s2[1] = {(uint64_t)Sd.H};
     ok &= make_map(&S.w2_8, w2c, 2, d2, s2, S.t_l8.nt, true);
   }
-  if (p.use_static && !f8) {
+  // the BF16 static model, or the BF16 logits layer of the FP8-hidden form (its W1 map unused)
+  if (p.use_static && (!f8 || p.precision == PMKLC_BF16_FP8HIDDEN)) {
     const uint64_t d1[2] = {(uint64_t)Sd.K1(), (uint64_t)Sd.H}, s1[1] = {(uint64_t)Sd.K1() * 2};
     ok &= make_map(&S.w1k[1], p.static_bf + Sd.off_w1(), 2, d1, s1, S.t_h.nt);
     const uint64_t d2[2] = {(uint64_t)Sd.A, (uint64_t)Sd.H}, s2[1] = {(uint64_t)Sd.A * 2};
@@ -1060,38 +1069,44 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which) {
   const double R = prof_work().pred_rows;
   const bool stat = p.use_static && (which & kFwdStatic), dyn = (which & kFwdDynamic) != 0;
   const bool f8 = p.use_static && p.st8 != nullptr;  // static model on its own E4M3 launches
+  const bool f8_logits = f8 && p.precision != PMKLC_BF16_FP8HIDDEN;  // its logits layer in E4M3 too
   if (stat && f8) {
-    {
-      ProfScope ps("fwd_hidden_static_fp8", 2.0 * R * p.st.K1() * p.st.H, 0, st);
-      HiddenF8 op;
-      op.p = p, op.T = T, op.ml = S.ml_h8, op.w1 = S.w1_8, op.table = S.table_h8;
-      tc::launch(op, p.Mmax, p.st.H, p.G, S.t_h8, S.ml_h8.bytes(), st);
-    }
+    ProfScope ps("fwd_hidden_static_fp8", 2.0 * R * p.st.K1() * p.st.H, 0, st);
+    HiddenF8 op;
+    op.p = p, op.T = T, op.ml = S.ml_h8, op.w1 = S.w1_8, op.table = S.table_h8;
+    tc::launch(op, p.Mmax, p.st.H, p.G, S.t_h8, S.ml_h8.bytes(), st);
+  }
+  if (stat && f8_logits) {
     ProfScope ps("fwd_logits_static_fp8", 2.0 * R * p.st.H * p.st.A, 0, st);
     LogitsF8 op;
     op.p = p, op.T = T, op.ml = S.ml_l8, op.w2 = S.w2_8;
     tc::launch(op, p.Mmax, p.st.A, p.G, S.t_l8, S.ml_l8.bytes(), st);
   }
-  // BF16 problems: z < G dynamic models, z >= G the static model; one launch covers [zb, zb + Z)
-  const bool sbf = stat && !f8;
-  if (!dyn && !sbf) return;
-  const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (sbf ? p.G : 0);
-  const char *hname = dyn && sbf ? "fwd_hidden_bf16" : dyn ? "fwd_hidden_dyn_bf16" : "fwd_hidden_static_bf16";
-  const char *lname = dyn && sbf ? "fwd_logits_bf16" : dyn ? "fwd_logits_dyn_bf16" : "fwd_logits_static_bf16";
-  {
-    double fl = (dyn ? 2.0 * R * p.dm.K1() * p.dm.H : 0.0) + (sbf ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
+  // BF16 problems: z < G dynamic models, z >= G the static model; one launch covers [zb, zb + Z).
+  // The static hidden layer runs here in the BF16 form, its logits layer in the BF16 and the
+  // FP8-hidden forms (after HiddenF8 wrote its BF16 h)
+  const bool s_hid = stat && !f8, s_log = stat && !f8_logits;
+  if (dyn || s_hid) {
+    const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (s_hid ? p.G : 0);
+    const char *hname = dyn && s_hid ? "fwd_hidden_bf16" : dyn ? "fwd_hidden_dyn_bf16" : "fwd_hidden_static_bf16";
+    double fl = (dyn ? 2.0 * R * p.dm.K1() * p.dm.H : 0.0) + (s_hid ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
     ProfScope ps(hname, fl, 0, st);
     HiddenT op;
     op.p = p, op.T = T, op.ml = S.ml_h, op.w1[0] = S.w1k[0], op.w1[1] = S.w1k[1], op.zb = zb;
     op.table[0] = S.table_h[0], op.table[1] = S.table_h[1];
     tc::launch(op, p.Mmax, p.use_static ? max(p.dm.H, p.st.H) : p.dm.H, Z, S.t_h, S.ml_h.bytes(), st);
   }
-  double fl = (dyn ? 2.0 * R * p.dm.H * p.dm.A : 0.0) + (sbf ? 2.0 * R * p.st.H * p.st.A : 0.0);
-  ProfScope ps(lname, fl, 0, st);
-  LogitsT op;
-  op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0], op.w2[1] = S.w2mn[1];
-  op.zb = zb;
-  tc::launch(op, p.Mmax, p.dm.A, Z, S.t_l, S.ml_l.bytes(), st);
+  if (dyn || s_log) {
+    const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (s_log ? p.G : 0);
+    const char *lname = dyn && s_log ? "fwd_logits_bf16" : dyn ? "fwd_logits_dyn_bf16" : "fwd_logits_static_bf16";
+    double fl = (dyn ? 2.0 * R * p.dm.H * p.dm.A : 0.0) + (s_log ? 2.0 * R * p.st.H * p.st.A : 0.0);
+    ProfScope ps(lname, fl, 0, st);
+    LogitsT op;
+    op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0],
+    op.w2[1] = S.w2mn[1];
+    op.zb = zb;
+    tc::launch(op, p.Mmax, p.dm.A, Z, S.t_l, S.ml_l.bytes(), st);
+  }
 }
 
 void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss) {

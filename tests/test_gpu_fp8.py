@@ -1,6 +1,7 @@
 """The frozen static predictor in FP8 (E4M3): the quantiser's codes and scales equal the oracle's
 bit for bit; the FP8 forward (kind::f8f6f4 GEMMs) matches the oracle's FP8 forward; compress /
-decompress round trips with the FP8 static model and stays within 0.5 % of the oracle's size."""
+decompress round trips with the FP8 static model and stays within 0.5 % of the oracle's size.
+The same for the FP8-hidden form (E4M3 embedding and hidden layer, BF16 logits layer)."""
 import numpy as np
 import pytest
 
@@ -108,3 +109,37 @@ def test_fp8_rejects_unsupported_static_shape(P):
     with pytest.raises(P.PmklcError) as e:
         P.pmklc_compress(seq, [3000], P.ModelConfig(**kw, static_weights=sw, precision=P.PMKLC_BF16_FP8STATIC))
     assert e.value.rc == P.PMKLC_EINVAL
+
+
+@pytest.mark.parametrize("k,E,t,H,rows", [(4, 32, 8, 128, 130), (6, 32, 8, 256, 70)])
+def test_fp8_hidden_forward_matches_oracle(P, torch, k, E, t, H, rows):
+    """pmklc_predict in the FP8-hidden form against the oracle's: the same E4M3 embedding and W1
+    codes, h rounded to BF16 and W2 in BF16 on the GPU (FP64 and the stored W2 in the oracle), so
+    the bars are the BF16 form's (probabilities within 2e-2)."""
+    rng = np.random.default_rng(k * 37 + rows)
+    sh = Shape(4 ** k, E, t, H)
+    w = _model(sh, 7 + k, zero_rows=False)
+    ctx = rng.integers(0, sh.A, (rows, t))
+    want = fp8.forward_hidden(fp8.quantize_model(w, sh), w, ctx)
+    d_out = torch.zeros((rows, sh.A), dtype=torch.float32, device="cuda")
+    P.pmklc_predict(dev(torch, w), k, E, t, H, dev(torch, ctx.astype(np.uint16).view(np.int16)), d_out,
+                    precision=P.PMKLC_BF16_FP8HIDDEN)
+    got = d_out.cpu().numpy().astype(np.float64)
+    assert np.abs(softmax(got) - softmax(want)).max() < 2e-2
+    assert np.median(np.abs(got - want)) < 1e-2 * np.abs(want).max()
+
+
+def test_fp8_hidden_round_trip_and_size_against_oracle(P):
+    seq = synth.markov(12000, 5, 0.40, 1002).tobytes()
+    kw = dict(s=2, k=4, use_static=True, emb_s=32, ctx_s=8, hid_s=128, emb_d=16, ctx_d=8, hid_d=64,
+              lanes_per_block=8, count_order=5, smp_mode=2, fallback=0)
+    sw = _model(Shape(256, 32, 8, 128), 2001, zero_rows=False)
+    lens = [4096, 4096, 3808]
+    cfg = P.ModelConfig(**kw, static_weights=sw, precision=P.PMKLC_BF16_FP8HIDDEN)
+    out = P.pmklc_compress(seq, lens, cfg)
+    back, bl = P.pmklc_decompress(out, sw)
+    assert back == seq and list(bl) == lens
+    ref = ocodec.compress(seq, lens, ocodec.Config(**kw, precision=3), sw)
+    assert out[:80] == ref[:80]
+    assert abs(len(out) - len(ref)) <= 0.005 * len(ref), (len(out), len(ref))
+    assert ocodec.parse_header(out)[0].precision == 3

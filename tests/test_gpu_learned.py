@@ -63,7 +63,12 @@ def test_fp8_static_form_bits_close_to_fp32(P, data):
     fp32 = _size(P, held, lens, trained, P.PMKLC_FP32_PLAIN)
     bf16 = _size(P, held, lens, trained, P.PMKLC_BF16_BATCHED)
     fp8 = _size(P, held, lens, trained, P.PMKLC_BF16_FP8STATIC)
+    fp8h = _size(P, held, lens, trained, P.PMKLC_BF16_FP8HIDDEN)
     n = held.size
+    print(f"bits/base: FP8-hidden {8 * fp8h / n:.4f} ({(fp8h - fp32) / fp32:+.3%} vs FP32)")
+    # E4M3 embedding and hidden layer, BF16 logits layer: within the 0.3 % a frozen FP8 static
+    # model must stay within (the logits layer's E4M3 weights carry the FP8 form's loss)
+    assert abs(fp8h - fp32) <= 0.003 * fp32
     print(f"bits/base: FP32 {8 * fp32 / n:.4f}, BF16 {8 * bf16 / n:.4f} ({(bf16 - fp32) / fp32:+.3%}), "
           f"FP8 static {8 * fp8 / n:.4f} ({(fp8 - fp32) / fp32:+.3%} vs FP32, {(fp8 - bf16) / bf16:+.3%} vs BF16)")
     assert abs(bf16 - fp32) <= 0.005 * fp32

@@ -42,7 +42,7 @@ def _patched(data: bytes, offset: int, fmt: str, value) -> bytes:
     (5, "<B", 0),          # s = 0
     (5, "<B", 5),          # s > k
     (6, "<B", 9),          # k > 8 (and s <= k)
-    (8, "<B", 3),          # precision
+    (8, "<B", 4),          # precision
     (9, "<B", 2),          # optimiser
     (10, "<B", 3),         # SMP mode
     (11, "<B", 8),         # count order
@@ -97,7 +97,7 @@ def test_short_inputs_are_corrupt(P, container, cut):
     assert _rc(P, lambda: P.pmklc_decompress(container[:cut])) == P.PMKLC_ECORRUPT
 
 
-@pytest.mark.parametrize("change", [dict(s=5, k=4), dict(s=1, k=9), dict(precision=3), dict(optimizer=2),
+@pytest.mark.parametrize("change", [dict(s=5, k=4), dict(s=1, k=9), dict(precision=4), dict(optimizer=2),
                                     dict(smp_mode=3), dict(count_order=8), dict(fallback=3),
                                     dict(emb_d=0), dict(smp_fraction=1.5), dict(lanes_per_block=(1 << 20) + 1)])
 def test_invalid_configurations_are_rejected(P, change):

@@ -29,6 +29,8 @@ CASES = [
     dict(s=4, k=5, lanes_per_block=1),
     dict(lanes_per_block=50),
     dict(lanes_per_block=40, lane_tokens=30),
+    dict(precision=2, fallback=0),
+    dict(precision=3, fallback=0),
 ]
 
 

@@ -93,3 +93,24 @@ def test_fp8_forward_within_activation_rounding_bound():
 @pytest.mark.parametrize("bad", [np.float32(np.inf), np.float32(-np.inf)])
 def test_infinities_saturate(bad):
     assert fp8.decode(fp8.encode(bad)) == np.sign(bad) * 448.0
+
+
+def test_fp8_hidden_forward_is_the_plain_forward_with_e4m3_embedding_and_w1():
+    """The FP8-hidden form equals the plain forward of the model whose embedding and W1 are the
+    dequantised E4M3 values and whose b1, W2 and b2 are the stored ones, element by element."""
+    shape = Shape(16, 8, 3, 16)
+    rng = np.random.default_rng(9)
+    flat = (init_params(shape, 6) + rng.normal(0, 0.05, shape.count)).astype(np.float32)
+    fq = fp8.quantize_model(flat, shape)
+    deq = fp8.dequantize_model(fq)
+    mixed = flat.astype(np.float64).copy()
+    off = shape.offsets()
+    for name in ("emb", "w1"):
+        lo, hi = off[name]
+        mixed[lo:hi] = deq[lo:hi]
+    ctx = np.array(list(itertools.product(range(16), repeat=3))[:300])
+    got = fp8.forward_hidden(fq, flat, ctx)
+    want = forward(mixed, shape, ctx)[3]
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+    # the logits layer really is the stored one: the FP8 form (E4M3 W2 and h) differs
+    assert np.max(np.abs(fp8.forward(fq, ctx) - got)) > 1e-6
