@@ -167,3 +167,81 @@ def test_count_model_totals_stay_below_2_13_with_1024_lanes():
             assert -math.log2(f.min() / tot) < 13
         t.finish_substep(lanes, bases.tolist())
     assert 2 * 4 * (countmodel.LIMIT - 1) + 4 >= worst > 4 * countmodel.LIMIT  # reached the high range
+
+
+def _two_lane_golden():
+    """The two hand-worked multi-lane examples of tests/golden/countmodel_two_lanes.txt."""
+    sections, cur = {}, None
+    for line in open(os.path.join(GOLDEN, "countmodel_two_lanes.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = line.split()
+        if w[0] in ("lanes", "halving"):
+            cur = sections[w[0]] = {"args": w[1:], "rows": []}
+        else:
+            cur["rows"].append(w)
+    return sections
+
+
+def test_count_model_lanes_share_one_table_hand_worked():
+    """Lane streams (k digits of a lane's first token, then s per later token), one table per block
+    read by every lane before any lane adds, and cross-lane sharing of counts, against a two-lane
+    example worked by hand (the oracle's lane coder, recording what it codes)."""
+    from oracle import codec
+    g = _two_lane_golden()["lanes"]
+    block, s_, k_, m, M = g["args"][0], *map(int, g["args"][1:])
+    cfg = codec.Config(s=s_, k=k_, emb_d=2, ctx_d=2, hid_d=2, lanes_per_block=M, fallback=2, count_order=m)
+    (b,), _ = codec._prepare(cfg, [base_codes(block.encode())])
+    seen = []
+
+    class Recorder:
+        def __init__(self, r):
+            self.r = r
+
+        def encode(self, cum, freq, total):
+            seen.append((self.r, Fraction(freq, total), cum))
+
+    b.count_encode, b.cenc, b.table = True, [Recorder(r) for r in range(len(b.lens))], countmodel.Table(m, len(b.lens))
+    got = []
+    for j in range(max(b.lens)):
+        before = len(seen)
+        codec._count_step(cfg, b, j)
+        live = sorted({r for r, _, _ in seen[before:]})
+        per_lane = {r: 0 for r in live}
+        for r, q, cum in seen[before:]:
+            got.append((j, per_lane[r], r, q, cum))
+            per_lane[r] += 1
+    want = [(int(st), int(sub), int(lane), Fraction(q)) for st, sub, lane, base, q in g["rows"]]
+    assert [(j, sub, r, q) for j, sub, r, q, _ in got] == want
+    # the coded base is the one worked by hand: A alone starts at cumulative frequency 0
+    for (j, sub, r, q, cum), row in zip(got, g["rows"]):
+        assert (row[3] == "A") == (cum == 0)
+
+
+def test_count_model_halving_once_per_context_hand_worked():
+    """Two lanes in one context at the halving limit: both read the old counts, the context is halved
+    once after both have added (hand-worked)."""
+    g = _two_lane_golden()["halving"]
+    m = int(g["args"][0])
+    t = countmodel.Table(m, 2)
+    ctx0, counts0 = g["args"][1].split(":")
+    t.c["ACGT".index(ctx0)] = [int(x) for x in counts0.split(",")]
+    rows = g["rows"]
+    i = 0
+    while i < len(rows):
+        sub = [r for r in rows[i:] if r[0] != "after"]
+        sub = sub[:2]
+        lanes, bases = [], []
+        for sub_i, lane, ctx, base, q in sub:
+            t.ctx[int(lane)] = "ACGT".index(ctx)
+        for sub_i, lane, ctx, base, q in sub:
+            f, tot = t.freqs(int(lane))
+            assert Fraction(int(f["ACGT".index(base)]), tot) == Fraction(q), (sub_i, lane)
+            lanes.append(int(lane))
+            bases.append("ACGT".index(base))
+        t.finish_substep(lanes, bases)
+        i += len(sub)
+        assert rows[i][0] == "after"
+        ctx, counts = rows[i][1].split(":")
+        assert t.c["ACGT".index(ctx)].tolist() == [int(x) for x in counts.split(",")]
+        i += 1
