@@ -1,23 +1,30 @@
-"""Benchmark: compress + decompress MB/s of the learned DNA compressor on GB300.
+"""Benchmark: compress and decompress MB/s of the learned DNA compressor on GB300.
 
 One step = compress + decompress of the whole workload (every row of the hot
 path: tokenise, static + dynamic predictor forward, Eq. (1) mixer, CDF, range
 coding, Backward Controller update, step-wise model passing, count-model
 judge).  `value` is the paper's Eq. (4) throughput THP = size / (CT + DT) in
 MB/s (10^6 bases), with the input resident in device memory when the timed
-region starts; `e2e` is the same metric through the host-buffer C-ABI calls
-(host->device and device->host copies inside the timed region).
+region starts; compress and decompress MB/s are reported apart; `e2e` is the
+same metric through the host-buffer C-ABI calls (host->device and device->host
+copies inside the timed region).
 
-Default workload ("plain"): 2^24 bases from a seeded order-5 Markov source
-(GC 0.40), 64 blocks of 2^18, (s,k) = (2,4), static + dynamic MLP predictors
-(E 32, t 32, H 128), tree step-wise model passing, count-model judge.  Both
-forms run: the FP32 plain form (64 lanes per block) and the BF16 batched form
-(lanes per block autotuned on 8 blocks), which is the headline `value`; the
-FP32 figures are reported under `fp32_plain`.  Every step is preceded by a
-256 MB write that flushes the 129 MB L2.  SM clocks and throttle reasons are
-sampled with nvidia-smi during the measurement; one that saw a hardware or
-thermal slowdown is taken once more (`clocks.remeasured`).  `--block-bases` cuts every block
-(the same per-step shapes, fewer steps) for profiling runs.
+Default workload ("human"): 2^28 bases of a human-like synthetic genome (GC
+0.41, CpG depleted 4x, 10 % Alu-like repeat families, 5 % tandem repeats), 1024
+blocks of 2^18, (s,k) = (3,6), static + dynamic MLP predictors (E 32, t 64,
+H 256), overlap-masked coding, tree step-wise model passing, count-model judge.
+The static model is pre-trained by the library (pmklc_train_model) on 2^25
+bases of another genome of the same species (cached under .cache/).  Both
+forms run: the BF16 batched form (lanes per block autotuned on 8 blocks) is the
+headline `value`; the FP32 plain form is timed on --fp32-steps steps and
+reported under `fp32_plain`.  Every step is preceded by a 256 MB write that
+flushes the 129 MB L2.  The library's sampled kernel profiler runs in a
+separate, untimed pass after the timed steps.  SM clocks and throttle reasons
+are sampled with nvidia-smi during the measurement; one that saw a hardware or
+thermal slowdown is taken once more (`clocks.remeasured`).  `--workload plain`
+runs the 2^24-base order-5 Markov workload ((s,k) = (2,4), H 128);
+`--block-bases` cuts every block (the same per-step shapes, fewer steps) for
+profiling runs.
 """
 from __future__ import annotations
 
@@ -37,11 +44,19 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (synth workload, model kwargs)
+    "human": ("human", dict(s=3, k=6, use_static=True, emb_s=32, ctx_s=64, hid_s=256, emb_d=32, ctx_d=64, hid_d=256,
+                            lanes_per_block=128, count_order=6, smp_mode=2, smp_fraction=0.05, overlap_mask=1,
+                            alpha_init=1.0)),
     "plain": ("plain", dict(s=2, k=4, use_static=True, emb_s=32, ctx_s=32, hid_s=128, emb_d=32, ctx_d=32, hid_d=128,
-                            lanes_per_block=64, count_order=6, smp_mode=2, smp_fraction=0.05)),
+                            lanes_per_block=64, count_order=6, smp_mode=2, smp_fraction=0.05, overlap_mask=1,
+                            alpha_init=1.0)),
     "tiny": ("tiny", dict(s=1, k=3, use_static=False, emb_d=16, ctx_d=16, hid_d=32, lanes_per_block=1,
-                          count_order=6, smp_mode=0)),
+                          count_order=6, smp_mode=0, overlap_mask=1)),
 }
+# pre-training of the static model: bases of the workload's species (synth.pretrain_corpus), epochs,
+# lanes, init seed.  With a pre-trained static model alpha starts at 1 (Eq. (1): the coder starts from
+# the static predictor alone and blends the dynamic model in as alpha learns).
+PRETRAIN = dict(bases=1 << 25, epochs=1, lanes=256, seed=2001)
 STATIC_SEED = 2001
 
 
@@ -144,10 +159,40 @@ def workload_name(name, w, kw) -> str:
     return f"{name}: {w.recipe}, {int(w.seq.size)} bases, {len(w.block_lens)} blocks, (s,k)=({kw['s']},{kw['k']})"
 
 
-def static_weights(P, kw):
+CACHE = os.path.join(ROOT, ".cache")
+
+
+def static_weights(P, name, kw):
+    """The workload's static model, pre-trained by the library's kernels (pmklc_train_model) on
+    PRETRAIN["bases"] bases of other genomes of the workload's species (synth.pretrain_corpus),
+    cached by its recipe; (weights, description).  Untimed."""
     if not kw.get("use_static"):
-        return None
-    return P.pmklc_init_model(kw["k"], kw["emb_s"], kw["ctx_s"], kw["hid_s"], STATIC_SEED)
+        return None, None
+    import hashlib
+    import synth
+    recipe = dict(PRETRAIN, workload=name, s=kw["s"], k=kw["k"], E=kw["emb_s"], t=kw["ctx_s"], H=kw["hid_s"],
+                  overlap_mask=kw.get("overlap_mask", 0), abi=P.pmklc_abi_version())
+    key = hashlib.sha1(json.dumps(recipe, sort_keys=True).encode()).hexdigest()[:16]
+    path = os.path.join(CACHE, f"static_{name}_{key}.npy")
+    t_train = None
+    if os.path.exists(path):
+        w = np.load(path)
+    else:
+        corpus = synth.pretrain_corpus(name, PRETRAIN["bases"], PRETRAIN["seed"])
+        cfg = P.ModelConfig(s=kw["s"], k=kw["k"], emb_d=kw["emb_s"], ctx_d=kw["ctx_s"], hid_d=kw["hid_s"],
+                            lanes_per_block=PRETRAIN["lanes"], precision=P.PMKLC_BF16_BATCHED, seed=PRETRAIN["seed"],
+                            overlap_mask=kw.get("overlap_mask", 0))
+        t0 = time.perf_counter()
+        w = P.pmklc_train_model(corpus, cfg, epochs=PRETRAIN["epochs"])
+        t_train = time.perf_counter() - t0
+        os.makedirs(CACHE, exist_ok=True)
+        np.save(path + ".tmp.npy", w)
+        os.replace(path + ".tmp.npy", path)
+    desc = {"kind": "pre-trained by pmklc_train_model (BF16 batched form)", "corpus": f"synth.pretrain_corpus"
+            f"('{name}', {PRETRAIN['bases']}, seed {PRETRAIN['seed']}): other genomes of the workload's species",
+            "epochs": PRETRAIN["epochs"], "lanes": PRETRAIN["lanes"], "init_seed": PRETRAIN["seed"],
+            "sha1": hashlib.sha1(w.astype(np.float32).tobytes()).hexdigest()[:16], "train_s": t_train, "cache": key}
+    return w, desc
 
 
 def peaks():
@@ -176,13 +221,16 @@ def oracle_threads() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(w, kw, sw, budget_s: float = 20.0):
-    """The oracle as it stands, on a bounded sample: the first blocks' leading bases."""
+# bases of the oracle's bounded sample (the first bases of block 0, coded as one block): about 10-30 s
+# of oracle work for cpu_baseline on the machine's host cores; the reference arm codes half of it per step
+CPU_SAMPLE = {"human": 1 << 16, "plain": 1 << 18, "tiny": 100_000}
+
+
+def cpu_baseline(name, w, kw, sw):
+    """The oracle as it stands, on a bounded sample: the first bases of block 0 as one block."""
     from oracle import codec as ocodec
     cfg = ocodec.Config(**{k: v for k, v in kw.items()})
-    n = int(w.block_lens[0])
-    frac = 1  # one whole block: about 15 s of oracle work on 16 Arm cores
-    sample = w.seq[: n // frac].tobytes()
+    sample = w.seq[: min(int(w.block_lens[0]), CPU_SAMPLE[name])].tobytes()
     t0 = time.perf_counter()
     out = ocodec.compress(sample, [len(sample)], cfg, sw)
     t1 = time.perf_counter()
@@ -190,7 +238,7 @@ def cpu_baseline(w, kw, sw, budget_s: float = 20.0):
     t2 = time.perf_counter()
     assert back == sample
     return {"value": len(sample) / 1e6 / (t2 - t0), "unit": "MB/s", "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"block 0 ({len(sample)} bases) as one block, "
+            "sample": f"the first {len(sample)} bases of block 0 as one block, "
                       f"compress {t1 - t0:.1f} s + decompress {t2 - t1:.1f} s",
             "bits_per_base": 8 * len(out) / len(sample)}
 
@@ -199,7 +247,7 @@ def run_reference(args, w, kw, sw):
     """--impl reference: the CPU oracle, timed on the host cores, same metric."""
     from oracle import codec as ocodec
     cfg = ocodec.Config(**kw)
-    n = int(w.block_lens[0]) // 2
+    n = min(int(w.block_lens[0]), CPU_SAMPLE[args.workload]) // 2
     sample = w.seq[:n].tobytes()
     for _ in range(min(args.warmup, 1)):
         ocodec.decompress(ocodec.compress(sample, [n], cfg, sw), sw)
@@ -283,11 +331,17 @@ def roofline(prof: dict, pk: dict, pk_kind: str):
 FORMS = {"bf16": 1, "fp32": 0}
 
 
-AUTOTUNE_LANES = (64, 128, 192, 256, 320)  # candidates; the first is the FP32 plain form's setting
+AUTOTUNE_LANES = (64, 128, 192, 256, 320)  # candidates from the FP32 plain form's setting up
+
+
+def lane_candidates(kw):
+    return tuple(x for x in AUTOTUNE_LANES if x >= kw["lanes_per_block"])
 
 
 def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, lanes=0):
-    """Device-resident compress+decompress of the workload: per-step times (CUDA events) + stats."""
+    """Device-resident compress + decompress of the workload: per-step compress and decompress times
+    (CUDA events on the launching stream), then one untimed step under the library's sampled kernel
+    profiler (every PROFILE_EVERY-th global step's launches bracketed with events)."""
     cfg = P.ModelConfig(**kw, static_weights=sw, precision=FORMS[form])
     n = int(w.seq.size)
     tune = None
@@ -296,9 +350,10 @@ def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, 
         tune = {"lanes_per_block": lanes, "rule": "fixed by --lanes"}
     elif form == "bf16":  # the batched form picks its batch size (lanes per block) on a sample, untimed
         d = torch.from_numpy(w.seq).to(dev)
-        chosen, sizes, tms = P.pmklc_autotune_lanes(d, w.block_lens, cfg, AUTOTUNE_LANES, sample_blocks=8,
+        cand = lane_candidates(kw)
+        chosen, sizes, tms = P.pmklc_autotune_lanes(d, w.block_lens, cfg, cand, sample_blocks=8,
                                                     max_rel_size=0.005)
-        tune = {"lanes_per_block": chosen, "candidates": list(AUTOTUNE_LANES), "sample_bytes": [int(x) for x in sizes],
+        tune = {"lanes_per_block": chosen, "candidates": list(cand), "sample_bytes": [int(x) for x in sizes],
                 "sample_ms": [round(float(x), 2) for x in tms], "sample": "first 8 blocks, compress only",
                 "rule": "fastest with coded size <= 1.005 x the first candidate's"}
         del d
@@ -309,40 +364,53 @@ def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, 
     d_back = torch.empty(n, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step():
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
         clen = P.pmklc_compress_dev(d_seq, w.block_lens, cfg, d_out)
         s1 = P.pmklc_last_stats()
+        if ev:
+            ev[1].record(stream)
         P.pmklc_decompress_dev(d_out, clen, d_back, sw)
         s2 = P.pmklc_last_stats()
+        if ev:
+            ev[2].record(stream)
         return clen, s1["kernel_launches"] + s2["kernel_launches"], s1
 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     assert torch.equal(d_back, d_seq), "round trip failed"
-    times, launches = [], 0
-    P.pmklc_profile_read()
-    if profile:
-        P.pmklc_profile_enable(PROFILE_EVERY)
+    ct, dt, launches = [], [], 0
+    P.pmklc_profile_enable(0)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     for _ in range(steps):
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        clen, nl, st1 = step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        clen, nl, st1 = step(ev)
+        ev[2].synchronize()
+        ct.append(ev[0].elapsed_time(ev[1]))
+        dt.append(ev[1].elapsed_time(ev[2]))
         launches += nl
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    P.pmklc_profile_enable(0)
-    prof = P.pmklc_profile_read()
+    assert torch.equal(d_back, d_seq), "round trip failed"
+    prof = {}
+    if profile:  # a separate, untimed pass under the sampled profiler
+        P.pmklc_profile_read()
+        flush.zero_()
+        P.pmklc_profile_enable(PROFILE_EVERY)
+        step()
+        torch.cuda.synchronize()
+        P.pmklc_profile_enable(0)
+        prof = P.pmklc_profile_read()
     del flush
-    return {"cfg": cfg, "times": times, "launches": launches, "clen": clen, "stats": st1, "prof": prof, "tune": tune}
+    times = [a + b for a, b in zip(ct, dt)]
+    return {"cfg": cfg, "times": times, "ct": ct, "dt": dt, "launches": launches, "clen": clen, "stats": st1,
+            "prof": prof, "tune": tune}
 
 
 def main():
@@ -351,10 +419,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="human", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "bf16", "fp32"])
+    ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the FP32 plain form (with --form both)")
+    ap.add_argument("--fp32-warmup", type=int, default=1)
     ap.add_argument("--lanes", type=int, default=0, help="BF16 lanes per block (0: autotune)")
+    ap.add_argument("--no-profile", action="store_true", help="skip the untimed profiled pass")
     ap.add_argument("--block-bases", type=int, default=0,
                     help="cut every block to this many bases (profiling: same per-step shapes, fewer steps)")
     args = ap.parse_args()
@@ -363,14 +434,22 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the oracle alone: its own initialiser draws the frozen static weights (the same splitmix64
-        # values the library's pmklc_init_model returns), so no library code runs on this arm
+        # the oracle alone: the cached pre-trained static model when one is there, else the oracle's own
+        # initialiser (its speed does not depend on the weights' values), so no library code runs here
         from oracle.model import Shape, init_params
         w, kw = load_workload(args.workload, args.block_bases)
-        sw = None
+        sw, sdesc = None, None
         if kw.get("use_static"):
-            sw = init_params(Shape(4 ** kw["k"], kw["emb_s"], kw["ctx_s"], kw["hid_s"]), STATIC_SEED)
-        print(json.dumps(run_reference(args, w, kw, sw)))
+            cached = sorted(f for f in (os.listdir(CACHE) if os.path.isdir(CACHE) else [])
+                            if f.startswith(f"static_{args.workload}_"))
+            if cached:
+                sw, sdesc = np.load(os.path.join(CACHE, cached[0])), f"pre-trained ({cached[0]})"
+            else:
+                sw = init_params(Shape(4 ** kw["k"], kw["emb_s"], kw["ctx_s"], kw["hid_s"]), STATIC_SEED)
+                sdesc = f"seeded random (init seed {STATIC_SEED}): no pre-trained model cached"
+        line = run_reference(args, w, kw, sw)
+        line["config"]["static_model"] = sdesc
+        print(json.dumps(line))
         return
 
     import torch
@@ -381,21 +460,26 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
     w, kw = load_workload(args.workload, args.block_bases)
-    sw = static_weights(P, kw)
+    sw, sdesc = static_weights(P, args.workload, kw)
     n = int(w.seq.size)
+    forms = [args.form] if args.form != "both" else ["bf16", "fp32"]
     # a measurement whose clock record shows a hardware or thermal slowdown is taken once more
     # (decided over all ranks together, so every rank runs the same collectives)
     for attempt in range(2):
         results = {}
         with ClockSampler(dev) as clk:
-            for form in ([args.form] if args.form != "both" else ["fp32", "bf16"]):
-                results[form] = measure(P, torch, w, kw, sw, form, args.steps, args.warmup, dev, world,
-                                        lanes=args.lanes)
+            for form in forms:
+                head_form = form == forms[0]
+                results[form] = measure(P, torch, w, kw, sw, form, args.steps if head_form else args.fp32_steps,
+                                        args.warmup if head_form else args.fp32_warmup, dev, world,
+                                        profile=head_form and not args.no_profile, lanes=args.lanes)
         if attempt == 1 or max_over_ranks(1.0 if throttled(clk.summary()) else 0.0, dev) == 0.0:
             break
-    head = results["bf16"] if "bf16" in results else results[args.form]
-    form = "bf16" if "bf16" in results else args.form
+    form = forms[0]
+    head = results[form]
     ms = max_over_ranks(statistics.mean(head["times"]), dev)
+    cms = max_over_ranks(statistics.mean(head["ct"]), dev)
+    dms = max_over_ranks(statistics.mean(head["dt"]), dev)
     value = job_throughput(world, n, ms)
 
     # end to end through the host-buffer C ABI (H2D of the input and of the container, D2H of both results)
@@ -411,34 +495,47 @@ def main():
     e2e_ms = max_over_ranks(1e3 * statistics.mean(e2e_times), dev)
     e2e = {"value": job_throughput(world, n, e2e_ms), "unit": "MB/s",
            "h2d_bytes_per_step": n + len(blob), "d2h_bytes_per_step": len(blob) + n}
-    fms = max_over_ranks(statistics.mean(results["fp32"]["times"]), dev) if "fp32" in results else None
+    other = {f: {k: max_over_ranks(statistics.mean(results[f][k]), dev) for k in ("times", "ct", "dt")}
+             for f in forms[1:]}
 
     if rank != 0:
         return
     pk, pk_kind = peaks()
     st1 = head["stats"]
+    names = {"bf16": "BF16 batched", "fp32": "FP32 plain"}
+
+    def judge(r):
+        st = r["stats"]
+        return {"net_blocks": st["net_blocks"], "count_blocks": st["count_blocks"],
+                "bits_per_base_network": 8 * st["net_bytes"] / n if st["net_bytes"] else None,
+                "bits_per_base_count_model": 8 * st["count_bytes"] / n if st["count_bytes"] else None,
+                "note": "payload bytes of each coding over every block (lane streams and their lengths)"}
+
     line = {
         "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if form == "bf16" else "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args.workload, w, kw), "model": kw,
-                   "form": {"bf16": "BF16 batched", "fp32": "FP32 plain"}[form],
-                   "bits_per_base": 8 * head["clen"] / n, "compressed_bytes": head["clen"],
-                   "net_blocks": st1["net_blocks"], "count_blocks": st1["count_blocks"],
+        "compress": {"value": job_throughput(world, n, cms), "unit": "MB/s", "ms": cms},
+        "decompress": {"value": job_throughput(world, n, dms), "unit": "MB/s", "ms": dms},
+        "config": {"workload": workload_name(args.workload, w, kw), "model": kw, "form": names[form],
+                   "bits_per_base": 8 * head["clen"] / n, "compressed_bytes": head["clen"], "judge": judge(head),
                    "global_steps": st1["global_steps"], "l2": "flushed (256 MB write) before every step",
-                   "static_model": f"seeded random (init seed {STATIC_SEED})",
-                   "lanes_per_block": head["cfg"].lanes_per_block, "autotune": head["tune"]},
+                   "static_model": sdesc, "lanes_per_block": head["cfg"].lanes_per_block, "autotune": head["tune"],
+                   "profile": "separate untimed step, every 8th global step's launches timed with CUDA events"},
         "e2e": e2e, "gpu_launches": head["launches"], "clocks": dict(clk.summary(), remeasured=attempt),
         "peaks": pk_kind,
     }
-    if "fp32" in results and form != "fp32":
-        f = results["fp32"]
-        line["fp32_plain"] = {"value": job_throughput(world, n, fms), "unit": "MB/s", "ms_per_step": fms,
-                              "bits_per_base": 8 * f["clen"] / n, "gpu_launches": f["launches"]}
-        line["bits_per_base_rel_diff_vs_fp32"] = (head["clen"] - f["clen"]) / f["clen"]
+    for f in forms[1:]:
+        r, o = results[f], other[f]
+        line[{"fp32": "fp32_plain", "bf16": "bf16_batched"}[f]] = {
+            "value": job_throughput(world, n, o["times"]), "unit": "MB/s", "ms_per_step": o["times"],
+            "compress": job_throughput(world, n, o["ct"]), "decompress": job_throughput(world, n, o["dt"]),
+            "steps": len(r["times"]), "warmup": args.fp32_warmup, "bits_per_base": 8 * r["clen"] / n,
+            "judge": judge(r), "lanes_per_block": r["cfg"].lanes_per_block, "gpu_launches": r["launches"]}
+        line[f"bits_per_base_rel_diff_vs_{f}"] = (head["clen"] - r["clen"]) / r["clen"]
     line["roofline"], line["kernels"] = roofline(head["prof"], pk, pk_kind)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, kw, sw)
+        line["cpu_baseline"] = cpu_baseline(args.workload, w, kw, sw)
     print(json.dumps(line))
 
 

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define PMKLC_ABI_VERSION 2
+#define PMKLC_ABI_VERSION 3
 
 /* error codes */
 #define PMKLC_OK 0
@@ -121,6 +121,9 @@ int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint6
  * state).  The trained FP32 parameters of shape (emb_d, ctx_d, hid_d), starting
  * from pmklc_init_model(..., cfg->seed), go to out (host,
  * pmklc_model_count(k, emb_d, ctx_d, hid_d) floats).  cfg->use_static must be 0.
+ * Without a static model the mixer of Eq. (1) forms the logits (1 - alpha) L, and alpha
+ * trains alongside the weights; the returned logits layer (W2, b2) is multiplied by the final
+ * (1 - alpha) (in FP32), so the returned predictor alone computes the logits the training fitted.
  */
 int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, uint32_t epochs, void *stream,
                       float *out);
@@ -318,12 +321,16 @@ int pmklc_crc32(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
  */
 int pmklc_crc32_noalloc(const uint8_t *d_data, size_t n, uint32_t *crc, void *stream);
 
-/* Last run's statistics (per thread): compressed payload split and timings. */
+/* Last run's statistics (per thread): compressed payload split and timings.  After a
+ * compression, net_bytes and count_bytes are what the network's and the count model's codings of
+ * every block cost (lane payloads and their length fields, as the judge compares them; 0 for a
+ * coding that did not run: the count model with fallback 0, the network with fallback 2). */
 typedef struct {
   uint64_t net_blocks, count_blocks;
   uint64_t global_steps;
   uint64_t kernel_launches;
   double ms_total;
+  uint64_t net_bytes, count_bytes;
 } pmklc_stats;
 int pmklc_last_stats(pmklc_stats *st);
 

@@ -521,3 +521,23 @@ def size_breakdown(data: bytes) -> dict:
     """Per-block coding modes and the payload size (for reports)."""
     cfg, meta = parse_header(data)
     return {"cfg": cfg, **meta, "bytes": len(data)}
+
+
+def train_model(seq, cfg: Config, epochs: int = 1) -> np.ndarray:
+    """Pre-training of a static predictor (§4, the static public model, Fig. 2(a)) with the
+    dynamic-model loop alone: the bases are tokenised and cut into cfg.lanes_per_block lanes, and
+    the loop of compress runs over them `epochs` times without coding, each epoch a group that starts
+    from the previous one's final state (step-wise passing with f = 1), the first from
+    init_params(dm_shape, cfg.seed).  Without a static model Eq. (1) gives the logits
+    (1 - alpha) L^m; the returned parameters carry that factor in the logits layer (W2, b2), so the
+    predictor alone computes the logits the training fitted."""
+    codes = base_codes(seq)
+    c = replace(cfg, use_static=False, smp_mode=SMP_CHAIN, smp_fraction=1.0, fallback=0)
+    blocks, _ = _prepare(c, [codes] * epochs)
+    for b in blocks:
+        b.replay = True  # tokens known, nothing coded
+    st = _run(c, blocks, None)[-1]
+    theta = st.theta.copy()
+    lo = c.dm_shape.offsets()["w2"][0]
+    theta[lo:] *= 1.0 - st.alpha
+    return theta

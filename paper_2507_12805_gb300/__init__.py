@@ -54,7 +54,7 @@ class CKernelProf(ctypes.Structure):
 class CStats(ctypes.Structure):
     _fields_ = [("net_blocks", ctypes.c_uint64), ("count_blocks", ctypes.c_uint64),
                 ("global_steps", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("net_bytes", ctypes.c_uint64), ("count_bytes", ctypes.c_uint64)]
 
 
 _vp, _sz, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int

@@ -791,7 +791,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   put_le<uint32_t>(H, (uint32_t)c.lane_tokens);
   std::vector<unsigned long long> seg;  // (src, dst-relative, len, which)
   unsigned long long pay = 0;
-  uint64_t n_net = 0, n_cnt = 0;
+  uint64_t n_net = 0, n_cnt = 0, net_bytes = 0, cnt_bytes = 0;
   for (int g = 0; g < L.G; ++g) {
     long long tl = tail_len_of((long long)lens[g], c.s, c.k);
     size_t tbytes = (size_t)(tl * 2 + 7) / 8;
@@ -801,6 +801,8 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
       cnt_cost += cnt_len[r] + varint_len(cnt_len[r]);
     }
     bool use_cnt = c.fallback == 2 || (c.fallback == 1 && cnt_cost < net_cost);
+    net_bytes += c.fallback == 2 ? 0 : net_cost;
+    cnt_bytes += c.fallback == 0 ? 0 : cnt_cost;
     put_varint(H, lens[g]);
     H.push_back(use_cnt ? 1 : 0);
     uint8_t tb[2] = {0, 0};
@@ -829,6 +831,8 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   *out_len = total;
   g_stats.net_blocks = n_net;
   g_stats.count_blocks = n_cnt;
+  g_stats.net_bytes = net_bytes;
+  g_stats.count_bytes = cnt_bytes;
   g_stats.global_steps = (uint64_t)R.S.T_total;
   g_stats.kernel_launches = R.launches;
   g_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1028,6 +1032,7 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
   rc = crc32_device(d_seq, (size_t)P.n, &crc, st);
   if (rc) return rc;
   if (crc != P.crc) return PMKLC_ECORRUPT;
+  g_stats.net_bytes = g_stats.count_bytes = 0;  // a decompression codes nothing
   g_stats.global_steps = (uint64_t)R.S.T_total;
   g_stats.kernel_launches = R.launches;
   g_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1324,10 +1329,19 @@ int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, 
     int h_err = 0;
     cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
     int last = R.L.G - 1;
+    float alpha = 0.f;
     cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&alpha, R.p.alpha + last, sizeof(float), cudaMemcpyDeviceToHost, st);
     PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
     PMKLC_CUDA_TRY(cudaGetLastError());
-    return h_err ? err_to_rc(h_err) : PMKLC_OK;
+    if (h_err) return err_to_rc(h_err);
+    // Without a static model Eq. (1) gives the logits (1 - alpha) L^m, and alpha trains with the
+    // weights: only the product is determined, and the pair drifts along (alpha, L^m) ->
+    // (alpha', L^m (1 - alpha) / (1 - alpha')).  The predictor the training fitted is the product,
+    // so (1 - alpha) goes into the logits layer (W2 and b2).
+    const float keep = 1.f - alpha;
+    for (size_t i = c.dm.off_w2(); i < c.dm.count(); ++i) out[i] *= keep;
+    return PMKLC_OK;
   });
 }
 

@@ -30,6 +30,12 @@ class ProfScope {
   void *a_ = nullptr;
 };
 
+// Raises `func`'s dynamic shared-memory limit to at least `bytes` on the current device: one
+// attribute call per (kernel, device, larger size), under a process-wide mutex, so host threads
+// driving several devices share it safely.  False when the attribute call failed (the error stays
+// recorded for the caller's cudaGetLastError).
+bool smem_optin(const void *func, int bytes);
+
 // tokenize.cu ---------------------------------------------------------------
 // Checks every byte is one of A, C, G, T (sets kErrBadBase in *d_err otherwise).
 void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st);

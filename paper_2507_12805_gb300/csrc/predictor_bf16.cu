@@ -250,11 +250,7 @@ void run_tgemm(const Op &op, int Mmax, int Nmax, int Z, cudaStream_t st) {
   if (Mmax <= 0 || Nmax <= 0 || Z <= 0) return;
   dim3 grid((Mmax + TBM - 1) / TBM, (Nmax + TBN - 1) / TBN, Z);
   constexpr int smem = tgemm_smem<Op>();
-  static bool attr = false;  // one attribute call per kernel instantiation and process
-  if (!attr) {
-    cudaFuncSetAttribute(tgemm_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  if (!smem_optin((const void *)tgemm_kernel<Op>, smem)) return;  // error left for cudaGetLastError
   tgemm_kernel<Op><<<grid, TTH, smem, st>>>(op);
 }
 

@@ -8,7 +8,10 @@
 // so achieved FLOP/s or bytes/s = work / time over the sampled launches.
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -60,6 +63,19 @@ ProfScope::~ProfScope() {
   cudaEvent_t b = g_prof.get();
   cudaEventRecord(b, st_);
   g_prof.recs.push_back(Rec{name_, (cudaEvent_t)a_, b, flops_, bytes_});
+}
+
+bool smem_optin(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> done;  // (kernel, device) -> limit set
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  int &have = done[{func, dev}];
+  if (have >= bytes) return true;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+  have = bytes;
+  return true;
 }
 
 }  // namespace pmklc

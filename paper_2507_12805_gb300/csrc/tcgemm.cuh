@@ -460,12 +460,9 @@ template <class Op>
 void launch(const Op &op, int Mmax, int Nmax, int Z, const TilePlan &t, size_t meta_bytes, cudaStream_t st) {
   if (Mmax <= 0 || Nmax <= 0 || Z <= 0) return;
   const int smem = (int)smem_bytes(t, meta_bytes);
-  static int configured = 0;  // per op type: the opt-in limit covers static + dynamic shared memory
-  if (configured < smem) {
-    if (cudaFuncSetAttribute(gemm_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return;  // recorded for the caller's cudaGetLastError
-    configured = smem;
-  }
+  // the opt-in limit covers static + dynamic shared memory; a failure stays recorded for the
+  // caller's cudaGetLastError
+  if (!smem_optin((const void *)gemm_kernel<Op>, smem)) return;
   dim3 grid((Mmax + kRows - 1) / kRows, (Nmax + t.nt - 1) / t.nt, Z);
   launch_pdl(gemm_kernel<Op>, grid, dim3(kThreads), (size_t)smem, st, op, t.nt, pow2_at_least(t.nt), t.ns);
 }

@@ -45,7 +45,7 @@ def _load():
             lib.synth_markov_sample.argtypes = [vp, u64, i32, vp, u64]
             lib.synth_markov_sample.restype = i32
             lib.synth_plant_repeats.argtypes = [vp, u64, i32, u64, dbl, u64]
-            lib.synth_plant_families.argtypes = [vp, u64, i32, u64, dbl, dbl, u64]
+            lib.synth_plant_families.argtypes = [vp, u64, i32, u64, dbl, dbl, u64, u64]
             lib.synth_plant_families.restype = i32
             lib.synth_plant_tandem.argtypes = [vp, u64, dbl, i32, i32, dbl, u64]
             lib.synth_lognormal_lengths.argtypes = [vp, i32, dbl, dbl, u64, u64, u64, u64]
@@ -90,8 +90,12 @@ def plant_repeats(buf: np.ndarray, count: int, length: int, mu: float, seed: int
     return buf
 
 
-def plant_families(buf: np.ndarray, n_fam: int, fam_len: int, coverage: float, mu: float, seed: int):
-    if _load().synth_plant_families(_ptr(buf), buf.size, n_fam, fam_len, coverage, mu, seed) != 0:
+def plant_families(buf: np.ndarray, n_fam: int, fam_len: int, coverage: float, mu: float, seed: int,
+                   place_seed: int | None = None):
+    """Copies of n_fam consensus sequences (drawn from `seed`) at `mu` point mutation until `coverage`
+    of buf is covered; their places and mutations come from `place_seed` (default: the same stream)."""
+    ps = seed if place_seed is None else place_seed
+    if _load().synth_plant_families(_ptr(buf), buf.size, n_fam, fam_len, coverage, mu, seed, ps) != 0:
         raise MemoryError("synth_plant_families")
     return buf
 
@@ -126,12 +130,18 @@ class Workload:
     recipe: str
 
 
-def human_like(n: int, seed: int) -> np.ndarray:
+def human_like(n: int, seed: int, sample_seed: int | None = None) -> np.ndarray:
     """GC 0.41, CpG depleted 4x, order-6 background; 10% of bases from 30 Alu-like 300-bp
-    families at 12% mutation; 5% tandem repeats with periods 2-6 (mean run 40 bp)."""
-    seq = sample(n, markov_table(6, 0.41, seed, cpg_factor=4.0), seed + 1)
-    plant_families(seq, 30, 300, 0.10, 0.12, seed + 2)
-    plant_tandem(seq, 0.05, 2, 6, 40.0, seed + 3)
+    families at 12% mutation; 5% tandem repeats with periods 2-6 (mean run 40 bp).
+
+    `seed` fixes the "species" (the order-6 table and the family consensus sequences) and, by
+    default, the sample; another `sample_seed` draws another genome of the same species (its own
+    background sample, family copies and tandem repeats), e.g. the public data a static model is
+    pre-trained on."""
+    ss = seed if sample_seed is None else sample_seed
+    seq = sample(n, markov_table(6, 0.41, seed, cpg_factor=4.0), ss + 1)
+    plant_families(seq, 30, 300, 0.10, 0.12, seed + 2, ss + 2)
+    plant_tandem(seq, 0.05, 2, 6, 40.0, ss + 3)
     return seq
 
 
@@ -140,6 +150,24 @@ SPECIES_GC = (0.30, 0.3875, 0.475, 0.5625, 0.65)
 
 def species_tables(seed: int = 2001):
     return [markov_table(6, gc, seed + 17 * i) for i, gc in enumerate(SPECIES_GC)]
+
+
+def pretrain_corpus(name: str, n: int, seed: int = 2001) -> np.ndarray:
+    """n bases of other genomes from the same source as a workload (its "species"), drawn with their
+    own sample seed: the public data a static model is pre-trained on.  plain: the order-5 table of
+    seed 1002; human: the human-like species of seed 1003 (its table and repeat families); batch /
+    heldout: the five species profiles in turn (unperturbed)."""
+    if name == "plain":
+        return sample(n, markov_table(5, 0.40, 1002), seed)
+    if name == "human":
+        return human_like(n, 1003, sample_seed=seed)
+    if name in ("batch", "heldout"):
+        tabs = species_tables()
+        part = -(-n // 5)
+        return np.concatenate([sample(min(part, n - i * part), tabs[i], seed + i) for i in range(5)])
+    if name == "tiny":
+        return sample(n, markov_table(3, 0.42, 1001), seed)
+    raise KeyError(name)
 
 
 def workload(name: str, scale: float = 1.0) -> Workload:

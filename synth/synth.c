@@ -170,13 +170,16 @@ void synth_plant_repeats(uint8_t *buf, uint64_t n, int count, uint64_t len, doub
  * fam_len; mutated copies (rate mu) are written at random positions until `coverage`
  * of the bases are covered. */
 int synth_plant_families(uint8_t *buf, uint64_t n, int n_fam, uint64_t fam_len, double coverage,
-                         double mu, uint64_t seed) {
+                         double mu, uint64_t seed, uint64_t place_seed) {
   if (n < fam_len + 1 || n_fam <= 0) return 0;
   rng_t r;
   rng_seed(&r, seed);
   uint8_t *cons = (uint8_t *)malloc((size_t)(n_fam * fam_len));
   if (!cons) return -1;
   for (uint64_t i = 0; i < (uint64_t)n_fam * fam_len; ++i) cons[i] = (uint8_t)ACGT[rng_below(&r, 4)];
+  /* the copies' places and mutations: the same stream, or (place_seed != seed) their own, so that
+   * another genome of the same "species" shares the family consensus sequences */
+  if (place_seed != seed) rng_seed(&r, place_seed);
   uint64_t target = (uint64_t)(coverage * (double)n), done = 0;
   while (done < target) {
     const uint8_t *f = cons + rng_below(&r, (uint64_t)n_fam) * fam_len;

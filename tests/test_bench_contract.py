@@ -70,8 +70,8 @@ def test_reference_arm_runs_the_oracle_alone(monkeypatch, capsys):
     import json
     import sys
     monkeypatch.delitem(sys.modules, "paper_2507_12805_gb300", raising=False)
-    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                                      "--block-bases", "2048"])
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "plain", "--steps", "1",
+                                      "--warmup", "0", "--block-bases", "2048"])
     bench.main()
     assert "paper_2507_12805_gb300" not in sys.modules
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -89,3 +89,9 @@ def test_throttle_detection():
     assert not bench.throttled({"reasons": ["unsampled"]})
     for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
         assert bench.throttled({"reasons": ["sw_power_cap", r]})
+
+
+def test_autotune_candidates_start_at_the_plain_forms_lanes():
+    _, kw = bench.load_workload("plain", 1 << 12)
+    assert bench.lane_candidates(kw)[0] == kw["lanes_per_block"] == 64
+    assert bench.lane_candidates(dict(bench.WORKLOADS["human"][1]))[0] == 128
