@@ -296,8 +296,10 @@ def _count_step(cfg: Config, b: _Block, j: int):
                 b.tokens[pos] = (int(b.tokens[pos - 1]) % (4 ** (cfg.k - cfg.s))) * (4 ** cfg.s) + v
 
 
-def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
-    """Run the lockstep loop over all blocks (groups) in compress or decompress mode."""
+def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None, only=None):
+    """Run the lockstep loop over all blocks (groups) in compress or decompress mode.  `only`
+    (optional) maps the groups to run to the global step they stop at (None: their end); the
+    schedule is still that of every block."""
     dshape, sshape = cfg.dm_shape, cfg.static_shape
     S = (1 if cfg.use_static else 0, 0, 1)
     # precision 2 / 3: the frozen static model in its FP8 / FP8-hidden form (fp8.py), else as stored
@@ -313,6 +315,8 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
     zeros = np.zeros(dshape.count)
     for T in range(T_total + 1):
         for g in range(len(blocks)):
+            if only is not None and g not in only:
+                continue
             if start[g] == T and groups[g] is None:
                 groups[g] = (groups[parent[g]].copy() if parent[g] >= 0 else
                              _Group(init.copy(), zeros.copy(), zeros.copy(), cfg.f32("alpha_init")))
@@ -323,6 +327,8 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None):
         for g, b in enumerate(blocks):
             j = T - start[g]
             if j < 0 or j >= steps[g]:
+                continue
+            if only is not None and (g not in only or (only[g] is not None and T >= only[g])):
                 continue
             if b.count_encode or b.count_decode:
                 _count_step(cfg, b, j)
@@ -541,3 +547,28 @@ def train_model(seq, cfg: Config, epochs: int = 1) -> np.ndarray:
     lo = c.dm_shape.offsets()["w2"][0]
     theta[lo:] *= 1.0 - st.alpha
     return theta
+
+
+def block_streams(seq, block_lens, cfg: Config, static_w, g: int):
+    """The network's lane streams of block g alone (cfg.fallback is ignored: no count model), coded
+    from the state that step-wise model passing delivers to it: only g's ancestors in the schedule
+    run, without coding, each until the global step at which its child in the chain starts."""
+    _check_cfg(cfg, static_w)
+    codes = base_codes(seq)
+    offs = np.concatenate([[0], np.cumsum([int(x) for x in block_lens])]).astype(np.int64)
+    blocks, _ = _prepare(cfg, [codes[offs[i]:offs[i + 1]] for i in range(len(block_lens))])
+    steps = [max(b.lens) if b.lens else 0 for b in blocks]
+    start, parent = schedule(steps, cfg.smp_mode, cfg.f32("smp_fraction"))
+    only = {g: None}
+    child = g
+    while parent[child] >= 0:
+        only[parent[child]] = start[child]
+        child = parent[child]
+    for i, b in enumerate(blocks):
+        if i == g:
+            b.enc = [Encoder() for _ in b.lens]
+        else:
+            b.replay = True
+    sw = None if static_w is None else np.asarray(static_w, dtype=np.float32).astype(np.float64)
+    _run(replace(cfg, fallback=0), blocks, sw, only=only)
+    return [e.finish() for e in blocks[g].enc]

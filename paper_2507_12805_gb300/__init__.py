@@ -283,9 +283,22 @@ def pmklc_wait_selftest(polls: int, stream=None) -> int:
     return lib.pmklc_wait_selftest(polls, _stream(stream))
 
 
+def _byte_count(d_data, n, where: str) -> int:
+    """The bytes to read from a contiguous device tensor: all of them, or the first n (n larger than
+    the tensor is refused here, before the library could read past it)."""
+    if not d_data.is_contiguous():
+        raise PmklcError(PMKLC_EINVAL, where)
+    nbytes = d_data.numel() * d_data.element_size()
+    if n is None:
+        return nbytes
+    if n < 0 or n > nbytes:
+        raise PmklcError(PMKLC_EINVAL, where)
+    return int(n)
+
+
 def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:
     crc = ctypes.c_uint32()
-    _check(lib.pmklc_crc32(_ptr(d_data), d_data.numel() if n is None else n, ctypes.byref(crc), _stream(stream)),
+    _check(lib.pmklc_crc32(_ptr(d_data), _byte_count(d_data, n, "pmklc_crc32"), ctypes.byref(crc), _stream(stream)),
            "pmklc_crc32")
     return crc.value
 
@@ -293,7 +306,7 @@ def pmklc_crc32(d_data, n: int | None = None, stream=None) -> int:
 def pmklc_crc32_noalloc(d_data, n: int | None = None, stream=None) -> int:
     """CRC-32 of device bytes without any device allocation (fixed library scratch, inputs up to 256 MiB)."""
     crc = ctypes.c_uint32()
-    _check(lib.pmklc_crc32_noalloc(_ptr(d_data), d_data.numel() if n is None else n, ctypes.byref(crc),
+    _check(lib.pmklc_crc32_noalloc(_ptr(d_data), _byte_count(d_data, n, "pmklc_crc32_noalloc"), ctypes.byref(crc),
                                    _stream(stream)), "pmklc_crc32_noalloc")
     return crc.value
 

@@ -104,24 +104,24 @@ def _ce_alone(theta, shape, seq, s, k, overlap):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_train_model_against_oracle(P, precision):
-    """pmklc_train_model against the oracle's pre-training (two epochs, overlap-masked coding): the
-    returned parameters and the predictor's cross entropy on held-out bases."""
+    """pmklc_train_model against the oracle's pre-training (overlap-masked coding, ~1,000 Adam steps):
+    the returned parameters and the predictor's cross entropy on held-out bases of the same source."""
     from oracle import codec as ocodec
     tab = synth.markov_table(3, 0.42, 31)
-    seq = synth.sample(8000, tab, 32)
-    held = synth.sample(4000, tab, 33)  # other bases of the same source
-    kw = dict(s=2, k=4, emb_d=16, ctx_d=8, hid_d=64, lanes_per_block=16, seed=2001, overlap_mask=1, lr=5e-3)
-    got = P.pmklc_train_model(seq, P.ModelConfig(**kw, precision=precision), epochs=2)
-    want = ocodec.train_model(seq.tobytes(), ocodec.Config(**kw), epochs=2)
+    seq = synth.sample(1 << 15, tab, 32)
+    held = synth.sample(1 << 13, tab, 33)  # other bases of the same source
+    kw = dict(s=2, k=4, emb_d=8, ctx_d=8, hid_d=64, lanes_per_block=16, seed=2001, overlap_mask=1)
+    got = P.pmklc_train_model(seq, P.ModelConfig(**kw, precision=precision), epochs=1)
+    want = ocodec.train_model(seq.tobytes(), ocodec.Config(**kw), epochs=1)
     shape = ocodec.Config(**kw).dm_shape
     d = np.abs(got.astype(np.float64) - want)
     ce_g = _ce_alone(got, shape, held.tobytes(), 2, 4, True)
     ce_w = _ce_alone(want, shape, held.tobytes(), 2, 4, True)
-    ce_0 = _ce_alone(P.pmklc_init_model(4, 16, 8, 64, 2001), shape, held.tobytes(), 2, 4, True)
+    ce_0 = _ce_alone(P.pmklc_init_model(4, 8, 8, 64, 2001), shape, held.tobytes(), 2, 4, True)
     print(f"precision {precision}: |dw| median {np.median(d):.2e} p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e}; "
           f"CE alone GPU {ce_g:.4f} oracle {ce_w:.4f} init {ce_0:.4f} bits/base")
     assert ce_w < ce_0  # the pre-training learned something about the source
-    if precision == 0:  # FP32 GEMMs against FP64 over ~500 Adam steps: rounding-level differences
+    if precision == 0:  # FP32 GEMMs against FP64 over ~1,000 Adam steps: rounding-level differences
         assert d.max() <= 1e-4
     else:  # BF16 operands: each gradient within ~1e-2 relative, Adam steps of at most ~lr
         assert np.median(d) <= 1e-3

@@ -172,3 +172,34 @@ def test_online_learning_beats_uniform():
     bpb = 8 * len(out) / 6000
     assert bpb < 0.5 * (2 + entropy)  # far below 2 bits/base
     assert codec.decompress(out) == seq
+
+
+@pytest.mark.parametrize("smp_mode", [0, 1, 2])
+def test_block_streams_equal_the_full_runs_payloads(smp_mode):
+    """block_streams(g) runs only g's ancestors, each until its child starts: its lane streams equal
+    block g's payloads in the whole network-only run, for every block of a 5-block input."""
+    import synth
+    seq = synth.markov(2600, 2, 0.45, 13).tobytes()
+    lens = [700, 500, 600, 400, 400]
+    kw = dict(s=2, k=3, use_static=True, emb_s=4, ctx_s=3, hid_s=8, emb_d=4, ctx_d=4, hid_d=8,
+              lanes_per_block=3, smp_mode=smp_mode, smp_fraction=0.2, fallback=0, overlap_mask=1)
+    sw = init_params(codec.Config(**kw).static_shape, 5)
+    full = codec.compress(seq, lens, codec.Config(**kw), sw)
+    cfg, meta = codec.parse_header(full)
+    pos, sizes = 80, []
+    for n in lens:
+        n_b, pos = codec.read_varint(full, pos)
+        pos += 1 + (codec.tail_len(n_b, 2, 3) * 2 + 7) // 8
+        lane_sizes = []
+        for _ in codec.lanes(codec.n_tokens(n_b, 2, 3), 3)[0]:
+            x, pos = codec.read_varint(full, pos)
+            lane_sizes.append(x)
+        sizes.append(lane_sizes)
+    payload = full[pos:]
+    off = 0
+    for g, lane_sizes in enumerate(sizes):
+        want = []
+        for x in lane_sizes:
+            want.append(payload[off:off + x])
+            off += x
+        assert codec.block_streams(seq, lens, codec.Config(**kw), sw, g) == want, g

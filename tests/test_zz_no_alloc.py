@@ -28,11 +28,36 @@ def test_noalloc_crc32_equals_allocating_entry_point_twice():
         assert got == want == zlib.crc32(data[off:].tobytes())
 
 
-def test_noalloc_crc32_rejects_inputs_beyond_its_scratch():
+def test_noalloc_crc32_at_exact_capacity_and_one_chunk_beyond():
+    """An unaligned input that fills every chunk register of the scratch (65,536 chunks of 4 KiB after
+    the head bytes, plus a 4,095-byte tail): the registers end right where the fold's matrices start.
+    One more chunk is refused before any device access."""
+    import torch
+    import paper_2507_12805_gb300 as P
+    chunks, chunk = 65536, 4096
+    rng = np.random.default_rng(7)
+    host = rng.integers(0, 256, (chunks + 1) * chunk + 64, dtype=np.uint8)
+    base = torch.from_numpy(host).cuda()
+    off = 5
+    d = base[off:]
+    head = (16 - (d.data_ptr() & 15)) & 15
+    assert head > 0
+    n = head + chunks * chunk + (chunk - 1)
+    want = zlib.crc32(host[off:off + n].tobytes())
+    assert P.pmklc_crc32_noalloc(d, n=n) == want == P.pmklc_crc32(d, n=n)
+    assert P.pmklc_crc32_noalloc(d, n=n) == want  # a second call over the same full scratch
+    with pytest.raises(P.PmklcError) as e:
+        P.pmklc_crc32_noalloc(d, n=head + (chunks + 1) * chunk)
+    assert e.value.rc == P.PMKLC_EINVAL
+
+
+def test_noalloc_crc32_rejects_inputs_beyond_its_scratch_or_tensor():
     import torch
     import paper_2507_12805_gb300 as P
     d = torch.zeros(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(P.PmklcError) as e:
-        P.pmklc_crc32_noalloc(d, n=(256 << 20) + 2 * 4096 + 16)  # rejected before any access
+        P.pmklc_crc32_noalloc(d, n=(256 << 20) + 2 * 4096 + 16)  # more than the tensor holds
     assert e.value.rc == P.PMKLC_EINVAL
     assert P.pmklc_crc32_noalloc(d, n=16) == zlib.crc32(bytes(16))
+    w = torch.arange(8, dtype=torch.int32, device="cuda")  # a wider element type: all of its bytes
+    assert P.pmklc_crc32_noalloc(w) == zlib.crc32(np.arange(8, dtype=np.int32).tobytes())
