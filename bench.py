@@ -380,7 +380,8 @@ def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    assert torch.equal(d_back, d_seq), "round trip failed"
+    if warmup:
+        assert torch.equal(d_back, d_seq), "round trip failed"
     ct, dt, launches = [], [], 0
     P.pmklc_profile_enable(0)
     if world > 1:

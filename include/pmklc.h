@@ -56,6 +56,9 @@ extern "C" {
    embedding, E4M3 W1 with one scale per hidden unit; h written in BF16) and its logits layer in
    BF16: the logits layer's E4M3 weights carry almost all of PMKLC_BF16_FP8STATIC's loss */
 #define PMKLC_BF16_FP8HIDDEN 3
+#define PMKLC_UPDATE_AUTO 0
+#define PMKLC_UPDATE_STREAM 1
+#define PMKLC_UPDATE_FUSED 2
 /* optimisers */
 #define PMKLC_ADAM 0
 #define PMKLC_SGD 1
@@ -94,6 +97,12 @@ typedef struct {
                                   k - s digits of token j - 1 (the only ones that can follow):
                                   uniform over them in the first t symbols, else the softmax of
                                   their mixed logits, trained on that slice's cross entropy */
+  uint32_t update_path;        /* where the BF16 forms apply the optimiser to W1 and W2 (an
+                                  implementation choice: every coded byte is the same either way):
+                                  PMKLC_UPDATE_AUTO (0, by the size of the run), PMKLC_UPDATE_STREAM
+                                  (1, gradients stored, then the streaming optimiser) or
+                                  PMKLC_UPDATE_FUSED (2, in the epilogues of the gradient GEMMs on the
+                                  tcgen05 engine, where that engine runs them; else as 1) */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);

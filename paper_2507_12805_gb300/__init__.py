@@ -24,6 +24,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 PMKLC_OK, PMKLC_EINVAL, PMKLC_ENOMEM, PMKLC_ECUDA = 0, -1, -2, -3
 PMKLC_ECORRUPT, PMKLC_EMODEL, PMKLC_ETIMEOUT, PMKLC_ENOSPC = -4, -5, -6, -7
 PMKLC_FP32_PLAIN, PMKLC_BF16_BATCHED, PMKLC_BF16_FP8STATIC, PMKLC_BF16_FP8HIDDEN = 0, 1, 2, 3
+PMKLC_UPDATE_AUTO, PMKLC_UPDATE_STREAM, PMKLC_UPDATE_FUSED = 0, 1, 2
 PMKLC_ADAM, PMKLC_SGD = 0, 1
 PMKLC_SMP_NONE, PMKLC_SMP_CHAIN, PMKLC_SMP_TREE = 0, 1, 2
 
@@ -43,7 +44,7 @@ class CModelCfg(ctypes.Structure):
                 ("smp_mode", ctypes.c_uint32), ("smp_fraction", ctypes.c_float), ("count_order", ctypes.c_uint32),
                 ("fallback", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32),
-                ("overlap_mask", ctypes.c_uint32)]
+                ("overlap_mask", ctypes.c_uint32), ("update_path", ctypes.c_uint32)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -127,6 +128,7 @@ class ModelConfig:
     static_weights: np.ndarray | None = field(default=None, repr=False)
     lane_tokens: int = 0
     overlap_mask: int = 0    # 1: code token j >= 1 over the 4^s tokens consistent with token j - 1
+    update_path: int = 0     # PMKLC_UPDATE_AUTO / _STREAM / _FUSED (same bytes either way)
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()

@@ -151,6 +151,7 @@ struct Cfg {
   float lr, alpha0, smp_f;
   uint64_t seed;
   int mask = 0;                        // overlap-masked coding (s < k)
+  int update_path = PMKLC_UPDATE_AUTO;  // where W1 and W2 are updated (the same bytes either way)
   int A() const { return 1 << (2 * k); }
   int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
 };
@@ -175,7 +176,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
   if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
-  if (c->overlap_mask > 1) return PMKLC_EINVAL;
+  if (c->overlap_mask > 1 || c->update_path > PMKLC_UPDATE_FUSED) return PMKLC_EINVAL;
   o.s = (int)c->s;
   o.k = (int)c->k;
   o.use_static = c->use_static ? 1 : 0;
@@ -188,6 +189,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
   o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
   o.mask = (int)c->overlap_mask;
+  o.update_path = (int)c->update_path;
   o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
   o.lane_tokens = (int)c->lane_tokens;
   o.lr = c->lr;
@@ -485,7 +487,20 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
       p.dx_np = np, p.dx_ct = ct;
     }
   }
+  // BF16 forms on the tcgen05 engine update W1 and W2 in their gradient GEMMs' epilogues when those
+  // GEMMs have enough tiles to keep every SM streaming optimiser state (at least 8 of dW2's
+  // 128 x 128 tiles per SM); with fewer, the full-grid streaming optimiser is faster.  Both apply the
+  // same explicitly rounded rule to the same FP32 gradients: the results are identical either way.
+  const long long w2_tiles = (long long)L.G * ((c.dm.H + 127) / 128) * ((c.dm.A + 127) / 128);
+  const bool fuse = c.update_path == PMKLC_UPDATE_FUSED || (c.update_path == PMKLC_UPDATE_AUTO && w2_tiles >= 8LL * 152);
+  p.fused_w = bf_form(c.precision) && fuse && tc_supported(p) ? 1 : 0;
   cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
+  // the mixer writes a row's dz only inside the coded slice (overlap masking) and clears the
+  // previous one, so every row starts at zero
+  if (p.dz_b)
+    cudaMemsetAsync(p.dz_b, 0, sizeof(__nv_bfloat16) * NL * A, ar.st);
+  else
+    cudaMemsetAsync(p.dz, 0, sizeof(float) * NL * A, ar.st);
   cudaMemsetAsync(p.err, 0, sizeof(int), ar.st);
   std::vector<float> init;
   init_params(c.dm, c.seed, init);
@@ -695,6 +710,8 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   std::vector<int> grp_mode(L.G, kEncode);
   long long *d_base_off = ar.upload(L.base_off);
   long long *d_tok_off = ar.upload(L.tok_off);
+  const std::vector<int> tok_cta = tokenize_ctas(L.base_off);
+  int *d_tok_cta = ar.upload(tok_cta);
   uint16_t *d_tokens = ar.alloc<uint16_t>(L.n_tok);
   uint8_t *d_tail = ar.alloc<uint8_t>((size_t)L.G * 8);
   // lane output buffers: cap = 3 len + 8 (at most 3 byte shifts per symbol + flush)
@@ -717,9 +734,9 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   if (rc) return rc;
   prof_step(0, StepWork{0.0, 0.0});
   {
-    ProfScope ps("validate_tokenize", 0, 2.0 * n + 2.0 * L.n_tok, st);
-    launch_validate(d_seq, n, R.p.err, st);
-    launch_tokenize(d_seq, d_base_off, d_tok_off, L.G, L.n_tok, c.s, c.k, d_tokens, st);
+    ProfScope ps("validate_tokenize", 0, 1.0 * n + 2.0 * L.n_tok, st);
+    launch_validate_tokenize(d_seq, n, d_base_off, d_tok_off, d_tok_cta, L.G, tok_cta[L.G], c.s, c.k, d_tokens,
+                             R.p.err, st);
   }
   launch_tails(d_seq, d_base_off, d_tok_off, L.G, c.s, c.k, d_tail, st);
   // count model (judge / fallback): same lanes, coded inside the same steps
@@ -1299,16 +1316,14 @@ int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, 
     make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
     Arena ar(st);
     uint8_t *d_seq = ar.alloc<uint8_t>(n);
-    long long *d_base_off = ar.upload(R.L.base_off);
-    long long *d_tok_off = ar.upload(R.L.tok_off);
     uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
     if (ar.failed) return PMKLC_ENOMEM;
-    // every epoch reads the same bases: the blocks all start at offset 0
-    std::vector<long long> zero_off(R.L.G + 1, 0);
-    for (int g = 0; g <= R.L.G; ++g) zero_off[g] = (long long)n * std::min(g, 1);
-    long long *d_epoch_off = ar.upload(zero_off);
-    std::vector<long long> tok_one = {0, R.L.tok_off[1]};
+    // every epoch reads the same bases: tokenised once as one block, copied to the other epochs
+    const std::vector<long long> one_off = {0, (long long)n}, tok_one = {0, R.L.tok_off[1]};
+    const std::vector<int> one_cta = tokenize_ctas(one_off);
+    long long *d_one_off = ar.upload(one_off);
     long long *d_tok_one = ar.upload(tok_one);
+    int *d_one_cta = ar.upload(one_cta);
     std::vector<int> grp_mode(R.L.G, kReplay);
     R.p.tokens = d_tokens;
     R.p.lane_buf = nullptr;
@@ -1320,11 +1335,11 @@ int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, 
     rc = setup_run(ar, R, grp_mode, nullptr);
     if (rc) return rc;
     cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
-    launch_validate(d_seq, n, R.p.err, st);
-    for (int g = 0; g < R.L.G; ++g)  // identical tokens for every epoch
-      launch_tokenize(d_seq, d_epoch_off, d_tok_one, 1, R.L.tok_off[1], c.s, c.k, d_tokens + R.L.tok_off[g], st);
-    (void)d_base_off;
-    (void)d_tok_off;
+    launch_validate_tokenize(d_seq, n, d_one_off, d_tok_one, d_one_cta, 1, one_cta[1], c.s, c.k, d_tokens,
+                             R.p.err, st);
+    for (int g = 1; g < R.L.G; ++g)  // identical tokens for every epoch
+      cudaMemcpyAsync(d_tokens + R.L.tok_off[g], d_tokens, sizeof(uint16_t) * (size_t)R.L.tok_off[1],
+                      cudaMemcpyDeviceToDevice, st);
     run_steps(R, grp_mode, st);
     int h_err = 0;
     cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1376,13 +1391,14 @@ int pmklc_tokenize(const uint8_t *d_seq, size_t n, uint32_t s, uint32_t k, uint1
     cudaStream_t st = (cudaStream_t)stream;
     Arena ar(st);
     std::vector<long long> boff = {0, (long long)n}, toff = {0, l};
+    const std::vector<int> cta = tokenize_ctas(boff);
     long long *d_boff = ar.upload(boff), *d_toff = ar.upload(toff);
+    int *d_cta = ar.upload(cta);
     int *d_err = ar.alloc<int>(1);
     uint8_t *d_t8 = ar.alloc<uint8_t>(8);
     if (ar.failed) return PMKLC_ENOMEM;
     cudaMemsetAsync(d_err, 0, sizeof(int), st);
-    launch_validate(d_seq, n, d_err, st);
-    launch_tokenize(d_seq, d_boff, d_toff, 1, l, (int)s, (int)k, d_tokens, st);
+    launch_validate_tokenize(d_seq, n, d_boff, d_toff, d_cta, 1, cta[1], (int)s, (int)k, d_tokens, d_err, st);
     launch_tails(d_seq, d_boff, d_toff, 1, (int)s, (int)k, d_t8, st);
     long long tl = tail_len_of((long long)n, (int)s, (int)k);
     if (tl) cudaMemcpyAsync(d_tail, d_t8, (size_t)tl, cudaMemcpyDeviceToDevice, st);
@@ -1456,6 +1472,7 @@ static int one_step(const Cfg &c, uint32_t G, uint32_t M, float *d_params, float
   R.p.lane_buf_off = nullptr;
   R.p.lane_buf_cap = nullptr;
   int rc = setup_run(ar, R, mode, d_static);
+  if (d_grad) R.p.fused_w = 0;  // the gradient is wanted: stored by the GEMMs, applied by the optimiser
   if (rc) return rc;
   // use the caller's state in place of the seeded init
   R.p.params = d_params;

@@ -73,6 +73,8 @@ struct Plan {
   unsigned *hs_rowmax;
   int precision;                    // PMKLC_FP32_PLAIN / PMKLC_BF16_BATCHED / PMKLC_BF16_FP8STATIC
   const float *bc1, *bc2;      // Adam bias corrections 1 - beta^tau, indexed by tau
+  int fused_w;                 // 1: W1 and W2 are updated in the epilogues of their gradient GEMMs
+                               // (BF16 forms on the tcgen05 engine; no stored gradient for them)
   // activations (NL rows)
   float *hd, *hs, *zm, *zu, *dz, *dh, *dalpha_row, *dalpha_grp;
   float *out_P;                // optional: mixed probabilities of predicted rows (tests)
@@ -144,14 +146,17 @@ __device__ __forceinline__ float alpha_grad(const Plan &p, int T, int g) {
 template <int n>
 __device__ __forceinline__ void adam_n(float *t, float *m, float *v, const float *g, float lr, float bc1, float bc2,
                                        bool adam) {
+  // every operation rounded explicitly (no contraction left to the compiler), so each kernel that
+  // applies the rule - the streaming optimiser or a gradient GEMM's epilogue - gets the same bits
 #pragma unroll
   for (int e = 0; e < n; ++e) {
     if (adam) {
-      m[e] = 0.9f * m[e] + 0.1f * g[e];
-      v[e] = 0.999f * v[e] + 0.001f * g[e] * g[e];
-      t[e] -= lr * (m[e] / bc1) / (sqrtf(v[e] / bc2) + 1e-8f);
+      m[e] = __fadd_rn(__fmul_rn(0.9f, m[e]), __fmul_rn(0.1f, g[e]));
+      v[e] = __fadd_rn(__fmul_rn(0.999f, v[e]), __fmul_rn(__fmul_rn(0.001f, g[e]), g[e]));
+      const float den = __fadd_rn(__fsqrt_rn(__fdiv_rn(v[e], bc2)), 1e-8f);
+      t[e] = __fsub_rn(t[e], __fdiv_rn(__fmul_rn(lr, __fdiv_rn(m[e], bc1)), den));
     } else {
-      t[e] -= lr * g[e];
+      t[e] = __fsub_rn(t[e], __fmul_rn(lr, g[e]));
     }
   }
 }

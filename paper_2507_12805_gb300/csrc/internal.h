@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pmklc {
@@ -37,12 +39,14 @@ class ProfScope {
 bool smem_optin(const void *func, int bytes);
 
 // tokenize.cu ---------------------------------------------------------------
-// Checks every byte is one of A, C, G, T (sets kErrBadBase in *d_err otherwise).
-void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st);
-// Tokens of every block: block b has bases [base_off[b], base_off[b+1]) and tokens
-// [tok_off[b], tok_off[b+1]) in d_tokens.
-void launch_tokenize(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
-                     long long n_tok, int s, int k, uint16_t *d_tokens, cudaStream_t st);
+// Validation (kErrBadBase in *d_err for a byte other than A, C, G, T) and tokens of every block:
+// block b has bases [base_off[b], base_off[b+1]) of d_seq (n bytes) and tokens [tok_off[b],
+// tok_off[b+1]) in d_tokens.  d_cta is tokenize_ctas(base_off) on the device: the first CTA of
+// every block (n_blocks + 1 entries, the last one n_cta), then the block of every CTA (n_cta entries).
+std::vector<int> tokenize_ctas(const std::vector<long long> &base_off);
+void launch_validate_tokenize(const uint8_t *d_seq, size_t n, const long long *d_base_off, const long long *d_tok_off,
+                              const int *d_cta, int n_blocks, int n_cta, int s, int k, uint16_t *d_tokens,
+                              int *d_err, cudaStream_t st);
 // Tail codes of every block (at most 7 per block) into d_tail[b*8 + i].
 void launch_tails(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
                   int s, int k, uint8_t *d_tail, cudaStream_t st);

@@ -350,15 +350,23 @@ __global__ void __launch_bounds__(256) mixcode_kernel(Plan p, int T) {
   const float inv_n = 1.f / (float)n_pred;
   float *outP = p.out_P ? p.out_P + ro : nullptr;
   float da = 0.f;
-  if (W < A) {  // outside the slice: zero gradient (and probability)
-    for (int a = lane; a < A; a += 32) {
-      if (a >= base && a < base + W) continue;
-      if (p.dz_b)
-        p.dz_b[(size_t)r * A + a] = __float2bfloat16_rn(0.f);
-      else
-        p.dz[(size_t)r * A + a] = 0.f;
-      if (p.out_P) p.out_P[(size_t)r * A + a] = 0.f;
+  if (W < A) {
+    // outside the slice the gradient is zero.  The row's dz starts at zero (set once per run) and
+    // only slices are ever written, so the previous step's slice (the one of token j - 1, if that
+    // token was predicted) is the only non-zero part left to clear.
+    if (j - 1 >= p.t_eff) {
+      const int pbase = ((int)p.tokens[tpos - 2] % p.ov_mod) * W;
+      if (pbase != base)
+        for (int a = pbase + lane; a < pbase + W; a += 32) {
+          if (p.dz_b)
+            p.dz_b[(size_t)r * A + a] = __float2bfloat16_rn(0.f);
+          else
+            p.dz[(size_t)r * A + a] = 0.f;
+        }
     }
+    if (p.out_P)
+      for (int a = lane; a < A; a += 32)
+        if (a < base || a >= base + W) p.out_P[(size_t)r * A + a] = 0.f;
   }
   if constexpr (NR > 0) {
     RegRow<NR> R;

@@ -357,95 +357,139 @@ struct DXOp : RowBase {
 };
 
 // Optimiser over every parameter of every training group, streamed in float4 groups: the
-// gradient comes from `grad` (W1, b1, W2, b2) or from the fixed-point embedding accumulators
-// (Emb, zeroed on the way); all loads of a group are issued before its stores.  The FP32
-// master, Adam moments and, in the BF16 form, the BF16 copy are rewritten in place.  Grid row
-// blockIdx.y is a group; its blocks stride over the group's float4 groups with 32-bit indices
-// (no 64-bit division, whose FP64-based code is slow on GB300).  The first warp of a group's
-// first block also updates the group's mixing weight alpha (Eq. 1) by the same rule.
-__global__ void __launch_bounds__(256) opt_stream_kernel(Plan p, int T) {
+// gradient comes from `grad` (W1, b1, W2, b2), from the dX tiles' FP32 partials, or from the
+// fixed-point embedding accumulators (Emb, zeroed on the way).  The FP32 master, Adam moments
+// and, in the BF16 form, the BF16 copy are rewritten in place.  The work is cut into chunks of
+// kOptChunk parameters of one group; the CTAs (one resident wave) stride over the
+// (group, chunk) pairs, and a thread issues the loads of both of its float4 groups of a chunk
+// before any store, so enough bytes are in flight to keep HBM busy.  Indices are 32-bit (no 64-bit
+// division, whose FP64-based code is slow on GB300).  The first warp on a group's first chunk also
+// updates the group's mixing weight alpha (Eq. 1) by the same rule.
+constexpr int kOptThreads = 256, kOptVec = 2, kOptChunk = kOptThreads * 4 * kOptVec;
+
+struct OptGroup {
+  float *th, *mm, *vv;
+  const float *gr, *part;
+  long long *acc;
+  __nv_bfloat16 *wb;
+  int npart;
+};
+
+__device__ __forceinline__ void opt_load4(const Plan &p, const OptGroup &o, uint32_t i0, uint32_t nemb, float *t,
+                                          float *m, float *v, float *gg) {
+  const float4 a = *reinterpret_cast<const float4 *>(o.th + i0), b = *reinterpret_cast<const float4 *>(o.mm + i0),
+               c = *reinterpret_cast<const float4 *>(o.vv + i0);
+  t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
+  m[0] = b.x, m[1] = b.y, m[2] = b.z, m[3] = b.w;
+  v[0] = c.x, v[1] = c.y, v[2] = c.z, v[3] = c.w;
+  if (i0 < nemb && o.part) {  // the dX tiles' FP32 partials, summed in partial order
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < o.npart; ++k) {
+      const float4 q = *reinterpret_cast<const float4 *>(o.part + (size_t)k * nemb + i0);
+      a4.x += q.x, a4.y += q.y, a4.z += q.z, a4.w += q.w;
+    }
+    gg[0] = a4.x, gg[1] = a4.y, gg[2] = a4.z, gg[3] = a4.w;
+  } else if (i0 < nemb) {  // A*E is a multiple of 4: a float4 group never straddles the embedding boundary
+    const longlong2 q0 = *reinterpret_cast<const longlong2 *>(o.acc + i0),
+                    q1 = *reinterpret_cast<const longlong2 *>(o.acc + i0 + 2);
+    gg[0] = unfix40(q0.x), gg[1] = unfix40(q0.y), gg[2] = unfix40(q1.x), gg[3] = unfix40(q1.y);
+    *reinterpret_cast<longlong2 *>(o.acc + i0) = make_longlong2(0, 0);
+    *reinterpret_cast<longlong2 *>(o.acc + i0 + 2) = make_longlong2(0, 0);
+  } else {
+    const float4 d = *reinterpret_cast<const float4 *>(o.gr + i0);
+    gg[0] = d.x, gg[1] = d.y, gg[2] = d.z, gg[3] = d.w;
+  }
+}
+
+__device__ __forceinline__ void opt_store4(const OptGroup &o, uint32_t i0, const float *t, const float *m,
+                                           const float *v, bool adam) {
+  *reinterpret_cast<float4 *>(o.th + i0) = make_float4(t[0], t[1], t[2], t[3]);
+  if (adam) {
+    *reinterpret_cast<float4 *>(o.mm + i0) = make_float4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<float4 *>(o.vv + i0) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  if (o.wb) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(t[0], t[1]), hi = __floats2bfloat162_rn(t[2], t[3]);
+    *reinterpret_cast<uint2 *>(o.wb + i0) =
+        make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+  }
+}
+
+// The parameters the streaming optimiser updates, as a contiguous "virtual" range: all P of a
+// group, or, when W1 and W2 are updated in their gradient GEMMs' epilogues (p.fused_w), the
+// embedding, b1 and b2 only (their offsets and lengths are multiples of 4 there: H % 64 == 0).
+__device__ __forceinline__ uint32_t opt_count(const Plan &p) {
+  return p.fused_w ? (uint32_t)(p.dm.A * p.dm.E + p.dm.H + p.dm.A) : (uint32_t)p.P;
+}
+__device__ __forceinline__ uint32_t opt_index(const Plan &p, uint32_t i) {
+  if (!p.fused_w) return i;
+  const uint32_t ae = (uint32_t)(p.dm.A * p.dm.E), h = (uint32_t)p.dm.H;
+  if (i < ae) return i;
+  if (i < ae + h) return (uint32_t)p.dm.off_b1() + (i - ae);
+  return (uint32_t)p.dm.off_b2() + (i - ae - h);
+}
+
+__global__ void __launch_bounds__(kOptThreads, 4) opt_stream_kernel(Plan p, int T, int chunks_per_group) {
   pdl_wait();
   pdl_trigger();
-  const int g = blockIdx.y;
-  if (!group_trains(p, T, g)) return;
-  const uint32_t P = (uint32_t)p.P, nq = (P + 3) / 4, nemb = (uint32_t)(p.dm.A * p.dm.E);
+  const uint32_t P = opt_count(p), nemb = (uint32_t)(p.dm.A * p.dm.E);
   const bool adam = p.optimizer == PMKLC_ADAM;
-  const size_t base = (size_t)g * p.P;
-  const int tau = group_tau(p, T, g);
-  const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
-  float *__restrict__ th = p.params + base;
-  float *__restrict__ mm = p.m + base;
-  float *__restrict__ vv = p.v + base;
-  const float *__restrict__ gr = p.grad + base;
-  long long *__restrict__ acc = p.demb_acc + (size_t)g * nemb;
-  // the group's partials of the embedding gradient: its row tiles x the column tiles
-  const float *__restrict__ part = p.demb_part ? p.demb_part + (size_t)g * p.dx_np * nemb : nullptr;
-  const int npart = p.demb_part ? ((p.grp_lane_off[g + 1] - p.grp_lane_off[g] + 127) / 128) * p.dx_ct : 0;
-  const bool aligned = (base & 3) == 0;
-  if (blockIdx.x == 0 && threadIdx.x < 32) {  // the mixing weight alpha of Eq. (1), same rule
-    const float ga = alpha_grad(p, T, g);
-    if (threadIdx.x == 0) {
-      p.dalpha_grp[g] = ga;
-      float t1[4] = {p.alpha[g], 0, 0, 0}, m1[4] = {p.alpha_m[g], 0, 0, 0}, v1[4] = {p.alpha_v[g], 0, 0, 0},
-            g1[4] = {ga, 0, 0, 0};
-      adam_n<1>(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
-      p.alpha[g] = t1[0];
-      p.alpha_m[g] = m1[0];
-      p.alpha_v[g] = v1[0];
+  const int n_chunks = p.G * chunks_per_group;
+  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const int g = ch / chunks_per_group, cg = ch - g * chunks_per_group;
+    if (!group_trains(p, T, g)) continue;  // the same for the whole CTA
+    const size_t base = (size_t)g * p.P;
+    const int tau = group_tau(p, T, g);
+    const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
+    OptGroup o;
+    o.th = p.params + base, o.mm = p.m + base, o.vv = p.v + base, o.gr = p.grad + base;
+    o.acc = p.demb_acc + (size_t)g * nemb;
+    // the group's partials of the embedding gradient: its row tiles x the column tiles
+    o.part = p.demb_part ? p.demb_part + (size_t)g * p.dx_np * nemb : nullptr;
+    o.npart = p.demb_part ? ((p.grp_lane_off[g + 1] - p.grp_lane_off[g] + 127) / 128) * p.dx_ct : 0;
+    o.wb = p.wbf ? p.wbf + base : nullptr;
+    if (cg == 0 && threadIdx.x < 32) {  // the mixing weight alpha of Eq. (1), same rule
+      const float ga = alpha_grad(p, T, g);
+      if (threadIdx.x == 0) {
+        p.dalpha_grp[g] = ga;
+        float t1[4] = {p.alpha[g], 0, 0, 0}, m1[4] = {p.alpha_m[g], 0, 0, 0}, v1[4] = {p.alpha_v[g], 0, 0, 0},
+              g1[4] = {ga, 0, 0, 0};
+        adam_n<1>(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
+        p.alpha[g] = t1[0];
+        p.alpha_m[g] = m1[0];
+        p.alpha_v[g] = v1[0];
+      }
     }
-  }
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nq; w += gridDim.x * blockDim.x) {
-    const uint32_t i0 = w * 4;
-    float t[4], m[4], v[4], gg[4];
-    if (aligned && i0 + 3 < P) {
-      float4 a = *reinterpret_cast<const float4 *>(th + i0), b = *reinterpret_cast<const float4 *>(mm + i0),
-             c = *reinterpret_cast<const float4 *>(vv + i0);
-      t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
-      m[0] = b.x, m[1] = b.y, m[2] = b.z, m[3] = b.w;
-      v[0] = c.x, v[1] = c.y, v[2] = c.z, v[3] = c.w;
-      if (i0 < nemb && part) {  // the dX tiles' FP32 partials, summed in partial order
-        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 0; k < npart; ++k) {
-          const float4 q = *reinterpret_cast<const float4 *>(part + (size_t)k * nemb + i0);
-          a4.x += q.x, a4.y += q.y, a4.z += q.z, a4.w += q.w;
-        }
-        gg[0] = a4.x, gg[1] = a4.y, gg[2] = a4.z, gg[3] = a4.w;
-      } else if (i0 < nemb) {  // A*E is a multiple of 4: a group never straddles the embedding boundary
-        longlong2 q0 = *reinterpret_cast<const longlong2 *>(acc + i0),
-                  q1 = *reinterpret_cast<const longlong2 *>(acc + i0 + 2);
-        gg[0] = unfix40(q0.x), gg[1] = unfix40(q0.y), gg[2] = unfix40(q1.x), gg[3] = unfix40(q1.y);
-        *reinterpret_cast<longlong2 *>(acc + i0) = make_longlong2(0, 0);
-        *reinterpret_cast<longlong2 *>(acc + i0 + 2) = make_longlong2(0, 0);
-      } else {
-        float4 d = *reinterpret_cast<const float4 *>(gr + i0);
-        gg[0] = d.x, gg[1] = d.y, gg[2] = d.z, gg[3] = d.w;
+    const uint32_t c0 = (uint32_t)cg * kOptChunk + 4u * threadIdx.x;
+    if ((base & 3) == 0 && (uint32_t)cg * kOptChunk + kOptChunk <= P) {  // a whole, aligned chunk
+      float t[kOptVec][4], m[kOptVec][4], v[kOptVec][4], gg[kOptVec][4];
+#pragma unroll
+      for (int q = 0; q < kOptVec; ++q)
+        opt_load4(p, o, opt_index(p, c0 + q * 4 * kOptThreads), nemb, t[q], m[q], v[q], gg[q]);
+#pragma unroll
+      for (int q = 0; q < kOptVec; ++q) {
+        adam_n<4>(t[q], m[q], v[q], gg[q], p.lr, bc1, bc2, adam);
+        opt_store4(o, opt_index(p, c0 + q * 4 * kOptThreads), t[q], m[q], v[q], adam);
       }
-      adam_n<4>(t, m, v, gg, p.lr, bc1, bc2, adam);
-      *reinterpret_cast<float4 *>(th + i0) = make_float4(t[0], t[1], t[2], t[3]);
-      if (adam) {
-        *reinterpret_cast<float4 *>(mm + i0) = make_float4(m[0], m[1], m[2], m[3]);
-        *reinterpret_cast<float4 *>(vv + i0) = make_float4(v[0], v[1], v[2], v[3]);
-      }
-      if (p.wbf) {
-        __nv_bfloat162 lo = __floats2bfloat162_rn(t[0], t[1]), hi = __floats2bfloat162_rn(t[2], t[3]);
-        *reinterpret_cast<uint2 *>(p.wbf + base + i0) =
-            make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
-      }
-    } else {
-      for (uint32_t i = i0; i < i0 + 4 && i < P; ++i) {
-        float t1[4] = {th[i], 0, 0, 0}, m1[4] = {mm[i], 0, 0, 0}, v1[4] = {vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
-        if (i < nemb && part) {
-          for (int k = 0; k < npart; ++k) g1[0] += part[(size_t)k * nemb + i];
+      continue;
+    }
+    for (int q = 0; q < kOptVec; ++q) {  // the group's last chunk, or unaligned groups: element by element
+      const uint32_t v0 = c0 + q * 4 * kOptThreads;
+      for (uint32_t vi = v0; vi < v0 + 4 && vi < P; ++vi) {
+        const uint32_t i = opt_index(p, vi);
+        float t1[4] = {o.th[i], 0, 0, 0}, m1[4] = {o.mm[i], 0, 0, 0}, v1[4] = {o.vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
+        if (i < nemb && o.part) {
+          for (int k = 0; k < o.npart; ++k) g1[0] += o.part[(size_t)k * nemb + i];
         } else if (i < nemb) {
-          g1[0] = unfix40(acc[i]);
-          acc[i] = 0;
+          g1[0] = unfix40(o.acc[i]);
+          o.acc[i] = 0;
         } else {
-          g1[0] = gr[i];
+          g1[0] = o.gr[i];
         }
         adam_n<1>(t1, m1, v1, g1, p.lr, bc1, bc2, adam);
-        th[i] = t1[0];
-        if (adam) mm[i] = m1[0], vv[i] = v1[0];
-        if (p.wbf) p.wbf[base + i] = __float2bfloat16_rn(t1[0]);
+        o.th[i] = t1[0];
+        if (adam) o.mm[i] = m1[0], o.vv[i] = v1[0];
+        if (o.wb) o.wb[i] = __float2bfloat16_rn(t1[0]);
       }
     }
   }
@@ -533,14 +577,16 @@ void launch_update(const Plan &p, int T, cudaStream_t st) {
   const double nemb = (double)p.dm.A * p.dm.E;
   const double per = p.wbf ? 30.0 : 28.0;
   const double emb_extra = p.demb_part ? nemb * 4.0 * (p.dx_np - 1) : nemb * 12.0;
+  const size_t count = p.fused_w ? (size_t)p.dm.A * p.dm.E + p.dm.H + p.dm.A : p.P;
   {
-    ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)p.P * per + emb_extra), st);
-    // about 16 blocks of 256 threads per SM over all groups; each grid row is one group
-    const size_t nq = (p.P + 3) / 4;
-    size_t gx = (nq + 255) / 256;
-    const size_t cap = std::max<size_t>(1, (size_t)152 * 16 / std::max(1, p.G));
-    if (gx > cap) gx = cap;
-    launch_pdl(opt_stream_kernel, dim3((unsigned)gx, (unsigned)p.G), dim3(256), 0, st, p, T);  // also updates alpha
+    ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)count * per + emb_extra), st);
+    // one resident wave (4 blocks of 256 threads per SM, the launch bound) striding over the
+    // (group, chunk) pairs
+    const int per_group = (int)((count + kOptChunk - 1) / kOptChunk);
+    const long long chunks = (long long)per_group * p.G;
+    const unsigned grid = (unsigned)std::min<long long>(chunks, 152LL * 4);
+    if (grid == 0) return;
+    launch_pdl(opt_stream_kernel, dim3(grid), dim3(kOptThreads), 0, st, p, T, per_group);  // also updates alpha
   }
 }
 

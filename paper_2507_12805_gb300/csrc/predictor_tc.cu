@@ -69,6 +69,18 @@ struct TBase {
     return p.lane_tok[rw] + (T - p.grp_start[g]);
   }
   __device__ int npred(int g) const { return live_lanes(p, g, T - p.grp_start[g]); }
+  // Columns [lo, hi) of the logits the mixer reads for the row whose target is at tpos: with
+  // overlap masking the slice of 4^s tokens that agree with the previous token (a predicted row's
+  // token has index >= t_eff >= 1 in its lane), else all A.  A kEpi == 0 thread owns one tile row,
+  // rl = 32 (warp % 4) + lane.
+  __device__ void logit_cols(long long tpos, int A, int &lo, int &hi) const {
+    lo = 0, hi = A;
+    if (p.ov_w > 0 && tpos >= 1) {
+      lo = ((int)p.tokens[tpos - 1] % p.ov_mod) * p.ov_w;
+      hi = lo + p.ov_w;
+    }
+  }
+  __device__ static int epi_row() { return ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31); }
   __device__ const bf16 *wb(int g) const { return p.wbf + (size_t)g * p.P; }
   __device__ const long long *tp(const uint8_t *meta) const { return reinterpret_cast<const long long *>(meta); }
   __device__ const uint16_t *tk(const uint8_t *meta) const {
@@ -279,8 +291,9 @@ struct LogitsT : TwoModels {
     const float *b2;
     float *out;
     int A;
+    int lo, hi;  // the columns the mixer reads for this thread's row (the coded slice)
     __device__ void epilogue(int m, int rl, int n, const float *v) const {
-      if (tp[rl] < 0) return;
+      if (tp[rl] < 0 || n + 8 <= lo || n >= hi) return;
       float x[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) x[j] = v[j] + b2[n + j];
@@ -289,7 +302,10 @@ struct LogitsT : TwoModels {
   };
   __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
     const Dims D = d(z);
-    return {tp(meta), w32(z) + D.off_b2(), (stat(z) ? p.zu : p.zm) + (size_t)row(grp(z), 0) * D.A, D.A};
+    Epi e{tp(meta), w32(z) + D.off_b2(), (stat(z) ? p.zu : p.zm) + (size_t)row(grp(z), 0) * D.A, D.A, 0, 0};
+    const long long t = e.tp[epi_row()];
+    if (t >= 0) logit_cols(t, D.A, e.lo, e.hi);
+    return e;
   }
 };
 
@@ -659,6 +675,88 @@ struct DW1T : TBase {
   }
 };
 
+// ---- Adam in the epilogue of a weight-gradient GEMM (p.fused_w) ----
+// The 64-column chunks of the tile's FP32 gradient are staged in shared memory (kEpi 2); the whole
+// CTA then streams the chunk's master weights and moments with 16-byte accesses (16 threads per
+// row of the matrix, so a warp touches two 256-byte row segments), every load of a batch of four
+// float4 groups issued before its first store, applies the optimiser rule of the streaming
+// optimiser (adam_n, explicitly rounded: the same bits) and rewrites w, m, v and the BF16 copy.
+// The gradient of W1 and W2 never reaches global memory.  Every element of the matrix belongs to
+// exactly one tile, so each parameter is updated once per step.
+struct AdamEpi {
+  float *w, *m, *v;  // element (0, 0) of the group's matrix in each array (row pitch ld)
+  bf16 *wb;
+  int ld, rows, cols, m0, n0;
+  float lr, bc1, bc2;
+  bool adam;
+  __device__ void chunk(const float *stg, int c0) const {
+    constexpr int kPer = tc::kRows * 16 / tc::kThreads;  // float4 groups of the chunk per thread
+    constexpr int kBatch = 4;
+#pragma unroll 1
+    for (int b = 0; b < kPer; b += kBatch) {
+      float t[kBatch][4], mm[kBatch][4], vv[kBatch][4], g[kBatch][4];
+      size_t idx[kBatch];
+      bool ok[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const int f = threadIdx.x + (b + q) * tc::kThreads, r = f >> 4, c4 = (f & 15) * 4;
+        const int row = m0 + r, col = n0 + c0 + c4;
+        ok[q] = row < rows && col < cols;  // cols is a multiple of 64: a float4 is all in or all out
+        idx[q] = ok[q] ? (size_t)row * ld + col : 0;
+        if (ok[q]) {
+          const float4 a = *reinterpret_cast<const float4 *>(w + idx[q]);
+          t[q][0] = a.x, t[q][1] = a.y, t[q][2] = a.z, t[q][3] = a.w;
+          if (adam) {
+            const float4 b4 = *reinterpret_cast<const float4 *>(m + idx[q]);
+            const float4 c = *reinterpret_cast<const float4 *>(v + idx[q]);
+            mm[q][0] = b4.x, mm[q][1] = b4.y, mm[q][2] = b4.z, mm[q][3] = b4.w;
+            vv[q][0] = c.x, vv[q][1] = c.y, vv[q][2] = c.z, vv[q][3] = c.w;
+          }
+          const float4 gs = *reinterpret_cast<const float4 *>(stg + r * tc::kFloatPitch + c4);
+          g[q][0] = gs.x, g[q][1] = gs.y, g[q][2] = gs.z, g[q][3] = gs.w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        if (!ok[q]) continue;
+        adam_n<4>(t[q], mm[q], vv[q], g[q], lr, bc1, bc2, adam);
+        *reinterpret_cast<float4 *>(w + idx[q]) = make_float4(t[q][0], t[q][1], t[q][2], t[q][3]);
+        if (adam) {
+          *reinterpret_cast<float4 *>(m + idx[q]) = make_float4(mm[q][0], mm[q][1], mm[q][2], mm[q][3]);
+          *reinterpret_cast<float4 *>(v + idx[q]) = make_float4(vv[q][0], vv[q][1], vv[q][2], vv[q][3]);
+        }
+        __nv_bfloat162 lo = __floats2bfloat162_rn(t[q][0], t[q][1]), hi = __floats2bfloat162_rn(t[q][2], t[q][3]);
+        *reinterpret_cast<uint2 *>(wb + idx[q]) =
+            make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ AdamEpi adam_epi(const Plan &p, int T, int g, size_t off, int rows, int cols, int m0,
+                                            int n0) {
+  const int tau = group_tau(p, T, g);
+  const size_t base = (size_t)g * p.P + off;
+  return {p.params + base, p.m + base, p.v + base, p.wbf + base, cols, rows, cols, m0, n0,
+          p.lr, p.bc1[tau], p.bc2[tau], p.optimizer == PMKLC_ADAM};
+}
+
+// dW2 with the update of W2 in its epilogue
+struct DW2F : DW2T {
+  static constexpr int kEpi = 2;
+  __device__ AdamEpi epi_ctx(const uint8_t *, int z, int m0, int n0) const {
+    return adam_epi(p, T, z, p.dm.off_w2(), p.dm.H, p.dm.A, m0, n0);
+  }
+};
+
+// dW1 with the update of W1 (stored transposed, W1t[h][i]) in its epilogue
+struct DW1F : DW1T {
+  static constexpr int kEpi = 2;
+  __device__ AdamEpi epi_ctx(const uint8_t *, int z, int m0, int n0) const {
+    return adam_epi(p, T, z, p.dm.off_w1(), p.dm.H, p.dm.K1(), m0, n0);
+  }
+};
+
 // ---- the frozen static model in FP8 (E4M3): hidden layer and logits on kind::f8f6f4 ----
 // h = relu((X_q W1_q) c1[h] + b1) in FP32, X_q gathered from the E4M3 embedding codes (16 codes per
 // 16-byte chunk; E % 16 == 0), W1_q = the W1t codes by TMA (K-major).  The epilogue also raises the
@@ -796,8 +894,9 @@ struct LogitsF8 : TBase {
     const float *rs, *s2, *b2;
     float *zu;  // row 0 of the group
     int A;
+    int lo, hi;  // the columns the mixer reads for this thread's row (the coded slice)
     __device__ void epilogue(int m, int rl, int n, const float *v) const {
-      if (tp[rl] < 0) return;
+      if (tp[rl] < 0 || n + 8 <= lo || n >= hi) return;
       const float sr = rs[2 * rl];
       float x[8];
 #pragma unroll
@@ -806,8 +905,11 @@ struct LogitsF8 : TBase {
     }
   };
   __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
-    return {tp(meta), rs(meta), p.st8_s2, p.static_params + p.st.off_b2(), p.zu + (size_t)row(z, 0) * p.st.A,
-            p.st.A};
+    Epi e{tp(meta), rs(meta), p.st8_s2, p.static_params + p.st.off_b2(), p.zu + (size_t)row(z, 0) * p.st.A,
+          p.st.A, 0, 0};
+    const long long t = e.tp[epi_row()];
+    if (t >= 0) logit_cols(t, p.st.A, e.lo, e.hi);
+    return e;
   }
 };
 
@@ -892,7 +994,7 @@ struct TcSetup {
   Dims dm, st;
   size_t P;
   bool ok;
-  tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8;
+  tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8, t_w2f, t_w1f;
   MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
   int table_h[2], table_w1, sacc_dx, table_h8, dx_owner;
   CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
@@ -963,9 +1065,16 @@ bool build(TcSetup &S, const Plan &p) {
       return false;
   }
   S.t_w1 = tc::plan_tiles(D.H, D.K1(), p.Mmax, p.G, S.ml_w1.bytes());
+  // with the optimiser in their epilogues (p.fused_w) the weight-gradient GEMMs are bound by the
+  // stream of optimiser state: 128-column tiles and two stage buffers (their K, the predicted lanes,
+  // is a few 64-row blocks), so two CTAs share an SM and one's epilogue overlaps the other's MMAs;
+  // the staged epilogue's 128 x kFloatPitch floats fit in the two buffers
+  S.t_w2f = {min(128, D.A), 2};
+  S.t_w1f = {min(128, D.K1()), 2};
   for (const auto &pr : {std::make_pair(S.t_h, S.ml_h.bytes()), std::make_pair(S.t_l, S.ml_l.bytes()),
                          std::make_pair(S.t_dh, S.ml_dh.bytes()), std::make_pair(S.t_w2, S.ml_w2.bytes()),
-                         std::make_pair(S.t_dx, S.ml_dx.bytes()), std::make_pair(S.t_w1, S.ml_w1.bytes())})
+                         std::make_pair(S.t_dx, S.ml_dx.bytes()), std::make_pair(S.t_w1, S.ml_w1.bytes()),
+                         std::make_pair(S.t_w2f, S.ml_w2.bytes()), std::make_pair(S.t_w1f, S.ml_w1.bytes())})
     if (tc::smem_bytes(pr.first, pr.second) > limit) return false;
   // per-group weights: [G][P] BF16 with W1t [H][t*E] and W2 [H][A] inside
   const uint64_t gs = (uint64_t)p.P * 2;
@@ -1115,14 +1224,18 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
   const double R = prof_work().pred_rows;
   const Dims &D = p.dm;
   // dW2 reads only h and dz: with auxiliary streams it starts beside dh; dX and dW1 follow dh side
-  // by side, and the bias sums (db1 needs dh) follow both dW2 and dh
+  // by side, and the bias sums (db1 needs dh) follow both dW2 and dh.  With the optimiser in the
+  // dW epilogues (p.fused_w) W2 may change only once dh has read it and W1 once dX has: dW2 then
+  // follows dh, and dW1 follows dX on dX's stream.
   cudaStream_t s1 = st, s2 = st;
   if (ss) {
     cudaEventRecord(ss->fork, st);
     cudaStreamWaitEvent(ss->aux[0], ss->fork, 0);
     s1 = ss->aux[0], s2 = ss->aux[1];
   }
-  {
+  // Adam bytes of a fused update: read w, m, v, write w, m, v and the BF16 copy
+  const double tg = prof_work().train_groups, adam_b = p.optimizer == PMKLC_ADAM ? 26.0 : 10.0;
+  if (!p.fused_w) {
     ProfScope ps("bwd_dw2_bf16", 2.0 * R * D.A * D.H, 0, s1);
     DW2T op;
     op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
@@ -1141,6 +1254,12 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
   }
   launch_pdl(bias_grad_kernel, dim3((D.H + D.A + 8 * kBiasChunks - 1) / (8 * kBiasChunks), p.G),
              dim3(kBiasChunks * kBiasSlices), 0, s1, p, T);
+  if (p.fused_w) {
+    ProfScope ps("bwd_dw2_adam_bf16", 2.0 * R * D.A * D.H, tg * adam_b * D.H * D.A, s1);
+    DW2F op;
+    op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
+    tc::launch(op, D.H, D.A, p.G, S.t_w2f, S.ml_w2.bytes(), s1);
+  }
   if (S.dx_owner) {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXOwnT op;
@@ -1154,7 +1273,12 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     op.eshift = (D.E & (D.E - 1)) == 0 ? __builtin_ctz((unsigned)D.E) : -1;
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
   }
-  {
+  if (p.fused_w) {
+    ProfScope ps("bwd_dw1_adam_bf16", 2.0 * R * D.K1() * D.H, tg * adam_b * D.H * D.K1(), s2);
+    DW1F op;
+    op.p = p, op.T = T, op.ml = S.ml_w1, op.dh = S.dhmn, op.table = S.table_w1;
+    tc::launch(op, D.H, D.K1(), p.G, S.t_w1f, S.ml_w1.bytes(), s2);
+  } else {
     ProfScope ps("bwd_dw1_bf16", 2.0 * R * D.K1() * D.H, 0, st);
     DW1T op;
     op.p = p, op.T = T, op.ml = S.ml_w1, op.dh = S.dhmn, op.table = S.table_w1;

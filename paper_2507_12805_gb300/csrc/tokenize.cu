@@ -3,8 +3,9 @@
 //
 // The paper's encoder maps A/C/G/T to 0..3 and reads each window of k bases,
 // taken every s bases, as a base-4 number with the first base most
-// significant ("CGG" -> 26).  Here one thread produces one token; the
-// bases are read as bytes (they are HBM-bound streams of <= 8 bytes per token).
+// significant ("CGG" -> 26).  Here a CTA reads a segment of bases with 16-byte
+// loads, validates and packs them to 2 bits in shared memory, and cuts each token
+// from the packed stream with a shift and a mask.
 #include <stdio.h>
 
 #include <mutex>
@@ -17,35 +18,6 @@ namespace pmklc {
 __device__ __forceinline__ bool is_acgt(uint32_t c) { return c == 'A' || c == 'C' || c == 'G' || c == 'T'; }
 // A=0x41 -> 0, C=0x43 -> 1, G=0x47 -> 2, T=0x54 -> 3
 __device__ __forceinline__ uint32_t base_code(uint32_t c) { return ((c >> 1) & 3u) ^ ((c >> 2) & 1u); }
-
-__global__ void validate_kernel(const uint8_t *__restrict__ seq, size_t n, int *err) {
-  size_t head = (16 - (reinterpret_cast<uintptr_t>(seq) & 15)) & 15;
-  if (head > n) head = n;
-  size_t nvec = (n - head) / 16;
-  const uint4 *v = reinterpret_cast<const uint4 *>(seq + head);
-  size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
-  bool bad = false;
-  for (size_t i = tid; i < nvec; i += stride) {
-    uint4 w = v[i];
-    uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bad |= !is_acgt((words[q] >> (8 * b)) & 0xFF);
-  }
-  if (tid < head) bad |= !is_acgt(seq[tid]);
-  size_t t0 = head + nvec * 16;
-  if (t0 + tid < n) bad |= !is_acgt(seq[t0 + tid]);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrBadBase);
-}
-
-void launch_validate(const uint8_t *d_seq, size_t n, int *d_err, cudaStream_t st) {
-  if (n == 0) return;
-  size_t nvec = n / 16 + 1;
-  size_t grid = (nvec + 255) / 256;
-  if (grid > 152u * 16u) grid = 152u * 16u;
-  validate_kernel<<<(unsigned)grid, 256, 0, st>>>(d_seq, n, d_err);
-}
 
 __device__ __forceinline__ int find_block(const long long *off, int n_blocks, long long x) {
   // largest b with off[b] <= x (off has n_blocks + 1 ascending entries)
@@ -60,24 +32,93 @@ __device__ __forceinline__ int find_block(const long long *off, int n_blocks, lo
   return lo;
 }
 
-__global__ void tokenize_kernel(const uint8_t *__restrict__ seq, const long long *__restrict__ base_off,
-                                const long long *__restrict__ tok_off, int n_blocks, long long n_tok, int s, int k,
-                                uint16_t *__restrict__ tokens) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n_tok) return;
-  int b = find_block(tok_off, n_blocks, i);
-  long long j = i - tok_off[b];
-  const uint8_t *p = seq + base_off[b] + j * s;
-  uint32_t v = 0;
-  for (int m = 0; m < k; ++m) v = (v << 2) | base_code(p[m]);
-  tokens[i] = (uint16_t)v;
+// Fused validation and (s,k)-mer encoding.  Each CTA owns kTokSeg consecutive bases of one block
+// (its block read from a per-CTA table, then the block's offsets in one round of loads): it reads its bases
+// plus the k - 1 after them with 16-byte loads, checks the bases it owns, packs all of them to 2
+// bits (16 per 32-bit word, the first base in the most significant bits) in shared memory, and
+// writes the tokens j whose first base j*s lies in its range: token j is the 2k-bit field of the
+// packed stream at base j*s, cut from a 64-bit window of two words.
+constexpr int kTokSeg = 8192;                     // bases owned by one CTA
+constexpr int kTokWin = kTokSeg + 48;             // bytes loaded: alignment slack (< 16) + owned + k - 1 + pad
+constexpr int kTokWords = kTokWin / 16 + 1;       // packed words (+1 so a window's second word exists)
+constexpr int kTokThreads = 256;
+
+__global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
+    const uint8_t *__restrict__ seq, size_t n_all, const long long *__restrict__ base_off,
+    const long long *__restrict__ tok_off, const int *__restrict__ cta_off, const int *__restrict__ cta_blk, int s,
+    int k, uint16_t *__restrict__ tokens, int *err) {
+  __shared__ uint32_t words[kTokWords];
+  const int tid = threadIdx.x;
+  const int c = blockIdx.x;
+  const int b = cta_blk[c];  // the block this CTA works in
+  const long long nb = base_off[b + 1] - base_off[b];
+  const long long a = (long long)(c - cta_off[b]) * kTokSeg;  // first owned base (block-relative)
+  const long long own = min((long long)kTokSeg, nb - a);       // owned bases
+  const uint8_t *ga = seq + base_off[b] + a;
+  const uint8_t *g0 = reinterpret_cast<const uint8_t *>(reinterpret_cast<uintptr_t>(ga) & ~(uintptr_t)15);
+  const int sh = (int)(ga - g0);                    // window byte of owned base 0
+  const uint8_t *end = seq + n_all;
+  bool bad = false;
+  for (int w = tid; w < kTokWords; w += kTokThreads) {
+    const uint8_t *p = g0 + 16 * (size_t)w;
+    uint32_t word = 0;
+    if (p + 16 <= end && p >= seq) {  // whole vector inside the sequence
+      const uint4 v = *reinterpret_cast<const uint4 *>(p);
+      const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const uint32_t ch = (q[i >> 2] >> (8 * (i & 3))) & 0xFF;
+        const long long rel = 16LL * w + i - sh;  // owned-base index of this byte
+        if (rel >= 0 && rel < own) bad |= !is_acgt(ch);
+        word |= base_code(ch) << (30 - 2 * i);
+      }
+    } else {  // the sequence's first or last partial vector: byte loads inside it only
+#pragma unroll 1
+      for (int i = 0; i < 16; ++i) {
+        const uint8_t *pi = p + i;
+        if (pi < seq || pi >= end) continue;  // outside the sequence: code 0, never part of a token
+        const uint32_t ch = *pi;
+        const long long rel = 16LL * w + i - sh;
+        if (rel >= 0 && rel < own) bad |= !is_acgt(ch);
+        word |= base_code(ch) << (30 - 2 * i);
+      }
+    }
+    words[w] = word;
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(err, kErrBadBase);
+  __syncthreads();
+  // tokens j of this block with a <= j*s < a + own
+  const long long l = tok_off[b + 1] - tok_off[b];
+  const long long j0 = (a + s - 1) / s;
+  const long long j1 = min(l, (a + own + s - 1) / s);
+  const uint32_t mask = (1u << (2 * k)) - 1u;
+  uint16_t *out = tokens + tok_off[b];
+  for (long long j = j0 + tid; j < j1; j += kTokThreads) {
+    const int q = (int)(j * s - a) + sh;  // window byte of the token's first base
+    const int w = q >> 4, o = q & 15;
+    const unsigned long long win = ((unsigned long long)words[w] << 32) | words[w + 1];
+    out[j] = (uint16_t)((win >> (64 - 2 * o - 2 * k)) & mask);
+  }
 }
 
-void launch_tokenize(const uint8_t *d_seq, const long long *d_base_off, const long long *d_tok_off, int n_blocks,
-                     long long n_tok, int s, int k, uint16_t *d_tokens, cudaStream_t st) {
-  if (n_tok <= 0) return;
-  tokenize_kernel<<<(unsigned)((n_tok + 255) / 256), 256, 0, st>>>(d_seq, d_base_off, d_tok_off, n_blocks, n_tok, s,
-                                                                    k, d_tokens);
+std::vector<int> tokenize_ctas(const std::vector<long long> &base_off) {
+  const size_t nb = base_off.empty() ? 0 : base_off.size() - 1;
+  std::vector<int> cta(nb + 1, 0), blk;
+  for (size_t b = 0; b < nb; ++b) {
+    const int n = (int)((base_off[b + 1] - base_off[b] + kTokSeg - 1) / kTokSeg);
+    cta[b + 1] = cta[b] + n;
+    blk.insert(blk.end(), (size_t)n, (int)b);
+  }
+  cta.insert(cta.end(), blk.begin(), blk.end());
+  return cta;
+}
+
+void launch_validate_tokenize(const uint8_t *d_seq, size_t n, const long long *d_base_off, const long long *d_tok_off,
+                              const int *d_cta, int n_blocks, int n_cta, int s, int k, uint16_t *d_tokens,
+                              int *d_err, cudaStream_t st) {
+  if (n_cta <= 0) return;
+  tokenize_packed_kernel<<<n_cta, kTokThreads, 0, st>>>(d_seq, n, d_base_off, d_tok_off, d_cta, d_cta + n_blocks + 1,
+                                                        s, k, d_tokens, d_err);
 }
 
 __global__ void tails_kernel(const uint8_t *__restrict__ seq, const long long *__restrict__ base_off,

@@ -210,3 +210,57 @@ def test_bf16_bits_per_base_close_to_fp32(P):
     b = P.pmklc_compress(w.seq, w.block_lens, P.ModelConfig(**kw, static_weights=sw, precision=1))
     assert P.pmklc_decompress(b, sw)[0] == w.seq.tobytes()
     assert abs(len(b) - len(a)) <= 0.005 * len(a), (len(a), len(b))
+
+
+@pytest.mark.parametrize("optimizer", [0, 1])
+def test_update_in_gradient_epilogues_equals_the_streaming_optimiser(P, torch, optimizer):
+    """On the tcgen05 engine W1 and W2 are updated in the epilogues of their gradient GEMMs; when the
+    gradient is exported they are stored and the streaming optimiser applies the same rule.  Both
+    paths give the same parameters, moments and mixing weight bit for bit (the update arithmetic is
+    explicitly rounded, the gradients are the same FP32 values)."""
+    from oracle.codec import Config
+    from tests.test_gpu_steps import _model
+    rng = np.random.default_rng(88 + optimizer)
+    cfg_o = Config(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128)
+    G, M = 3, 150
+    dsh = cfg_o.dm_shape
+    params = np.stack([_model(rng, dsh, 5 + g, 0.05) for g in range(G)])
+    m = (rng.normal(0, 1e-3, params.shape)).astype(np.float32)
+    v = (1e-6 + rng.random(params.shape) * 1e-5).astype(np.float32)
+    alpha = np.array([0.5, 0.25, 0.8], np.float32)
+    am = np.array([1e-3, 0, -1e-3], np.float32)
+    av = np.array([1e-6, 1e-7, 2e-6], np.float32)
+    static = _model(rng, cfg_o.static_shape, 77, 0.05)
+    ctx = rng.integers(0, dsh.A, (G * M, cfg_o.t_eff)).astype(np.uint16).view(np.int16)
+    tgt = rng.integers(0, dsh.A, G * M).astype(np.uint16).view(np.int16)
+    cfg = P.ModelConfig(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128,
+                        lr=1e-3, optimizer=optimizer, static_weights=static, precision=P.PMKLC_BF16_BATCHED,
+                        update_path=P.PMKLC_UPDATE_FUSED)
+    out = []
+    for export in (False, True):
+        d = {k_: dev(torch, x) for k_, x in dict(params=params, m=m, v=v, alpha=alpha, am=am, av=av).items()}
+        d_grad = torch.zeros(params.shape, dtype=torch.float32, device="cuda") if export else None
+        P.pmklc_train_step(cfg, G, M, d["params"], d["m"], d["v"], d["alpha"], d["am"], d["av"], dev(torch, static),
+                           dev(torch, ctx), dev(torch, tgt), 3, None, d_grad, None)
+        out.append({k_: x.cpu().numpy() for k_, x in d.items()})
+    assert not np.array_equal(out[0]["params"], params)  # the step updated the parameters
+    for name in ("params", "m", "v", "alpha", "am", "av"):
+        assert np.array_equal(out[0][name].view(np.uint32), out[1][name].view(np.uint32)), name
+
+
+def test_update_paths_give_identical_containers(P):
+    """A whole BF16 run on tcgen05 shapes with W1 and W2 updated in the gradient GEMMs' epilogues,
+    by the streaming optimiser, and by the size rule: the same container byte for byte, and it
+    decodes (the decoder picks its own path)."""
+    import synth
+    from oracle.model import Shape, init_params
+    seq = synth.markov(24000, 5, 0.40, 77).tobytes()
+    lens = [8000, 8000, 8000]
+    kw = dict(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128,
+              lanes_per_block=24, smp_mode=P.PMKLC_SMP_TREE, fallback=0, overlap_mask=1,
+              precision=P.PMKLC_BF16_BATCHED)
+    sw = init_params(Shape(256, 16, 8, 64), 3)
+    outs = [P.pmklc_compress(seq, lens, P.ModelConfig(**kw, static_weights=sw, update_path=u))
+            for u in (P.PMKLC_UPDATE_STREAM, P.PMKLC_UPDATE_FUSED, P.PMKLC_UPDATE_AUTO)]
+    assert outs[0] == outs[1] == outs[2]
+    assert P.pmklc_decompress(outs[1], sw)[0] == seq
