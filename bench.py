@@ -140,13 +140,19 @@ def throttled(clocks: dict) -> bool:
     return any(r in clocks.get("reasons", []) for r in SLOWDOWNS)
 
 
-def load_workload(name: str, block_bases: int = 0):
+def load_workload(name: str, block_bases: int = 0, blocks: int = 0):
     """The named workload; block_bases > 0 keeps its number of blocks but cuts every block to that
-    many bases (same per-step shapes and model state, fewer steps: the small case for profiling)."""
+    many bases (same per-step shapes and model state, fewer steps: the small case for profiling);
+    blocks > 0 keeps only the first `blocks` blocks (fewer groups: a small device footprint for a
+    profiler capture of one kernel)."""
     import dataclasses
     import synth
     wname, kw = WORKLOADS[name]
     w = synth.workload(wname)
+    if blocks > 0 and blocks < len(w.block_lens):
+        nb = int(np.sum(w.block_lens[:blocks]))
+        w = dataclasses.replace(w, seq=np.ascontiguousarray(w.seq[:nb]), block_lens=w.block_lens[:blocks].copy(),
+                                recipe=f"{w.recipe}, first {blocks} blocks")
     if block_bases > 0:
         nb = len(w.block_lens)
         w = dataclasses.replace(w, seq=np.ascontiguousarray(w.seq[: nb * block_bases]),
@@ -272,16 +278,23 @@ PROFILE_EVERY = 8  # every 8th global step's launches are bracketed with CUDA ev
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of step kernels, from the
-# ncu --set full capture summarised in profiles/ncu_step_kernels_plain_bf16.md (the plain workload
-# cut to 2^14-base blocks: the same 64 groups x 128 lanes per launch as the full workload, so a
-# steady-state launch moves the same bytes).  Valid for the kernels as they stand in that capture.
+# DRAM traffic of step kernels from one ncu --set full capture each (dram__bytes_read.sum +
+# dram__bytes_write.sum of the captured launch, and that launch's algorithmic bytes), summarised in
+# profiles/: the captured case (the human-like workload's first 64 blocks, cut to 2^17 bases, a step
+# at which every group trains) moves the same bytes per group as the full workload, so a launch's
+# traffic is reported as the measured DRAM bytes per algorithmic byte x its algorithmic bytes.
+# Valid for the kernels as they stand in that capture.
 NCU_TRAFFIC = {
-    "bwd_dx_bf16": 10051584 + 0,            # gemm_kernel<DXOwnT>
-    "fwd_hidden_dyn_bf16": 9544448 + 0,     # gemm_kernel<HiddenT>, the 64 dynamic models
-    "fwd_hidden_static_bf16": 897792 + 0,   # gemm_kernel<HiddenT>, the shared static model
-    "update_adam": 95683840 + 19200768,     # opt_stream_kernel
+    # name: (DRAM bytes of the captured launch, its algorithmic bytes: 64 groups x H x A x 26)
+    "bwd_dw2_adam_bf16": (876706304 + 877779968, 64 * 256 * 4096 * 26),
 }
+
+
+def _traffic(name: str, work_bytes_per_launch: float):
+    if name not in NCU_TRAFFIC or not work_bytes_per_launch:
+        return None
+    dram, alg = NCU_TRAFFIC[name]
+    return dram / alg * work_bytes_per_launch
 
 
 def _bound(name: str, d: dict, pk: dict, pk_kind: str):
@@ -303,11 +316,12 @@ def _bound(name: str, d: dict, pk: dict, pk_kind: str):
         ach = d["flops"] / sec / 1e12
         return {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": ach, "peak": fpeak,
                 "unit": "TFLOP/s", "frac": ach / fpeak, "peak_source": fsrc,
-                "traffic": NCU_TRAFFIC.get(name), "work_per_launch": d["flops"] / max(d["launches"], 1),
-                "work_unit": "FLOP"}
+                "traffic": _traffic(name, d["bytes"] / max(d["launches"], 1)),
+                "work_per_launch": d["flops"] / max(d["launches"], 1), "work_unit": "FLOP"}
     ach = d["bytes"] / sec / 1e9 if d["bytes"] else 0.0
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs", "traffic": NCU_TRAFFIC.get(name),
+            "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
+            "traffic": _traffic(name, d["bytes"] / max(d["launches"], 1)),
             "work_per_launch": d["bytes"] / max(d["launches"], 1), "work_unit": "byte"}
 
 
@@ -429,6 +443,7 @@ def main():
     ap.add_argument("--no-profile", action="store_true", help="skip the untimed profiled pass")
     ap.add_argument("--block-bases", type=int, default=0,
                     help="cut every block to this many bases (profiling: same per-step shapes, fewer steps)")
+    ap.add_argument("--blocks", type=int, default=0, help="keep the first N blocks (profiling: fewer groups)")
     args = ap.parse_args()
     rank, world = _dist()
 
@@ -438,7 +453,7 @@ def main():
         # the oracle alone: the cached pre-trained static model when one is there, else the oracle's own
         # initialiser (its speed does not depend on the weights' values), so no library code runs here
         from oracle.model import Shape, init_params
-        w, kw = load_workload(args.workload, args.block_bases)
+        w, kw = load_workload(args.workload, args.block_bases, args.blocks)
         sw, sdesc = None, None
         if kw.get("use_static"):
             cached = sorted(f for f in (os.listdir(CACHE) if os.path.isdir(CACHE) else [])
@@ -460,7 +475,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    w, kw = load_workload(args.workload, args.block_bases)
+    w, kw = load_workload(args.workload, args.block_bases, args.blocks)
     sw, sdesc = static_weights(P, args.workload, kw)
     n = int(w.seq.size)
     forms = [args.form] if args.form != "both" else ["bf16", "fp32"]
@@ -486,7 +501,7 @@ def main():
     # end to end through the host-buffer C ABI (H2D of the input and of the container, D2H of both results)
     host = np.ascontiguousarray(w.seq)
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(1 if ms > 10_000 else max(1, min(args.steps, 2))):  # one when a step takes over 10 s
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         blob = P.pmklc_compress(host, w.block_lens, head["cfg"])

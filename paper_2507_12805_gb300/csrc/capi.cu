@@ -521,7 +521,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
   // optimiser of step T (it reads only tokens decoded by step T), joined by events before the
   // kernels that read their results
   StepStreams ss;
-  bool use_ss = true;
+  bool use_ss = !prof_enabled();
   for (auto &a : ss.aux) use_ss = use_ss && cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
   for (cudaEvent_t *e : {&ss.fork, &ss.join[0], &ss.join[1], &ss.count_done, &ss.mix_done, &ss.static_done})
     use_ss = use_ss && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;

@@ -17,6 +17,9 @@ struct StepWork {
 };
 void prof_step(int T, const StepWork &w);
 void prof_stop_sampling();
+// True while sampled profiling is on: the step loop then runs every kernel on the caller's stream,
+// so each sampled kernel's event time is its own duration (no concurrent kernels share its SMs).
+bool prof_enabled();
 const StepWork &prof_work();
 // Brackets one kernel launch with events when the current step is sampled.
 class ProfScope {

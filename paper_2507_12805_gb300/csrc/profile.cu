@@ -49,6 +49,7 @@ void prof_step(int T, const StepWork &w) {
   g_prof.work = w;
 }
 void prof_stop_sampling() { g_prof.on = false; }
+bool prof_enabled() { return g_prof.every > 0; }
 const StepWork &prof_work() { return g_prof.work; }
 
 ProfScope::ProfScope(const char *name, double flops, double bytes, cudaStream_t st)
