@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define PMKLC_ABI_VERSION 1
+#define PMKLC_ABI_VERSION 2
 
 /* error codes */
 #define PMKLC_OK 0
@@ -85,6 +85,15 @@ typedef struct {
   uint32_t lane_tokens;        /* 0: a block of l tokens gets min(lanes_per_block, l) lanes; else
                                   min(lanes_per_block, l, ceil(l / lane_tokens)), so lanes of uneven
                                   blocks take about the same number of steps */
+  uint32_t private_model;      /* Model Selector (§4.2.1): 0 = the static model as given (or none);
+                                  1 = a static private model (SPrM, §4.2.3) of the static shape
+                                  (emb_s, ctx_s, hid_s), pre-trained on the input by the library's
+                                  own kernels (as pmklc_train_model, starting from static_weights
+                                  when use_static, else from the seeded init), stored in the
+                                  container in BF16 and used in the static slot of Eq. (1); 2 =
+                                  automatic: SPrM for inputs above 500 MB (5e8 bases), else as 0 */
+  uint32_t private_epochs;     /* pre-training passes over the input (0 = 1) */
+  uint64_t private_bases;      /* bases at the head of the input that pre-training reads (0 = all) */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);

@@ -42,7 +42,9 @@ class CModelCfg(ctypes.Structure):
                 ("optimizer", ctypes.c_uint32), ("lr", ctypes.c_float), ("alpha_init", ctypes.c_float),
                 ("smp_mode", ctypes.c_uint32), ("smp_fraction", ctypes.c_float), ("count_order", ctypes.c_uint32),
                 ("fallback", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32)]
+                ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32),
+                ("private_model", ctypes.c_uint32), ("private_epochs", ctypes.c_uint32),
+                ("private_bases", ctypes.c_uint64)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -125,6 +127,9 @@ class ModelConfig:
     seed: int = 42
     static_weights: np.ndarray | None = field(default=None, repr=False)
     lane_tokens: int = 0
+    private_model: int = 0   # Model Selector: 0 static model as given, 1 SPrM, 2 SPrM above 500 MB
+    private_epochs: int = 1
+    private_bases: int = 0
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()
