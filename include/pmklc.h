@@ -145,7 +145,8 @@ int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, siz
 /*
  * Inverse of pmklc_compress (paper §2, decompression: the decoder replays
  * the same model updates).  static_weights/static_count must be the ones
- * used to compress when the container says a static model was used.
+ * used to compress when the container says a static model was used, unless it
+ * stores its own static private model (then they are not used).
  * Outputs: *seq (*n bases) and *block_lens (*n_blocks entries), both
  * library-allocated.  Errors: ECORRUPT, EMODEL, ENOMEM, ECUDA, ETIMEOUT.
  */
