@@ -103,6 +103,17 @@ typedef struct {
                                   (1, gradients stored, then the streaming optimiser) or
                                   PMKLC_UPDATE_FUSED (2, in the epilogues of the gradient GEMMs on the
                                   tcgen05 engine, where that engine runs them; else as 1) */
+  uint32_t private_model;      /* Model Selector (§4.2.1): 0 = the static model as given (or none);
+                                  1 = a static private model (SPrM, §4.2.3) of the static shape
+                                  (emb_s, ctx_s, hid_s), pre-trained on the input by the library's
+                                  own kernels (as pmklc_train_model, starting from static_weights
+                                  when use_static, else from the seeded init), stored in the
+                                  container in BF16 and used in the static slot of Eq. (1); 2 =
+                                  automatic: SPrM for inputs above 500 MB (5e8 bases), else as 0 */
+  uint32_t private_epochs;     /* pre-training passes over the input (0 = 1) */
+  uint64_t private_bases;      /* bases at the head of the input that pre-training reads (0 = all) */
+  uint64_t private_threshold;  /* private_model 2 selects SPrM for inputs above this many bases
+                                  (0 = 5e8, the paper's 500 MB; smaller values scale the rule down) */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);
@@ -157,7 +168,8 @@ int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, siz
 /*
  * Inverse of pmklc_compress (paper §2, decompression: the decoder replays
  * the same model updates).  static_weights/static_count must be the ones
- * used to compress when the container says a static model was used.
+ * used to compress when the container says a static model was used, unless it
+ * stores its own static private model (then they are not used).
  * Outputs: *seq (*n bases) and *block_lens (*n_blocks entries), both
  * library-allocated.  Errors: ECORRUPT, EMODEL, ENOMEM, ECUDA, ETIMEOUT.
  */

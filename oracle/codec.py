@@ -37,6 +37,16 @@ Readings where the paper is silent:
            and coded as the index within it; the loss is the slice's cross
            entropy (zero gradient outside it).  Token 0 of a lane keeps the
            full alphabet.  Recorded in the header's variant field (bit 0).
+  SPrM     the Model Selector (§4.2.1) chooses a static private model
+           (§4.2.3) when private_model is 1, or 2 and the input exceeds
+           500 MB: a model of the static shape pre-trained on the input's head
+           (private_bases, 0 = all) by this module's dynamic-model loop without
+           coding (§4(b)), private_epochs passes chained like SMP with f = 1,
+           starting from the public static model when one is given (the two
+           share structure and parameters), else from the seeded init.  Its
+           parameters are rounded to BF16 (ties to even) and stored after the
+           block records (2 bytes each, little-endian; flag bit 3); it takes
+           the static slot of Eq. (1), with the stored values.
   judge    fallback 1: the count model (countmodel.py) codes every block in the
            same lanes alongside the network, and a block is stored with it when
            that costs fewer bytes (flag in the container); fallback 2: the count
@@ -102,6 +112,10 @@ class Config:
     variant: int = 0
     lane_tokens: int = 0
     overlap_mask: int = 0
+    private_model: int = 0
+    private_epochs: int = 1
+    private_bases: int = 0
+    private_threshold: int = 0
 
     def f32(self, name: str) -> float:
         return float(np.float32(getattr(self, name)))
@@ -296,10 +310,11 @@ def _count_step(cfg: Config, b: _Block, j: int):
                 b.tokens[pos] = (int(b.tokens[pos - 1]) % (4 ** (cfg.k - cfg.s))) * (4 ** cfg.s) + v
 
 
-def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None, only=None):
+def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None, only=None, init_w=None):
     """Run the lockstep loop over all blocks (groups) in compress or decompress mode.  `only`
     (optional) maps the groups to run to the global step they stop at (None: their end); the
-    schedule is still that of every block."""
+    schedule is still that of every block.  `init_w` (optional) replaces the seeded initial
+    dynamic-model weights."""
     dshape, sshape = cfg.dm_shape, cfg.static_shape
     S = (1 if cfg.use_static else 0, 0, 1)
     # precision 2 / 3: the frozen static model in its FP8 / FP8-hidden form (fp8.py), else as stored
@@ -309,7 +324,7 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None, only=None)
     uni = TOTAL // A
     steps = [max(b.lens) if b.lens else 0 for b in blocks]
     start, parent = schedule(steps, cfg.smp_mode, cfg.f32("smp_fraction"))
-    init = init_params(dshape, cfg.seed).astype(np.float64)
+    init = (init_params(dshape, cfg.seed) if init_w is None else np.asarray(init_w, np.float32)).astype(np.float64)
     groups = [None] * len(blocks)
     T_total = max([start[g] + steps[g] for g in range(len(blocks))] + [0])
     zeros = np.zeros(dshape.count)
@@ -407,6 +422,50 @@ def _prepare(cfg: Config, codes_blocks):
     return blocks, tails
 
 
+PRIVATE_THRESHOLD = 500_000_000  # bases: the Model Selector's 500 MB (§4.2.1)
+PRIVATE_FLAG = 8                  # container flag bit: a static private model is stored
+
+
+def select_private(cfg: Config, n: int) -> bool:
+    """The Model Selector (§4.2.1): the static private model for inputs above 500 MB."""
+    return cfg.private_model == 1 or (cfg.private_model == 2 and n > (cfg.private_threshold or PRIVATE_THRESHOLD))
+
+
+def bf16_round(w) -> np.ndarray:
+    """float32 values rounded to the nearest BF16 (ties to even), as float32."""
+    u = np.asarray(w, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _pretrain(codes, cfg: Config, init_w, epochs: int) -> np.ndarray:
+    """The dynamic-model loop of cfg's dynamic shape over the tokens of `codes` in
+    cfg.lanes_per_block lanes, without coding, `epochs` passes chained like SMP with f = 1 (each
+    pass a group continuing from the previous one's state), starting from init_w (else the seeded
+    init).  Without a static model Eq. (1) forms the logits (1 - alpha) L^m and alpha trains with
+    the weights, so only their product is determined: the returned parameters carry the final
+    (1 - alpha) in the logits layer (W2, b2), so the predictor alone computes the logits the
+    training fitted (FP64).  alpha starts at cfg.alpha_init from the seeded init, and at 0 from a
+    given predictor (init_w), whose logits the training then starts from as they are."""
+    tcfg = replace(cfg, use_static=False, smp_mode=SMP_CHAIN, smp_fraction=1.0, fallback=0, private_model=0)
+    if init_w is not None:
+        tcfg = replace(tcfg, alpha_init=0.0)
+    blocks, _ = _prepare(tcfg, [np.asarray(codes)] * max(1, epochs))
+    for b in blocks:
+        b.replay = True  # tokens known, nothing coded
+    st = _run(tcfg, blocks, None, init_w=init_w)[-1]
+    theta = st.theta.copy()
+    theta[tcfg.dm_shape.offsets()["w2"][0]:] *= 1.0 - st.alpha
+    return theta
+
+
+def pretrain(codes, cfg: Config, init_w, epochs: int) -> np.ndarray:
+    """Pre-training of the static private model (§4(b), §4.2.3): a model of cfg's static shape,
+    trained as _pretrain does; returns the float32 parameters."""
+    tcfg = replace(cfg, emb_d=cfg.emb_s, ctx_d=cfg.ctx_s, hid_d=cfg.hid_s)
+    return _pretrain(codes, tcfg, init_w, epochs).astype(np.float32)
+
+
 def _check_cfg(cfg: Config, static_w):
     if not (1 <= cfg.s <= cfg.k <= 8):
         raise ValueError("need 1 <= s <= k <= 8")
@@ -415,11 +474,25 @@ def _check_cfg(cfg: Config, static_w):
     if cfg.use_static:
         if static_w is None or np.asarray(static_w).size != cfg.static_shape.count:
             raise ValueError("static weights missing or of the wrong size")
+    if cfg.private_model not in (0, 1, 2) or cfg.private_epochs < 0 or cfg.private_bases < 0:
+        raise ValueError("bad private-model settings")
+    if cfg.private_model and min(cfg.emb_s, cfg.ctx_s, cfg.hid_s) < 1:
+        raise ValueError("a private model needs the static shape")
 
 
-def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> bytes:
+def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None, private_w=None) -> bytes:
+    """private_w: the static private model to store when the Model Selector picks one (default:
+    pre-trained here, see the module docstring)."""
     _check_cfg(cfg, static_w)
     codes = base_codes(seq)
+    private = select_private(cfg, codes.size)
+    if private:
+        if private_w is None:
+            head = codes[: cfg.private_bases] if cfg.private_bases else codes
+            init = static_w if cfg.use_static else init_params(cfg.static_shape, cfg.seed)
+            private_w = pretrain(head, cfg, init, cfg.private_epochs)
+        private_w = bf16_round(private_w)
+        cfg, static_w = replace(cfg, use_static=True), private_w
     block_lens = [int(x) for x in block_lens]
     if sum(block_lens) != codes.size:
         raise ValueError("block lengths do not sum to the sequence length")
@@ -444,7 +517,9 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None) -> byte
         for x in (cnt if use_count else net):
             out_hdr += varint(len(x))
             payload += x
-    flags = (1 if cfg.use_static else 0) | (int(cfg.fallback) << 1)
+    flags = (1 if cfg.use_static else 0) | (int(cfg.fallback) << 1) | (PRIVATE_FLAG if private else 0)
+    if private:  # the private model's BF16 bits follow the block records
+        out_hdr += (np.asarray(static_w, np.float32).view(np.uint32) >> 16).astype("<u2").tobytes()
     head = HEADER.pack(MAGIC, VERSION, cfg.s, cfg.k, flags, cfg.precision, cfg.optimizer, cfg.smp_mode,
                        cfg.count_order, cfg.emb_d, cfg.ctx_d, cfg.hid_d,
                        *((cfg.emb_s, cfg.ctx_s, cfg.hid_s) if cfg.use_static else (0, 0, 0)),
@@ -466,12 +541,17 @@ def parse_header(data: bytes):
                  emb_s=f[12], ctx_s=f[13], hid_s=f[14], lanes_per_block=f[15], lr=f[16], alpha_init=f[17],
                  smp_fraction=f[18], seed=f[19], variant=f[24] & ~1, lane_tokens=f[25],
                  overlap_mask=f[24] & 1)
-    return cfg, {"static_hash": f[20], "n": f[21], "n_blocks": f[22], "crc": f[23]}
+    return cfg, {"static_hash": f[20], "n": f[21], "n_blocks": f[22], "crc": f[23],
+                 "private": bool(f[4] & PRIVATE_FLAG)}
 
 
 def decompress(data: bytes, static_w=None) -> bytes:
     cfg, meta = parse_header(data)
-    if cfg.use_static and static_hash(static_w) != meta["static_hash"]:
+    if meta["private"] and not cfg.use_static:
+        raise CorruptStream("a private model is flagged without the static slot")
+    if meta["private"]:  # the stored private model replaces any given static model
+        static_w = None
+    if cfg.use_static and not meta["private"] and static_hash(static_w) != meta["static_hash"]:
         raise ModelMismatch("static weights differ from the ones used to compress")
     if cfg.fallback > 2:
         raise CorruptStream("bad fallback mode")
@@ -496,6 +576,15 @@ def decompress(data: bytes, static_w=None) -> bytes:
             x, pos = read_varint(data, pos)
             sizes.append(x)
         recs.append((n, mode, tail, sizes))
+    if meta["private"]:
+        cnt = cfg.static_shape.count
+        if pos + 2 * cnt > len(data):
+            raise CorruptStream("truncated private model")
+        bits = np.frombuffer(data, dtype="<u2", count=cnt, offset=pos).astype(np.uint32) << 16
+        static_w = bits.view(np.float32)
+        pos += 2 * cnt
+        if static_hash(static_w) != meta["static_hash"]:
+            raise CorruptStream("private model does not match its hash")
     blocks = []
     for n, mode, tail, sizes in recs:
         l = n_tokens(n, cfg.s, cfg.k)
@@ -531,22 +620,9 @@ def size_breakdown(data: bytes) -> dict:
 
 def train_model(seq, cfg: Config, epochs: int = 1) -> np.ndarray:
     """Pre-training of a static predictor (§4, the static public model, Fig. 2(a)) with the
-    dynamic-model loop alone: the bases are tokenised and cut into cfg.lanes_per_block lanes, and
-    the loop of compress runs over them `epochs` times without coding, each epoch a group that starts
-    from the previous one's final state (step-wise passing with f = 1), the first from
-    init_params(dm_shape, cfg.seed).  Without a static model Eq. (1) gives the logits
-    (1 - alpha) L^m; the returned parameters carry that factor in the logits layer (W2, b2), so the
-    predictor alone computes the logits the training fitted."""
-    codes = base_codes(seq)
-    c = replace(cfg, use_static=False, smp_mode=SMP_CHAIN, smp_fraction=1.0, fallback=0)
-    blocks, _ = _prepare(c, [codes] * epochs)
-    for b in blocks:
-        b.replay = True  # tokens known, nothing coded
-    st = _run(c, blocks, None)[-1]
-    theta = st.theta.copy()
-    lo = c.dm_shape.offsets()["w2"][0]
-    theta[lo:] *= 1.0 - st.alpha
-    return theta
+    dynamic-model loop alone, as _pretrain: the bases are tokenised and cut into
+    cfg.lanes_per_block lanes, `epochs` passes, starting from init_params(dm_shape, cfg.seed)."""
+    return _pretrain(base_codes(seq), cfg, None, epochs)
 
 
 def block_streams(seq, block_lens, cfg: Config, static_w, g: int):

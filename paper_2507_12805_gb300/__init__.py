@@ -44,7 +44,9 @@ class CModelCfg(ctypes.Structure):
                 ("smp_mode", ctypes.c_uint32), ("smp_fraction", ctypes.c_float), ("count_order", ctypes.c_uint32),
                 ("fallback", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32),
-                ("overlap_mask", ctypes.c_uint32), ("update_path", ctypes.c_uint32)]
+                ("overlap_mask", ctypes.c_uint32), ("update_path", ctypes.c_uint32),
+                ("private_model", ctypes.c_uint32), ("private_epochs", ctypes.c_uint32),
+                ("private_bases", ctypes.c_uint64), ("private_threshold", ctypes.c_uint64)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -129,6 +131,10 @@ class ModelConfig:
     lane_tokens: int = 0
     overlap_mask: int = 0    # 1: code token j >= 1 over the 4^s tokens consistent with token j - 1
     update_path: int = 0     # PMKLC_UPDATE_AUTO / _STREAM / _FUSED (same bytes either way)
+    private_model: int = 0   # Model Selector: 0 static model as given, 1 SPrM, 2 SPrM above 500 MB
+    private_epochs: int = 1
+    private_bases: int = 0
+    private_threshold: int = 0  # private_model 2: SPrM above this many bases (0 = 5e8)
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()

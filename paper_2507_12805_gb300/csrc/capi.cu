@@ -140,6 +140,7 @@ constexpr uint8_t kVersion = 1;
 // Each block is one model group; the GEMMs run the groups of both models (static and dynamic)
 // along the grid's z dimension and the per-group kernels along y, both limited to 65,535.
 constexpr uint32_t kMaxGroups = 32767;
+constexpr uint8_t kPrivateFlag = 8;  // container flags bit 3: a static private model is stored
 
 // ---------------------------------------------------------------- configuration
 
@@ -152,6 +153,9 @@ struct Cfg {
   uint64_t seed;
   int mask = 0;                        // overlap-masked coding (s < k)
   int update_path = PMKLC_UPDATE_AUTO;  // where W1 and W2 are updated (the same bytes either way)
+  int priv = 0, priv_epochs = 1;      // Model Selector: static private model (0 off, 1 on, 2 auto)
+  unsigned long long priv_bases = 0;  // bases of the input's head its pre-training reads (0 = all)
+  unsigned long long priv_threshold = 0;  // the selector's input size in bases (0 = 5e8, the paper's 500 MB)
   int A() const { return 1 << (2 * k); }
   int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
 };
@@ -177,6 +181,10 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
   if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
   if (c->overlap_mask > 1 || c->update_path > PMKLC_UPDATE_FUSED) return PMKLC_EINVAL;
+  if (c->private_model > 2 || c->private_epochs > kMaxGroups) return PMKLC_EINVAL;
+  if (c->private_model && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
+                           c->hid_s > 65535))
+    return PMKLC_EINVAL;
   o.s = (int)c->s;
   o.k = (int)c->k;
   o.use_static = c->use_static ? 1 : 0;
@@ -187,7 +195,11 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   o.fallback = (int)c->fallback;
   int A = 1 << (2 * c->k);
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
-  o.st = o.use_static ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
+  o.st = o.use_static || c->private_model ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
+  o.priv = (int)c->private_model;
+  o.priv_epochs = c->private_epochs ? (int)c->private_epochs : 1;
+  o.priv_bases = c->private_bases;
+  o.priv_threshold = c->private_threshold;
   o.mask = (int)c->overlap_mask;
   o.update_path = (int)c->update_path;
   o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
@@ -237,7 +249,7 @@ bool layout_fits(const std::vector<unsigned long long> &lens, const Cfg &c, int 
     lanes += Mb;
     mx = std::max(mx, steps[g]);
   }
-  const long long hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
+  const long long hmax = std::max(c.dm.H, c.use_static || c.priv ? c.st.H : 0);
   if (lanes > kMaxLanes || lanes * hmax >= (1LL << 31)) return false;
   long long T = 0, start = 0;
   const long long D = (long long)ceil(f * (double)mx);
@@ -342,6 +354,7 @@ struct Run {
   std::vector<int> pair_off;  // T -> offset (pairs) into d_pairs
   uint64_t launches = 0;
   bool net = true;            // run the network (false: count model only)
+  const float *init_host = nullptr;  // initial parameters of every group (default: the seeded init)
   CountPlan cp{};
   std::vector<int> cmode;     // per group: count model 0 off, 1 encode, 2 decode
 };
@@ -503,7 +516,10 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
     cudaMemsetAsync(p.dz, 0, sizeof(float) * NL * A, ar.st);
   cudaMemsetAsync(p.err, 0, sizeof(int), ar.st);
   std::vector<float> init;
-  init_params(c.dm, c.seed, init);
+  if (R.init_host)
+    init.assign(R.init_host, R.init_host + c.dm.count());
+  else
+    init_params(c.dm, c.seed, init);
   float *d_init = ar.upload(init);
   if (ar.failed) return PMKLC_ENOMEM;
   launch_init_groups(p, d_init, c.alpha0, ar.st);
@@ -660,8 +676,27 @@ int err_to_rc(int e) {
   return PMKLC_OK;
 }
 
+// The Model Selector (§4.2.1): the static private model for inputs above 500 MB (5e8 bases), or
+// above the configured threshold
+bool private_selected(const Cfg &c, unsigned long long n) {
+  return c.priv == 1 || (c.priv == 2 && n > (c.priv_threshold ? c.priv_threshold : 500000000ull));
+}
+
+// float32 rounded to the nearest BF16 (ties to even), as float32
+float bf16_round_host(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  float y;
+  memcpy(&y, &u, 4);
+  return y;
+}
+
 size_t bound_of(const std::vector<unsigned long long> &lens, const Cfg &c) {
   size_t b = kHeader;
+  unsigned long long n_all = 0;
+  for (unsigned long long n : lens) n_all += n;
+  if (private_selected(c, n_all)) b += 2 * c.st.count();  // the stored private model, BF16
   for (unsigned long long n : lens) {
     long long l = n_tokens_of((long long)n, c.s, c.k);
     long long Mb = lanes_of(l, c.lanes, c.lane_tokens);
@@ -674,6 +709,89 @@ size_t bound_of(const std::vector<unsigned long long> &lens, const Cfg &c) {
     b += 10 + 1 + 2 + (size_t)Mb * 10 + stream;
   }
   return b;
+}
+
+// ---------------------------------------------------------------- pre-training
+
+// The dynamic-model loop over device bases without coding (the pre-training of a static model,
+// §4(b)): the n bases are tokenised and cut into c.lanes lanes; `epochs` passes are consecutive
+// groups chained with f = 1, each continuing from the previous one's state; the last state's
+// parameters go to out (host).  init: the starting parameters (host), else the seeded init.
+// Without a static model Eq. (1) forms the logits (1 - alpha) L^m, and alpha trains with the
+// weights: only the product is determined, and the pair drifts along (alpha, L^m) -> (alpha',
+// L^m (1 - alpha) / (1 - alpha')).  So the final (1 - alpha) goes into the returned logits layer
+// (W2 and b2, in FP32): the returned predictor alone computes the logits the training fitted.
+// alpha starts at c.alpha0 from the seeded init, and at 0 from a given predictor (init), whose
+// logits the training then starts from as they are.
+int train_dev(const Cfg &c, const uint8_t *d_seq, size_t n, uint32_t epochs, const float *init, float *out,
+              cudaStream_t st) {
+  if (c.use_static || !out || (n && !d_seq) || epochs < 1 || epochs > kMaxGroups) return PMKLC_EINVAL;
+  Run R;
+  R.c = c;
+  if (init) R.c.alpha0 = 0.f;
+  R.init_host = init;
+  std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
+  if (!layout_fits(lens, c, PMKLC_SMP_CHAIN, 1.0f)) return PMKLC_EINVAL;
+  make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
+  make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
+  Arena ar(st);
+  uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
+  if (ar.failed) return PMKLC_ENOMEM;
+  // every epoch reads the same bases: tokenised once as one block, copied to the other epochs
+  const std::vector<long long> one_off = {0, (long long)n}, tok_one = {0, R.L.tok_off[1]};
+  const std::vector<int> one_cta = tokenize_ctas(one_off);
+  long long *d_one_off = ar.upload(one_off);
+  long long *d_tok_one = ar.upload(tok_one);
+  int *d_one_cta = ar.upload(one_cta);
+  std::vector<int> grp_mode(R.L.G, kReplay);
+  R.p.tokens = d_tokens;
+  R.p.lane_buf = nullptr;
+  std::vector<unsigned long long> zoff(std::max(R.L.NL, 1), 0);
+  std::vector<uint32_t> zcap(std::max(R.L.NL, 1), 0);
+  R.p.lane_buf_off = ar.upload(zoff);
+  R.p.lane_buf_cap = ar.upload(zcap);
+  if (ar.failed) return PMKLC_ENOMEM;
+  int rc = setup_run(ar, R, grp_mode, nullptr);
+  if (rc) return rc;
+  launch_validate_tokenize(d_seq, n, d_one_off, d_tok_one, d_one_cta, 1, one_cta[1], c.s, c.k, d_tokens, R.p.err,
+                           st);
+  for (int g = 1; g < R.L.G; ++g)  // identical tokens for every epoch
+    cudaMemcpyAsync(d_tokens + R.L.tok_off[g], d_tokens, sizeof(uint16_t) * (size_t)R.L.tok_off[1],
+                    cudaMemcpyDeviceToDevice, st);
+  run_steps(R, grp_mode, st);
+  int h_err = 0;
+  float alpha = 0.f;
+  cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const int last = R.L.G - 1;
+  cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&alpha, R.p.alpha + last, sizeof(float), cudaMemcpyDeviceToHost, st);
+  PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
+  PMKLC_CUDA_TRY(cudaGetLastError());
+  if (h_err) return err_to_rc(h_err);
+  const float keep = 1.f - alpha;
+  for (size_t i = c.dm.off_w2(); i < c.dm.count(); ++i) out[i] *= keep;
+  return PMKLC_OK;
+}
+
+// The static private model of a compression (§4.2.3): a model of the static shape pre-trained on
+// the input's head, starting from the public static model when one is given (the two share
+// structure and parameters), else from the seeded init; returned rounded to BF16.
+int pretrain_private(const Cfg &c, const pmklc_model_cfg *cfg, const uint8_t *d_seq, size_t n, cudaStream_t st,
+                     std::vector<float> &w) {
+  Cfg tc = c;
+  tc.use_static = 0, tc.priv = 0, tc.fallback = 0;
+  tc.dm = c.st;
+  const size_t n_train = c.priv_bases ? (size_t)std::min<unsigned long long>(c.priv_bases, n) : n;
+  std::vector<float> init;
+  if (c.use_static)
+    init.assign(cfg->static_weights, cfg->static_weights + c.st.count());
+  else
+    init_params(c.st, c.seed, init);
+  w.assign(c.st.count(), 0.f);
+  int rc = train_dev(tc, d_seq, n_train, (uint32_t)c.priv_epochs, init.data(), w.data(), st);
+  if (rc) return rc;
+  for (float &x : w) x = bf16_round_host(x);
+  return PMKLC_OK;
 }
 
 // ---------------------------------------------------------------- compress
@@ -692,6 +810,15 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   for (auto x : lens) sum += x;
   if (sum != n || !layout_fits(lens, c, c.smp_mode, c.smp_f)) return PMKLC_EINVAL;
   if (out_cap < bound_of(lens, c)) return PMKLC_ENOSPC;
+  // Model Selector (§4.2.1): a static private model (§4.2.3) pre-trained on the input takes the
+  // static slot of Eq. (1); its BF16 values are what both sides use
+  std::vector<float> priv_w;
+  const bool priv = private_selected(c, n);
+  if (priv) {
+    rc = pretrain_private(c, cfg, d_seq, n, st, priv_w);
+    if (rc) return rc;
+    R.c.use_static = 1;
+  }
   make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
   make_schedule(R.L, c.smp_mode, c.smp_f, c.t_eff(), R.S);
   const Layout &L = R.L;
@@ -701,10 +828,11 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   uint64_t shash = 0;
   if (c.use_static) {
     size_t cnt = c.st.count();
-    shash = fnv1a(cfg->static_weights, cnt * sizeof(float));
+    const float *sw = priv ? priv_w.data() : cfg->static_weights;
+    shash = fnv1a(sw, cnt * sizeof(float));
     float *d = ar.alloc<float>(cnt);
     if (!d) return PMKLC_ENOMEM;
-    cudaMemcpyAsync(d, cfg->static_weights, cnt * sizeof(float), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d, sw, cnt * sizeof(float), cudaMemcpyHostToDevice, st);
     d_static = d;
   }
   std::vector<int> grp_mode(L.G, kEncode);
@@ -785,7 +913,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   std::vector<uint8_t> H;
   H.reserve(kHeader + (size_t)L.G * 16 + (size_t)L.NL * 3);
   H.insert(H.end(), {'P', 'M', 'K', 'L'});
-  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback << 1));
+  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback << 1) | (priv ? kPrivateFlag : 0));
   uint8_t b8[8] = {kVersion, (uint8_t)c.s, (uint8_t)c.k, flags, (uint8_t)c.precision, (uint8_t)c.optimizer,
                    (uint8_t)c.smp_mode, (uint8_t)c.count_order};
   H.insert(H.end(), b8, b8 + 8);
@@ -833,6 +961,11 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
     }
     (use_cnt ? n_cnt : n_net)++;
   }
+  for (float x : priv_w) {  // the private model's BF16 bits follow the block records
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    put_le<uint16_t>(H, (uint16_t)(u >> 16));
+  }
   size_t total = H.size() + pay;
   if (total > out_cap) return PMKLC_ENOSPC;
   for (size_t q = 0; q < seg.size(); q += 4) seg[q + 1] += H.size();
@@ -868,6 +1001,8 @@ struct Parsed {
   std::vector<std::vector<uint64_t>> sizes;  // per block: lane sizes or {count size}
   size_t header_len = 0;
   unsigned long long payload = 0;
+  bool priv = false;            // a static private model is stored after the block records
+  std::vector<float> priv_w;    // its values (BF16, widened)
 };
 
 int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
@@ -881,6 +1016,8 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.smp_mode = h[10];
   c.count_order = h[11];
   c.fallback = (h[7] >> 1) & 3;
+  P.priv = (h[7] & kPrivateFlag) != 0;
+  if (P.priv && !c.use_static) return PMKLC_ECORRUPT;  // the private model takes the static slot
   if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 ||
       c.fallback > 2 || c.precision > PMKLC_BF16_FP8HIDDEN)
     return PMKLC_ECORRUPT;
@@ -947,6 +1084,17 @@ int parse_records(const uint8_t *h, size_t len, size_t in_len, Parsed &P) {
     }
   }
   if (sum != P.n || !layout_fits(P.lens, c, c.smp_mode, c.smp_f)) return PMKLC_ECORRUPT;
+  if (P.priv) {  // the private model's BF16 values, checked against the header's hash
+    const size_t cnt = c.st.count();
+    if (pos > len || cnt > (len - pos) / 2) return PMKLC_ECORRUPT;
+    P.priv_w.resize(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+      const uint32_t u = ((uint32_t)h[pos + 2 * i] | (uint32_t)h[pos + 2 * i + 1] << 8) << 16;
+      memcpy(&P.priv_w[i], &u, 4);
+    }
+    pos += 2 * cnt;
+    if (fnv1a(P.priv_w.data(), cnt * sizeof(float)) != P.shash) return PMKLC_ECORRUPT;
+  }
   P.header_len = pos;
   P.payload = pay;
   if (pos + pay != in_len) return PMKLC_ECORRUPT;
@@ -967,7 +1115,11 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
   // the block records end within n_blocks x (23 + 10 x lanes) bytes of the fixed header
   const size_t per_block = 23 + 10 * (size_t)P.c.lanes;
   size_t hl = in_len;
-  if (P.n_blocks <= (in_len - kHeader) / per_block) hl = std::min(in_len, kHeader + P.n_blocks * per_block);
+  if (P.n_blocks <= (in_len - kHeader) / per_block) {
+    hl = std::min(in_len, kHeader + P.n_blocks * per_block);
+    const size_t model = P.priv ? 2 * P.c.st.count() : 0;  // and the stored private model
+    hl = model > in_len - hl ? in_len : hl + model;
+  }
   h.resize(hl);
   PMKLC_CUDA_TRY(cudaMemcpyAsync(h.data(), d_in, hl, cudaMemcpyDeviceToHost, st));
   PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -979,7 +1131,10 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
   Run R;
   R.c = P.c;
   const Cfg &c = R.c;
-  if (c.use_static) {
+  if (P.priv) {  // the container's own private model (any given static model is not used)
+    static_weights = P.priv_w.data();
+    static_count = P.priv_w.size();
+  } else if (c.use_static) {
     if (!static_weights || static_count != c.st.count()) return PMKLC_EMODEL;
     if (fnv1a(static_weights, static_count * sizeof(float)) != P.shash) return PMKLC_EMODEL;
   }
@@ -1307,56 +1462,11 @@ int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, 
     if (rc) return rc;
     if (c.use_static || !out || (n && !seq) || epochs < 1 || epochs > kMaxGroups) return PMKLC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    Run R;
-    R.c = c;
-    // one group holding all training tokens; epochs are consecutive groups chained with f = 1
-    std::vector<unsigned long long> lens(epochs, (unsigned long long)n);
-    if (!layout_fits(lens, c, PMKLC_SMP_CHAIN, 1.0f)) return PMKLC_EINVAL;
-    make_layout(lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
-    make_schedule(R.L, PMKLC_SMP_CHAIN, 1.0f, c.t_eff(), R.S);
     Arena ar(st);
     uint8_t *d_seq = ar.alloc<uint8_t>(n);
-    uint16_t *d_tokens = ar.alloc<uint16_t>(R.L.n_tok);
     if (ar.failed) return PMKLC_ENOMEM;
-    // every epoch reads the same bases: tokenised once as one block, copied to the other epochs
-    const std::vector<long long> one_off = {0, (long long)n}, tok_one = {0, R.L.tok_off[1]};
-    const std::vector<int> one_cta = tokenize_ctas(one_off);
-    long long *d_one_off = ar.upload(one_off);
-    long long *d_tok_one = ar.upload(tok_one);
-    int *d_one_cta = ar.upload(one_cta);
-    std::vector<int> grp_mode(R.L.G, kReplay);
-    R.p.tokens = d_tokens;
-    R.p.lane_buf = nullptr;
-    std::vector<unsigned long long> zoff(std::max(R.L.NL, 1), 0);
-    std::vector<uint32_t> zcap(std::max(R.L.NL, 1), 0);
-    R.p.lane_buf_off = ar.upload(zoff);
-    R.p.lane_buf_cap = ar.upload(zcap);
-    if (ar.failed) return PMKLC_ENOMEM;
-    rc = setup_run(ar, R, grp_mode, nullptr);
-    if (rc) return rc;
     cudaMemcpyAsync(d_seq, seq, n, cudaMemcpyHostToDevice, st);
-    launch_validate_tokenize(d_seq, n, d_one_off, d_tok_one, d_one_cta, 1, one_cta[1], c.s, c.k, d_tokens,
-                             R.p.err, st);
-    for (int g = 1; g < R.L.G; ++g)  // identical tokens for every epoch
-      cudaMemcpyAsync(d_tokens + R.L.tok_off[g], d_tokens, sizeof(uint16_t) * (size_t)R.L.tok_off[1],
-                      cudaMemcpyDeviceToDevice, st);
-    run_steps(R, grp_mode, st);
-    int h_err = 0;
-    cudaMemcpyAsync(&h_err, R.p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    int last = R.L.G - 1;
-    float alpha = 0.f;
-    cudaMemcpyAsync(out, R.p.params + (size_t)last * R.p.P, sizeof(float) * R.p.P, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&alpha, R.p.alpha + last, sizeof(float), cudaMemcpyDeviceToHost, st);
-    PMKLC_CUDA_TRY(cudaStreamSynchronize(st));
-    PMKLC_CUDA_TRY(cudaGetLastError());
-    if (h_err) return err_to_rc(h_err);
-    // Without a static model Eq. (1) gives the logits (1 - alpha) L^m, and alpha trains with the
-    // weights: only the product is determined, and the pair drifts along (alpha, L^m) ->
-    // (alpha', L^m (1 - alpha) / (1 - alpha')).  The predictor the training fitted is the product,
-    // so (1 - alpha) goes into the logits layer (W2 and b2).
-    const float keep = 1.f - alpha;
-    for (size_t i = c.dm.off_w2(); i < c.dm.count(); ++i) out[i] *= keep;
-    return PMKLC_OK;
+    return train_dev(c, d_seq, n, epochs, nullptr, out, st);
   });
 }
 

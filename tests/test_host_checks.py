@@ -228,3 +228,44 @@ def test_lane_partition_matches_oracle_through_the_size_bound(P):
             stream = 3 * l + 8 * Mb if fallback != 2 else 2 * (k * Mb + s * (l - Mb)) + 8 * Mb
             want += 13 + 10 * Mb + stream
         assert P.pmklc_compress_bound(sum(lens), lens, P.ModelConfig(**kw)) == want, (kw, lens)
+
+
+def _private_container():
+    from oracle.codec import Config
+    seq = (b"ACGTTGCAAC" * 40)
+    cfg = Config(s=1, k=3, emb_s=8, ctx_s=4, hid_s=16, emb_d=4, ctx_d=4, hid_d=8, lanes_per_block=2,
+                 count_order=3, fallback=0, private_model=1)
+    return ocodec.compress(seq, [len(seq)], cfg), cfg
+
+
+def test_private_model_container_parses_on_the_host(P):
+    """An oracle-written container with a stored private model passes the host parser (the call
+    then reaches the device stage: ECUDA without a GPU); a private flag without the static slot,
+    a cut model and a flipped model bit are corrupt."""
+    out, cfg = _private_container()
+    assert ocodec.parse_header(out)[1]["private"]
+    assert _rc(P, lambda: P.pmklc_decompress(out)) == P.PMKLC_ECUDA
+    bad = bytearray(out)
+    bad[7] &= ~1
+    assert _rc(P, lambda: P.pmklc_decompress(bytes(bad))) == P.PMKLC_ECORRUPT
+    # one block record (varint n, mode, no tail bytes, one length per lane), then the model
+    p = 80 + len(ocodec.varint(400)) + 1
+    for _ in ocodec.lanes(ocodec.n_tokens(400, 1, 3), 2)[1]:
+        _, p = ocodec.read_varint(out, p)
+    n_model = 2 * P.model_count(3, 8, 4, 16)
+    flip = bytearray(out)
+    flip[p + 11] ^= 0x02
+    assert _rc(P, lambda: P.pmklc_decompress(bytes(flip))) == P.PMKLC_ECORRUPT
+    assert _rc(P, lambda: P.pmklc_decompress(out[:p + n_model - 1])) == P.PMKLC_ECORRUPT
+
+
+def test_private_model_bound_and_configuration(P):
+    kw = dict(s=1, k=3, emb_d=4, ctx_d=4, hid_d=8, lanes_per_block=2, fallback=0)
+    plain = P.pmklc_compress_bound(400, [400], P.ModelConfig(**kw))
+    with_p = P.pmklc_compress_bound(400, [400], P.ModelConfig(**kw, private_model=1, emb_s=8, ctx_s=4, hid_s=16))
+    assert with_p - plain == 2 * P.model_count(3, 8, 4, 16)
+    # automatic selection: only inputs above 500 MB get the private model
+    auto = P.pmklc_compress_bound(400, [400], P.ModelConfig(**kw, private_model=2, emb_s=8, ctx_s=4, hid_s=16))
+    assert auto == plain
+    for bad in [dict(private_model=3, emb_s=8, ctx_s=4, hid_s=16), dict(private_model=1)]:
+        assert P.pmklc_compress_bound(400, [400], P.ModelConfig(**kw, **bad)) == 0
