@@ -348,6 +348,11 @@ FORMS = {"bf16": 1, "fp32": 0}
 AUTOTUNE_LANES = (64, 128, 192, 256, 320)  # candidates from the FP32 plain form's setting up
 
 
+# kernel variants: gemm_tiles (0 default plan, 1 column tiles <= 128, 2 <= 64) | update_path << 2
+# (1 streaming optimiser, 2 Adam in the dW epilogues)
+VARIANTS = tuple(t | (u << 2) for t in (0, 1, 2) for u in (1, 2))
+
+
 def lane_candidates(kw):
     return tuple(x for x in AUTOTUNE_LANES if x >= kw["lanes_per_block"])
 
@@ -370,6 +375,15 @@ def measure(P, torch, w, kw, sw, form, steps, warmup, dev, world, profile=True, 
         tune = {"lanes_per_block": chosen, "candidates": list(cand), "sample_bytes": [int(x) for x in sizes],
                 "sample_ms": [round(float(x), 2) for x in tms], "sample": "first 8 blocks, compress only",
                 "rule": "fastest with coded size <= 1.005 x the first candidate's"}
+        # the kernel variant (row-GEMM tile cap x where W1/W2 are updated): the same bytes for every
+        # one, timed on the heads of all blocks (every global step has the full run's groups and lanes)
+        head = chosen * (max(kw["ctx_d"], kw.get("ctx_s", 0)) + 64) * kw["s"]
+        code, vms = P.pmklc_autotune_variant(d, w.block_lens, cfg, VARIANTS, head_bases=head)
+        tune.update({"variant": code, "variant_candidates": list(VARIANTS),
+                     "variant_ms": [round(float(x), 2) for x in vms],
+                     "variant_sample": f"the first {head} bases of every block, compress only",
+                     "variant_rule": "fastest (every variant codes the same bytes)",
+                     "gemm_tiles": cfg.gemm_tiles, "update_path": cfg.update_path})
         del d
     stream = torch.cuda.current_stream()
     d_seq = torch.from_numpy(w.seq).to(dev)

@@ -114,6 +114,12 @@ typedef struct {
   uint64_t private_bases;      /* bases at the head of the input that pre-training reads (0 = all) */
   uint64_t private_threshold;  /* private_model 2 selects SPrM for inputs above this many bases
                                   (0 = 5e8, the paper's 500 MB; smaller values scale the rule down) */
+  uint32_t gemm_tiles;         /* tile variant of the tcgen05 row GEMMs (hidden, logits, dh, dX):
+                                  0 the default plan, 1 column tiles of at most 128, 2 at most 64;
+                                  like update_path an implementation choice that leaves every coded
+                                  byte unchanged (the reduction over K of each output element is the
+                                  same); both are recorded in the container's variant field, so
+                                  decompression runs the same kernels */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);
@@ -147,6 +153,18 @@ int pmklc_init_model(uint32_t k, uint32_t emb, uint32_t ctx, uint32_t hid, uint6
  */
 int pmklc_train_model(const uint8_t *seq, size_t n, const pmklc_model_cfg *cfg, uint32_t epochs, void *stream,
                       float *out);
+
+/*
+ * Kernel-variant autotuner (measurement support; the paper has no counterpart): times a
+ * compression of the heads of all n_blocks blocks (the first head_bases bases of each, so every
+ * global step has the full run's groups and lanes) under each candidate variant code
+ * (gemm_tiles | update_path << 2), picks the fastest and sets cfg->gemm_tiles and cfg->update_path.
+ * Every variant gives the same container.  d_seq: the device input (n bases); ms (optional, host):
+ * n_variants times in milliseconds.  Errors: EINVAL (bad cfg, codes, block lengths), ENOMEM, ECUDA.
+ */
+int pmklc_autotune_variant(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                           uint64_t head_bases, pmklc_model_cfg *cfg, const uint32_t *variants, size_t n_variants,
+                           void *stream, float *ms);
 
 /* Default configuration for (s,k) with dynamic model (E,t,H) = (emb, ctx, hid). */
 void pmklc_default_cfg(pmklc_model_cfg *cfg, uint32_t s, uint32_t k, uint32_t emb, uint32_t ctx,

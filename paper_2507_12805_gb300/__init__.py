@@ -46,7 +46,8 @@ class CModelCfg(ctypes.Structure):
                 ("static_weights", ctypes.POINTER(ctypes.c_float)), ("lane_tokens", ctypes.c_uint32),
                 ("overlap_mask", ctypes.c_uint32), ("update_path", ctypes.c_uint32),
                 ("private_model", ctypes.c_uint32), ("private_epochs", ctypes.c_uint32),
-                ("private_bases", ctypes.c_uint64), ("private_threshold", ctypes.c_uint64)]
+                ("private_bases", ctypes.c_uint64), ("private_threshold", ctypes.c_uint64),
+                ("gemm_tiles", ctypes.c_uint32)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -90,6 +91,7 @@ _sigs = {
     "pmklc_init_model": ([_u32, _u32, _u32, _u32, _u64, _vp], _i),
     "pmklc_train_model": ([_vp, _sz, _cfgp, _u32, _vp, _vp], _i),
     "pmklc_autotune_lanes": ([_vp, _sz, _vp, _sz, _sz, _cfgp, _vp, _sz, ctypes.c_float, _vp, _vp, _vp], _i),
+    "pmklc_autotune_variant": ([_vp, _sz, _vp, _sz, _u64, _cfgp, _vp, _sz, _vp, _vp], _i),
     "pmklc_profile_enable": ([_i], _i),
     "pmklc_profile_read": ([ctypes.POINTER(CKernelProf), _i, ctypes.POINTER(_i)], _i),
 }
@@ -135,6 +137,7 @@ class ModelConfig:
     private_epochs: int = 1
     private_bases: int = 0
     private_threshold: int = 0  # private_model 2: SPrM above this many bases (0 = 5e8)
+    gemm_tiles: int = 0      # row GEMMs' column tiles: 0 default, 1 at most 128, 2 at most 64 (same bytes)
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()
@@ -375,3 +378,17 @@ def pmklc_init_model(k: int, E: int, t: int, H: int, seed: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.float32)
     _check(lib.pmklc_init_model(k, E, t, H, seed, out.ctypes.data_as(_vp)), "pmklc_init_model")
     return out
+
+
+def pmklc_autotune_variant(d_seq, block_lens, cfg: ModelConfig, variants, head_bases: int, stream=None):
+    """Pick the fastest kernel variant (gemm_tiles | update_path << 2) for `cfg` on the heads of all
+    blocks; returns (chosen code, ms) and sets cfg.gemm_tiles and cfg.update_path."""
+    bl = np.ascontiguousarray(block_lens, dtype=np.uint64)
+    codes = np.ascontiguousarray(variants, dtype=np.uint32)
+    c = cfg.to_c()
+    ms = np.zeros(codes.size, dtype=np.float32)
+    _check(lib.pmklc_autotune_variant(_ptr(d_seq), d_seq.numel(), bl.ctypes.data_as(_vp), bl.size, head_bases,
+                                      ctypes.byref(c), codes.ctypes.data_as(_vp), codes.size, _stream(stream),
+                                      ms.ctypes.data_as(_vp)), "pmklc_autotune_variant")
+    cfg.gemm_tiles, cfg.update_path = int(c.gemm_tiles), int(c.update_path)
+    return cfg.gemm_tiles | (cfg.update_path << 2), ms

@@ -153,6 +153,7 @@ struct Cfg {
   uint64_t seed;
   int mask = 0;                        // overlap-masked coding (s < k)
   int update_path = PMKLC_UPDATE_AUTO;  // where W1 and W2 are updated (the same bytes either way)
+  int gemm_tiles = 0;                   // row GEMMs' column-tile cap: 0 default, 1 128, 2 64 (same bytes)
   int priv = 0, priv_epochs = 1;      // Model Selector: static private model (0 off, 1 on, 2 auto)
   unsigned long long priv_bases = 0;  // bases of the input's head its pre-training reads (0 = all)
   unsigned long long priv_threshold = 0;  // the selector's input size in bases (0 = 5e8, the paper's 500 MB)
@@ -180,7 +181,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (!(c->lr > 0.f) || !isfinite(c->lr) || !isfinite(c->alpha_init)) return PMKLC_EINVAL;
   if (!(c->smp_fraction >= 0.f && c->smp_fraction <= 1.f)) return PMKLC_EINVAL;
   if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
-  if (c->overlap_mask > 1 || c->update_path > PMKLC_UPDATE_FUSED) return PMKLC_EINVAL;
+  if (c->overlap_mask > 1 || c->update_path > PMKLC_UPDATE_FUSED || c->gemm_tiles > 2) return PMKLC_EINVAL;
   if (c->private_model > 2 || c->private_epochs > kMaxGroups) return PMKLC_EINVAL;
   if (c->private_model && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
                            c->hid_s > 65535))
@@ -202,6 +203,7 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   o.priv_threshold = c->private_threshold;
   o.mask = (int)c->overlap_mask;
   o.update_path = (int)c->update_path;
+  o.gemm_tiles = (int)c->gemm_tiles;
   o.lanes = c->lanes_per_block ? (int)c->lanes_per_block : 64;
   o.lane_tokens = (int)c->lane_tokens;
   o.lr = c->lr;
@@ -500,6 +502,7 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
       p.dx_np = np, p.dx_ct = ct;
     }
   }
+  p.tile_cap = c.gemm_tiles == 1 ? 128 : c.gemm_tiles == 2 ? 64 : 0;
   // BF16 forms on the tcgen05 engine update W1 and W2 in their gradient GEMMs' epilogues when those
   // GEMMs have enough tiles to keep every SM streaming optimiser state (at least 8 of dW2's
   // 128 x 128 tiles per SM); with fewer, the full-grid streaming optimiser is faster.  Both apply the
@@ -932,7 +935,9 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   put_le<uint64_t>(H, (uint64_t)n);
   put_le<uint32_t>(H, (uint32_t)n_blocks);
   put_le<uint32_t>(H, crc);
-  put_le<uint32_t>(H, c.mask ? 1u : 0u);  // variant: bit 0 = overlap-masked coding
+  // variant: bit 0 overlap-masked coding; bits 8-9 the GEMM tile variant and bits 10-11 the update
+  // path (kernel choices that leave every byte unchanged, kept so decoding runs the same kernels)
+  put_le<uint32_t>(H, (c.mask ? 1u : 0u) | ((uint32_t)c.gemm_tiles << 8) | ((uint32_t)c.update_path << 10));
   put_le<uint32_t>(H, (uint32_t)c.lane_tokens);
   std::vector<unsigned long long> seg;  // (src, dst-relative, len, which)
   unsigned long long pay = 0;
@@ -1040,7 +1045,11 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   P.n_blocks = get_le<uint32_t>(h + 64);
   if (P.n_blocks > kMaxGroups) return PMKLC_ECORRUPT;
   P.crc = get_le<uint32_t>(h + 68);
-  c.mask = (int)(get_le<uint32_t>(h + 72) & 1u);
+  const uint32_t variant = get_le<uint32_t>(h + 72);
+  c.mask = (int)(variant & 1u);
+  c.gemm_tiles = (int)((variant >> 8) & 3u);
+  c.update_path = (int)((variant >> 10) & 3u);
+  if ((variant & ~0xF01u) || c.gemm_tiles > 2 || c.update_path > PMKLC_UPDATE_FUSED) return PMKLC_ECORRUPT;
   c.lane_tokens = (int)get_le<uint32_t>(h + 76);
   if (c.lane_tokens < 0) return PMKLC_ECORRUPT;
   if (!(c.smp_f >= 0.f && c.smp_f <= 1.f) || !(c.lr > 0.f) || !isfinite(c.lr) || !isfinite(c.alpha0))
@@ -1352,6 +1361,73 @@ int pmklc_autotune_lanes(const uint8_t *d_seq, size_t n, const uint64_t *block_l
       if (sizes) sizes[i] = sz[i];
       if (ms) ms[i] = tm[i];
     }
+    return PMKLC_OK;
+  });
+}
+
+int pmklc_autotune_variant(const uint8_t *d_seq, size_t n, const uint64_t *block_lens, size_t n_blocks,
+                           uint64_t head_bases, pmklc_model_cfg *cfg, const uint32_t *variants, size_t n_variants,
+                           void *stream, float *ms) {
+  return guarded<int>([&]() -> int {
+    if (!cfg || !variants || n_variants == 0 || n_blocks == 0 || !block_lens || head_bases == 0 || (n && !d_seq))
+      return PMKLC_EINVAL;
+    for (size_t i = 0; i < n_variants; ++i)
+      if ((variants[i] & 3u) > 2 || ((variants[i] >> 2) & 3u) > PMKLC_UPDATE_FUSED || variants[i] > 15u)
+        return PMKLC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the heads of every block, gathered into one device buffer (one copy per block)
+    std::vector<uint64_t> heads(n_blocks);
+    unsigned long long sum = 0, off = 0;
+    for (size_t b = 0; b < n_blocks; ++b) {
+      heads[b] = std::min<uint64_t>(block_lens[b], head_bases);
+      sum += heads[b];
+      off += block_lens[b];
+    }
+    if (off != n) return PMKLC_EINVAL;
+    pmklc_model_cfg trial = *cfg;
+    const size_t cap = pmklc_compress_bound(sum, heads.data(), n_blocks, &trial);
+    if (cap == 0) return PMKLC_EINVAL;
+    uint8_t *d_heads = nullptr, *d_out = nullptr;
+    PMKLC_CUDA_TRY(cudaMallocAsync((void **)&d_heads, std::max<size_t>(sum, 1), st));
+    if (cudaMallocAsync((void **)&d_out, cap, st) != cudaSuccess) {
+      cudaFreeAsync(d_heads, st);
+      return PMKLC_ENOMEM;
+    }
+    off = 0;
+    unsigned long long dst = 0;
+    for (size_t b = 0; b < n_blocks; ++b) {
+      if (heads[b]) cudaMemcpyAsync(d_heads + dst, d_seq + off, heads[b], cudaMemcpyDeviceToDevice, st);
+      dst += heads[b];
+      off += block_lens[b];
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = PMKLC_OK, best = -1;
+    std::vector<float> tm(n_variants, 0.f);
+    for (size_t i = 0; i < n_variants && rc == PMKLC_OK; ++i) {
+      trial.gemm_tiles = variants[i] & 3u;
+      trial.update_path = (variants[i] >> 2) & 3u;
+      size_t len = 0;
+      rc = compress_dev_impl(d_heads, sum, heads.data(), n_blocks, &trial, st, d_out, cap, &len);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      rc = compress_dev_impl(d_heads, sum, heads.data(), n_blocks, &trial, st, d_out, cap, &len);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&tm[i], e0, e1);
+      if (best < 0 || tm[i] < tm[best]) best = (int)i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(d_out, st);
+    cudaFreeAsync(d_heads, st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    cfg->gemm_tiles = variants[best] & 3u;
+    cfg->update_path = (variants[best] >> 2) & 3u;
+    if (ms)
+      for (size_t i = 0; i < n_variants; ++i) ms[i] = tm[i];
     return PMKLC_OK;
   });
 }

@@ -73,6 +73,7 @@ struct Plan {
   unsigned *hs_rowmax;
   int precision;                    // PMKLC_FP32_PLAIN / PMKLC_BF16_BATCHED / PMKLC_BF16_FP8STATIC
   const float *bc1, *bc2;      // Adam bias corrections 1 - beta^tau, indexed by tau
+  int tile_cap;                // 0, or the widest column tile of the row GEMMs (hidden, logits, dh, dX)
   int fused_w;                 // 1: W1 and W2 are updated in the epilogues of their gradient GEMMs
                                // (BF16 forms on the tcgen05 engine; no stored gradient for them)
   // activations (NL rows)

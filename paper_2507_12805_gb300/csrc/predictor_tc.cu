@@ -995,6 +995,7 @@ struct TcSetup {
   size_t P;
   bool ok;
   tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8, t_w2f, t_w1f;
+  int tile_cap = 0;
   MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
   int table_h[2], table_w1, sacc_dx, table_h8, dx_owner;
   CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
@@ -1005,7 +1006,7 @@ bool same_key(const TcSetup &a, const Plan &p) {
   return a.wbf == p.wbf && a.static_bf == p.static_bf && a.hd_b == p.hd_b && a.hs_b == p.hs_b && a.dz_b == p.dz_b &&
          a.dh_b == p.dh_b && a.st8 == p.st8 && a.G == p.G && a.NL == p.NL && a.Mmax == p.Mmax &&
          a.use_static == p.use_static &&
-         dims_eq(a.dm, p.dm) && (!p.use_static || dims_eq(a.st, p.st)) && a.P == p.P;
+         dims_eq(a.dm, p.dm) && (!p.use_static || dims_eq(a.st, p.st)) && a.P == p.P && a.tile_cap == p.tile_cap;
 }
 
 // dX by owner warps: the group's FP32 table fits in 32 KB and E divides the 64-column chunks
@@ -1026,6 +1027,7 @@ bool build(TcSetup &S, const Plan &p) {
   S.wbf = p.wbf, S.static_bf = p.static_bf, S.hd_b = p.hd_b, S.hs_b = p.hs_b, S.dz_b = p.dz_b, S.dh_b = p.dh_b;
   S.st8 = p.st8;
   S.G = p.G, S.NL = p.NL, S.Mmax = p.Mmax, S.use_static = p.use_static, S.dm = p.dm, S.st = p.st, S.P = p.P;
+  S.tile_cap = p.tile_cap;
   S.ok = false;
   if (!shapes_ok(p) || !encode_fn()) return false;
   const Dims &D = p.dm, &Sd = p.st;
@@ -1044,11 +1046,17 @@ bool build(TcSetup &S, const Plan &p) {
   S.ml_dx = {tc::kRows, D.t, S.sacc_dx ? D.A * D.E * 8 : 0};
   S.ml_w1 = {p.Mmax, D.t, S.table_w1 ? D.A * D.E * 2 : 0};
   const int Hmax = p.use_static ? max(D.H, Sd.H) : D.H, K1max = p.use_static ? max(D.K1(), Sd.K1()) : D.K1();
-  S.t_h = tc::plan_tiles(p.Mmax, Hmax, K1max, Z, S.ml_h.bytes(), false);
-  S.t_l = tc::plan_tiles(p.Mmax, D.A, Hmax, Z, S.ml_l.bytes());
-  S.t_dh = tc::plan_tiles(p.Mmax, D.H, D.A, p.G, S.ml_dh.bytes());
+  // a kernel variant may cap the row GEMMs' column tiles (more, narrower CTAs; the reduction over
+  // K of every output element is unchanged, so the results are the same)
+  auto capped = [&](tc::TilePlan t) {
+    while (p.tile_cap >= 64 && t.nt > p.tile_cap && (t.nt / 2) % 64 == 0) t.nt /= 2;
+    return t;
+  };
+  S.t_h = capped(tc::plan_tiles(p.Mmax, Hmax, K1max, Z, S.ml_h.bytes(), false));
+  S.t_l = capped(tc::plan_tiles(p.Mmax, D.A, Hmax, Z, S.ml_l.bytes()));
+  S.t_dh = capped(tc::plan_tiles(p.Mmax, D.H, D.A, p.G, S.ml_dh.bytes()));
   S.t_w2 = tc::plan_tiles(D.H, D.A, p.Mmax, p.G, S.ml_w2.bytes());
-  S.t_dx = tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes());
+  S.t_dx = capped(tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes()));
   if (S.sacc_dx && S.t_dx.nt > 8 * D.E) {  // over 8 positions per tile the 22-bit low sums could overflow
     S.sacc_dx = 0;
     S.ml_dx.table = 0;

@@ -38,6 +38,27 @@ __device__ __forceinline__ int find_block(const long long *off, int n_blocks, lo
 // bits (16 per 32-bit word, the first base in the most significant bits) in shared memory, and
 // writes the tokens j whose first base j*s lies in its range: token j is the 2k-bit field of the
 // packed stream at base j*s, cut from a 64-bit window of two words.
+// Four bases per 32-bit operation (byte i of x is base i): their codes, one per byte (the A/C/G/T
+// map of base_code applied bytewise)...
+__device__ __forceinline__ uint32_t swar_codes(uint32_t x) {
+  return ((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u);
+}
+// ... packed to 8 bits with base 0 most significant ...
+__device__ __forceinline__ uint32_t swar_pack(uint32_t t) {
+  return ((t & 3u) << 6) | (((t >> 8) & 3u) << 4) | (((t >> 16) & 3u) << 2) | ((t >> 24) & 3u);
+}
+// ... and the bytes (under mask) that are not the letter their code stands for: the four letters
+// rebuilt from the codes by a byte permutation of "ACGT" and compared with the input.
+__device__ __forceinline__ uint32_t swar_bad(uint32_t x, uint32_t t, uint32_t mask) {
+  const uint32_t sel = (t & 3u) | ((t >> 4) & 0x30u) | ((t >> 8) & 0x300u) | ((t >> 12) & 0x3000u);
+  return (__byte_perm(0x54474341u, 0u, sel) ^ x) & mask;
+}
+// Byte mask of the window bytes [o, o + 4) that lie in the owned range [sh, sh + own).
+__device__ __forceinline__ uint32_t owned_bytes(int o, int sh, int own) {
+  const int lo = max(sh - o, 0), hi = min(sh + own - o, 4);
+  return lo >= hi ? 0u : ((0xFFFFFFFFu >> (8 * (4 - hi))) & (0xFFFFFFFFu << (8 * lo)));
+}
+
 constexpr int kTokSeg = 8192;                     // bases owned by one CTA
 constexpr int kTokWin = kTokSeg + 48;             // bytes loaded: alignment slack (< 16) + owned + k - 1 + pad
 constexpr int kTokWords = kTokWin / 16 + 1;       // packed words (+1 so a window's second word exists)
@@ -62,15 +83,14 @@ __global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
   for (int w = tid; w < kTokWords; w += kTokThreads) {
     const uint8_t *p = g0 + 16 * (size_t)w;
     uint32_t word = 0;
-    if (p + 16 <= end && p >= seq) {  // whole vector inside the sequence
+    if (p + 16 <= end && p >= seq) {  // whole vector inside the sequence: four bytes per operation
       const uint4 v = *reinterpret_cast<const uint4 *>(p);
       const uint32_t q[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const uint32_t ch = (q[i >> 2] >> (8 * (i & 3))) & 0xFF;
-        const long long rel = 16LL * w + i - sh;  // owned-base index of this byte
-        if (rel >= 0 && rel < own) bad |= !is_acgt(ch);
-        word |= base_code(ch) << (30 - 2 * i);
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t t = swar_codes(q[i]);
+        bad |= swar_bad(q[i], t, owned_bytes(16 * w + 4 * i, sh, (int)own)) != 0;
+        word |= swar_pack(t) << (24 - 8 * i);
       }
     } else {  // the sequence's first or last partial vector: byte loads inside it only
 #pragma unroll 1
@@ -89,8 +109,17 @@ __global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
   __syncthreads();
   // tokens j of this block with a <= j*s < a + own
   const long long l = tok_off[b + 1] - tok_off[b];
-  const long long j0 = (a + s - 1) / s;
-  const long long j1 = min(l, (a + own + s - 1) / s);
+  // 64-bit integer division compiles to slow FP64-based code on GB300: blocks below 2^31 bases
+  // (every practical one) divide in 32 bits
+  long long j0, j1;
+  if (a + own + s < (1LL << 31)) {
+    j0 = (long long)((unsigned)(a + s - 1) / (unsigned)s);
+    j1 = (long long)((unsigned)(a + own + s - 1) / (unsigned)s);
+  } else {
+    j0 = (a + s - 1) / s;
+    j1 = (a + own + s - 1) / s;
+  }
+  j1 = min(l, j1);
   const uint32_t mask = (1u << (2 * k)) - 1u;
   uint16_t *out = tokens + tok_off[b];
   for (long long j = j0 + tid; j < j1; j += kTokThreads) {

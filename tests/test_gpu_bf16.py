@@ -250,8 +250,8 @@ def test_update_in_gradient_epilogues_equals_the_streaming_optimiser(P, torch, o
 
 def test_update_paths_give_identical_containers(P):
     """A whole BF16 run on tcgen05 shapes with W1 and W2 updated in the gradient GEMMs' epilogues,
-    by the streaming optimiser, and by the size rule: the same container byte for byte, and it
-    decodes (the decoder picks its own path)."""
+    by the streaming optimiser, and by the size rule: the same container byte for byte but for the
+    variant field that records the path, and it decodes."""
     import synth
     from oracle.model import Shape, init_params
     seq = synth.markov(24000, 5, 0.40, 77).tobytes()
@@ -262,5 +262,35 @@ def test_update_paths_give_identical_containers(P):
     sw = init_params(Shape(256, 16, 8, 64), 3)
     outs = [P.pmklc_compress(seq, lens, P.ModelConfig(**kw, static_weights=sw, update_path=u))
             for u in (P.PMKLC_UPDATE_STREAM, P.PMKLC_UPDATE_FUSED, P.PMKLC_UPDATE_AUTO)]
-    assert outs[0] == outs[1] == outs[2]
+    # identical except the variant field (bytes 72-76), which records the path taken
+    for out in outs[1:]:
+        assert out[:72] == outs[0][:72] and out[76:] == outs[0][76:]
     assert P.pmklc_decompress(outs[1], sw)[0] == seq
+
+
+def test_kernel_variants_give_identical_containers(P, torch):
+    """Every kernel variant the autotuner offers (row-GEMM tile caps 0 / 128 / 64 x update path
+    streaming / fused) codes the same bytes: the containers differ only in the variant field that
+    records the choice, every one decodes, and the autotuner picks one of them."""
+    import synth
+    from oracle.model import Shape, init_params
+    seq = synth.markov(24000, 5, 0.40, 78)
+    lens = [8000, 8000, 8000]
+    kw = dict(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128,
+              lanes_per_block=24, smp_mode=P.PMKLC_SMP_TREE, fallback=0, overlap_mask=1,
+              precision=P.PMKLC_BF16_BATCHED)
+    sw = init_params(Shape(256, 16, 8, 64), 4)
+    codes = [t | (u << 2) for t in (0, 1, 2) for u in (P.PMKLC_UPDATE_STREAM, P.PMKLC_UPDATE_FUSED)]
+    outs = []
+    for code in codes:
+        out = P.pmklc_compress(seq, lens, P.ModelConfig(**kw, static_weights=sw, gemm_tiles=code & 3,
+                                                        update_path=code >> 2))
+        variant = int.from_bytes(out[72:76], "little")
+        assert (variant >> 8) & 3 == code & 3 and (variant >> 10) & 3 == code >> 2 and variant & 1 == 1
+        outs.append(out)
+        assert P.pmklc_decompress(out, sw)[0] == seq.tobytes()
+    for out in outs[1:]:
+        assert out[:72] == outs[0][:72] and out[76:] == outs[0][76:]
+    cfg = P.ModelConfig(**kw, static_weights=sw)
+    chosen, ms = P.pmklc_autotune_variant(torch.from_numpy(seq).cuda(), lens, cfg, codes, head_bases=4000)
+    assert chosen in codes and len(ms) == len(codes) and np.all(ms > 0)

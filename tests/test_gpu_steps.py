@@ -53,17 +53,19 @@ def test_tokenize_bit_exact(P, torch, s, k):
 
 
 def test_tokenize_unaligned_and_invalid(P, torch):
-    seq = synth.markov(5000, 2, 0.5, 9)
+    seq = synth.markov(20000, 2, 0.5, 9)
     buf = dev(torch, np.concatenate([np.frombuffer(b"xyz", np.uint8), seq]))
     d = buf[3:]  # 3-byte offset: not 16-byte aligned
-    d_tok = torch.zeros(5000, dtype=torch.int16, device="cuda")
+    d_tok = torch.zeros(20000, dtype=torch.int16, device="cuda")
     d_tail = torch.zeros(8, dtype=torch.uint8, device="cuda")
     l = P.pmklc_tokenize(d, 1, 4, d_tok, d_tail)
     want, _ = tokenize(base_codes(seq.tobytes()), 1, 4)
     assert np.array_equal(d_tok[:l].cpu().numpy().view(np.uint16), want)
-    for pos in (0, 17, 4095, 4999):
+    # every position class: the first bytes, inside a 16-byte vector, the edges of a CTA's 8,192-base
+    # segment, the last byte
+    for i, pos in enumerate((0, 1, 17, 4095, 8191, 8192, 8193, 8207, 16383, 19999)):
         bad = seq.copy()
-        bad[pos] = ord("N")
+        bad[pos] = ord("Na\nt"[i % 4])  # N, lower case, a line break
         with pytest.raises(P.PmklcError) as e:
             P.pmklc_tokenize(dev(torch, bad), 1, 4, d_tok, d_tail)
         assert e.value.rc == P.PMKLC_EINVAL

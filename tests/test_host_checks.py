@@ -61,6 +61,9 @@ def _patched(data: bytes, offset: int, fmt: str, value) -> bytes:
     (64, "<I", 2),         # block count: the records run out
     (64, "<I", 32768),     # more blocks (model groups) than one launch grid dimension holds
     (80, "<H", 0x7FFF),    # first block length 16383 (varint FF 7F), above n
+    (72, "<I", 1 << 4),    # a variant bit no kernel choice uses
+    (72, "<I", 3 << 8),    # GEMM tile variant 3 (0-2 exist)
+    (72, "<I", 3 << 10),   # update path 3 (0-2 exist)
 ])
 def test_damaged_header_fields_are_corrupt(P, container, offset, fmt, value):
     bad = _patched(container, offset, fmt, value)
@@ -99,7 +102,8 @@ def test_short_inputs_are_corrupt(P, container, cut):
 
 @pytest.mark.parametrize("change", [dict(s=5, k=4), dict(s=1, k=9), dict(precision=4), dict(optimizer=2),
                                     dict(smp_mode=3), dict(count_order=8), dict(fallback=3),
-                                    dict(emb_d=0), dict(smp_fraction=1.5), dict(lanes_per_block=(1 << 20) + 1)])
+                                    dict(emb_d=0), dict(smp_fraction=1.5), dict(lanes_per_block=(1 << 20) + 1),
+                                    dict(gemm_tiles=3), dict(update_path=3)])
 def test_invalid_configurations_are_rejected(P, change):
     kw = dict(s=2, k=4, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=2)
     kw.update(change)
