@@ -264,7 +264,15 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           default: asm volatile("cp.async.wait_group 3;\n" ::); break;
         }
       }
-      if (ok) ok = mbar_wait(sa(&full[s]), par);
+      if (Op::kGather) {
+        if (ok) ok = mbar_wait(sa(&full[s]), par);  // every thread waits at every stage: in step
+      } else {
+        // the tail of a TMA-only op: only thread 0 has waited on the earlier stages, so another
+        // thread's parity wait here could see this buffer's previous phase (same parity) and pass
+        // before the copy landed; thread 0 waits, and the barrier releases the others
+        if (tid == 0 && ok) ok = mbar_wait(sa(&full[s]), par);
+        __syncthreads();
+      }
       if (tail && ok) zero_tail(s, max(0, K - kt * BK));
       asm volatile("fence.proxy.async.shared::cta;\n" ::);
       __syncthreads();

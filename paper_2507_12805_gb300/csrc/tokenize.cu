@@ -43,14 +43,19 @@ __device__ __forceinline__ int find_block(const long long *off, int n_blocks, lo
 __device__ __forceinline__ uint32_t swar_codes(uint32_t x) {
   return ((x >> 1) & 0x03030303u) ^ ((x >> 2) & 0x01010101u);
 }
-// ... packed to 8 bits with base 0 most significant ...
+// ... packed to 8 bits with base 0 most significant (bytes reversed, then two shift-ors fold the
+// four 2-bit codes into the low byte) ...
 __device__ __forceinline__ uint32_t swar_pack(uint32_t t) {
-  return ((t & 3u) << 6) | (((t >> 8) & 3u) << 4) | (((t >> 16) & 3u) << 2) | ((t >> 24) & 3u);
+  const uint32_t r = __byte_perm(t, 0u, 0x0123u);  // c3 | c2 << 8 | c1 << 16 | c0 << 24
+  const uint32_t x = r | (r >> 6);                 // low byte c3 | c2 << 2, byte 2 c1 | c0 << 2
+  return (x | (x >> 12)) & 0xFFu;
 }
 // ... and the bytes (under mask) that are not the letter their code stands for: the four letters
 // rebuilt from the codes by a byte permutation of "ACGT" and compared with the input.
 __device__ __forceinline__ uint32_t swar_bad(uint32_t x, uint32_t t, uint32_t mask) {
-  const uint32_t sel = (t & 3u) | ((t >> 4) & 0x30u) | ((t >> 8) & 0x300u) | ((t >> 12) & 0x3000u);
+  // the codes as the permutation's four selector nibbles: c0 | c1 << 4 in byte 0 and c2 | c3 << 4
+  // in byte 2 of t | t >> 4, moved to bytes 0 and 1 (the upper two selector bytes pick zeros)
+  const uint32_t sel = __byte_perm(t | (t >> 4), 0u, 0x4420u);
   return (__byte_perm(0x54474341u, 0u, sel) ^ x) & mask;
 }
 // Byte mask of the window bytes [o, o + 4) that lie in the owned range [sh, sh + own).
@@ -87,9 +92,10 @@ __global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
       const uint4 v = *reinterpret_cast<const uint4 *>(p);
       const uint32_t q[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
+      const bool inside = 16 * w >= sh && 16 * w + 16 <= sh + (int)own;  // every byte owned
       for (int i = 0; i < 4; ++i) {
         const uint32_t t = swar_codes(q[i]);
-        bad |= swar_bad(q[i], t, owned_bytes(16 * w + 4 * i, sh, (int)own)) != 0;
+        bad |= swar_bad(q[i], t, inside ? 0xFFFFFFFFu : owned_bytes(16 * w + 4 * i, sh, (int)own)) != 0;
         word |= swar_pack(t) << (24 - 8 * i);
       }
     } else {  // the sequence's first or last partial vector: byte loads inside it only
@@ -120,13 +126,17 @@ __global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
     j1 = (a + own + s - 1) / s;
   }
   j1 = min(l, j1);
-  const uint32_t mask = (1u << (2 * k)) - 1u;
-  uint16_t *out = tokens + tok_off[b];
-  for (long long j = j0 + tid; j < j1; j += kTokThreads) {
-    const int q = (int)(j * s - a) + sh;  // window byte of the token's first base
+  // from here on 32-bit offsets from the CTA's first token: q is the window byte of a token's first
+  // base, and its 2k bits are the top of the 64-bit window (words[w], words[w + 1]) shifted left by
+  // 2 (q mod 16) (one funnel shift; 2 (q mod 16) + 2k <= 46 bits stay inside the window)
+  const int cnt = (int)max(0LL, j1 - j0);
+  const int q0 = (int)(j0 * s - a) + sh;
+  uint16_t *out = tokens + tok_off[b] + j0;
+  for (int jj = tid; jj < cnt; jj += kTokThreads) {
+    const int q = q0 + jj * s;
     const int w = q >> 4, o = q & 15;
-    const unsigned long long win = ((unsigned long long)words[w] << 32) | words[w + 1];
-    out[j] = (uint16_t)((win >> (64 - 2 * o - 2 * k)) & mask);
+    const uint32_t top = __funnelshift_l(words[w + 1], words[w], 2 * o);
+    out[jj] = (uint16_t)(top >> (32 - 2 * k));
   }
 }
 

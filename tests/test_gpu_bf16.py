@@ -212,17 +212,19 @@ def test_bf16_bits_per_base_close_to_fp32(P):
     assert abs(len(b) - len(a)) <= 0.005 * len(a), (len(a), len(b))
 
 
-@pytest.mark.parametrize("optimizer", [0, 1])
-def test_update_in_gradient_epilogues_equals_the_streaming_optimiser(P, torch, optimizer):
+@pytest.mark.parametrize("optimizer,M", [(0, 150), (1, 150), (0, 200), (0, 500), (1, 1000)])
+def test_update_in_gradient_epilogues_equals_the_streaming_optimiser(P, torch, optimizer, M):
     """On the tcgen05 engine W1 and W2 are updated in the epilogues of their gradient GEMMs; when the
     gradient is exported they are stored and the streaming optimiser applies the same rule.  Both
     paths give the same parameters, moments and mixing weight bit for bit (the update arithmetic is
-    explicitly rounded, the gradients are the same FP32 values)."""
+    explicitly rounded, the gradients are the same FP32 values).  Lane counts whose last K block is
+    partial and whose stage buffers are reused (more K blocks than buffers) cover the tail stage's
+    synchronisation."""
     from oracle.codec import Config
     from tests.test_gpu_steps import _model
-    rng = np.random.default_rng(88 + optimizer)
+    rng = np.random.default_rng(88 + optimizer + M)
     cfg_o = Config(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128)
-    G, M = 3, 150
+    G = 3
     dsh = cfg_o.dm_shape
     params = np.stack([_model(rng, dsh, 5 + g, 0.05) for g in range(G)])
     m = (rng.normal(0, 1e-3, params.shape)).astype(np.float32)
@@ -294,3 +296,25 @@ def test_kernel_variants_give_identical_containers(P, torch):
     cfg = P.ModelConfig(**kw, static_weights=sw)
     chosen, ms = P.pmklc_autotune_variant(torch.from_numpy(seq).cuda(), lens, cfg, codes, head_bases=4000)
     assert chosen in codes and len(ms) == len(codes) and np.all(ms > 0)
+
+
+@pytest.mark.parametrize("lanes", [200, 1000])
+def test_many_lanes_per_block_round_trip_on_both_update_paths(P, lanes):
+    """Uneven blocks with a lane-length target and up to `lanes` lanes per block (K blocks beyond
+    the stage buffers in the lane-reducing GEMMs, partial last K blocks), network only: both update
+    paths decode exactly and code the same bytes."""
+    import synth
+    from oracle.model import Shape, init_params
+    tabs = synth.species_tables()
+    lens = [400_000, 100_000, 30_000]
+    seq = np.concatenate([synth.sample(L, tabs[i], 950 + i) for i, L in enumerate(lens)])
+    kw = dict(s=3, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128,
+              lanes_per_block=lanes, lane_tokens=128, smp_mode=P.PMKLC_SMP_TREE, fallback=0, overlap_mask=1,
+              precision=P.PMKLC_BF16_BATCHED)
+    sw = init_params(Shape(256, 16, 8, 64), 6)
+    outs = []
+    for upd in (P.PMKLC_UPDATE_STREAM, P.PMKLC_UPDATE_FUSED):
+        out = P.pmklc_compress(seq, lens, P.ModelConfig(**kw, static_weights=sw, update_path=upd))
+        assert P.pmklc_decompress(out, sw)[0] == seq.tobytes()
+        outs.append(out)
+    assert outs[0][:72] == outs[1][:72] and outs[0][76:] == outs[1][76:]
