@@ -92,11 +92,18 @@ __global__ void __launch_bounds__(kTokThreads) tokenize_packed_kernel(
       const uint4 v = *reinterpret_cast<const uint4 *>(p);
       const uint32_t q[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      const bool inside = 16 * w >= sh && 16 * w + 16 <= sh + (int)own;  // every byte owned
+      uint32_t t[4];
+#pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const uint32_t t = swar_codes(q[i]);
-        bad |= swar_bad(q[i], t, inside ? 0xFFFFFFFFu : owned_bytes(16 * w + 4 * i, sh, (int)own)) != 0;
-        word |= swar_pack(t) << (24 - 8 * i);
+        t[i] = swar_codes(q[i]);
+        word |= swar_pack(t[i]) << (24 - 8 * i);
+      }
+      if (16 * w >= sh && 16 * w + 16 <= sh + (int)own) {  // every byte owned (all but the edges)
+        bad |= (swar_bad(q[0], t[0], ~0u) | swar_bad(q[1], t[1], ~0u) | swar_bad(q[2], t[2], ~0u) |
+                swar_bad(q[3], t[3], ~0u)) != 0;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bad |= swar_bad(q[i], t[i], owned_bytes(16 * w + 4 * i, sh, (int)own)) != 0;
       }
     } else {  // the sequence's first or last partial vector: byte loads inside it only
 #pragma unroll 1
