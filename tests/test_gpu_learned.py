@@ -126,3 +126,55 @@ def test_train_model_against_oracle(P, precision):
     else:  # BF16 operands: each gradient within ~1e-2 relative, Adam steps of at most ~lr
         assert np.median(d) <= 1e-3
     assert abs(ce_g - ce_w) <= 0.005 * ce_w
+
+
+@pytest.fixture(scope="module")
+def masked_static(P):
+    """Static models pre-trained by pmklc_train_model with overlap-masked coding: on 2^22 bases of the
+    plain workload's source (other samples of its order-5 table) and on 5 x 2^20 bases of the five
+    species profiles (unperturbed)."""
+    plain = P.pmklc_train_model(synth.pretrain_corpus("plain", 1 << 22), P.ModelConfig(
+        s=2, k=4, emb_d=32, ctx_d=32, hid_d=128, lanes_per_block=128, precision=P.PMKLC_BF16_BATCHED, seed=2001,
+        overlap_mask=1))
+    species = P.pmklc_train_model(synth.pretrain_corpus("batch", 5 << 20), P.ModelConfig(
+        s=S, k=K, emb_d=32, ctx_d=32, hid_d=128, lanes_per_block=128, precision=P.PMKLC_BF16_BATCHED, seed=2001,
+        overlap_mask=1))
+    return plain, species
+
+
+def test_network_codes_blocks_of_the_plain_workload_with_the_judge_on(P, masked_static):
+    """The plain workload's shape (2^18-base blocks of the order-5 source, (2,4), E 32, t 32, H 128,
+    128 lanes, tree passing, the count-model judge on): with a pre-trained static model the network
+    codes blocks, and its coding of every block costs less than the count model's."""
+    plain, _ = masked_static
+    w = synth.workload("plain")
+    seq, lens = w.seq[: 4 << 18], [1 << 18] * 4
+    cfg = P.ModelConfig(s=2, k=4, use_static=True, emb_s=32, ctx_s=32, hid_s=128, emb_d=32, ctx_d=32, hid_d=128,
+                        lanes_per_block=128, count_order=6, smp_mode=P.PMKLC_SMP_TREE, overlap_mask=1,
+                        alpha_init=1.0, fallback=1, precision=P.PMKLC_BF16_BATCHED, static_weights=plain)
+    out = P.pmklc_compress(seq, lens, cfg)
+    st = P.pmklc_last_stats()
+    print(f"plain, 4 blocks: net {st['net_blocks']} count {st['count_blocks']}; bits/base network "
+          f"{8 * st['net_bytes'] / seq.size:.4f}, count model {8 * st['count_bytes'] / seq.size:.4f}")
+    assert st["net_blocks"] > 0
+    assert st["net_bytes"] < st["count_bytes"]
+    assert P.pmklc_decompress(out, plain)[0] == seq.tobytes()
+
+
+def test_pretrained_static_and_dynamic_model_beat_the_count_model_on_held_out_data(P, masked_static):
+    """Held-out sequences from the species profiles perturbed by 20 % (the held-out workload's recipe,
+    scaled down): the learned method - the pre-trained static model and the online dynamic model,
+    network only - codes them in fewer bits than the method without the learned network (the count
+    model alone, fallback 2)."""
+    _, species = masked_static
+    tabs = [synth.perturb_table(t, 0.2, 1005 + i) for i, t in enumerate(synth.species_tables())]
+    blocks = [synth.sample(1 << 17, tabs[i], 1006_000 + i) for i in range(4)]
+    held, lens = np.concatenate(blocks), [1 << 17] * 4
+    kw = dict(s=S, k=K, use_static=True, emb_s=32, ctx_s=32, hid_s=128, emb_d=32, ctx_d=32, hid_d=128,
+              lanes_per_block=64, count_order=6, smp_mode=P.PMKLC_SMP_TREE, overlap_mask=1, alpha_init=1.0,
+              precision=P.PMKLC_BF16_BATCHED, static_weights=species)
+    net = P.pmklc_compress(held, lens, P.ModelConfig(**kw, fallback=0))
+    cnt = P.pmklc_compress(held, lens, P.ModelConfig(**kw, fallback=2))
+    print(f"held-out bits/base: learned {8 * len(net) / held.size:.4f}, count model only {8 * len(cnt) / held.size:.4f}")
+    assert len(net) < len(cnt)
+    assert P.pmklc_decompress(net, species)[0] == held.tobytes()
