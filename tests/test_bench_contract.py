@@ -96,6 +96,10 @@ def test_reference_arm_runs_the_oracle_alone(monkeypatch, capsys):
     assert line["e2e"] == {"value": line["value"], "unit": "MB/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "1024 bases" in line["cpu_baseline"]["sample"]
+    # the same config object the GPU arm prints: the workload and the L2 policy, no model keys
+    w, kw = bench.load_workload("plain", 2048)
+    assert line["config"] == bench.bench_config("plain", w, kw)
+    assert set(line["config"]) == {"workload", "l2"} and line["details"]["model"] == kw
 
 
 def test_throttle_detection():
