@@ -469,7 +469,8 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
     p.dz_b = ar.alloc<__nv_bfloat16>(NL * A);
     p.dh_b = ar.alloc<__nv_bfloat16>(NL * c.dm.H);
   }
-  p.demb_acc = ar.alloc<long long>(G * A * c.dm.E);
+  p.demb_acc = nullptr;
+  p.dx_rows = nullptr;
   p.err = ar.alloc<int>(1);
   std::vector<float> bc1(R.S.max_tau + 2), bc2(R.S.max_tau + 2);
   for (size_t t = 0; t < bc1.size(); ++t) {
@@ -500,7 +501,15 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
       p.demb_part = ar.alloc<float>(G * (size_t)np * A * c.dm.E);
       if (ar.failed) return PMKLC_ENOMEM;
       p.dx_np = np, p.dx_ct = ct;
+    } else if (dx_rows_rule(p)) {  // large tables on tcgen05: dX rows, summed per range of table rows
+      p.dx_rows = ar.alloc<float>(NL * (size_t)c.dm.K1());
+      if (ar.failed) return PMKLC_ENOMEM;
     }
+  }
+  // the other forms add the embedding gradient into fixed-point accumulators (zeroed below)
+  if (!p.demb_part && !p.dx_rows) {
+    p.demb_acc = ar.alloc<long long>(G * A * c.dm.E);
+    if (ar.failed) return PMKLC_ENOMEM;
   }
   p.tile_cap = c.gemm_tiles == 1 ? 128 : c.gemm_tiles == 2 ? 64 : 0;
   // BF16 forms on the tcgen05 engine update W1 and W2 in their gradient GEMMs' epilogues when those
@@ -510,7 +519,7 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   const long long w2_tiles = (long long)L.G * ((c.dm.H + 127) / 128) * ((c.dm.A + 127) / 128);
   const bool fuse = c.update_path == PMKLC_UPDATE_FUSED || (c.update_path == PMKLC_UPDATE_AUTO && w2_tiles >= 8LL * 152);
   p.fused_w = bf_form(c.precision) && fuse && tc_supported(p) ? 1 : 0;
-  cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
+  if (p.demb_acc) cudaMemsetAsync(p.demb_acc, 0, sizeof(long long) * G * A * c.dm.E, ar.st);
   // the mixer writes a row's dz only inside the coded slice (overlap masking) and clears the
   // previous one, so every row starts at zero
   if (p.dz_b)
@@ -562,6 +571,9 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
     return w;
   };
   const bool bf = bf_form(R.p.precision);
+  // kernels of one backward + update: dh, the bias sums, dW2, dX (+ the embedding sum of stored dX
+  // rows), dW1 and the optimiser on tcgen05; dh, dW2, dX, dW1 and the optimiser otherwise
+  const int bwd_launches = bf && tc_supported(R.p) ? (R.p.dx_rows ? 7 : 6) : 5;
   const bool split_static = R.net && use_ss && bf && R.p.use_static && tc_supported(R.p);
   int static_for = -1;  // the step whose static forward is already queued on ss.aux[2]
   for (int T = 0; T < S.T_total; ++T) {
@@ -641,7 +653,7 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
       } else {
         launch_backward_update(R.p, T, st);
       }
-      R.launches += 5;
+      R.launches += bwd_launches;
     } else {
       queue_static_next();
     }

@@ -81,7 +81,11 @@ struct Plan {
   float *out_P;                // optional: mixed probabilities of predicted rows (tests)
   __nv_bfloat16 *hd_b, *hs_b, *dz_b, *dh_b;  // BF16 activations of the BF16 form (else nullptr)
   float *hpart;                // split-K partial sums of the hidden layer (BF16 form, mma.sync engine)
-  long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E
+  long long *demb_acc;         // fixed-point embedding gradient accumulators, G x A x E (else nullptr)
+  // BF16 form on tcgen05 with tables too large for shared memory: dX of every lane row (NL x t*E
+  // FP32), summed per group into the embedding gradient (grad's embedding part) by a kernel that
+  // owns a range of table rows; nullptr otherwise
+  float *dx_rows;
   // BF16 form with small tables: per group, dx_np partial FP32 tables (A x E) of the dX tiles
   // (row tile bx, column tile by at partial bx * dx_ct + by), summed by the optimiser in that
   // order; nullptr: the fixed-point accumulators above

@@ -103,6 +103,15 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which = kFwdBo
 // partial embedding-gradient tables per group of the dX GEMM when it sums its tiles in FP32 by
 // owner warps (small tables), else 0; *ct = its column tiles
 int dx_partials(const Plan &p, int *ct);
+// true when the dX GEMM stores its rows (Plan::dx_rows, NL x t*E FP32) for a separate sum into the
+// embedding gradient: tables too large for the shared-memory forms
+bool dx_rows_rule(const Plan &p);
+// slice.cu: with overlap-masked coding (slice width 4^s of 16 to 64 tokens) the logits layer and dh
+// formed over each row's coded slice only, reading every group's W2 about once per step.
+// launch_slice_logits: problems zb .. zb + Z - 1 (z < G dynamic, z >= G static on group z - G)
+bool slice_rule(const Plan &p);
+void launch_slice_logits(const Plan &p, int T, cudaStream_t st, int zb, int Z);
+void launch_slice_dh(const Plan &p, int T, cudaStream_t st);
 // ss (optional): run dW2, dX and dW1 concurrently on st and ss->aux
 void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams *ss);
 // predictor_bf16.cu: the BF16 form (tcgen05 engine where tc_supported, else mma.sync)

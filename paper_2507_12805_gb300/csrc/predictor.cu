@@ -357,8 +357,9 @@ struct DXOp : RowBase {
 };
 
 // Optimiser over every parameter of every training group, streamed in float4 groups: the
-// gradient comes from `grad` (W1, b1, W2, b2), from the dX tiles' FP32 partials, or from the
-// fixed-point embedding accumulators (Emb, zeroed on the way).  The FP32 master, Adam moments
+// gradient comes from `grad` (W1, b1, W2, b2, and Emb when it was summed from stored dX rows),
+// from the dX tiles' FP32 partials, or from the fixed-point embedding accumulators (Emb, zeroed on
+// the way).  The FP32 master, Adam moments
 // and, in the BF16 form, the BF16 copy are rewritten in place.  The work is cut into chunks of
 // kOptChunk parameters of one group; the CTAs (one resident wave) stride over the
 // (group, chunk) pairs, and a thread issues the loads of both of its float4 groups of a chunk
@@ -389,7 +390,7 @@ __device__ __forceinline__ void opt_load4(const Plan &p, const OptGroup &o, uint
       a4.x += q.x, a4.y += q.y, a4.z += q.z, a4.w += q.w;
     }
     gg[0] = a4.x, gg[1] = a4.y, gg[2] = a4.z, gg[3] = a4.w;
-  } else if (i0 < nemb) {  // A*E is a multiple of 4: a float4 group never straddles the embedding boundary
+  } else if (i0 < nemb && o.acc) {  // A*E is a multiple of 4: a float4 group never straddles the embedding boundary
     const longlong2 q0 = *reinterpret_cast<const longlong2 *>(o.acc + i0),
                     q1 = *reinterpret_cast<const longlong2 *>(o.acc + i0 + 2);
     gg[0] = unfix40(q0.x), gg[1] = unfix40(q0.y), gg[2] = unfix40(q1.x), gg[3] = unfix40(q1.y);
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kOptThreads, 4) opt_stream_kernel(Plan p, int 
     const float bc1 = p.bc1[tau], bc2 = p.bc2[tau];
     OptGroup o;
     o.th = p.params + base, o.mm = p.m + base, o.vv = p.v + base, o.gr = p.grad + base;
-    o.acc = p.demb_acc + (size_t)g * nemb;
+    o.acc = p.demb_acc ? p.demb_acc + (size_t)g * nemb : nullptr;  // else the gradient buffer holds it
     // the group's partials of the embedding gradient: its row tiles x the column tiles
     o.part = p.demb_part ? p.demb_part + (size_t)g * p.dx_np * nemb : nullptr;
     o.npart = p.demb_part ? ((p.grp_lane_off[g + 1] - p.grp_lane_off[g] + 127) / 128) * p.dx_ct : 0;
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kOptThreads, 4) opt_stream_kernel(Plan p, int 
         float t1[4] = {o.th[i], 0, 0, 0}, m1[4] = {o.mm[i], 0, 0, 0}, v1[4] = {o.vv[i], 0, 0, 0}, g1[4] = {0, 0, 0, 0};
         if (i < nemb && o.part) {
           for (int k = 0; k < o.npart; ++k) g1[0] += o.part[(size_t)k * nemb + i];
-        } else if (i < nemb) {
+        } else if (i < nemb && o.acc) {
           g1[0] = unfix40(o.acc[i]);
           o.acc[i] = 0;
         } else {
@@ -576,7 +577,7 @@ void launch_update(const Plan &p, int T, cudaStream_t st) {
   // the 4-byte gradient, or reads the dX partials (dx_np of 4 bytes)
   const double nemb = (double)p.dm.A * p.dm.E;
   const double per = p.wbf ? 30.0 : 28.0;
-  const double emb_extra = p.demb_part ? nemb * 4.0 * (p.dx_np - 1) : nemb * 12.0;
+  const double emb_extra = p.demb_part ? nemb * 4.0 * (p.dx_np - 1) : p.demb_acc ? nemb * 12.0 : 0.0;
   const size_t count = p.fused_w ? (size_t)p.dm.A * p.dm.E + p.dm.H + p.dm.A : p.P;
   {
     ProfScope ps("update_adam", 0, prof_work().train_groups * ((double)count * per + emb_extra), st);
@@ -607,8 +608,10 @@ __global__ void export_grad_kernel(Plan p, float *out) {
     } else if (p.demb_part) {  // the same partial order as the optimiser
       v = 0.f;
       for (int k = 0; k < npart; ++k) v += p.demb_part[((size_t)g * p.dx_np + k) * nemb + i];
-    } else {
+    } else if (p.demb_acc) {
       v = unfix40(p.demb_acc[(size_t)g * nemb + i]);
+    } else {  // summed from the dX rows into the gradient buffer
+      v = p.grad[(size_t)g * p.P + i];
     }
     out[(size_t)g * p.P + i] = v;
   }

@@ -4,11 +4,13 @@
 //   forward   h  = relu(X W1 + b1)    X gathered from the embedding rows of the context tokens
 //             L  = h W2 + b2          dynamic model (z < G) and static model (z >= G) in one launch
 //   backward  dh = (dz W2^T) * [h > 0]
-//             dW2 = h^T dz,  dX = dh W1^T (scattered into the embedding rows),  dW1 = X^T dh
+//             dW2 = h^T dz,  dX = dh W1^T (summed into the embedding rows),  dW1 = X^T dh
 //             db2 = sum of dz, db1 = sum of dh over the predicted rows (fixed-order column sums)
-// The weight-gradient epilogues store the gradient; the streaming optimiser of predictor.cu then
-// updates every parameter (spread over all SMs at full occupancy it outruns an optimiser applied
-// in these epilogues, whose four-to-eight warps per SM keep too few accesses in flight).
+// With enough weight-gradient tiles to keep every SM streaming optimiser state (p.fused_w), Adam
+// on W1 and W2 runs in the epilogues of their gradient GEMMs; otherwise those epilogues store the
+// gradient and the streaming optimiser of predictor.cu updates every parameter.  The embedding
+// and biases always go through the streaming optimiser.  With overlap-masked coding the logits
+// layer and dh run over each row's coded slice only (slice.cu).
 //
 // Operand majors follow the stored layouts, so every dense operand is one TMA box per stage:
 // W1 is stored transposed (W1t[h][i]: K-major for the hidden layer, MN-major for dX), W2 as
@@ -388,12 +390,12 @@ struct DXT : TBase {
   static constexpr int kGather = 0;
   static constexpr bool kFinish = true;
   CUtensorMap dh, w1;
-  int sacc;    // sum the tile in shared memory (ml.table bytes: low parts [A*E] then high parts [A*E])
   int eshift;  // log2 E when E is a power of two, else -1
   __device__ bool active(int z) const { return group_trains(p, T, z); }
   __device__ int M(int z) const { return nrows(z); }
   __device__ int N(int) const { return p.dm.K1(); }
   __device__ int K(int) const { return p.dm.H; }
+  // the tile's sums (ml.table bytes: low parts [A*E] then high parts [A*E])
   __device__ uint32_t *lo_s(const uint8_t *meta) const {
     return reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(meta) + ml.tab_off());
   }
@@ -401,11 +403,9 @@ struct DXT : TBase {
     MetaLayout l = ml;
     l.table = 0;  // the accumulator region is not an embedding copy
     fill(meta, l, z, m0, tc::kRows, nullptr, 0);
-    if (sacc) {
-      uint4 *a = reinterpret_cast<uint4 *>(lo_s(meta));
-      const int n4 = p.dm.A * p.dm.E / 2;
-      for (int i = threadIdx.x; i < n4; i += tc::kThreads) a[i] = make_uint4(0, 0, 0, 0);
-    }
+    uint4 *a = reinterpret_cast<uint4 *>(lo_s(meta));
+    const int n4 = p.dm.A * p.dm.E / 2;
+    for (int i = threadIdx.x; i < n4; i += tc::kThreads) a[i] = make_uint4(0, 0, 0, 0);
   }
   __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
   __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
@@ -414,38 +414,26 @@ struct DXT : TBase {
   struct Epi {
     const long long *tp;
     const uint16_t *tk;
-    uint32_t *lo;               // shared-memory sums (sacc), else nullptr
-    unsigned long long *glob;   // the group's global accumulators
+    uint32_t *lo;  // shared-memory sums
     int E, t, AE, eshift;
     __device__ bool row_active(int rl) const { return tp[rl] >= 0; }
-    // fixed point v 2^40: shared sums take (low 22 bits, the rest), global ones the two 32-bit halves
-    __device__ uint2 stage(float v) const {
-      if (lo) return fix40_split22(v);
-      const long long q = fix40(v);
-      return make_uint2((uint32_t)(unsigned long long)q, (uint32_t)((unsigned long long)q >> 32));
-    }
+    // fixed point v 2^40 as (low 22 bits, the rest)
+    __device__ uint2 stage(float v) const { return fix40_split22(v); }
     // table entry of column n of tile row rl: its context token's row, embedding offset
     __device__ uint32_t index(int rl, int n) const {
       const int pos = eshift >= 0 ? n >> eshift : n / E;
       return (uint32_t)tk[rl * t + pos] * (uint32_t)E + (uint32_t)(n - pos * E);
     }
     __device__ void add(uint32_t i, uint2 s) const {
-      if (lo) {
-        if (s.x) atomicAdd(lo + i, s.x);  // results unused: reductions, no return
-        if (s.y) atomicAdd(reinterpret_cast<int *>(lo) + AE + i, (int)s.y);
-      } else if (s.x | s.y) {
-        atomicAdd(glob + i, ((unsigned long long)s.y << 32) | s.x);
-      }
+      if (s.x) atomicAdd(lo + i, s.x);  // results unused: reductions, no return
+      if (s.y) atomicAdd(reinterpret_cast<int *>(lo) + AE + i, (int)s.y);
     }
   };
-  __device__ Epi epi_ctx(const uint8_t *meta, int z, int, int) const {
-    const int AE = p.dm.A * p.dm.E;
-    return {tp(meta), tk(meta), sacc ? lo_s(meta) : nullptr,
-            reinterpret_cast<unsigned long long *>(p.demb_acc) + (size_t)z * AE, p.dm.E, p.dm.t, AE, eshift};
+  __device__ Epi epi_ctx(const uint8_t *meta, int, int, int) const {
+    return {tp(meta), tk(meta), lo_s(meta), p.dm.E, p.dm.t, p.dm.A * p.dm.E, eshift};
   }
   // every thread, after the epilogue's last barrier: the non-zero sums of the tile to global memory
   __device__ void finish(uint8_t *meta, int z) const {
-    if (!sacc) return;
     const int AE = p.dm.A * p.dm.E;
     const uint32_t *lo = lo_s(meta);
     const int *hi = reinterpret_cast<const int *>(lo) + AE;
@@ -456,6 +444,153 @@ struct DXT : TBase {
     }
   }
 };
+
+// dX = dh W1^T stored per lane row (FP32, t*E columns) for groups whose embedding gradient table
+// is too large to sum in shared memory; emb_grad_kernel then sums the rows into the table.  The
+// tile leaves tensor memory through the stage buffers 64 columns at a time and each warp writes
+// whole 256-byte row segments.
+struct DXRowsT : TBase {
+  static constexpr bool kAMN = false, kBMN = true, kTail = false;
+  static constexpr int kEpi = 2;
+  static constexpr int kGather = 0;
+  CUtensorMap dh, w1;
+  __device__ bool active(int z) const { return group_trains(p, T, z); }
+  __device__ int M(int z) const { return nrows(z); }
+  __device__ int N(int) const { return p.dm.K1(); }
+  __device__ int K(int) const { return p.dm.H; }
+  __device__ void prepare(uint8_t *meta, int z, int m0) const { fill(meta, ml, z, m0, tc::kRows, nullptr, 0); }
+  __device__ tc::TmaOperand tma_a(int) const { return {&dh, 2, 0, 0}; }
+  __device__ tc::TmaOperand tma_b(int z) const { return {&w1, 3, z, 0}; }
+  __device__ int row_a(int z, int m0) const { return row(z, m0); }
+  __device__ int row_b(int, int n0) const { return n0; }
+  struct Epi {
+    const long long *tp;
+    float *out;  // row m0 of the tile, column n0
+    int K1;
+    __device__ void chunk(const float *stg, int c0) const {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int r = warp; r < tc::kRows; r += tc::kThreads / 32) {
+        if (tp[r] < 0) continue;  // rows that predict nothing are never read
+        const float2 v = *reinterpret_cast<const float2 *>(stg + r * tc::kFloatPitch + 2 * lane);
+        *reinterpret_cast<float2 *>(out + (size_t)r * K1 + c0 + 2 * lane) = v;
+      }
+    }
+  };
+  __device__ Epi epi_ctx(const uint8_t *meta, int z, int m0, int n0) const {
+    return {tp(meta), p.dx_rows + (size_t)row(z, m0) * p.dm.K1() + n0, p.dm.K1()};
+  }
+};
+
+// The embedding gradient of every training group from its stored dX rows: CTA (x, g) owns table
+// rows [x R, x R + R) of group g and sums them in shared memory in the 2^40 fixed point of the
+// other dX forms, as a low unsigned word and a high signed word whose carry is taken from the
+// value the low word's atomic add returns: every add is exact modulo 2^64, so the sums do not
+// depend on the order of the adds and equal those of the forms that add in global memory.  The
+// group's rows are taken kEmbPairs context pairs at a time: the threads list the pairs whose token
+// lies in the CTA's range (loads issued eight at a time), then add their E values, one 8-value
+// chunk per work item.  The sums go to the embedding part of the group's gradient as FP32 (one
+// rounding), where the streaming optimiser reads them.
+constexpr int kEmbThreads = 512;
+constexpr int kEmbTableBytes = 64 * 1024;  // two CTAs per SM with the pass lists
+constexpr int kEmbPairs = 4096;            // context pairs per pass (at least one row's t)
+
+__host__ __device__ inline int emb_rows_per_pass(int t) { return max(1, kEmbPairs / t); }
+__host__ __device__ inline size_t emb_smem_bytes(int range, int E, int t, int A) {
+  const size_t tab = (size_t)min(range, A) * E * 8, cap = (size_t)emb_rows_per_pass(t) * t;
+  return tab + (size_t)emb_rows_per_pass(t) * 8 + cap * 8 + 16;
+}
+
+__device__ __forceinline__ void emb_add(uint32_t *lo, int *hi, int i, long long q) {
+  const uint32_t ql = (uint32_t)(unsigned long long)q;
+  const uint32_t old = atomicAdd(lo + i, ql);
+  const int qh = (int)(q >> 32) + (old + ql < old ? 1 : 0);  // the low word's carry
+  if (qh) atomicAdd(hi + i, qh);
+}
+
+__global__ void __launch_bounds__(kEmbThreads, 2) emb_grad_kernel(Plan p, int T, int range) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) uint8_t emb_smem[];
+  __shared__ int nmatch;
+  const int g = blockIdx.y;
+  if (!group_trains(p, T, g)) return;  // the same for the whole CTA
+  const int E = p.dm.E, t = p.dm.t, K1 = t * E;
+  const int a0 = blockIdx.x * range, na = min(range, p.dm.A - a0);
+  if (na <= 0) return;
+  const int tid = threadIdx.x, n = na * E, rc = emb_rows_per_pass(t);
+  uint32_t *lo = reinterpret_cast<uint32_t *>(emb_smem);
+  int *hi = reinterpret_cast<int *>(lo + n);
+  long long *base = reinterpret_cast<long long *>(emb_smem + (size_t)n * 8);
+  int *mpair = reinterpret_cast<int *>(base + rc), *mtok = mpair + rc * t;
+  for (int i = tid; i < n; i += kEmbThreads) lo[i] = 0u, hi[i] = 0;
+  const int r0 = p.grp_lane_off[g], rows = p.grp_lane_off[g + 1] - r0;
+  const long long j = T - p.grp_start[g];
+  const int lane = tid & 31, cpp = E >> 3;  // 8-value chunks per pair
+  for (int rr0 = 0; rr0 < rows; rr0 += rc) {
+    const int nr = min(rc, rows - rr0), np = nr * t;
+    for (int r = tid; r < nr; r += kEmbThreads) {  // first context token of each predicted row
+      const int rw = r0 + rr0 + r;
+      base[r] = row_pred(p, T, rw, g) ? p.lane_tok[rw] + j - t : -1;
+    }
+    if (tid == 0) nmatch = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < np; i0 += 8 * kEmbThreads) {
+      int tok[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = i0 + q * kEmbThreads + tid;
+        tok[q] = -1;
+        if (i < np) {
+          const int r = i / t;
+          const long long b = base[r];
+          if (b >= 0) tok[q] = p.tokens[b + (i - r * t)];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = i0 + q * kEmbThreads + tid;
+        const bool hit = tok[q] >= a0 && tok[q] < a0 + na;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        int slot = 0;
+        if (lane == 0 && m) slot = atomicAdd(&nmatch, __popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+        if (hit) mpair[slot] = i, mtok[slot] = tok[q] - a0;
+      }
+    }
+    __syncthreads();
+    const int items = nmatch * cpp;
+    for (int it0 = 0; it0 < items; it0 += 2 * kEmbThreads) {
+      float x[2][8];
+      int dst[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {  // both items' loads before any add
+        const int it = it0 + u * kEmbThreads + tid;
+        dst[u] = -1;
+        if (it < items) {
+          const int m = it / cpp, c = it - m * cpp, i = mpair[m], r = i / t;
+          const float4 *src =
+              reinterpret_cast<const float4 *>(p.dx_rows + (size_t)(r0 + rr0 + r) * K1 + (i - r * t) * E + 8 * c);
+          const float4 v0 = src[0], v1 = src[1];
+          x[u][0] = v0.x, x[u][1] = v0.y, x[u][2] = v0.z, x[u][3] = v0.w;
+          x[u][4] = v1.x, x[u][5] = v1.y, x[u][6] = v1.z, x[u][7] = v1.w;
+          dst[u] = mtok[m] * E + 8 * c;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (dst[u] >= 0)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const long long v = fix40(x[u][q]);
+            if (v) emb_add(lo, hi, dst[u] + q, v);
+          }
+    }
+    __syncthreads();  // the pass's bases and lists are rewritten by the next pass
+  }
+  float *gr = p.grad + (size_t)g * p.P + p.dm.off_emb() + (size_t)a0 * E;
+  for (int i = tid; i < n; i += kEmbThreads)
+    gr[i] = unfix40((long long)(((unsigned long long)(uint32_t)hi[i] << 32) | lo[i]));
+}
 
 // dX = dh W1^T summed into the embedding rows without atomics (groups whose table A x E fits in
 // 32 KB of FP32 and E divides 64): the tile is staged out of tensor memory 64 columns at a time
@@ -997,7 +1132,7 @@ struct TcSetup {
   tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8, t_w2f, t_w1f;
   int tile_cap = 0;
   MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
-  int table_h[2], table_w1, sacc_dx, table_h8, dx_owner;
+  int table_h[2], table_w1, sacc_dx, table_h8, dx_owner, dx_rows, emb_range;
   CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
 };
 
@@ -1057,20 +1192,28 @@ bool build(TcSetup &S, const Plan &p) {
   S.t_dh = capped(tc::plan_tiles(p.Mmax, D.H, D.A, p.G, S.ml_dh.bytes()));
   S.t_w2 = tc::plan_tiles(D.H, D.A, p.Mmax, p.G, S.ml_w2.bytes());
   S.t_dx = capped(tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes()));
-  if (S.sacc_dx && S.t_dx.nt > 8 * D.E) {  // over 8 positions per tile the 22-bit low sums could overflow
-    S.sacc_dx = 0;
-    S.ml_dx.table = 0;
-    S.t_dx = tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes());
-  }
-  // the staged epilogue needs kStagedBytes of stage buffers (checked against the limit below)
-  while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < tc::kStagedBytes) ++S.t_dx.ns;
-  if (S.t_dx.ns > tc::kStages) return false;
+  if (S.sacc_dx && S.t_dx.nt > 8 * D.E) S.sacc_dx = 0;  // over 8 positions per tile the 22-bit low sums could overflow
   S.dx_owner = dx_owner_rule(p);
+  S.dx_rows = !S.dx_owner && !S.sacc_dx;
+  S.emb_range = 0;
   if (S.dx_owner) {  // 128-column tiles, two stage buffers: two CTAs per SM
     S.ml_dx = {tc::kRows, D.t, D.A * D.E * 4};
     S.t_dx = {dx_owner_nt(p), 2};
     if ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < (size_t)tc::kRows * tc::kFloatPitch * 4)
       return false;
+  } else if (S.dx_rows) {  // dX rows stored, then summed per range of table rows (emb_grad_kernel)
+    S.ml_dx = {tc::kRows, 0, 0};
+    S.t_dx = capped(tc::plan_tiles(p.Mmax, D.K1(), D.H, p.G, S.ml_dx.bytes()));
+    // the staged epilogue's 128 x kFloatPitch floats fit in the stage buffers
+    while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < (size_t)tc::kRows * tc::kFloatPitch * 4)
+      ++S.t_dx.ns;
+    if (S.t_dx.ns > tc::kStages) return false;
+    S.emb_range = kEmbTableBytes / (8 * D.E);
+    if (S.emb_range < 1 || emb_smem_bytes(S.emb_range, D.E, D.t, D.A) > limit) return false;
+  } else {
+    // the staged epilogue needs kStagedBytes of stage buffers (checked against the limit below)
+    while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < tc::kStagedBytes) ++S.t_dx.ns;
+    if (S.t_dx.ns > tc::kStages) return false;
   }
   S.t_w1 = tc::plan_tiles(D.H, D.K1(), p.Mmax, p.G, S.ml_w1.bytes());
   // with the optimiser in their epilogues (p.fused_w) the weight-gradient GEMMs are bound by the
@@ -1165,6 +1308,12 @@ bool tc_supported(const Plan &p) {
   return get_setup(p, S);
 }
 
+bool dx_rows_rule(const Plan &p) {
+  if (!shapes_ok(p)) return false;
+  TcSetup S;
+  return get_setup(p, S) && S.dx_rows;
+}
+
 namespace {
 // The bounded-wait path of every kernel here, on its own: one thread waits, at most `polls` polls,
 // on an mbarrier that expects one arrival which never comes, gives up and reports kErrTimeout in
@@ -1217,6 +1366,15 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which) {
     const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (s_log ? p.G : 0);
     const char *lname = dyn && s_log ? "fwd_logits_bf16" : dyn ? "fwd_logits_dyn_bf16" : "fwd_logits_static_bf16";
     double fl = (dyn ? 2.0 * R * p.dm.H * p.dm.A : 0.0) + (s_log ? 2.0 * R * p.st.H * p.st.A : 0.0);
+    if (slice_rule(p)) {  // only each row's coded slice: bound by reading W2 (BF16)
+      const double sfl = (dyn ? 2.0 * R * p.dm.H * p.ov_w : 0.0) + (s_log ? 2.0 * R * p.st.H * p.ov_w : 0.0);
+      const double sb = (dyn ? prof_work().train_groups * 2.0 * p.dm.H * p.dm.A : 0.0) +
+                        (s_log ? 2.0 * p.st.H * p.st.A : 0.0);
+      ProfScope ps(dyn && s_log ? "fwd_logits_slice" : dyn ? "fwd_logits_slice_dyn" : "fwd_logits_slice_static", sfl,
+                   sb, st);
+      launch_slice_logits(p, T, st, zb, Z);
+      return;
+    }
     ProfScope ps(lname, fl, 0, st);
     LogitsT op;
     op.p = p, op.T = T, op.ml = S.ml_l, op.h[0] = S.hk[0], op.h[1] = S.hk[1], op.w2[0] = S.w2mn[0],
@@ -1249,7 +1407,10 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     op.p = p, op.T = T, op.ml = S.ml_w2, op.h = S.hmn, op.dz = S.dzmn;
     tc::launch(op, D.H, D.A, p.G, S.t_w2, S.ml_w2.bytes(), s1);
   }
-  {
+  if (slice_rule(p)) {  // only each row's coded slice: bound by reading W2 (BF16)
+    ProfScope ps("bwd_dh_slice", 2.0 * R * p.ov_w * D.H, tg * 2.0 * D.H * D.A, st);
+    launch_slice_dh(p, T, st);
+  } else {
     ProfScope ps("bwd_dh_bf16", 2.0 * R * D.A * D.H, 0, st);
     DhT op;
     op.p = p, op.T = T, op.ml = S.ml_dh, op.dz = S.dzk, op.w2 = S.w2k;
@@ -1274,10 +1435,22 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
     op.qshift = __builtin_ctz((unsigned)(64 / D.E));
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
+  } else if (S.dx_rows) {
+    {
+      ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
+      DXRowsT op;
+      op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
+      tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
+    }
+    // bytes: the predicted rows' dX read (t E FP32 each), every training group's table written
+    ProfScope ps("bwd_emb_grad", 0, R * D.K1() * 4.0 + tg * D.A * D.E * 4.0, s2);
+    const int nx = (D.A + S.emb_range - 1) / S.emb_range, smem = (int)emb_smem_bytes(S.emb_range, D.E, D.t, D.A);
+    if (smem_optin((const void *)emb_grad_kernel, smem))
+      launch_pdl(emb_grad_kernel, dim3(nx, p.G), dim3(kEmbThreads), smem, s2, p, T, S.emb_range);
   } else {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXT op;
-    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn, op.sacc = S.sacc_dx;
+    op.p = p, op.T = T, op.ml = S.ml_dx, op.dh = S.dhk, op.w1 = S.w1mn;
     op.eshift = (D.E & (D.E - 1)) == 0 ? __builtin_ctz((unsigned)D.E) : -1;
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
   }

@@ -91,6 +91,9 @@ GRAD_CASES = [
     (6, 8, 8, 64, 2, 90, None),
     (4, 32, 8, 64, 3, 37, (16, 12, 48)),
     (4, 16, 12, 144, 2, 150, None),
+    # 4^6 x 32 embedding table: too large to sum in shared memory, so the dX GEMM stores its rows and
+    # a second kernel sums them into the table (tcgen05 engine)
+    (6, 32, 8, 64, 2, 150, (32, 8, 64)),
 ]
 
 
@@ -201,6 +204,64 @@ def test_bf16_round_trip_and_determinism(P, kw):
     assert back == seq and list(bl) == lens
 
 
+@pytest.mark.parametrize("s,k,E", [(2, 4, 16), (3, 6, 32)])
+def test_masked_train_step_bf16_matches_oracle(P, torch, s, k, E):
+    """Overlap-masked coding: the logits layer and dh are formed over each row's coded slice only
+    (4^s columns selected by the previous token).  One BF16 step against the FP64 oracle's masked
+    step (softmax over the slice, zero elsewhere): probabilities within 2e-2, every gradient block
+    within 2e-2 of the BF16-operand restatement and 0.15 of the exact gradient (the bars of the
+    unmasked test above).  Slices of 16 and 64 columns, 150 rows per group (two 16-row chunks of
+    one slice and many one-row slices)."""
+    from oracle.codec import Config
+    from oracle.mixer import loss_grads
+    from oracle.model import backward
+    rng = np.random.default_rng(500 + 10 * s + k)
+    G, M, t, H = 2, 150, 8, 64
+    cfg_o = Config(s=s, k=k, use_static=True, emb_s=E, ctx_s=8, hid_s=64, emb_d=E, ctx_d=t, hid_d=H, lr=1e-3)
+    dsh, ssh = cfg_o.dm_shape, cfg_o.static_shape
+    W, mod = 4 ** s, 4 ** (k - s)
+    params = np.stack([_model_params(rng, dsh, g) for g in range(G)])
+    static = _model_params(rng, ssh, 77)
+    ctx = rng.integers(0, dsh.A, (G * M, cfg_o.t_eff))
+    ctx[:40, -1] = 5  # forty rows of group 0 share one slice
+    base = (ctx[:, -1] % mod) * W
+    tgt = base + rng.integers(0, W, G * M)
+    z0 = np.zeros(G, np.float32)
+    cfg = P.ModelConfig(s=s, k=k, use_static=True, emb_s=E, ctx_s=8, hid_s=64, emb_d=E, ctx_d=t, hid_d=H, lr=1e-3,
+                        static_weights=static, precision=P.PMKLC_BF16_BATCHED, overlap_mask=1)
+    d = {k_: dev(torch, x) for k_, x in dict(params=params, m=np.zeros_like(params), v=np.zeros_like(params),
+                                             alpha=np.full(G, 0.5, np.float32), am=z0, av=z0).items()}
+    d_P = torch.zeros((G * M, dsh.A), dtype=torch.float32, device="cuda")
+    d_grad = torch.zeros(params.shape, dtype=torch.float32, device="cuda")
+    P.pmklc_train_step(cfg, G, M, d["params"], d["m"], d["v"], d["alpha"], d["am"], d["av"], dev(torch, static),
+                       dev(torch, ctx.astype(np.uint16).view(np.int16)), dev(torch, tgt.astype(np.uint16).view(np.int16)),
+                       1, d_P, d_grad, None)
+    gP, gg = d_P.cpu().numpy(), d_grad.cpu().numpy()
+    for g in range(G):
+        rows = slice(g * M, (g + 1) * M)
+        cd = ctx[rows, ctx.shape[1] - t:]
+        X, a, h, Lm = forward(params[g].astype(np.float64), dsh, cd)
+        Lu = forward(static.astype(np.float64), ssh, ctx[rows, ctx.shape[1] - 8:])[3]
+        zz = mix(Lu, Lm, 0.5, (1, 0, 1))
+        Pr = np.zeros_like(zz)
+        for i, b in enumerate(base[rows]):
+            Pr[i, b:b + W] = softmax(zz[i, b:b + W])
+        assert np.abs(gP[rows] - Pr).max() < 2e-2
+        dLm = loss_grads(Pr, tgt[rows], Lu, Lm, 0.5, (1, 0, 1))[0]
+        emu = _bf16_operand_grads(params[g], dsh, cd, dLm)
+        exact = backward(params[g].astype(np.float64), dsh, cd, X, a, h, dLm)
+        for name, (lo, hi) in dsh.offsets().items():
+            got = gg[g, lo:hi].astype(np.float64)
+            for ref, bar in ((emu[lo:hi], 2e-2), (exact[lo:hi], 0.15)):
+                rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+                assert rel < bar, (g, name, bar, rel)
+
+
+def _model_params(rng, sh, seed):
+    from tests.test_gpu_steps import _model
+    return _model(rng, sh, seed, 0.05)
+
+
 def test_bf16_bits_per_base_close_to_fp32(P):
     w = synth.workload("plain", scale=1 / 16)
     kw = dict(s=2, k=4, use_static=True, emb_s=32, ctx_s=32, hid_s=128, emb_d=32, ctx_d=32, hid_d=128,
@@ -270,18 +331,20 @@ def test_update_paths_give_identical_containers(P):
     assert P.pmklc_decompress(outs[1], sw)[0] == seq
 
 
-def test_kernel_variants_give_identical_containers(P, torch):
+@pytest.mark.parametrize("s,k,E", [(2, 4, 16), (3, 6, 32)])
+def test_kernel_variants_give_identical_containers(P, torch, s, k, E):
     """Every kernel variant the autotuner offers (row-GEMM tile caps 0 / 128 / 64 x update path
     streaming / fused) codes the same bytes: the containers differ only in the variant field that
-    records the choice, every one decodes, and the autotuner picks one of them."""
+    records the choice, every one decodes, and the autotuner picks one of them.  (3,6) with E 32
+    sums the embedding gradient from stored dX rows, (2,4) in the dX tiles."""
     import synth
     from oracle.model import Shape, init_params
     seq = synth.markov(24000, 5, 0.40, 78)
     lens = [8000, 8000, 8000]
-    kw = dict(s=2, k=4, use_static=True, emb_s=16, ctx_s=8, hid_s=64, emb_d=16, ctx_d=8, hid_d=128,
+    kw = dict(s=s, k=k, use_static=True, emb_s=E, ctx_s=8, hid_s=64, emb_d=E, ctx_d=8, hid_d=128,
               lanes_per_block=24, smp_mode=P.PMKLC_SMP_TREE, fallback=0, overlap_mask=1,
               precision=P.PMKLC_BF16_BATCHED)
-    sw = init_params(Shape(256, 16, 8, 64), 4)
+    sw = init_params(Shape(4 ** k, E, 8, 64), 4)
     codes = [t | (u << 2) for t in (0, 1, 2) for u in (P.PMKLC_UPDATE_STREAM, P.PMKLC_UPDATE_FUSED)]
     outs = []
     for code in codes:
