@@ -471,6 +471,8 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   }
   p.demb_acc = nullptr;
   p.dx_rows = nullptr;
+  p.emb_pairs = nullptr;
+  p.emb_bin_off = nullptr;
   p.err = ar.alloc<int>(1);
   std::vector<float> bc1(R.S.max_tau + 2), bc2(R.S.max_tau + 2);
   for (size_t t = 0; t < bc1.size(); ++t) {
@@ -501,8 +503,10 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
       p.demb_part = ar.alloc<float>(G * (size_t)np * A * c.dm.E);
       if (ar.failed) return PMKLC_ENOMEM;
       p.dx_np = np, p.dx_ct = ct;
-    } else if (dx_rows_rule(p)) {  // large tables on tcgen05: dX rows, summed per range of table rows
+    } else if (const int nb = dx_rows_bins(p)) {  // large tables on tcgen05: dX rows, summed per range of table rows
       p.dx_rows = ar.alloc<float>(NL * (size_t)c.dm.K1());
+      p.emb_pairs = ar.alloc<uint32_t>(NL * (size_t)c.dm.t);
+      p.emb_bin_off = ar.alloc<int>(G * (size_t)(nb + 1));
       if (ar.failed) return PMKLC_ENOMEM;
     }
   }
@@ -572,8 +576,9 @@ void run_steps(Run &R, const std::vector<int> &grp_mode, cudaStream_t st) {
   };
   const bool bf = bf_form(R.p.precision);
   // kernels of one backward + update: dh, the bias sums, dW2, dX (+ the embedding sum of stored dX
-  // rows), dW1 and the optimiser on tcgen05; dh, dW2, dX, dW1 and the optimiser otherwise
-  const int bwd_launches = bf && tc_supported(R.p) ? (R.p.dx_rows ? 7 : 6) : 5;
+  // rows, listed first by table-row range), dW1 and the optimiser on tcgen05; dh, dW2, dX, dW1 and
+  // the optimiser otherwise
+  const int bwd_launches = bf && tc_supported(R.p) ? (R.p.dx_rows ? 8 : 6) : 5;
   const bool split_static = R.net && use_ss && bf && R.p.use_static && tc_supported(R.p);
   int static_for = -1;  // the step whose static forward is already queued on ss.aux[2]
   for (int T = 0; T < S.T_total; ++T) {

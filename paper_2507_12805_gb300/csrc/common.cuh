@@ -86,6 +86,8 @@ struct Plan {
   // FP32), summed per group into the embedding gradient (grad's embedding part) by a kernel that
   // owns a range of table rows; nullptr otherwise
   float *dx_rows;
+  uint32_t *emb_pairs;  // with dx_rows: every predicted row's (row, position) pairs by bin (NL x t)
+  int *emb_bin_off;     // with dx_rows: per group, the bins' first entries and the total
   // BF16 form with small tables: per group, dx_np partial FP32 tables (A x E) of the dX tiles
   // (row tile bx, column tile by at partial bx * dx_ct + by), summed by the optimiser in that
   // order; nullptr: the fixed-point accumulators above

@@ -106,6 +106,9 @@ int dx_partials(const Plan &p, int *ct);
 // true when the dX GEMM stores its rows (Plan::dx_rows, NL x t*E FP32) for a separate sum into the
 // embedding gradient: tables too large for the shared-memory forms
 bool dx_rows_rule(const Plan &p);
+// ... and then the number of bins (ranges of table rows) its pairs are listed by (Plan::emb_bin_off
+// holds G x (bins + 1) offsets), else 0
+int dx_rows_bins(const Plan &p);
 // slice.cu: with overlap-masked coding (slice width 4^s of 16 to 64 tokens) the logits layer and dh
 // formed over each row's coded slice only, reading every group's W2 about once per step.
 // launch_slice_logits: problems zb .. zb + Z - 1 (z < G dynamic, z >= G static on group z - G)

@@ -481,24 +481,22 @@ struct DXRowsT : TBase {
   }
 };
 
-// The embedding gradient of every training group from its stored dX rows: CTA (x, g) owns table
-// rows [x R, x R + R) of group g and sums them in shared memory in the 2^40 fixed point of the
-// other dX forms, as a low unsigned word and a high signed word whose carry is taken from the
-// value the low word's atomic add returns: every add is exact modulo 2^64, so the sums do not
-// depend on the order of the adds and equal those of the forms that add in global memory.  The
-// group's rows are taken kEmbPairs context pairs at a time: the threads list the pairs whose token
-// lies in the CTA's range (loads issued eight at a time), then add their E values, one 8-value
-// chunk per work item.  The sums go to the embedding part of the group's gradient as FP32 (one
-// rounding), where the streaming optimiser reads them.
+// The embedding gradient of every training group from its stored dX rows, in two kernels.
+// emb_bin_kernel (one CTA per group) lists the group's (row, context position) pairs of predicted
+// rows by range of R table rows ("bins"): entry = pair index << 12 | token - bin R, bin offsets per
+// group.  emb_grad_kernel (CTA (bin, group)) adds the E values of its bin's pairs into its R table
+// rows, kept in shared memory in the 2^40 fixed point of the other dX forms as a low unsigned word
+// and a high signed word whose carry is taken from the value the low word's atomic add returns:
+// every add is exact modulo 2^64, so neither the order of the bin's entries nor that of the adds
+// matters, and the sums equal those of the forms that add in global memory.  The sums go to the
+// embedding part of the group's gradient as FP32 (one rounding), where the streaming optimiser
+// reads them.
 constexpr int kEmbThreads = 512;
-constexpr int kEmbTableBytes = 64 * 1024;  // two CTAs per SM with the pass lists
-constexpr int kEmbPairs = 4096;            // context pairs per pass (at least one row's t)
+constexpr int kEmbTableBytes = 64 * 1024;  // two CTAs per SM
+constexpr int kEmbMaxBins = 256;
+constexpr int kEmbPairBits = 20;           // pair index bits of an entry (token offset: the low 12)
 
-__host__ __device__ inline int emb_rows_per_pass(int t) { return max(1, kEmbPairs / t); }
-__host__ __device__ inline size_t emb_smem_bytes(int range, int E, int t, int A) {
-  const size_t tab = (size_t)min(range, A) * E * 8, cap = (size_t)emb_rows_per_pass(t) * t;
-  return tab + (size_t)emb_rows_per_pass(t) * 8 + cap * 8 + 16;
-}
+__host__ __device__ inline int emb_range(int E) { return kEmbTableBytes / (8 * E); }
 
 __device__ __forceinline__ void emb_add(uint32_t *lo, int *hi, int i, long long q) {
   const uint32_t ql = (uint32_t)(unsigned long long)q;
@@ -507,86 +505,100 @@ __device__ __forceinline__ void emb_add(uint32_t *lo, int *hi, int i, long long 
   if (qh) atomicAdd(hi + i, qh);
 }
 
-__global__ void __launch_bounds__(kEmbThreads, 2) emb_grad_kernel(Plan p, int T, int range) {
+__global__ void __launch_bounds__(kEmbThreads) emb_bin_kernel(Plan p, int T, int range, int nbins) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ int cnt[kEmbMaxBins], cur[kEmbMaxBins];
+  const int g = blockIdx.x;
+  if (!group_trains(p, T, g)) return;  // the same for the whole CTA
+  const int t = p.dm.t, r0 = p.grp_lane_off[g], rows = p.grp_lane_off[g + 1] - r0;
+  const long long j = T - p.grp_start[g];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t *out = p.emb_pairs + (size_t)r0 * t;
+  for (int b = tid; b < nbins; b += kEmbThreads) cnt[b] = 0;
+  __syncthreads();
+  // two walks over the pairs, a warp per row, its lanes on the row's positions: count, then place
+  for (int walk = 0; walk < 2; ++walk) {
+    for (int r = warp; r < rows; r += kEmbThreads / 32) {
+      const int rw = r0 + r;
+      if (!row_pred(p, T, rw, g)) continue;  // the same for the whole warp
+      const long long b0 = p.lane_tok[rw] + j - t;
+      for (int pos0 = 0; pos0 < t; pos0 += 32) {
+        const int pos = pos0 + lane;
+        const bool in = pos < t;
+        const int a = in ? p.tokens[b0 + pos] : 0, bin = in ? a / range : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, in);
+        if (!in) continue;
+        const unsigned same = __match_any_sync(act, bin);
+        const int leader = __ffs(same) - 1, rank = __popc(same & ((1u << lane) - 1u));
+        if (walk == 0) {
+          if (lane == leader) atomicAdd(&cnt[bin], __popc(same));
+        } else {
+          int slot = 0;
+          if (lane == leader) slot = atomicAdd(&cur[bin], __popc(same));
+          slot = __shfl_sync(same, slot, leader) + rank;
+          out[slot] = ((uint32_t)(r * t + pos) << 12) | (uint32_t)(a - bin * range);
+        }
+      }
+    }
+    __syncthreads();
+    if (walk == 0 && tid == 0) {  // bin offsets within the group's entries
+      int* off = p.emb_bin_off + (size_t)g * (nbins + 1);
+      int o = 0;
+      for (int b = 0; b < nbins; ++b) off[b] = o, cur[b] = o, o += cnt[b];
+      off[nbins] = o;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kEmbThreads, 2) emb_grad_kernel(Plan p, int T, int range, int nbins) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) uint8_t emb_smem[];
-  __shared__ int nmatch;
   const int g = blockIdx.y;
   if (!group_trains(p, T, g)) return;  // the same for the whole CTA
   const int E = p.dm.E, t = p.dm.t, K1 = t * E;
   const int a0 = blockIdx.x * range, na = min(range, p.dm.A - a0);
   if (na <= 0) return;
-  const int tid = threadIdx.x, n = na * E, rc = emb_rows_per_pass(t);
+  const int tid = threadIdx.x, n = na * E, cpp = E >> 3;  // 8-value chunks per pair
   uint32_t *lo = reinterpret_cast<uint32_t *>(emb_smem);
   int *hi = reinterpret_cast<int *>(lo + n);
-  long long *base = reinterpret_cast<long long *>(emb_smem + (size_t)n * 8);
-  int *mpair = reinterpret_cast<int *>(base + rc), *mtok = mpair + rc * t;
   for (int i = tid; i < n; i += kEmbThreads) lo[i] = 0u, hi[i] = 0;
-  const int r0 = p.grp_lane_off[g], rows = p.grp_lane_off[g + 1] - r0;
-  const long long j = T - p.grp_start[g];
-  const int lane = tid & 31, cpp = E >> 3;  // 8-value chunks per pair
-  for (int rr0 = 0; rr0 < rows; rr0 += rc) {
-    const int nr = min(rc, rows - rr0), np = nr * t;
-    for (int r = tid; r < nr; r += kEmbThreads) {  // first context token of each predicted row
-      const int rw = r0 + rr0 + r;
-      base[r] = row_pred(p, T, rw, g) ? p.lane_tok[rw] + j - t : -1;
-    }
-    if (tid == 0) nmatch = 0;
-    __syncthreads();
-    for (int i0 = 0; i0 < np; i0 += 8 * kEmbThreads) {
-      int tok[8];
+  const int r0 = p.grp_lane_off[g];
+  const int *off = p.emb_bin_off + (size_t)g * (nbins + 1);
+  const int e0 = off[blockIdx.x], items = (off[blockIdx.x + 1] - e0) * cpp;
+  const uint32_t *ent = p.emb_pairs + (size_t)r0 * t + e0;
+  const float *dx = p.dx_rows + (size_t)r0 * K1;
+  __syncthreads();
+  for (int it0 = 0; it0 < items; it0 += 2 * kEmbThreads) {
+    float x[2][8];
+    int dst[2];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = i0 + q * kEmbThreads + tid;
-        tok[q] = -1;
-        if (i < np) {
-          const int r = i / t;
-          const long long b = base[r];
-          if (b >= 0) tok[q] = p.tokens[b + (i - r * t)];
+    for (int u = 0; u < 2; ++u) {  // both items' loads before any add
+      const int it = it0 + u * kEmbThreads + tid;
+      dst[u] = -1;
+      if (it < items) {
+        const int m = it / cpp, c = it - m * cpp;
+        const uint32_t en = ent[m];
+        const int i = (int)(en >> 12), r = i / t;
+        const float4 *src = reinterpret_cast<const float4 *>(dx + (size_t)r * K1 + (i - r * t) * E + 8 * c);
+        const float4 v0 = src[0], v1 = src[1];
+        x[u][0] = v0.x, x[u][1] = v0.y, x[u][2] = v0.z, x[u][3] = v0.w;
+        x[u][4] = v1.x, x[u][5] = v1.y, x[u][6] = v1.z, x[u][7] = v1.w;
+        dst[u] = (int)(en & 0xFFFu) * E + 8 * c;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (dst[u] >= 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const long long v = fix40(x[u][q]);
+          if (v) emb_add(lo, hi, dst[u] + q, v);
         }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = i0 + q * kEmbThreads + tid;
-        const bool hit = tok[q] >= a0 && tok[q] < a0 + na;
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        int slot = 0;
-        if (lane == 0 && m) slot = atomicAdd(&nmatch, __popc(m));
-        slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
-        if (hit) mpair[slot] = i, mtok[slot] = tok[q] - a0;
-      }
-    }
-    __syncthreads();
-    const int items = nmatch * cpp;
-    for (int it0 = 0; it0 < items; it0 += 2 * kEmbThreads) {
-      float x[2][8];
-      int dst[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {  // both items' loads before any add
-        const int it = it0 + u * kEmbThreads + tid;
-        dst[u] = -1;
-        if (it < items) {
-          const int m = it / cpp, c = it - m * cpp, i = mpair[m], r = i / t;
-          const float4 *src =
-              reinterpret_cast<const float4 *>(p.dx_rows + (size_t)(r0 + rr0 + r) * K1 + (i - r * t) * E + 8 * c);
-          const float4 v0 = src[0], v1 = src[1];
-          x[u][0] = v0.x, x[u][1] = v0.y, x[u][2] = v0.z, x[u][3] = v0.w;
-          x[u][4] = v1.x, x[u][5] = v1.y, x[u][6] = v1.z, x[u][7] = v1.w;
-          dst[u] = mtok[m] * E + 8 * c;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (dst[u] >= 0)
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const long long v = fix40(x[u][q]);
-            if (v) emb_add(lo, hi, dst[u] + q, v);
-          }
-    }
-    __syncthreads();  // the pass's bases and lists are rewritten by the next pass
   }
+  __syncthreads();
   float *gr = p.grad + (size_t)g * p.P + p.dm.off_emb() + (size_t)a0 * E;
   for (int i = tid; i < n; i += kEmbThreads)
     gr[i] = unfix40((long long)(((unsigned long long)(uint32_t)hi[i] << 32) | lo[i]));
@@ -1132,7 +1144,7 @@ struct TcSetup {
   tc::TilePlan t_h, t_l, t_dh, t_w2, t_dx, t_w1, t_h8, t_l8, t_w2f, t_w1f;
   int tile_cap = 0;
   MetaLayout ml_h, ml_l, ml_dh, ml_w2, ml_dx, ml_w1, ml_h8, ml_l8;
-  int table_h[2], table_w1, sacc_dx, table_h8, dx_owner, dx_rows, emb_range;
+  int table_h[2], table_w1, sacc_dx, table_h8, dx_owner, dx_rows, emb_range, emb_bins;
   CUtensorMap w1k[2], w1mn, w2mn[2], w2k, hk[2], dzk, dhk, hmn, dzmn, dhmn, w1_8, w2_8;
 };
 
@@ -1195,7 +1207,7 @@ bool build(TcSetup &S, const Plan &p) {
   if (S.sacc_dx && S.t_dx.nt > 8 * D.E) S.sacc_dx = 0;  // over 8 positions per tile the 22-bit low sums could overflow
   S.dx_owner = dx_owner_rule(p);
   S.dx_rows = !S.dx_owner && !S.sacc_dx;
-  S.emb_range = 0;
+  S.emb_range = S.emb_bins = 0;
   if (S.dx_owner) {  // 128-column tiles, two stage buffers: two CTAs per SM
     S.ml_dx = {tc::kRows, D.t, D.A * D.E * 4};
     S.t_dx = {dx_owner_nt(p), 2};
@@ -1208,8 +1220,12 @@ bool build(TcSetup &S, const Plan &p) {
     while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < (size_t)tc::kRows * tc::kFloatPitch * 4)
       ++S.t_dx.ns;
     if (S.t_dx.ns > tc::kStages) return false;
-    S.emb_range = kEmbTableBytes / (8 * D.E);
-    if (S.emb_range < 1 || emb_smem_bytes(S.emb_range, D.E, D.t, D.A) > limit) return false;
+    S.emb_range = emb_range(D.E);
+    S.emb_bins = S.emb_range > 0 ? (D.A + S.emb_range - 1) / S.emb_range : 0;
+    // entries hold a pair index in 20 bits and a token offset in 12
+    if (S.emb_range < 1 || S.emb_range > 4096 || S.emb_bins > kEmbMaxBins ||
+        (long long)p.Mmax * D.t >= (1LL << kEmbPairBits))
+      return false;
   } else {
     // the staged epilogue needs kStagedBytes of stage buffers (checked against the limit below)
     while ((size_t)S.t_dx.ns * (tc::kRows + S.t_dx.nt) * tc::kRowBytes < tc::kStagedBytes) ++S.t_dx.ns;
@@ -1308,10 +1324,12 @@ bool tc_supported(const Plan &p) {
   return get_setup(p, S);
 }
 
-bool dx_rows_rule(const Plan &p) {
-  if (!shapes_ok(p)) return false;
+bool dx_rows_rule(const Plan &p) { return dx_rows_bins(p) > 0; }
+
+int dx_rows_bins(const Plan &p) {
+  if (!shapes_ok(p)) return 0;
   TcSetup S;
-  return get_setup(p, S) && S.dx_rows;
+  return get_setup(p, S) && S.dx_rows ? S.emb_bins : 0;
 }
 
 namespace {
@@ -1436,6 +1454,10 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     op.qshift = __builtin_ctz((unsigned)(64 / D.E));
     tc::launch(op, p.Mmax, D.K1(), p.G, S.t_dx, S.ml_dx.bytes(), s2);
   } else if (S.dx_rows) {
+    {  // bytes: the context tokens read, one 4-byte entry per pair written
+      ProfScope ps("bwd_emb_bin", 0, R * D.t * 6.0, s2);
+      launch_pdl(emb_bin_kernel, dim3(p.G), dim3(kEmbThreads), 0, s2, p, T, S.emb_range, S.emb_bins);
+    }
     {
       ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
       DXRowsT op;
@@ -1444,9 +1466,10 @@ void launch_backward_tc(const Plan &p, int T, cudaStream_t st, const StepStreams
     }
     // bytes: the predicted rows' dX read (t E FP32 each), every training group's table written
     ProfScope ps("bwd_emb_grad", 0, R * D.K1() * 4.0 + tg * D.A * D.E * 4.0, s2);
-    const int nx = (D.A + S.emb_range - 1) / S.emb_range, smem = (int)emb_smem_bytes(S.emb_range, D.E, D.t, D.A);
+    const int smem = min(S.emb_range, D.A) * D.E * 8;
     if (smem_optin((const void *)emb_grad_kernel, smem))
-      launch_pdl(emb_grad_kernel, dim3(nx, p.G), dim3(kEmbThreads), smem, s2, p, T, S.emb_range);
+      launch_pdl(emb_grad_kernel, dim3(S.emb_bins, p.G), dim3(kEmbThreads), smem, s2, p, T, S.emb_range,
+                 S.emb_bins);
   } else {
     ProfScope ps("bwd_dx_bf16", 2.0 * R * D.K1() * D.H, 0, s2);
     DXT op;
