@@ -12,6 +12,7 @@ It is a plain, slow, FP64 restatement of the method, written from the paper:
   tokenizer   (s,k)-mer encoding GskE                     paper §4.1, Fig. 3
   rng         counter-based splitmix64 initialisation      (published generator)
   model       MLP predictor forward/backward, Adam         §2 steps (3)-(4), §4.2
+  bigru       BiGRU static predictor (SPuM/SPrM) forward   §4.2.2, §4.2.3
   mixer       probability mixer, softmax, cross entropy    Eq. (1), Eq. (2)
   quantize    probabilities -> integer frequency table     (paper silent; see module)
   rangecoder  byte-oriented range coder + exact rational   §2 step (3) "entropy encoder"
