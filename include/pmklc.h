@@ -291,6 +291,39 @@ int pmklc_predict(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uin
                   const uint16_t *d_ctx, size_t rows, uint32_t precision, float *d_logits, void *stream);
 
 /*
+ * BiGRU static predictor (paper §4.2.2: the static public model SPuM reads the
+ * t context tokens through an embedding of width E (16 in the paper), two
+ * bidirectional GRU layers and a Linear and a Dense layer of width 128; §4.2.3:
+ * the static private model SPrM has the same structure with one BiGRU layer).
+ * The paper gives the layers, not their equations; the reading used is the GRU
+ * with the reset gate on the recurrent projection after its bias,
+ *     r = sigmoid(Wi_r x + bi_r + Wh_r h + bh_r),  z = sigmoid(Wi_z x + bi_z + Wh_z h + bh_z),
+ *     n = tanh(Wi_n x + bi_n + r (Wh_n h + bh_n)),  h' = (1 - z) n + z h,  h = 0 at the start,
+ * a forward GRU over the positions oldest first and a backward one newest
+ * first per layer (layer output [h^f_p, h^b_p], the next layer's input), the
+ * summary u = [forward state after the newest token, backward state after the
+ * oldest], q = relu(W3 u + b3) (128 wide) and logits L = q W4 + b4.
+ * Parameters: one FP32 array
+ *     Emb[A][E]
+ *     for layer l = 0 .. layers-1, for direction forward then backward:
+ *         Wi[3Hg][in_l] | Wh[3Hg][Hg] | bi[3Hg] | bh[3Hg]   (gate rows r, z, n;
+ *                                                           in_0 = E, in_1 = 2Hg)
+ *     W3[128][2Hg] | b3[128] | W4[128][A] | b4[A]
+ * (row-major, A = 4^k; the size does not depend on t).  Hg is the GRU width per
+ * direction, which the paper does not state.
+ * pmklc_bigru_count: the number of parameters (0 for shapes outside those
+ * built: E in {8, 16, 32}, Hg in {16, 32}, layers 1 or 2, 1 <= k <= 8).
+ * pmklc_predict_bigru: for rows d_ctx[r*t .. r*t+t) (oldest first; 1 <= t <=
+ * 4096, rows <= 2^24) writes q into d_q (rows x 128, optional) and the logits
+ * into d_logits (rows x A, optional; at least one of the two).  FP32 on the CUDA
+ * cores.  It allocates its scratch (t x 2Hg x rows floats with two layers) on
+ * `stream`.  A token >= A is read as token 0 and the call returns EINVAL.
+ */
+size_t pmklc_bigru_count(uint32_t k, uint32_t E, uint32_t Hg, uint32_t layers);
+int pmklc_predict_bigru(const float *d_params, uint32_t k, uint32_t E, uint32_t t, uint32_t Hg, uint32_t layers,
+                        const uint16_t *d_ctx, size_t rows, float *d_q, float *d_logits, void *stream);
+
+/*
  * One update of G dynamic models from their own batches of M rows each
  * (paper §2 step 4, Eq. 1 and Eq. 2 with the Backward Controller):
  * forward of the dynamic (and, if use_static, static) predictor, Eq. (1)

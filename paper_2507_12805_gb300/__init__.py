@@ -81,6 +81,8 @@ _sigs = {
     "pmklc_range_encode": ([_vp, _vp, _u32, _u32, _u32, _vp, _u32, _vp, _vp], _i),
     "pmklc_range_decode": ([_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp], _i),
     "pmklc_predict": ([_vp, _u32, _u32, _u32, _u32, _vp, _sz, _u32, _vp, _vp], _i),
+    "pmklc_bigru_count": ([_u32, _u32, _u32, _u32], _sz),
+    "pmklc_predict_bigru": ([_vp, _u32, _u32, _u32, _u32, _u32, _vp, _sz, _vp, _vp, _vp], _i),
     "pmklc_train_step": ([_cfgp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp,
                           _vp], _i),
     "pmklc_quantize_static_fp8": ([_vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp], _i),
@@ -273,6 +275,19 @@ def pmklc_predict(d_params, k: int, E: int, t: int, H: int, d_ctx, d_logits, pre
     rows = d_ctx.shape[0]
     _check(lib.pmklc_predict(_ptr(d_params), k, E, t, H, _ptr(d_ctx), rows, precision, _ptr(d_logits),
                              _stream(stream)), "pmklc_predict")
+
+
+def pmklc_bigru_count(k: int, E: int, Hg: int, layers: int) -> int:
+    """Parameters of a BiGRU static predictor (0 for shapes the library does not build)."""
+    return int(lib.pmklc_bigru_count(k, E, Hg, layers))
+
+
+def pmklc_predict_bigru(d_params, k: int, E: int, t: int, Hg: int, layers: int, d_ctx, d_q=None, d_logits=None,
+                        stream=None):
+    """BiGRU static predictor forward: q (rows x 128) and/or logits (rows x 4^k) of the rows of d_ctx."""
+    rows = d_ctx.shape[0]
+    _check(lib.pmklc_predict_bigru(_ptr(d_params), k, E, t, Hg, layers, _ptr(d_ctx), rows, _ptr(d_q),
+                                   _ptr(d_logits), _stream(stream)), "pmklc_predict_bigru")
 
 
 def pmklc_train_step(cfg: ModelConfig, G: int, M: int, d_params, d_m, d_v, d_alpha, d_alpha_m, d_alpha_v, d_static,

@@ -69,6 +69,20 @@ void launch_quantize_fp8(const float *d_params, const Dims &d, uint8_t *d_codes,
 // c1[h] = s_emb * s_w1[h], the hidden layer's combined scale
 void launch_fp8_hidden_scale(const float *d_scales, const Dims &d, float *d_c1, cudaStream_t st);
 
+// bigru.cu -------------------------------------------------------------------
+// The BiGRU static predictor (§4.2.2 SPuM with two layers, §4.2.3 SPrM with one): element offsets
+// of its flat FP32 parameters, Emb [A][E], then per layer l and direction d (forward, backward)
+// Wi [3 Hg][in_l] | Wh [3 Hg][Hg] | bi [3 Hg] | bh [3 Hg] (gate rows r, z, n; in_0 = E, in_1 = 2 Hg),
+// then W3 [kGruDense][2 Hg] | b3 [kGruDense] | W4 [kGruDense][A] | b4 [A].
+constexpr int kGruDense = 128;  // width of the Linear layer (§4.2.2)
+struct GruOff {
+  size_t emb, wi[2][2], wh[2][2], bi[2][2], bh[2][2], w3, b3, w4, b4, count;
+};
+GruOff gru_offsets(int A, int E, int Hg, int layers);
+// the shapes the kernel is built for: E in {8, 16, 32}, Hg in {16, 32}, 1 or 2 layers, 1 <= t <= 4096
+bool gru_shape_ok(int k, int E, int t, int Hg, int layers);
+int gru_smem_bytes(int Hg);
+
 // countmodel.cu --------------------------------------------------------------
 void launch_count_step(const Plan &p, const CountPlan &c, int T, cudaStream_t st);
 void launch_count_init(const Plan &p, const CountPlan &c, int encode, cudaStream_t st);

@@ -119,3 +119,20 @@ def test_header_constants_equal_the_binding_and_the_library():
     codes = [int(v) for n, v in defs.items() if n.startswith("PMKLC_E") or n == "PMKLC_OK"]
     msgs = {P.lib.pmklc_strerror(c) for c in codes}
     assert len(msgs) == len(codes)
+
+
+def test_bigru_count_and_argument_checks(P):
+    """The BiGRU static predictor's parameter count equals the oracle layout's; shapes outside
+    those built and bad arguments are refused before any device work."""
+    from oracle.bigru import GruShape
+    for (k, E, Hg, layers) in [(6, 16, 32, 2), (3, 16, 32, 1), (2, 8, 16, 2), (8, 32, 16, 1)]:
+        assert P.pmklc_bigru_count(k, E, Hg, layers) == GruShape(4 ** k, E, 7, Hg, layers).count
+    for bad in [(6, 12, 32, 2), (6, 16, 24, 2), (6, 16, 32, 3), (0, 16, 32, 1), (9, 16, 32, 1)]:
+        assert P.pmklc_bigru_count(*bad) == 0
+    f = P.lib.pmklc_predict_bigru
+    one = ctypes.c_void_p(16)  # never dereferenced: every call below returns before device work
+    assert f(None, 3, 16, 8, 32, 2, None, 0, None, None, None) == P.PMKLC_OK  # no rows
+    assert f(one, 3, 16, 0, 32, 2, one, 4, one, None, None) == P.PMKLC_EINVAL  # t = 0
+    assert f(one, 3, 16, 8, 32, 2, one, 4, None, None, None) == P.PMKLC_EINVAL  # no output
+    assert f(one, 3, 12, 8, 32, 2, one, 4, one, None, None) == P.PMKLC_EINVAL  # E not built
+    assert f(one, 3, 16, 8, 32, 2, one, (1 << 24) + 1, one, None, None) == P.PMKLC_EINVAL  # rows
