@@ -22,7 +22,8 @@
  *   - A model's parameters are one FP32 array in the layout
  *         Emb[A][E] | W1t[H][t*E] | b1[H] | W2[H][A] | b2[A]     (A = 4^k)
  *     (row-major; W1 is stored transposed, row j holding the weights into
- *     hidden unit j), see pmklc_model_count().
+ *     hidden unit j), see pmklc_model_count(); a BiGRU static predictor's
+ *     layout is given at pmklc_predict_bigru().
  */
 #ifndef PMKLC_H
 #define PMKLC_H
@@ -34,7 +35,7 @@
 extern "C" {
 #endif
 
-#define PMKLC_ABI_VERSION 3
+#define PMKLC_ABI_VERSION 4
 
 /* error codes */
 #define PMKLC_OK 0
@@ -120,6 +121,14 @@ typedef struct {
                                   byte unchanged (the reduction over K of each output element is the
                                   same); both are recorded in the container's variant field, so
                                   decompression runs the same kernels */
+  uint32_t static_arch;        /* architecture of the static predictor: 0 the MLP of the layout above
+                                  (emb_s, ctx_s, hid_s); 1 or 2 the BiGRU static predictor of
+                                  pmklc_predict_bigru with that many BiGRU layers (§4.2.3 SPrM: one,
+                                  §4.2.2 SPuM: two), E = emb_s, t = ctx_s, GRU width hid_s, weights
+                                  in its layout (pmklc_bigru_count floats).  It needs use_static,
+                                  private_model 0 and precision PMKLC_FP32_PLAIN or
+                                  PMKLC_BF16_BATCHED; its Linear layer forms the static h (128
+                                  wide) and its Dense layer runs on the MLP logits kernels */
 } pmklc_model_cfg;
 
 int pmklc_abi_version(void);

@@ -47,6 +47,11 @@ Readings where the paper is silent:
            parameters are rounded to BF16 (ties to even) and stored after the
            block records (2 bytes each, little-endian; flag bit 3); it takes
            the static slot of Eq. (1), with the stored values.
+  BiGRU    static_arch 1 or 2: the static slot of Eq. (1) is the BiGRU static
+           predictor of bigru.py with that many layers (§4.2.3 SPrM's
+           structure: one; §4.2.2 SPuM's: two), E = emb_s, t = ctx_s and GRU
+           width hid_s; flag bits 4-5 of the container (0: the MLP).  It is
+           frozen: never a private model, and FP8 forms do not take it.
   judge    fallback 1: the count model (countmodel.py) codes every block in the
            same lanes alongside the network, and a block is stored with it when
            that costs fewer bytes (flag in the container); fallback 2: the count
@@ -65,7 +70,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-from . import countmodel, fp8
+from . import bigru, countmodel, fp8
 from .mixer import loss_grads, mix, softmax
 from .model import Shape, adam_step, backward, forward, init_params, sgd_step
 from .quantize import TOTAL, cumulative, quantize
@@ -116,6 +121,7 @@ class Config:
     private_epochs: int = 1
     private_bases: int = 0
     private_threshold: int = 0
+    static_arch: int = 0  # 0: MLP static predictor; 1, 2: BiGRU layers (hid_s = GRU width)
 
     def f32(self, name: str) -> float:
         return float(np.float32(getattr(self, name)))
@@ -131,6 +137,14 @@ class Config:
     @property
     def static_shape(self) -> Shape:
         return Shape(self.A, self.emb_s, self.ctx_s, self.hid_s)
+
+    @property
+    def gru_shape(self) -> bigru.GruShape:
+        return bigru.GruShape(self.A, self.emb_s, self.ctx_s, self.hid_s, self.static_arch)
+
+    @property
+    def static_count(self) -> int:
+        return self.gru_shape.count if self.static_arch else self.static_shape.count
 
     @property
     def t_eff(self) -> int:
@@ -369,7 +383,9 @@ def _run(cfg: Config, blocks, static_w, on_probs=None, on_state=None, only=None,
             Lu = None
             if cfg.use_static:
                 cs = np.stack([_ctx(b.tokens, b.starts[r], j, cfg.ctx_s) for r in pred])
-                if fq is None:
+                if cfg.static_arch:
+                    Lu = bigru.forward(static_w, cfg.gru_shape, cs)[1]
+                elif fq is None:
                     Lu = forward(static_w, sshape, cs)[3]
                 elif cfg.precision == 3:
                     Lu = fp8.forward_hidden(fq, static_w, cs)
@@ -471,8 +487,12 @@ def _check_cfg(cfg: Config, static_w):
         raise ValueError("need 1 <= s <= k <= 8")
     if cfg.lanes_per_block < 1:
         raise ValueError("lanes_per_block must be >= 1 for the oracle")
+    if cfg.static_arch not in (0, 1, 2):
+        raise ValueError("static_arch must be 0 (MLP), 1 or 2 (BiGRU layers)")
+    if cfg.static_arch and (not cfg.use_static or cfg.private_model or cfg.precision > 1):
+        raise ValueError("a BiGRU static predictor is frozen and given: use_static, no private model, FP32/BF16")
     if cfg.use_static:
-        if static_w is None or np.asarray(static_w).size != cfg.static_shape.count:
+        if static_w is None or np.asarray(static_w).size != cfg.static_count:
             raise ValueError("static weights missing or of the wrong size")
     if cfg.private_model not in (0, 1, 2) or cfg.private_epochs < 0 or cfg.private_bases < 0:
         raise ValueError("bad private-model settings")
@@ -517,7 +537,8 @@ def compress(seq, block_lens, cfg: Config, static_w=None, on_probs=None, private
         for x in (cnt if use_count else net):
             out_hdr += varint(len(x))
             payload += x
-    flags = (1 if cfg.use_static else 0) | (int(cfg.fallback) << 1) | (PRIVATE_FLAG if private else 0)
+    flags = ((1 if cfg.use_static else 0) | (int(cfg.fallback) << 1) | (PRIVATE_FLAG if private else 0) |
+             (int(cfg.static_arch) << 4))
     if private:  # the private model's BF16 bits follow the block records
         out_hdr += (np.asarray(static_w, np.float32).view(np.uint32) >> 16).astype("<u2").tobytes()
     head = HEADER.pack(MAGIC, VERSION, cfg.s, cfg.k, flags, cfg.precision, cfg.optimizer, cfg.smp_mode,
@@ -540,7 +561,7 @@ def parse_header(data: bytes):
                  optimizer=f[6], smp_mode=f[7], count_order=f[8], emb_d=f[9], ctx_d=f[10], hid_d=f[11],
                  emb_s=f[12], ctx_s=f[13], hid_s=f[14], lanes_per_block=f[15], lr=f[16], alpha_init=f[17],
                  smp_fraction=f[18], seed=f[19], variant=f[24] & ~1, lane_tokens=f[25],
-                 overlap_mask=f[24] & 1)
+                 overlap_mask=f[24] & 1, static_arch=(f[4] >> 4) & 3)
     return cfg, {"static_hash": f[20], "n": f[21], "n_blocks": f[22], "crc": f[23],
                  "private": bool(f[4] & PRIVATE_FLAG)}
 
@@ -549,6 +570,9 @@ def decompress(data: bytes, static_w=None) -> bytes:
     cfg, meta = parse_header(data)
     if meta["private"] and not cfg.use_static:
         raise CorruptStream("a private model is flagged without the static slot")
+    if data[7] & 0xC0 or cfg.static_arch == 3 or (cfg.static_arch and (not cfg.use_static or meta["private"]
+                                                                      or cfg.precision > 1)):
+        raise CorruptStream("bad static-architecture flags")
     if meta["private"]:  # the stored private model replaces any given static model
         static_w = None
     if cfg.use_static and not meta["private"] and static_hash(static_w) != meta["static_hash"]:

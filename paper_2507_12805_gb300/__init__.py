@@ -47,7 +47,7 @@ class CModelCfg(ctypes.Structure):
                 ("overlap_mask", ctypes.c_uint32), ("update_path", ctypes.c_uint32),
                 ("private_model", ctypes.c_uint32), ("private_epochs", ctypes.c_uint32),
                 ("private_bases", ctypes.c_uint64), ("private_threshold", ctypes.c_uint64),
-                ("gemm_tiles", ctypes.c_uint32)]
+                ("gemm_tiles", ctypes.c_uint32), ("static_arch", ctypes.c_uint32)]
 
 
 class CKernelProf(ctypes.Structure):
@@ -140,6 +140,7 @@ class ModelConfig:
     private_bases: int = 0
     private_threshold: int = 0  # private_model 2: SPrM above this many bases (0 = 5e8)
     gemm_tiles: int = 0      # row GEMMs' column tiles: 0 default, 1 at most 128, 2 at most 64 (same bytes)
+    static_arch: int = 0     # static predictor: 0 MLP, 1 / 2 BiGRU layers (SPrM / SPuM structure; hid_s = GRU width)
 
     def to_c(self) -> CModelCfg:
         c = CModelCfg()

@@ -49,6 +49,18 @@ struct CtxRows {
   __device__ int tok(int r, int pos) const { return ctx[(size_t)r * t + pos]; }
 };
 
+// context source: the lanes predicted at global step T of a run (the static model's t tokens
+// before each lane's target, oldest first)
+struct CtxLanes {
+  Plan p;
+  int T;
+  __device__ bool on(int r) const { return row_pred(p, T, r, p.lane_grp[r]); }
+  __device__ int tok(int r, int pos) const {
+    const long long tp = p.lane_tok[r] + (T - p.grp_start[p.lane_grp[r]]);
+    return p.tokens[tp - p.st.t + pos];
+  }
+};
+
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
 
 // One GRU direction over the positions of this thread's row.  sw: Wi [3 HG][IN] | Wh [3 HG][HG] |
@@ -267,6 +279,25 @@ int gru_smem_bytes(int Hg) {
   // the largest pass (input 2 Hg) + the gate columns; the Linear layer's W3 and b3 fit in it
   const int pass = 3 * Hg * 2 * Hg + 3 * Hg * Hg + 6 * Hg, cols = 2 * Hg * kThreads;
   return (int)sizeof(float) * (pass + cols);
+}
+
+void launch_bigru_static(const Plan &p, int T, cudaStream_t st) {
+  GruRun a{};
+  a.w = p.st_gru;
+  a.o = gru_offsets(p.st.A, p.st.E, p.gru_hg, p.gru_layers);
+  a.A = p.st.A, a.t = p.st.t, a.layers = p.gru_layers, a.rows = p.NL, a.y = p.gru_y, a.err = p.err;
+  if (p.hs_b)
+    a.qb = p.hs_b;
+  else
+    a.q = p.hs;
+  a.ldq = kGruDense;
+  // FLOPs per predicted row: every (layer, direction) pass does t x 3 Hg x (in + Hg) FMAs, the
+  // Linear layer 128 x 2 Hg
+  const double Hg = p.gru_hg;
+  double per = 2.0 * kGruDense * 2 * Hg;
+  for (int l = 0; l < p.gru_layers; ++l) per += 2.0 * 2 * p.st.t * 3 * Hg * ((l ? 2 * Hg : p.st.E) + Hg);
+  ProfScope ps("fwd_bigru_static", prof_work().pred_rows * per, 0, st);
+  launch_any(a, p.st.E, p.gru_hg, CtxLanes{p, T}, st);
 }
 
 }  // namespace pmklc

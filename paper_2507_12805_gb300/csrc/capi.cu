@@ -157,7 +157,13 @@ struct Cfg {
   int priv = 0, priv_epochs = 1;      // Model Selector: static private model (0 off, 1 on, 2 auto)
   unsigned long long priv_bases = 0;  // bases of the input's head its pre-training reads (0 = all)
   unsigned long long priv_threshold = 0;  // the selector's input size in bases (0 = 5e8, the paper's 500 MB)
+  // static predictor architecture: 0 the MLP (st its shape); 1 or 2 a BiGRU static predictor of
+  // that many layers (§4.2.3 SPrM, §4.2.2 SPuM), GRU width gru_hg, st = (A, E, t, 128) the shape
+  // of its Dense layer run as an MLP logits layer
+  int st_arch = 0, gru_hg = 0;
   int A() const { return 1 << (2 * k); }
+  // FP32 parameters of the static model as the caller passes it
+  size_t static_count() const { return st_arch ? gru_offsets(A(), st.E, gru_hg, st_arch).count : st.count(); }
   int t_eff() const { return std::max(dm.t, use_static ? st.t : 0); }
 };
 
@@ -183,6 +189,11 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   if (c->lanes_per_block > (1u << 20) || c->fallback > 2) return PMKLC_EINVAL;
   if (c->overlap_mask > 1 || c->update_path > PMKLC_UPDATE_FUSED || c->gemm_tiles > 2) return PMKLC_EINVAL;
   if (c->private_model > 2 || c->private_epochs > kMaxGroups) return PMKLC_EINVAL;
+  // a BiGRU static predictor: frozen, so never pre-trained as a private model here; FP32 or BF16
+  if (c->static_arch > 2 ||
+      (c->static_arch && (!c->use_static || c->private_model || c->precision > PMKLC_BF16_BATCHED ||
+                          !gru_shape_ok((int)c->k, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s, (int)c->static_arch))))
+    return PMKLC_EINVAL;
   if (c->private_model && (c->emb_s < 1 || c->ctx_s < 1 || c->hid_s < 1 || c->emb_s > 4096 || c->ctx_s > 4096 ||
                            c->hid_s > 65535))
     return PMKLC_EINVAL;
@@ -197,6 +208,11 @@ int check_cfg(const pmklc_model_cfg *c, Cfg &o) {
   int A = 1 << (2 * c->k);
   o.dm = Dims{A, (int)c->emb_d, (int)c->ctx_d, (int)c->hid_d};
   o.st = o.use_static || c->private_model ? Dims{A, (int)c->emb_s, (int)c->ctx_s, (int)c->hid_s} : Dims{A, 0, 0, 0};
+  o.st_arch = (int)c->static_arch;
+  if (o.st_arch) {
+    o.gru_hg = (int)c->hid_s;
+    o.st.H = kGruDense;
+  }
   o.priv = (int)c->private_model;
   o.priv_epochs = c->private_epochs ? (int)c->private_epochs : 1;
   o.priv_bases = c->private_bases;
@@ -417,6 +433,29 @@ int setup_run(Arena &ar, Run &R, const std::vector<int> &grp_mode, const float *
   p.alpha_v = ar.alloc<float>(G);
   p.dalpha_grp = ar.alloc<float>(G);
   p.static_params = d_static;
+  p.st_gru = nullptr;
+  p.gru_hg = p.gru_layers = 0;
+  p.gru_y = nullptr;
+  if (c.st_arch && c.use_static && d_static) {
+    // the BiGRU static predictor forms the static h itself; its Dense layer (W4, b4) runs as the
+    // logits layer of an MLP-layout block of shape st = (A, E, t, 128), the rest of it zero and
+    // never read
+    float *blk = ar.alloc<float>(c.st.count());
+    float *y = c.st_arch == 2 ? ar.alloc<float>((size_t)c.st.t * 2 * c.gru_hg * NL) : nullptr;
+    if (ar.failed) return PMKLC_ENOMEM;
+    const GruOff o = gru_offsets(c.A(), c.st.E, c.gru_hg, c.st_arch);
+    cudaMemsetAsync(blk, 0, sizeof(float) * c.st.count(), ar.st);
+    cudaMemcpyAsync(blk + c.st.off_w2(), d_static + o.w4, sizeof(float) * (size_t)kGruDense * c.A(),
+                    cudaMemcpyDeviceToDevice, ar.st);
+    cudaMemcpyAsync(blk + c.st.off_b2(), d_static + o.b4, sizeof(float) * (size_t)c.A(), cudaMemcpyDeviceToDevice,
+                    ar.st);
+    p.st_gru = d_static;
+    p.gru_hg = c.gru_hg;
+    p.gru_layers = c.st_arch;
+    p.gru_y = y;
+    p.static_params = blk;
+    d_static = blk;  // the BF16 copy below is the block's
+  }
   p.precision = c.precision;
   p.wbf = nullptr;
   p.static_bf = nullptr;
@@ -847,7 +886,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   const float *d_static = nullptr;
   uint64_t shash = 0;
   if (c.use_static) {
-    size_t cnt = c.st.count();
+    size_t cnt = c.static_count();
     const float *sw = priv ? priv_w.data() : cfg->static_weights;
     shash = fnv1a(sw, cnt * sizeof(float));
     float *d = ar.alloc<float>(cnt);
@@ -933,7 +972,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   std::vector<uint8_t> H;
   H.reserve(kHeader + (size_t)L.G * 16 + (size_t)L.NL * 3);
   H.insert(H.end(), {'P', 'M', 'K', 'L'});
-  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback << 1) | (priv ? kPrivateFlag : 0));
+  uint8_t flags = (uint8_t)((c.use_static ? 1 : 0) | (c.fallback << 1) | (priv ? kPrivateFlag : 0) | (c.st_arch << 4));
   uint8_t b8[8] = {kVersion, (uint8_t)c.s, (uint8_t)c.k, flags, (uint8_t)c.precision, (uint8_t)c.optimizer,
                    (uint8_t)c.smp_mode, (uint8_t)c.count_order};
   H.insert(H.end(), b8, b8 + 8);
@@ -942,7 +981,7 @@ int compress_dev_impl(const uint8_t *d_seq, size_t n, const uint64_t *block_lens
   put_le<uint16_t>(H, (uint16_t)c.dm.H);
   put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.E : 0));
   put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.t : 0));
-  put_le<uint16_t>(H, (uint16_t)(c.use_static ? c.st.H : 0));
+  put_le<uint16_t>(H, (uint16_t)(c.use_static ? (c.st_arch ? c.gru_hg : c.st.H) : 0));  // BiGRU: its GRU width
   put_le<uint32_t>(H, (uint32_t)c.lanes);
   put_le<float>(H, c.lr);
   put_le<float>(H, c.alpha0);
@@ -1040,6 +1079,9 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   c.fallback = (h[7] >> 1) & 3;
   P.priv = (h[7] & kPrivateFlag) != 0;
   if (P.priv && !c.use_static) return PMKLC_ECORRUPT;  // the private model takes the static slot
+  c.st_arch = (h[7] >> 4) & 3;  // flags bits 4-5: the BiGRU static predictor's layers (0: the MLP)
+  if ((h[7] & 0xC0) || c.st_arch == 3 || (c.st_arch && (!c.use_static || P.priv || h[8] > PMKLC_BF16_BATCHED)))
+    return PMKLC_ECORRUPT;
   if (c.s < 1 || c.s > c.k || c.k > 8 || c.optimizer > 1 || c.smp_mode > 2 || c.count_order > 7 ||
       c.fallback > 2 || c.precision > PMKLC_BF16_FP8HIDDEN)
     return PMKLC_ECORRUPT;
@@ -1051,6 +1093,11 @@ int parse_fixed(const uint8_t *h, size_t len, Parsed &P) {
   if (c.dm.E < 1 || c.dm.t < 1 || c.dm.H < 1 || c.dm.E > 4096 || c.dm.t > 4096) return PMKLC_ECORRUPT;
   if (c.use_static && (c.st.E < 1 || c.st.t < 1 || c.st.H < 1 || c.st.E > 4096 || c.st.t > 4096))
     return PMKLC_ECORRUPT;
+  if (c.st_arch) {
+    if (!gru_shape_ok(c.k, c.st.E, c.st.t, c.st.H, c.st_arch)) return PMKLC_ECORRUPT;
+    c.gru_hg = c.st.H;
+    c.st.H = kGruDense;
+  }
   c.lanes = (int)get_le<uint32_t>(h + 24);
   if (c.lanes < 1 || c.lanes > (1 << 20)) return PMKLC_ECORRUPT;
   c.lr = get_le<float>(h + 28);
@@ -1161,7 +1208,7 @@ int decompress_dev_impl(const uint8_t *d_in, size_t in_len, const float *static_
     static_weights = P.priv_w.data();
     static_count = P.priv_w.size();
   } else if (c.use_static) {
-    if (!static_weights || static_count != c.st.count()) return PMKLC_EMODEL;
+    if (!static_weights || static_count != c.static_count()) return PMKLC_EMODEL;
     if (fnv1a(static_weights, static_count * sizeof(float)) != P.shash) return PMKLC_EMODEL;
   }
   make_layout(P.lens, c.s, c.k, c.lanes, c.lane_tokens, R.L);
@@ -1775,6 +1822,7 @@ int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *
     if (tmp.use_static && !tmp.static_weights) tmp.static_weights = (const float *)d_static;  // only checked non-null
     int rc = check_cfg(&tmp, c);
     if (rc) return rc;
+    if (c.st_arch) return PMKLC_EINVAL;  // the step entry points take an MLP static model
     const long long hmax = std::max(c.dm.H, c.use_static ? c.st.H : 0);
     if ((long long)G * M > kMaxLanes || (long long)G * M * hmax >= (1LL << 31)) return PMKLC_EINVAL;
     if (!G || G > kMaxGroups || !M || tau < 1 || !d_params || !d_m || !d_v || !d_alpha || !d_alpha_m || !d_alpha_v || !d_ctx ||

@@ -62,6 +62,14 @@ struct Plan {
   // model state
   float *params, *m, *v, *grad, *alpha, *alpha_m, *alpha_v;
   const float *static_params;
+  // BiGRU static predictor (§4.2.2 / §4.2.3): its FP32 parameters (nullptr: the static model is an
+  // MLP), GRU width per direction and layer count, and with two layers a scratch for the first
+  // layer's outputs (st.t x 2 gru_hg x NL).  Its Linear layer writes the static h (st.H = 128
+  // columns); static_params then holds an MLP-layout block whose W2, b2 are the Dense layer's
+  // W4, b4, so the static logits run on the MLP's logits kernels.
+  const float *st_gru;
+  int gru_hg, gru_layers;
+  float *gru_y;
   __nv_bfloat16 *wbf;               // BF16 copy of every group's parameters (BF16 form), G x P
   const __nv_bfloat16 *static_bf;   // BF16 copy of the static parameters (BF16 form)
   // FP8 static form (PMKLC_BF16_FP8STATIC with a static model; else nullptr): E4M3 codes

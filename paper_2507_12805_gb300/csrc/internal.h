@@ -82,6 +82,9 @@ GruOff gru_offsets(int A, int E, int Hg, int layers);
 // the shapes the kernel is built for: E in {8, 16, 32}, Hg in {16, 32}, 1 or 2 layers, 1 <= t <= 4096
 bool gru_shape_ok(int k, int E, int t, int Hg, int layers);
 int gru_smem_bytes(int Hg);
+// The static h of the lanes predicted at global step T (p.hs in the FP32 form, p.hs_b in the BF16
+// forms), formed by the BiGRU static predictor of p.st_gru.
+void launch_bigru_static(const Plan &p, int T, cudaStream_t st);
 
 // countmodel.cu --------------------------------------------------------------
 void launch_count_step(const Plan &p, const CountPlan &c, int T, cudaStream_t st);

@@ -542,7 +542,9 @@ void launch_forward(const Plan &p, int T, cudaStream_t st) {
     run_ggemm(LogitsOp{{p, T}, 0}, p.Mmax, p.dm.A, p.G, st);
   }
   if (p.use_static) {
-    {
+    if (p.st_gru) {  // the BiGRU static predictor's Linear layer forms the static h
+      launch_bigru_static(p, T, st);
+    } else {
       ProfScope ps("fwd_hidden_static", 2.0 * R * p.st.K1() * p.st.H, 0, st);
       run_ggemm(HiddenOp{{p, T}, 1}, p.Mmax, p.st.H, p.G, st);
     }

@@ -541,15 +541,18 @@ void launch_forward_bf16(const Plan &p, int T, cudaStream_t st, int which) {
   const double R = prof_work().pred_rows;
   const int Z = p.use_static ? 2 * p.G : p.G;
   const int Hmax = p.use_static ? max(p.dm.H, p.st.H) : p.dm.H;
+  // a BiGRU static predictor forms its own h: the hidden GEMM then covers the dynamic models only
+  const bool s_hid = p.use_static && !p.st_gru;
   {
-    double fl = 2.0 * R * p.dm.K1() * p.dm.H + (p.use_static ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
+    double fl = 2.0 * R * p.dm.K1() * p.dm.H + (s_hid ? 2.0 * R * p.st.K1() * p.st.H : 0.0);
     ProfScope ps("fwd_hidden_bf16", fl, 0, st);
     HiddenB op{{p, T}, p.hpart, Hmax};
-    run_tgemm(op, p.Mmax, Hmax, Z * kHiddenSplit, st);
+    run_tgemm(op, p.Mmax, Hmax, (s_hid ? Z : p.G) * kHiddenSplit, st);
     size_t n = (size_t)p.NL * Hmax, grid = (n + 255) / 256;
     if (grid > 152 * 16) grid = 152 * 16;
-    hidden_reduce_kernel<<<dim3((unsigned)grid, p.use_static ? 2 : 1), 256, 0, st>>>(p, T, p.hpart, Hmax);
+    hidden_reduce_kernel<<<dim3((unsigned)grid, s_hid ? 2 : 1), 256, 0, st>>>(p, T, p.hpart, Hmax);
   }
+  if (p.use_static && p.st_gru) launch_bigru_static(p, T, st);
   double fl = 2.0 * R * p.dm.H * p.dm.A + (p.use_static ? 2.0 * R * p.st.H * p.st.A : 0.0);
   ProfScope ps("fwd_logits_bf16", fl, 0, st);
   run_tgemm(LogitsB{{p, T}}, p.Mmax, p.dm.A, Z, st);

@@ -1369,7 +1369,8 @@ void launch_forward_tc(const Plan &p, int T, cudaStream_t st, int which) {
   // BF16 problems: z < G dynamic models, z >= G the static model; one launch covers [zb, zb + Z).
   // The static hidden layer runs here in the BF16 form, its logits layer in the BF16 and the
   // FP8-hidden forms (after HiddenF8 wrote its BF16 h)
-  const bool s_hid = stat && !f8, s_log = stat && !f8_logits;
+  const bool s_hid = stat && !f8 && !p.st_gru, s_log = stat && !f8_logits;
+  if (stat && p.st_gru) launch_bigru_static(p, T, st);  // the BiGRU static predictor's h
   if (dyn || s_hid) {
     const int zb = dyn ? 0 : p.G, Z = (dyn ? p.G : 0) + (s_hid ? p.G : 0);
     const char *hname = dyn && s_hid ? "fwd_hidden_bf16" : dyn ? "fwd_hidden_dyn_bf16" : "fwd_hidden_static_bf16";

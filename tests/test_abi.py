@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(P):
 
 
 def test_host_entry_points(P):
-    assert P.pmklc_abi_version() == 3
+    assert P.pmklc_abi_version() == 4
     assert P.lib.pmklc_strerror(P.PMKLC_ECORRUPT) == b"corrupt compressed stream"
     # parameter count: A*E + t*E*H + H + H*A + A
     assert P.model_count(4, 32, 32, 128) == 256 * 32 + 1024 * 128 + 128 + 128 * 256 + 256 == 172416

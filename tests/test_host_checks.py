@@ -273,3 +273,39 @@ def test_private_model_bound_and_configuration(P):
     assert auto == plain
     for bad in [dict(private_model=3, emb_s=8, ctx_s=4, hid_s=16), dict(private_model=1)]:
         assert P.pmklc_compress_bound(400, [400], P.ModelConfig(**kw, **bad)) == 0
+
+
+def test_bigru_static_configurations(P):
+    """A BiGRU static predictor (static_arch 1 or 2) is accepted with use_static, FP32 or BF16, no
+    private model and a built shape (pmklc_compress_bound, host only); anything else is refused."""
+    from oracle.bigru import GruShape, init_bigru
+    sw = init_bigru(GruShape(256, 16, 8, 32, 2), 1)
+    ok = dict(s=2, k=4, emb_d=32, ctx_d=8, hid_d=64, lanes_per_block=4, use_static=True, emb_s=16, ctx_s=8,
+              hid_s=32, static_arch=2, static_weights=sw)
+    lens = [4096, 4096]
+    assert P.pmklc_compress_bound(8192, lens, P.ModelConfig(**ok)) > 0
+    assert P.pmklc_compress_bound(8192, lens, P.ModelConfig(**dict(ok, precision=P.PMKLC_BF16_BATCHED))) > 0
+    for change in [dict(static_arch=3), dict(use_static=False), dict(private_model=1),
+                   dict(precision=P.PMKLC_BF16_FP8STATIC), dict(precision=P.PMKLC_BF16_FP8HIDDEN),
+                   dict(emb_s=12), dict(hid_s=24), dict(ctx_s=0)]:
+        cfg = P.ModelConfig(**dict(ok, **change))
+        if not cfg.use_static:
+            cfg.static_weights = None
+        assert P.pmklc_compress_bound(8192, lens, cfg) == 0, change
+
+
+def test_bigru_container_flags_checked_by_the_host_parser(P):
+    """Flag bits 4-5 carry the BiGRU's layer count: 3, bits 6-7, or a BiGRU without the static slot,
+    with a private model or in an FP8 form are corrupt; an intact oracle-written container passes
+    the host parser (and then needs its static weights or the device)."""
+    from oracle.bigru import GruShape, init_bigru
+    seq = b"ACGTTGCAAC" * 30
+    cfg = ocodec.Config(s=2, k=4, emb_d=8, ctx_d=4, hid_d=16, lanes_per_block=2, count_order=3, fallback=1,
+                        use_static=True, emb_s=8, ctx_s=4, hid_s=16, static_arch=1)
+    good = ocodec.compress(seq, [len(seq)], cfg, init_bigru(GruShape(256, 8, 4, 16, 1), 2))
+    assert good[7] == 0x13  # static, judge, one BiGRU layer
+    for flags in (0x33, 0x53, 0x93, 0x12, 0x1B):
+        assert _rc(P, lambda: P.pmklc_decompress(_patched(good, 7, "<B", flags))) == P.PMKLC_ECORRUPT, hex(flags)
+    assert _rc(P, lambda: P.pmklc_decompress(_patched(good, 8, "<B", 2))) == P.PMKLC_ECORRUPT  # FP8 form
+    assert _rc(P, lambda: P.pmklc_decompress(_patched(good, 22, "<H", 24))) == P.PMKLC_ECORRUPT  # GRU width
+    assert _rc(P, lambda: P.pmklc_decompress(good)) in (P.PMKLC_ECUDA, P.PMKLC_EMODEL)

@@ -178,3 +178,66 @@ def test_layout_init_and_private_view():
     outs, _ = states(p, sh, ctx)
     u0 = np.concatenate([outs[0][:, -1, :32], outs[0][:, 0, 32:]], axis=1)
     np.testing.assert_allclose(q1, np.maximum(u0 @ w["w3"].T + w["b3"], 0), atol=1e-12)
+
+
+# ---------------------------------------------------------------- the BiGRU in the codec's static slot
+
+def _codec_case(arch, k=2):
+    import synth
+    from oracle import codec
+    seq = synth.markov(2400, 3, 0.45, 77).tobytes()
+    cfg = codec.Config(s=1, k=k, use_static=True, emb_s=8, ctx_s=4, hid_s=16, emb_d=8, ctx_d=6, hid_d=16,
+                       lanes_per_block=4, fallback=0, static_arch=arch, smp_mode=codec.SMP_CHAIN)
+    sh = GruShape(4 ** k, 8, 4, 16, arch)
+    return codec, seq, cfg, sh
+
+
+@pytest.mark.parametrize("arch", [1, 2])
+def test_codec_round_trip_and_header(arch):
+    codec, seq, cfg, sh = _codec_case(arch)
+    sw = _generic(sh, seed=3).astype(np.float32)
+    blob = codec.compress(seq, [1200, 1200], cfg, sw)
+    assert blob[7] >> 4 == arch and blob[7] & 1
+    pc, meta = codec.parse_header(blob)
+    assert pc.static_arch == arch and (pc.emb_s, pc.ctx_s, pc.hid_s) == (8, 4, 16)
+    assert codec.decompress(blob, sw) == seq
+    with pytest.raises(codec.ModelMismatch):
+        codec.decompress(blob, (sw * 1.5).astype(np.float32))
+    bad = bytearray(blob)
+    bad[7] |= 0x30  # static_arch 3
+    with pytest.raises(codec.CorruptStream):
+        codec.decompress(bytes(bad), sw)
+    bad[7] = blob[7] | 0x40
+    with pytest.raises(codec.CorruptStream):
+        codec.decompress(bytes(bad), sw)
+
+
+def test_codec_bigru_slot_enters_eq1_as_the_static_logits():
+    """A BiGRU whose Dense layer is zero gives L^u = 0, and Eq. (1) with L^u = 0 equals Eq. (1) with
+    S0 = 0: the payload is byte for byte that of the run without a static model (same t_eff).  Any
+    nonzero Dense layer changes it."""
+    codec, seq, cfg, sh = _codec_case(2)
+    sw = _generic(sh, seed=4)
+    lo, hi = sh.offsets()["w4"][0], sh.count
+    sw[lo:hi] = 0.0
+    sw = sw.astype(np.float32)
+    blob = codec.compress(seq, [2400], cfg, sw)
+    from dataclasses import replace
+    plain = codec.compress(seq, [2400], replace(cfg, use_static=False, static_arch=0, emb_s=0, ctx_s=0, hid_s=0))
+    hl = codec.HEADER.size
+    assert blob[hl:] == plain[hl:]
+    sw2 = sw.copy()
+    sw2[lo:hi] = _generic(sh, seed=5)[lo:hi]
+    assert codec.compress(seq, [2400], cfg, sw2)[hl:] != plain[hl:]
+
+
+def test_codec_bigru_config_errors():
+    from dataclasses import replace
+    codec, seq, cfg, sh = _codec_case(1)
+    sw = init_bigru(sh, 1)
+    with pytest.raises(ValueError):
+        codec.compress(seq, [2400], replace(cfg, private_model=1), sw)
+    with pytest.raises(ValueError):
+        codec.compress(seq, [2400], replace(cfg, precision=2), sw)
+    with pytest.raises(ValueError):
+        codec.compress(seq, [2400], cfg, sw[:-1])
