@@ -294,14 +294,13 @@ SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 # DRAM traffic of step kernels from one ncu --set full capture each (dram__bytes_read.sum +
 # dram__bytes_write.sum of the captured launch, and that launch's algorithmic bytes), summarised in
-# profiles/: the captured case (the human-like workload's first 64 blocks, cut to 2^17 bases, a step
-# at which every group trains) moves the same bytes per group as the full workload, so a launch's
-# traffic is reported as the measured DRAM bytes per algorithmic byte x its algorithmic bytes.
-# Valid for the kernels as they stand in that capture.
-NCU_TRAFFIC = {
-    # name: (DRAM bytes of the captured launch, its algorithmic bytes: 64 groups x H x A x 26)
-    "bwd_dw2_adam_bf16": (876706304 + 877779968, 64 * 256 * 4096 * 26),
-}
+# profiles/: a captured case that moves the same bytes per group as the full workload gives a
+# launch's traffic as the measured DRAM bytes per algorithmic byte x its algorithmic bytes.  Only
+# kernels whose code is unchanged since their capture are listed, so a changed kernel reports null.
+# The fused dW2 update's capture (profiles/ncu_dw2_adam_human.md: 876,706,304 + 877,779,968 DRAM
+# bytes for 64 x 256 x 4096 x 26 algorithmic ones) predates a change to the GEMM engine's tail stage
+# (which threads wait on its barrier), so it is not listed until it is captured again.
+NCU_TRAFFIC = {}
 
 
 def _traffic(name: str, work_bytes_per_launch: float):

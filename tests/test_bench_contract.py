@@ -31,16 +31,20 @@ def test_dominant_kernel_and_its_bound():
     assert sum(v["share"] for v in per.values()) == pytest.approx(1.0)
 
 
-def test_fused_update_is_hbm_bound_and_its_traffic_scales_with_its_bytes():
+def test_fused_update_is_hbm_bound_and_its_traffic_scales_with_its_bytes(monkeypatch):
     """The dW2 GEMM with the optimiser in its epilogue: HBM-bound (its 26 bytes per parameter take
-    longer than its FLOPs), and its traffic is the captured DRAM bytes per algorithmic byte times the
-    launch's algorithmic bytes."""
+    longer than its FLOPs); without a capture of the kernel as it stands its traffic is null, and with
+    one it is the captured DRAM bytes per algorithmic byte times the launch's algorithmic bytes (here
+    the figures of its last capture)."""
     alg = 1024 * 256 * 4096 * 26.0
     prof = {"bwd_dw2_adam_bf16": {"launches": 2, "ms": 2 * 5.0, "flops": 2 * 2.0 * 131072 * 256 * 4096,
                                   "bytes": 2 * alg}}
     r, _ = bench.roofline(prof, PEAKS, "measured")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(alg / 5e-3 / 1e9)
+    assert r["traffic"] is None
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "bwd_dw2_adam_bf16", (876706304 + 877779968, 64 * 256 * 4096 * 26))
+    r, _ = bench.roofline(prof, PEAKS, "measured")
     dram, alg64 = bench.NCU_TRAFFIC["bwd_dw2_adam_bf16"]
     assert r["traffic"] == pytest.approx(dram / alg64 * alg)
     assert 0.99 < dram / alg64 < 1.1  # the capture moved its algorithmic bytes, no re-reads
