@@ -346,6 +346,7 @@ int pmklc_predict_bigru(const float *d_params, uint32_t k, uint32_t E, uint32_t 
  *   d_P (optional, G*M x A) receives the mixed probabilities before the
  *   update; d_grad (optional, G x P) the gradient; d_dalpha (optional, G).
  * 1 <= G <= 32,767 (the limit of pmklc_compress's blocks), else EINVAL.
+ * The static model here is an MLP: cfg->static_arch other than 0 is EINVAL.
  */
 int pmklc_train_step(const pmklc_model_cfg *cfg, uint32_t G, uint32_t M, float *d_params, float *d_m,
                      float *d_v, float *d_alpha, float *d_alpha_m, float *d_alpha_v, const float *d_static,
