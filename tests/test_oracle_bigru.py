@@ -241,3 +241,56 @@ def test_codec_bigru_config_errors():
         codec.compress(seq, [2400], replace(cfg, precision=2), sw)
     with pytest.raises(ValueError):
         codec.compress(seq, [2400], cfg, sw[:-1])
+
+
+def test_planted_recurrence_mistakes_fail_the_torch_pin():
+    """Plausible mistakes in the recurrence, planted in a copy of the oracle's pass, each move the
+    layer output away from torch.nn.GRU's by far more than the pin's 1e-13: the reset gate applied
+    to h before the recurrent product (the other published GRU form), the update gate's two terms
+    swapped, the backward pass run oldest first, and the summary taken from the wrong end."""
+    torch = pytest.importorskip("torch")
+    from oracle import bigru as B
+    sh = GruShape(A=64, E=5, t=7, Hg=4, layers=1)
+    flat = _generic(sh, seed=13)
+    w = params(flat, sh)
+    ctx = np.random.default_rng(6).integers(0, sh.A, (9, sh.t))
+    x = w["emb"][ctx]
+    gru = torch.nn.GRU(sh.E, sh.Hg, num_layers=1, bidirectional=True, batch_first=True, dtype=torch.float64)
+    with torch.no_grad():
+        for d, suf in (("f", ""), ("b", "_reverse")):
+            for a, b in (("weight_ih", "wi"), ("weight_hh", "wh"), ("bias_ih", "bi"), ("bias_hh", "bh")):
+                getattr(gru, f"{a}_l0{suf}").copy_(torch.from_numpy(w[f"{b}0{d}"]))
+        want, hn = gru(torch.from_numpy(x))
+    want, hn = want.numpy(), hn.numpy()
+
+    def planted(wi, wh, bi, bh, reverse, mistake):
+        R, t, _ = x.shape
+        Hg = wh.shape[1]
+        h = np.zeros((R, Hg))
+        seq = np.zeros((R, t, Hg))
+        order = range(t - 1, -1, -1) if reverse and mistake != "backward_oldest_first" else range(t)
+        for p in order:
+            gi = x[:, p, :] @ wi.T + bi
+            gh = h @ wh.T + bh
+            r = B._sigmoid(gi[:, :Hg] + gh[:, :Hg])
+            z = B._sigmoid(gi[:, Hg:2 * Hg] + gh[:, Hg:2 * Hg])
+            if mistake == "reset_before_product":
+                n = np.tanh(gi[:, 2 * Hg:] + (r * h) @ wh[2 * Hg:].T + bh[2 * Hg:])
+            else:
+                n = np.tanh(gi[:, 2 * Hg:] + r * gh[:, 2 * Hg:])
+            h = z * n + (1.0 - z) * h if mistake == "update_swapped" else (1.0 - z) * n + z * h
+            seq[:, p, :] = h
+        return seq
+
+    def layer(mistake):
+        f = planted(w["wi0f"], w["wh0f"], w["bi0f"], w["bh0f"], False, mistake)
+        b = planted(w["wi0b"], w["wh0b"], w["bi0b"], w["bh0b"], True, mistake)
+        return np.concatenate([f, b], axis=2)
+
+    assert np.abs(layer(None) - want).max() < 1e-13  # the planted copy without a mistake is the oracle
+    for mistake in ("reset_before_product", "update_swapped", "backward_oldest_first"):
+        assert np.abs(layer(mistake) - want).max() > 1e-3, mistake
+    # the summary from the wrong ends (forward state after position 0, backward after t-1)
+    out = layer(None)
+    wrong_u = np.concatenate([out[:, 0, :sh.Hg], out[:, -1, sh.Hg:]], axis=1)
+    assert np.abs(wrong_u - np.concatenate([hn[-2], hn[-1]], axis=1)).max() > 1e-3
