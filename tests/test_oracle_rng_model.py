@@ -2,6 +2,7 @@
 import os
 
 import numpy as np
+import pytest
 
 from oracle.mixer import loss_grads, mix, softmax
 from oracle.model import (ADAM_EPS, Shape, adam_step, backward, forward, init_params, views)
@@ -118,3 +119,42 @@ def test_adam_first_step_closed_form():
     assert np.allclose(th, -1e-3 * g / (np.abs(g) + ADAM_EPS), rtol=1e-9, atol=0)
     adam_step(th, m, v, g, 2, 1e-3)  # constant gradient keeps the step at -lr*sign
     assert np.allclose(th, -2e-3 * g / (np.abs(g) + ADAM_EPS), rtol=1e-9, atol=0)
+
+
+def test_forward_backward_and_mixer_gradients_match_torch_autograd():
+    """An independent implementation: torch.nn.functional in float64 (embedding lookup, linear
+    layers, ReLU) with autograd through Eq. (1), the softmax and the mean cross entropy of Eq. (2).
+    The oracle's logits, its parameter gradient (the embedding's scattered adds included) and
+    d alpha agree to rounding."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    sh = Shape(A=16, E=3, t=4, H=5)
+    rng = np.random.default_rng(8)
+    p = init_params(sh, 4).astype(np.float64) + rng.normal(0, 0.3, sh.count)
+    ctx = rng.integers(0, sh.A, (7, sh.t))
+    ctx[3, :] = ctx[3, 0]  # one token repeated inside a context: several adds into one embedding row
+    tgt = rng.integers(0, sh.A, 7)
+    Lu = rng.normal(0, 1, (7, sh.A))
+    alpha = 0.37
+    X, a, h, Lm = forward(p, sh, ctx)
+    P = softmax(mix(Lu, Lm, alpha, (1, 0, 1)))
+    dLm, dal = loss_grads(P, tgt, Lu, Lm, alpha, (1, 0, 1))
+    g = backward(p, sh, ctx, X, a, h, dLm)
+
+    off = sh.offsets()
+    tp = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    ta = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    emb = tp[off["emb"][0]:off["emb"][1]].view(sh.A, sh.E)
+    w1t = tp[off["w1"][0]:off["w1"][1]].view(sh.H, sh.t * sh.E)
+    b1 = tp[off["b1"][0]:off["b1"][1]]
+    w2 = tp[off["w2"][0]:off["w2"][1]].view(sh.H, sh.A)
+    b2 = tp[off["b2"][0]:off["b2"][1]]
+    xt = F.embedding(torch.from_numpy(ctx), emb).reshape(7, sh.t * sh.E)
+    lm = F.linear(F.relu(F.linear(xt, w1t, b1)), w2.T, b2)
+    z = ta * torch.from_numpy(Lu) + (1 - ta) * lm
+    loss = F.cross_entropy(z, torch.from_numpy(tgt))
+    loss.backward()
+    np.testing.assert_allclose(Lm, lm.detach().numpy(), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(P, torch.softmax(z, 1).detach().numpy(), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g, tp.grad.numpy(), rtol=0, atol=1e-12)
+    assert abs(dal - float(ta.grad)) < 1e-12
