@@ -114,3 +114,23 @@ def test_fp8_hidden_forward_is_the_plain_forward_with_e4m3_embedding_and_w1():
     assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
     # the logits layer really is the stored one: the FP8 form (E4M3 W2 and h) differs
     assert np.max(np.abs(fp8.forward(fq, ctx) - got)) > 1e-6
+
+
+def test_encoder_matches_torch_float8_e4m3fn_within_range():
+    """torch's float8_e4m3fn cast (round to nearest even; the same OCP E4M3 format) on values within
+    +-448: random magnitudes over every exponent, the subnormals, and every midpoint between two
+    consecutive codes (the ties), both signs.  Beyond 448 the two differ by design: the oracle
+    saturates at 448, the cast gives NaN."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("this torch has no float8_e4m3fn")
+    from oracle.fp8 import decode, encode
+    rng = np.random.default_rng(21)
+    pos = decode(np.arange(0x7F))
+    mids = (pos[:-1] + pos[1:]) / 2
+    vals = np.concatenate([np.exp2(rng.uniform(-12, np.log2(448.0), 20000)), mids, pos,
+                           rng.uniform(0, 2.0 ** -6, 2000)])
+    vals = np.concatenate([vals, -vals]).astype(np.float32)  # float32 inputs: mids are exact in float32
+    assert np.abs(vals).max() <= 448.0
+    want = torch.from_numpy(vals).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(encode(vals), want)

@@ -158,3 +158,25 @@ def test_forward_backward_and_mixer_gradients_match_torch_autograd():
     np.testing.assert_allclose(P, torch.softmax(z, 1).detach().numpy(), rtol=0, atol=1e-14)
     np.testing.assert_allclose(g, tp.grad.numpy(), rtol=0, atol=1e-12)
     assert abs(dal - float(ta.grad)) < 1e-12
+
+
+def test_adam_matches_torch_optim_adam():
+    """torch.optim.Adam (float64; betas 0.9 / 0.999, eps 1e-8, bias correction by the step count,
+    eps added after the square root) over 25 steps of varying gradients, zeros included: the
+    parameters and both moments agree to rounding."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    th = rng.normal(0, 1, 40)
+    m, v = np.zeros(40), np.zeros(40)
+    tp = torch.tensor(th.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-3, betas=(0.9, 0.999), eps=ADAM_EPS)
+    for tau in range(1, 26):
+        g = rng.normal(0, 10.0 ** rng.uniform(-4, 1), 40)
+        g[rng.integers(0, 40, 5)] = 0.0
+        adam_step(th, m, v, g, tau, 1e-3)
+        tp.grad = torch.from_numpy(g.copy())
+        opt.step()
+    st = opt.state[tp]
+    np.testing.assert_allclose(th, tp.detach().numpy(), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(m, st["exp_avg"].numpy(), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(v, st["exp_avg_sq"].numpy(), rtol=1e-13, atol=0)
