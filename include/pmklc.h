@@ -89,7 +89,9 @@ typedef struct {
   uint32_t fallback;           /* 0: network only; 1: per block, the count model when it is smaller
                                   (needs lanes_per_block <= 1024); 2: count model only */
   uint64_t seed;               /* seed of the dynamic model's initialisation */
-  const float *static_weights; /* host FP32 static parameters (layout above); NULL if unused */
+  const float *static_weights; /* host FP32 static parameters (the MLP layout above, or with
+                                  static_arch 1 or 2 the BiGRU layout of pmklc_predict_bigru);
+                                  NULL if unused */
   uint32_t lane_tokens;        /* 0: a block of l tokens gets min(lanes_per_block, l) lanes; else
                                   min(lanes_per_block, l, ceil(l / lane_tokens)), so lanes of uneven
                                   blocks take about the same number of steps */
@@ -196,7 +198,9 @@ int pmklc_compress(const uint8_t *seq, size_t n, const uint64_t *block_lens, siz
  * Inverse of pmklc_compress (paper §2, decompression: the decoder replays
  * the same model updates).  static_weights/static_count must be the ones
  * used to compress when the container says a static model was used, unless it
- * stores its own static private model (then they are not used).
+ * stores its own static private model (then they are not used); static_count
+ * is their number of floats (pmklc_model_count, or pmklc_bigru_count for a
+ * BiGRU static predictor, flag bits 4-5 of the container).
  * Outputs: *seq (*n bases) and *block_lens (*n_blocks entries), both
  * library-allocated.  Errors: ECORRUPT, EMODEL, ENOMEM, ECUDA, ETIMEOUT.
  */
