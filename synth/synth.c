@@ -219,7 +219,12 @@ void synth_plant_tandem(uint8_t *buf, uint64_t n, double coverage, int pmin, int
 }
 
 /* log-normal sequence lengths: ln L ~ N(mu, sigma), clipped to [lo, hi], then scaled so the
- * lengths sum exactly to `total` (the rounding remainder goes to the longest sequences). */
+ * lengths sum exactly to `total` (the rounding remainder goes to the longest sequences).  When that
+ * scaling takes a length above hi (the full-size batching workload: the 8 MB cap), the scale is
+ * solved again with the clip inside it, L_i = clip(c x_i, lo, hi) with c such that the lengths sum
+ * to `total` (bisection), and the rounding remainder goes one base at a time to the longest
+ * sequences still below hi (or is taken from the longest above lo), so every length lies in
+ * [lo, hi].  Draws whose single scaling stays at or below hi keep it unchanged. */
 int synth_lognormal_lengths(uint64_t *lens, int count, double mu, double sigma, uint64_t lo, uint64_t hi,
                             uint64_t total, uint64_t seed) {
   rng_t r;
@@ -255,6 +260,48 @@ int synth_lognormal_lengths(uint64_t *lens, int count, double mu, double sigma, 
       if (take > lens[best] - 1) take = lens[best] - 1;
       lens[best] -= take;
       acc -= take;
+    }
+  }
+  int over = 0;
+  for (int i = 0; i < count; ++i) over |= lens[i] > hi;
+  if (over && (double)count * (double)lo <= (double)total && (double)total <= (double)count * (double)hi) {
+    double xmin = x[0];
+    for (int i = 1; i < count; ++i)
+      if (x[i] < xmin) xmin = x[i];
+    double c_lo = 0.0, c_hi = (double)hi / xmin;  /* f(c_hi) = count * hi >= total */
+    for (int it = 0; it < 200; ++it) {
+      double c = 0.5 * (c_lo + c_hi), f = 0;
+      for (int i = 0; i < count; ++i) {
+        double v = c * x[i];
+        f += v < (double)lo ? (double)lo : (v > (double)hi ? (double)hi : v);
+      }
+      if (f < (double)total)
+        c_lo = c;
+      else
+        c_hi = c;
+    }
+    acc = 0;
+    for (int i = 0; i < count; ++i) {
+      double v = c_lo * x[i];
+      v = v < (double)lo ? (double)lo : (v > (double)hi ? (double)hi : v);
+      lens[i] = (uint64_t)floor(v);
+      if (lens[i] < lo) lens[i] = lo;
+      acc += lens[i];
+    }
+    while (acc != total) {
+      int best = -1;
+      for (int i = 0; i < count; ++i) {
+        const int ok = acc < total ? lens[i] < hi : lens[i] > lo;
+        if (ok && (best < 0 || lens[i] > lens[best])) best = i;
+      }
+      if (best < 0) break; /* cannot happen: count lo <= total <= count hi */
+      if (acc < total) {
+        lens[best] += 1;
+        acc += 1;
+      } else {
+        lens[best] -= 1;
+        acc -= 1;
+      }
     }
   }
   free(x);
