@@ -56,13 +56,19 @@ def test_cpg_depletion_rule():
 
 def test_repeat_coverage():
     """Alu-like families cover about 10 % of the bases and tandem repeats about 5 %: planted into a
-    run of A, 3/4 of a planted random base differs from A."""
+    run of A, 3/4 of a planted random base differs from A.  Planted repeats carry their mutation
+    rate."""
     buf = np.full(1 << 20, ord("A"), np.uint8)
     synth.plant_families(buf, 30, 300, 0.10, 0.12, 5)
     assert 0.085 < (buf != ord("A")).mean() / 0.75 < 0.11
     buf = np.full(1 << 20, ord("A"), np.uint8)
     synth.plant_tandem(buf, 0.05, 2, 6, 40.0, 5)
     assert 0.04 < (buf != ord("A")).mean() / 0.75 < 0.06
+    # the tiny workload's 20 copies of 200-base segments at 10 % point mutation: copied from a run of
+    # A, only the mutated bases differ (a mutation picks another base): about 20 x 200 x 0.1 = 400
+    buf = np.full(100_000, ord("A"), np.uint8)
+    synth.plant_repeats(buf, 20, 200, 0.10, 1008)
+    assert 320 < int((buf != ord("A")).sum()) < 480
 
 
 def test_uneven_lengths_and_perturbation():
