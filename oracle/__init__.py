@@ -23,7 +23,8 @@ It is a plain, slow, FP64 restatement of the method, written from the paper:
 
 Parity status of each function is stated in its module header; every function
 is pinned by tests in ``tests/test_oracle_*.py`` against closed forms, the
-paper's worked example, brute force or invariants.  "parity unpinned" marks the
-one property that has no independent pin: the exact full-run probability
-trajectory of online training (only its compressed size is compared).
+paper's worked example, brute force or invariants.  The full-run probability
+trajectory of one block's online training is pinned against an independent
+float64 restatement in torch; only the CUDA path's trajectory against this one
+is compared by compressed size (FP32/BF16 and FP64 diverge over a long run).
 """

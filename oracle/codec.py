@@ -57,9 +57,11 @@ Readings where the paper is silent:
            that costs fewer bytes (flag in the container); fallback 2: the count
            model alone (the method without the learned network); 0: network only.
 Parity: each step is pinned in its own module; the full run is pinned by the
-exact decode round trip.  The exact probability trajectory over a whole run is
-"parity unpinned" (online FP64 training amplifies any rounding difference); the
-CUDA path is compared on compressed size instead.
+exact decode round trip, and one block's whole probability trajectory by an
+independent float64 restatement in torch (tests/test_oracle_trajectory.py).
+The CUDA path's trajectory diverges from this FP64 one over a long run (online
+training amplifies any rounding difference), so it is compared on compressed
+size instead.
 """
 from __future__ import annotations
 
