@@ -13,9 +13,11 @@ from oracle import codec as ocodec
 from oracle.model import Shape, init_params
 
 
-def _torch_run(torch, seq, cfg: ocodec.Config, static_w):
-    """Independent restatement, one block, network only: returns {(j): P rows of the predicting
-    lanes in lane order}."""
+def _torch_run(torch, seq, cfg: ocodec.Config, static_w, init=None, snapshot_at=None):
+    """Independent restatement, one block, network only: returns ({j: P rows of the predicting
+    lanes in lane order}, the state (weights, alpha, optimiser) as it stood before local step
+    snapshot_at).  init: a state to start from (a copy of a parent's), else the seeded init."""
+    import copy
     F = torch.nn.functional
     s, k, A = cfg.s, cfg.k, 4 ** cfg.k
     codes = np.frombuffer(seq, np.uint8)
@@ -46,8 +48,15 @@ def _torch_run(torch, seq, cfg: ocodec.Config, static_w):
     alpha = torch.tensor(float(np.float32(cfg.alpha_init)), dtype=torch.float64, requires_grad=True)
     sw = torch.tensor(np.asarray(static_w, np.float32).astype(np.float64))
     opt = torch.optim.Adam([theta, alpha], lr=float(np.float32(cfg.lr)), betas=(0.9, 0.999), eps=1e-8)
-    out = {}
+    if init is not None:
+        with torch.no_grad():
+            theta.copy_(init[0])
+            alpha.copy_(init[1])
+        opt.load_state_dict(copy.deepcopy(init[2]))
+    out, snap = {}, None
     for j in range(max(lens)):
+        if j == snapshot_at:
+            snap = (theta.detach().clone(), alpha.detach().clone(), copy.deepcopy(opt.state_dict()))
         rows = [r for r in range(M) if t_eff <= j < lens[r]]
         if not rows:
             continue
@@ -71,7 +80,9 @@ def _torch_run(torch, seq, cfg: ocodec.Config, static_w):
         opt.zero_grad()
         (loss / len(pos)).backward()
         opt.step()
-    return out
+    if snap is None and snapshot_at is not None:  # the parent ended first: its final state
+        snap = (theta.detach().clone(), alpha.detach().clone(), copy.deepcopy(opt.state_dict()))
+    return out, snap
 
 
 @pytest.mark.parametrize("s,k,mask", [(1, 2, 0), (1, 3, 1), (2, 2, 0)])
@@ -84,8 +95,37 @@ def test_oracle_run_matches_an_independent_torch_restatement(s, k, mask):
     sw = init_params(Shape(4 ** k, 3, 2, 5), 2001)
     got = {}
     ocodec.compress(seq, [len(seq)], cfg, sw, on_probs=lambda g, j, P: got.__setitem__(j, np.array(P)))
-    want = _torch_run(torch, seq, cfg, sw)
+    want, _ = _torch_run(torch, seq, cfg, sw)
     assert sorted(got) == sorted(want) and len(want) > 80
     worst = max(np.abs(got[j] - want[j]).max() for j in want)
     print(f"(s,k) = ({s},{k}) mask {mask}: {len(want)} steps, worst |P - P_torch| = {worst:.2e}")
     assert worst < 1e-10, worst
+
+
+def test_chain_hand_over_inside_the_trajectory():
+    """Two blocks under CHAIN step-wise model passing (f = 0.25): block 1 starts at global step
+    ceil(f L_0) from a full copy of block 0's state as it stands then (weights, Adam moments and
+    step count, alpha).  Both blocks' probabilities at every step agree with the restatement, which
+    runs block 0 alone, copies its state before its local step ceil(f L_0) and runs block 1 from it."""
+    import math
+    torch = pytest.importorskip("torch")
+    s, k = 1, 2
+    seq = synth.markov(1200, 3, 0.45, 9).tobytes()
+    lens = [700, 500]
+    cfg = ocodec.Config(s=s, k=k, use_static=True, emb_s=3, ctx_s=2, hid_s=5, emb_d=4, ctx_d=3, hid_d=6,
+                        lanes_per_block=4, fallback=0, smp_mode=ocodec.SMP_CHAIN, smp_fraction=0.25,
+                        alpha_init=0.5, lr=3e-3)
+    sw = init_params(Shape(4 ** k, 3, 2, 5), 2001)
+    got = {0: {}, 1: {}}
+    ocodec.compress(seq, lens, cfg, sw, on_probs=lambda g, j, P: got[g].__setitem__(j, np.array(P)))
+    L0 = -(-((lens[0] - k) // s + 1) // 4)  # block 0's steps: its longest lane
+    hand = math.ceil(float(np.float32(0.25)) * L0)
+    w0, snap = _torch_run(torch, seq[:lens[0]], cfg, sw, snapshot_at=hand)
+    w1, _ = _torch_run(torch, seq[lens[0]:], cfg, sw, init=snap)
+    for g, want in ((0, w0), (1, w1)):
+        assert sorted(got[g]) == sorted(want)
+        worst = max(np.abs(got[g][j] - want[j]).max() for j in want)
+        assert worst < 1e-10, (g, worst)
+    # the hand-over matters: block 1 from the seeded init codes other probabilities
+    cold, _ = _torch_run(torch, seq[lens[0]:], cfg, sw)
+    assert max(np.abs(got[1][j] - cold[j]).max() for j in cold) > 1e-3
