@@ -30,7 +30,7 @@ def _torch_run(torch, seq, cfg: ocodec.Config, static_w, init=None, snapshot_at=
     base, extra = divmod(l, M)
     lens = [base + (r < extra) for r in range(M)]
     starts = [r * base + min(r, extra) for r in range(M)]
-    t_eff = max(cfg.ctx_d, cfg.ctx_s)
+    t_eff = max(cfg.ctx_d, cfg.ctx_s if cfg.use_static else 0)
 
     def views(p, sh):
         o = sh.offsets()
@@ -46,8 +46,11 @@ def _torch_run(torch, seq, cfg: ocodec.Config, static_w, init=None, snapshot_at=
     dsh, ssh = cfg.dm_shape, cfg.static_shape
     theta = torch.tensor(init_params(dsh, cfg.seed).astype(np.float64), requires_grad=True)
     alpha = torch.tensor(float(np.float32(cfg.alpha_init)), dtype=torch.float64, requires_grad=True)
-    sw = torch.tensor(np.asarray(static_w, np.float32).astype(np.float64))
-    opt = torch.optim.Adam([theta, alpha], lr=float(np.float32(cfg.lr)), betas=(0.9, 0.999), eps=1e-8)
+    sw = torch.tensor(np.asarray(static_w, np.float32).astype(np.float64)) if cfg.use_static else None
+    if cfg.optimizer == ocodec.ADAM:
+        opt = torch.optim.Adam([theta, alpha], lr=float(np.float32(cfg.lr)), betas=(0.9, 0.999), eps=1e-8)
+    else:
+        opt = torch.optim.SGD([theta, alpha], lr=float(np.float32(cfg.lr)))
     if init is not None:
         with torch.no_grad():
             theta.copy_(init[0])
@@ -62,8 +65,10 @@ def _torch_run(torch, seq, cfg: ocodec.Config, static_w, init=None, snapshot_at=
             continue
         pos = [starts[r] + j for r in rows]
         cd = torch.tensor(np.stack([tok[q - cfg.ctx_d:q] for q in pos]))
-        cs = torch.tensor(np.stack([tok[q - cfg.ctx_s:q] for q in pos]))
-        z = alpha * logits(sw, ssh, cs) + (1 - alpha) * logits(theta, dsh, cd)
+        z = (1 - alpha) * logits(theta, dsh, cd)
+        if cfg.use_static:
+            cs = torch.tensor(np.stack([tok[q - cfg.ctx_s:q] for q in pos]))
+            z = z + alpha * logits(sw, ssh, cs)
         loss, Ps = 0.0, []
         for i, q in enumerate(pos):
             if cfg.overlap_mask and j > 0:
@@ -129,3 +134,21 @@ def test_chain_hand_over_inside_the_trajectory():
     # the hand-over matters: block 1 from the seeded init codes other probabilities
     cold, _ = _torch_run(torch, seq[lens[0]:], cfg, sw)
     assert max(np.abs(got[1][j] - cold[j]).max() for j in cold) > 1e-3
+
+
+@pytest.mark.parametrize("use_static,optimizer", [(False, 0), (True, 1)])
+def test_trajectory_without_static_model_and_with_sgd(use_static, optimizer):
+    """The same restatement for Eq. (1) without a static model (S0 = 0: z = (1 - alpha) L^m, alpha
+    still trained) and for the plain SGD update of the weights and alpha."""
+    torch = pytest.importorskip("torch")
+    seq = synth.markov(600, 3, 0.45, 21).tobytes()
+    static = dict(use_static=True, emb_s=3, ctx_s=2, hid_s=5) if use_static else {}
+    cfg = ocodec.Config(s=1, k=2, emb_d=4, ctx_d=3, hid_d=6, lanes_per_block=3, fallback=0,
+                        smp_mode=ocodec.SMP_NONE, alpha_init=0.5, lr=0.05 if optimizer else 3e-3,
+                        optimizer=optimizer, **static)
+    sw = init_params(Shape(16, 3, 2, 5), 2001) if use_static else None
+    got = {}
+    ocodec.compress(seq, [len(seq)], cfg, sw, on_probs=lambda g, j, P: got.__setitem__(j, np.array(P)))
+    want, _ = _torch_run(torch, seq, cfg, sw)
+    assert sorted(got) == sorted(want) and len(want) > 150
+    assert max(np.abs(got[j] - want[j]).max() for j in want) < 1e-10
